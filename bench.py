@@ -1,0 +1,450 @@
+"""Benchmark of the aggregate risk analysis hot path on GB300.
+
+One step = one pass of the whole single-layer path over the paper-scale
+workload (1,000,000 trials x 1000 events, one layer of 16 ELTs): rebuild the
+layer's direct-access table, run the analysis stage for every trial, select
+PML 1-in-100/250 and TVaR 99% from the YLT and read them back.  The headline
+runs in FP32 with a Kahan-compensated trial sum; the FP64 path and the FP32
+path with an FP64 trial sum are timed the same way and reported beside it.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+prints one JSON line.  Under torchrun (N > 1) each rank simulates its own
+block of 1,000,000 trials (weak scaling); the ranks' YLTs are gathered once
+per step for the PML/TVaR of the whole YET.  ``--impl reference`` times the
+CPU oracle on a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "G event-ELT lookups/s"
+UNIT = "G lookups/s"
+RPS = [100.0, 250.0]
+LEVELS = [0.99]
+PRECISION_NAMES = {0: "fp64", 1: "fp32_kahan", 2: "fp32_fp64agg"}
+DTYPES = {0: "f64", 1: "f32", 2: "f32"}
+FALLBACK_HBM_GBS = 6800.0
+SIM_SOURCE = os.path.join(ROOT, "paper_1308_2066_gb300", "csrc", "simulate.cu")
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=100)
+    p.add_argument("--warmup", type=int, default=10)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--trials", type=int, default=1_000_000)
+    p.add_argument("--precision", choices=list(PRECISION_NAMES.values()), default="fp32_kahan")
+    p.add_argument("--no-variants", action="store_true")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--cpu-seconds", type=float, default=10.0)
+    return p.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)),
+            int(os.environ.get("WORLD_SIZE", 1)))
+
+
+# ---------------------------------------------------------------------------
+# measured peaks, clocks, ncu traffic
+# ---------------------------------------------------------------------------
+
+def hbm_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def sim_source_sha():
+    with open(SIM_SOURCE, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def ncu_traffic(kernel_key: str):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on
+    the current simulate.cu (else None)."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            rec = json.load(f).get(kernel_key)
+    except (OSError, ValueError):
+        return None
+    if not rec or rec.get("simulate_cu_sha") != sim_source_sha():
+        return None
+    return rec.get("dram_bytes_per_launch")
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during a timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.lines: list[str] = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100", "-i", str(self.device)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.thread.join(timeout=5)
+
+    def summary(self):
+        sm, mx, power, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)),
+                "reasons": sorted(reasons), "samples": len(sm),
+                "power_w_median": float(np.median(power))}
+
+
+# ---------------------------------------------------------------------------
+# workload
+# ---------------------------------------------------------------------------
+
+def algorithmic_bytes(n_events: int, n_trials: int, J: int, elem: int) -> int:
+    """YET id (4 B) plus the event's table row in whole 32-byte sectors, per
+    event, plus the 8-byte trial loss written per trial."""
+    row = math.ceil(J * elem / 32) * 32
+    return n_events * (4 + row) + 8 * n_trials
+
+
+def kernel_key(prec: int, J: int) -> str:
+    jp = math.ceil(J * (8 if prec == 0 else 4) / 32) * 32 // (8 if prec == 0 else 4)
+    return f"k_simulate<{'double' if prec == 0 else 'float'},{jp},{prec},fixed>"
+
+
+class Resident:
+    """The workload loaded once into a context (device-resident inputs)."""
+
+    def __init__(self, are, ctx, wl, torch):
+        y = wl.yet
+        self.wl, self.are, self.ctx = wl, are, ctx
+        ids = torch.from_numpy(y.ids).cuda()
+        self.yet = are.are_load_yet(ctx, y.catalog, y.n_trials, None, y.k, ids)
+        del ids
+        self.elts = [are.are_load_elt(ctx, e.ids, e.losses, e.fx, e.ded, e.lim, e.share)
+                     for e in wl.elts]
+        L = wl.layers[0]
+        self.layer = are.are_define_layer(ctx, self.elts, L.occ_r, L.occ_l, L.agg_r, L.agg_l)
+
+
+def time_path(are, torch, res, prec, steps, warmup, stream, ylt, gather=None, world=1):
+    """Run warmup + timed steps of one precision; returns timing dict."""
+    ctx, wl = res.ctx, res.wl
+    n = wl.yet.n_trials
+    sim_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(steps)]
+    out = {}
+
+    def step(i=None):
+        are.are_prepare(ctx, res.layer, res.yet, prec, stream)
+        if i is not None:
+            sim_ev[i][0].record(stream)
+        are.are_simulate(ctx, res.layer, res.yet, 0, n, prec, ylt, stream)
+        if i is not None:
+            sim_ev[i][1].record(stream)
+        if gather is not None:
+            with torch.cuda.stream(stream):
+                full = gather(ylt)
+            out["pml"], out["tvar"] = are.are_risk_measures(ctx, full, None, RPS, LEVELS, stream)
+        else:
+            out["pml"], out["tvar"] = are.are_risk_measures(ctx, ylt, n, RPS, LEVELS, stream)
+
+    for _ in range(warmup):
+        step()
+    barrier(world)
+    torch.cuda.synchronize()
+    l0 = are.are_launch_count(ctx)
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        start.record(stream)
+        for i in range(steps):
+            step(i)
+        end.record(stream)
+        end.synchronize()
+    torch.cuda.synchronize()
+    barrier(world)
+    launches = are.are_launch_count(ctx) - l0
+    ms = start.elapsed_time(end)
+    sim_ms = float(np.mean([a.elapsed_time(b) for a, b in sim_ev]))
+    return {"ms": ms, "sim_ms": sim_ms, "launches": launches, "clocks": clk.summary(),
+            "pml": [float(x) for x in out["pml"]], "tvar": [float(x) for x in out["tvar"]]}
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int, torch) -> float:
+    if world == 1:
+        return x
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def roofline(n_events, n_trials, J, prec, sim_ms):
+    peak, src = hbm_peak()
+    elem = 8 if prec == 0 else 4
+    bytes_ = algorithmic_bytes(n_events, n_trials, J, elem)
+    achieved = bytes_ / (sim_ms * 1e-3) / 1e9
+    traffic = ncu_traffic(kernel_key(prec, J))
+    return {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "traffic": traffic,
+            "kernel": kernel_key(prec, J), "algorithmic_bytes_per_launch": bytes_,
+            "peak_source": f"{src} HBM copy bandwidth",
+            "note": ("algorithmic bytes = per event 4 B id + the event's table row in whole "
+                     "32-B sectors, + 8 B per trial; the table rows are gathered from L2")}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (cpu_baseline, and the reference arm)
+# ---------------------------------------------------------------------------
+
+def oracle_rate(wl, seconds: float, probe_trials: int = 200):
+    """Time the oracle on a prefix of the workload's trials sized to take about
+    `seconds`; returns (lookups/s, trials timed, threads, wall seconds)."""
+    import oracle
+    oracle.build()
+    J = len(wl.layers[0].elts)
+    k = wl.yet.k
+    t0 = time.perf_counter()
+    oracle.simulate_layer(wl, trials=np.arange(probe_trials))
+    per_trial = (time.perf_counter() - t0) / probe_trials
+    n = int(min(wl.yet.n_trials, max(probe_trials, seconds / max(per_trial, 1e-9))))
+    t0 = time.perf_counter()
+    oracle.simulate_layer(wl, trials=np.arange(n))
+    dt = time.perf_counter() - t0
+    return n * k * J / dt, n, oracle.max_threads(), dt
+
+
+def run_reference(args):
+    rank, _, world = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    budget_s = 150.0
+    per_step_s = min(2.0, budget_s / max(1, args.steps + args.warmup))
+    probe = W.paper_scale(n_trials=200)
+    t0 = time.perf_counter()
+    oracle.simulate_layer(probe)
+    per_trial = (time.perf_counter() - t0) / 200
+    n = int(max(50, min(args.trials, per_step_s / max(per_trial, 1e-9))))
+    wl = W.paper_scale(n_trials=n)
+    J, k = len(wl.layers[0].elts), wl.yet.k
+    for _ in range(args.warmup):
+        oracle.simulate_layer(wl)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        r = oracle.simulate_layer(wl)
+        oracle.risk_measures(r.ylt, RPS, LEVELS)
+    dt = time.perf_counter() - t0
+    value = args.steps * n * k * J / dt / 1e9
+    sample = (f"first {n} trials of the 1,000,000 x 1000-event, 16-ELT workload per step "
+              f"(full sort for PML/TVaR of that sample)")
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(dt / args.steps * 1e3, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "paper_scale_1000000_x_1000_j16", "sample_trials": n,
+                       "precision": "fp64 oracle"},
+            "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": oracle.max_threads(),
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# end-to-end through the C ABI with host buffers
+# ---------------------------------------------------------------------------
+
+def run_e2e(are, torch, ctx, wl, prec, steps, warmup, world):
+    y = wl.yet
+    ids_pinned = torch.from_numpy(y.ids).pin_memory()
+    L = wl.layers[0]
+    h2d = y.ids.nbytes + sum(e.ids.nbytes + e.losses.nbytes for e in wl.elts)
+    ylt = torch.empty(y.n_trials, dtype=torch.float64, device="cuda")
+    d2h = 8 * (len(RPS) + len(LEVELS))
+
+    def step():
+        yet = are.are_load_yet(ctx, y.catalog, y.n_trials, None, y.k, ids_pinned)
+        elts = [are.are_load_elt(ctx, e.ids, e.losses, e.fx, e.ded, e.lim, e.share)
+                for e in wl.elts]
+        layer = are.are_define_layer(ctx, elts, L.occ_r, L.occ_l, L.agg_r, L.agg_l)
+        are.are_prepare(ctx, layer, yet, prec)
+        are.are_simulate(ctx, layer, yet, 0, y.n_trials, prec, ylt)
+        are.are_risk_measures(ctx, ylt, y.n_trials, RPS, LEVELS)
+        are.are_free_layer(ctx, layer)
+        for h in elts:
+            are.are_free_elt(ctx, h)
+        are.are_free_yet(ctx, yet)
+
+    for _ in range(warmup):
+        step()
+    barrier(world)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        step()
+    torch.cuda.synchronize()
+    dt = max_over_ranks(time.perf_counter() - t0, world, torch)
+    J = len(L.elts)
+    value = world * steps * y.n_events * J / dt / 1e9
+    return {"value": round(value, 3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": int(d2h), "ms_per_step": round(dt / steps * 1e3, 3)}
+
+
+# ---------------------------------------------------------------------------
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    import paper_1308_2066_gb300 as are
+
+    rank, local_rank, world = dist_env()
+    torch.cuda.set_device(local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    prec = {v: k for k, v in PRECISION_NAMES.items()}[args.precision]
+
+    wl = W.paper_scale(n_trials=args.trials, shard=rank)
+    y = wl.yet
+    J = len(wl.layers[0].elts)
+    ctx = are.are_create(local_rank)
+    res = Resident(are, ctx, wl, torch)
+    stream = torch.cuda.Stream()
+    ylt = torch.empty(y.n_trials, dtype=torch.float64, device="cuda")
+    gather = None
+    if world > 1:
+        import torch.distributed as dist
+        full = torch.empty(world * y.n_trials, dtype=torch.float64, device="cuda")
+
+        def gather(local):
+            dist.all_gather_into_tensor(full, local)
+            return full
+
+    paths = [prec] + ([] if args.no_variants else [p for p in (0, 2, 1) if p != prec])
+    results = {}
+    for p in paths:
+        r = time_path(are, torch, res, p, args.steps, args.warmup, stream, ylt, gather, world)
+        r["ms"] = max_over_ranks(r["ms"], world, torch)
+        r["sim_ms"] = max_over_ranks(r["sim_ms"], world, torch)
+        results[p] = r
+
+    head = results[prec]
+    lookups = world * y.n_events * J
+    ms_step = head["ms"] / args.steps
+    line = {
+        "metric": METRIC,
+        "value": round(lookups / (ms_step * 1e-3) / 1e9, 3),
+        "unit": UNIT,
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(ms_step, 4),
+        "sim_time_s": round(head["sim_ms"] * 1e-3, 6),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": DTYPES[prec],
+        "data": "synthetic: seeded uniform YET ids, lognormal(11,1.5) ELT losses (paper's data is proprietary)",
+        "config": {"workload": wl.name, "trials_per_gpu": y.n_trials, "events_per_trial": y.k,
+                   "elts": J, "catalog": y.catalog, "precision": PRECISION_NAMES[prec],
+                   "step": "repack table + simulate all trials + PML 100/250 + TVaR 99 readback",
+                   "l2": "inputs larger than L2 (4 GB YET streamed every step)",
+                   "parallelism": f"trial blocks per GPU x{world}"},
+        "roofline": roofline(y.n_events, y.n_trials, J, prec, head["sim_ms"]),
+        "gpu_launches": head["launches"],
+        "clocks": head["clocks"],
+        "pml": head["pml"], "tvar": head["tvar"],
+    }
+    line["variants"] = {
+        PRECISION_NAMES[p]: {"ms_per_step": round(r["ms"] / args.steps, 4),
+                             "sim_ms": round(r["sim_ms"], 4),
+                             "value": round(lookups / (r["ms"] / args.steps * 1e-3) / 1e9, 3),
+                             "roofline": roofline(y.n_events, y.n_trials, J, p, r["sim_ms"]),
+                             "pml": r["pml"], "tvar": r["tvar"], "clocks": r["clocks"]}
+        for p, r in results.items() if p != prec}
+
+    if not args.no_e2e:
+        line["e2e"] = run_e2e(are, torch, ctx, wl, prec, max(1, min(args.steps, 10)), 1, world)
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, n, cores, dt = oracle_rate(wl, args.cpu_seconds)
+        line["cpu_baseline"] = {"value": round(rate / 1e9, 6), "unit": UNIT, "cores": cores,
+                                "kind": "oracle",
+                                "sample": f"first {n} of the {y.n_trials} trials ({dt:.1f} s wall, "
+                                          f"FP64 oracle, all host threads)"}
+    are.are_destroy(ctx)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,217 @@
+/*
+ * are.h -- C ABI of libare, a GB300 (sm_103a) engine for the aggregate risk
+ * analysis of Bahl, Baltzer, Rau-Chaplin and Varghese, "Parallel Simulations
+ * for Analysing Portfolios of Catastrophic Event Risk" (arXiv 1308.2066).
+ *
+ * The calls follow the paper's statement of the problem: load a Year Event
+ * Table and Event Loss Tables with their financial terms (Section II-A),
+ * define layers (Section II-A item 3, Table I), run the analysis stage to a
+ * Year Loss Table (Section II-B, Basic Algorithm) and read PML and TVaR from
+ * it (Section I and II-C).
+ *
+ * Conventions shared by every call
+ *   - Every call returns an are_status and never aborts the process.  On a
+ *     failure are_last_error() returns a message for the calling thread.
+ *   - Array arguments are plain pointers.  Unless a call says otherwise a
+ *     pointer may address host memory (pageable or pinned) or device memory
+ *     of the context's GPU; the library asks the CUDA runtime which it is.
+ *   - Inputs are copied: the caller keeps ownership and may free or reuse
+ *     its buffers when the call returns.
+ *   - Handles (YET, ELT, layer) are small positive integers owned by the
+ *     context; are_destroy() frees everything they refer to.
+ *   - Outputs go to caller-allocated buffers.
+ *   - "stream" is a cudaStream_t passed as void*.  With a stream the call
+ *     only enqueues its work there: device inputs must be ready in that
+ *     stream's order and device outputs are ready when the stream reaches
+ *     the call.  NULL means: wait for all earlier work on the device, run on
+ *     the context's own stream and finish before returning.  A call that
+ *     returns values in host memory always waits for them.
+ *   - The load calls (are_load_*) are synchronous; when given device
+ *     pointers they first wait for all earlier work on the device.
+ *   - Event ids are 0-based in [0, catalog_size).  Loss values, deductibles
+ *     and retentions are finite and >= 0; limits are >= 0 and may be +inf.
+ */
+#ifndef ARE_H
+#define ARE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define ARE_API __attribute__((visibility("default")))
+#else
+#define ARE_API
+#endif
+
+typedef struct are_ctx are_ctx;
+
+typedef int32_t are_status;
+#define ARE_OK 0
+#define ARE_EINVAL 1    /* bad argument or malformed input data */
+#define ARE_ENOMEM 2    /* over the context's memory budget, or the GPU is full */
+#define ARE_ECUDA 3     /* a CUDA runtime call failed */
+#define ARE_ETIMEOUT 4  /* a bounded wait ran out */
+#define ARE_EBUSY 5     /* the serving queue is full */
+#define ARE_ENOTFOUND 6 /* unknown handle or ticket */
+
+/* Largest number of ELTs in one layer (the paper's layers cover 3 to 30,
+ * Section II-A item 3). */
+#define ARE_MAX_ELTS_PER_LAYER 32
+
+/* Financial terms I of one ELT (Section II-A item 2: currency exchange rate
+ * and terms applied to each event loss).  The loss net of terms of an event
+ * with loss x is  share * min(max(fx * x - deductible, 0), limit).
+ * fx > 0 finite; deductible >= 0 finite; limit >= 0 (+inf = none);
+ * 0 <= share <= 1. */
+typedef struct {
+    double fx;
+    double deductible;
+    double limit;
+    double share;
+} are_fin_terms;
+
+/* Layer terms T of Table I: occurrence retention/limit, applied to each
+ * event occurrence; aggregate retention/limit, applied to the running sum of
+ * occurrence losses within a trial.  Retentions >= 0 finite; limits >= 0
+ * (+inf = none). */
+typedef struct {
+    double occ_ret;
+    double occ_lim;
+    double agg_ret;
+    double agg_lim;
+} are_layer_terms;
+
+/* Arithmetic of the analysis stage.
+ *   ARE_FP64          losses, terms and sums in FP64.
+ *   ARE_FP32_KAHAN    losses and terms in FP32, per-event sums in FP32, the
+ *                     trial's running sum in FP32 with Kahan compensation.
+ *   ARE_FP32_FP64AGG  losses and terms in FP32, the trial's running sum in
+ *                     FP64.
+ * The paper does not state its precision; its losses are doubles
+ * (Section III-B, data structure iii). */
+typedef enum {
+    ARE_FP64 = 0,
+    ARE_FP32_KAHAN = 1,
+    ARE_FP32_FP64AGG = 2
+} are_precision;
+
+/* ------------------------------------------------------------------------ */
+/* Context                                                                   */
+/* ------------------------------------------------------------------------ */
+
+/* Create a context on CUDA device `device`.  mem_budget_bytes caps the
+ * device memory the context allocates for YETs, ELTs, tables and scratch
+ * (0 = no cap); a load that would exceed it fails with ARE_ENOMEM and leaves
+ * the context unchanged.  *out receives the context.  ARE_ECUDA if the device
+ * cannot be used. */
+ARE_API are_status are_create(are_ctx **out, int device, size_t mem_budget_bytes);
+
+/* Free every device buffer and handle of the context, then the context.
+ * NULL is accepted.  The caller must not use the context afterwards. */
+ARE_API are_status are_destroy(are_ctx *ctx);
+
+/* Message of the last failed call made by the calling thread on `ctx`
+ * ("" if none).  The string stays valid until that thread's next call. */
+ARE_API const char *are_last_error(const are_ctx *ctx);
+
+/* Device memory the context holds now, in bytes (budget accounting). */
+ARE_API are_status are_memory_used(const are_ctx *ctx, size_t *bytes);
+
+/* Number of CUDA kernels the context has launched since it was created
+ * (every launch of every call, validation included). */
+ARE_API are_status are_launch_count(const are_ctx *ctx, uint64_t *launches);
+
+/* ------------------------------------------------------------------------ */
+/* Inputs (Section II-A)                                                     */
+/* ------------------------------------------------------------------------ */
+
+/* Load a Year Event Table: n_trials trials, each an ordered sequence of
+ * event ids (Section II-A item 1; the paper stores ids and trial boundaries,
+ * Section III-B data structures i and ii).
+ *   catalog_size      number of events in the catalog, > 0; ids in [0, C).
+ *   offsets           int64[n_trials + 1], offsets[0] = 0, non-decreasing;
+ *                     trial i is event_ids[offsets[i] .. offsets[i+1]).
+ *                     NULL when every trial holds events_per_trial events.
+ *   events_per_trial  > 0 when offsets is NULL, ignored otherwise.
+ *   event_ids         int32[total events], in stored (time-stamp) order.
+ *   timestamps        NULL, or float32[total events]; when given they must
+ *                     be non-decreasing within each trial.  They are checked
+ *                     and not kept: the method uses the stored order.
+ * Ids, offsets and timestamps are validated on the device; a violation
+ * returns ARE_EINVAL and loads nothing.  *yet_handle receives the handle. */
+ARE_API are_status are_load_yet(are_ctx *ctx, int32_t catalog_size, int64_t n_trials,
+                        const int64_t *offsets, int32_t events_per_trial,
+                        const int32_t *event_ids, const float *timestamps,
+                        int32_t *yet_handle);
+
+/* Load an Event Loss Table: n_entries (event id, loss) pairs (Section II-A
+ * item 2) with its financial terms.  Ids >= 0 and distinct within the ELT
+ * (duplicates are ARE_EINVAL); losses finite and >= 0.  n_entries may be 0.
+ * *elt_handle receives the handle. */
+ARE_API are_status are_load_elt(are_ctx *ctx, int32_t n_entries, const int32_t *event_ids,
+                        const double *losses, const are_fin_terms *terms,
+                        int32_t *elt_handle);
+
+/* Define a layer: 1..ARE_MAX_ELTS_PER_LAYER ELT handles (the same ELT may not
+ * appear twice) and its layer terms (Section II-A item 3, Table I).  The
+ * order of elt_handles fixes the order in which per-ELT losses are summed.
+ * *layer_handle receives the handle. */
+ARE_API are_status are_define_layer(are_ctx *ctx, const int32_t *elt_handles, int32_t n_elts,
+                            const are_layer_terms *terms, int32_t *layer_handle);
+
+/* Release a YET, an ELT (ARE_EINVAL while a layer uses it) or a layer,
+ * with any tables built for it.  ARE_ENOTFOUND for an unknown handle. */
+ARE_API are_status are_free_yet(are_ctx *ctx, int32_t yet_handle);
+ARE_API are_status are_free_elt(are_ctx *ctx, int32_t elt_handle);
+ARE_API are_status are_free_layer(are_ctx *ctx, int32_t layer_handle);
+
+/* ------------------------------------------------------------------------ */
+/* Analysis stage (Section II-B)                                             */
+/* ------------------------------------------------------------------------ */
+
+/* Preprocessing (Section II-B, stage 1; Section III-B's direct access
+ * tables): (re)build the layer's event-major direct-access table for the
+ * YET's catalog in the given precision, on `stream`.  are_simulate builds
+ * the table on first use; calling this first keeps that cost out of it. */
+ARE_API are_status are_prepare(are_ctx *ctx, int32_t layer, int32_t yet, are_precision precision,
+                       void *stream);
+
+/* Analysis stage for one layer (Basic Algorithm, Section II-B): for trials
+ * trial_begin .. trial_begin + n_trials - 1 of the YET, look up every event
+ * in every ELT of the layer, apply the financial terms, sum over ELTs, apply
+ * the occurrence terms, accumulate the trial's running sum and apply the
+ * aggregate terms; ylt[i] receives the loss of trial trial_begin + i
+ * (double[n_trials], host or device).  Trials are independent, so a run split
+ * into trial ranges gives the same YLT as one run.  Enqueued on `stream`;
+ * when ylt is host memory the call copies it back and synchronises. */
+ARE_API are_status are_simulate(are_ctx *ctx, int32_t layer, int32_t yet, int64_t trial_begin,
+                        int64_t n_trials, are_precision precision, double *ylt,
+                        void *stream);
+
+/* ------------------------------------------------------------------------ */
+/* Filters on the YLT (Section II-C): PML and TVaR                           */
+/* ------------------------------------------------------------------------ */
+
+/* From a YLT of n > 0 trial losses (host or device):
+ *   pml_out[r]  = the m-th largest loss, m = ceil(n / return_periods[r]),
+ *                 return period read to the nearest 1e-6 and >= 1;
+ *   tvar_out[r] = the mean of the m largest losses,
+ *                 m = ceil(n * (1 - tvar_levels[r])), level read to the
+ *                 nearest 1e-9 and strictly between 0 and 1.
+ * pml_out and tvar_out are host arrays.  The paper names these measures
+ * without defining them (Section I, Section II-C); this is the reading the
+ * library takes.  Synchronises `stream`. */
+ARE_API are_status are_risk_measures(are_ctx *ctx, const double *ylt, int64_t n,
+                             const double *return_periods, int32_t n_rp, double *pml_out,
+                             const double *tvar_levels, int32_t n_tv, double *tvar_out,
+                             void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ARE_H */

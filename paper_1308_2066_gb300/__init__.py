@@ -1,0 +1,232 @@
+"""Python binding of libare, the GB300 aggregate-risk-analysis engine.
+
+Argument marshalling only: every function here forwards to the C ABI entry
+point of the same name in ``libare.so`` (declared in ``include/are.h``); all
+computation happens in the library's CUDA kernels.  Arrays may be numpy
+arrays (host memory), torch tensors (host or device) or raw integer
+addresses.  A failed call raises :class:`AreError` with the library's status
+and message.  If ``libare.so`` has not been built the import of any function
+fails loudly: there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libare.so")
+
+ARE_OK, ARE_EINVAL, ARE_ENOMEM, ARE_ECUDA, ARE_ETIMEOUT, ARE_EBUSY, ARE_ENOTFOUND = range(7)
+ARE_FP64, ARE_FP32_KAHAN, ARE_FP32_FP64AGG = 0, 1, 2
+ARE_MAX_ELTS_PER_LAYER = 32
+STATUS_NAMES = {0: "ARE_OK", 1: "ARE_EINVAL", 2: "ARE_ENOMEM", 3: "ARE_ECUDA",
+                4: "ARE_ETIMEOUT", 5: "ARE_EBUSY", 6: "ARE_ENOTFOUND"}
+PRECISIONS = {"fp64": ARE_FP64, "fp32_kahan": ARE_FP32_KAHAN, "fp32_fp64agg": ARE_FP32_FP64AGG}
+
+
+class AreError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+        self.message = message
+
+
+class FinTerms(C.Structure):
+    _fields_ = [("fx", C.c_double), ("deductible", C.c_double), ("limit", C.c_double),
+                ("share", C.c_double)]
+
+
+class LayerTerms(C.Structure):
+    _fields_ = [("occ_ret", C.c_double), ("occ_lim", C.c_double), ("agg_ret", C.c_double),
+                ("agg_lim", C.c_double)]
+
+
+_lib = None
+_P = C.c_void_p
+_SIGS = {
+    "are_create": (C.c_int32, [C.POINTER(C.c_void_p), C.c_int, C.c_size_t]),
+    "are_destroy": (C.c_int32, [_P]),
+    "are_last_error": (C.c_char_p, [_P]),
+    "are_memory_used": (C.c_int32, [_P, C.POINTER(C.c_size_t)]),
+    "are_launch_count": (C.c_int32, [_P, C.POINTER(C.c_uint64)]),
+    "are_load_yet": (C.c_int32, [_P, C.c_int32, C.c_int64, _P, C.c_int32, _P, _P,
+                                 C.POINTER(C.c_int32)]),
+    "are_load_elt": (C.c_int32, [_P, C.c_int32, _P, _P, C.POINTER(FinTerms),
+                                 C.POINTER(C.c_int32)]),
+    "are_define_layer": (C.c_int32, [_P, _P, C.c_int32, C.POINTER(LayerTerms),
+                                     C.POINTER(C.c_int32)]),
+    "are_free_yet": (C.c_int32, [_P, C.c_int32]),
+    "are_free_elt": (C.c_int32, [_P, C.c_int32]),
+    "are_free_layer": (C.c_int32, [_P, C.c_int32]),
+    "are_prepare": (C.c_int32, [_P, C.c_int32, C.c_int32, C.c_int, _P]),
+    "are_simulate": (C.c_int32, [_P, C.c_int32, C.c_int32, C.c_int64, C.c_int64, C.c_int, _P,
+                                 _P]),
+    "are_risk_measures": (C.c_int32, [_P, _P, C.c_int64, _P, C.c_int32, _P, _P, C.c_int32, _P,
+                                      _P]),
+}
+
+
+def lib():
+    """The loaded libare.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                               "`python -c 'import __graft_entry__ as g; g.build()'`")
+        L = C.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(ctx, status: int):
+    if status != ARE_OK:
+        msg = lib().are_last_error(ctx) if ctx else b""
+        raise AreError(status, (msg or b"").decode(errors="replace"))
+
+
+def _addr(x, dtype=None):
+    """Address of an array argument: None, int, numpy array or torch tensor."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be contiguous")
+        if dtype is not None and x.dtype != np.dtype(dtype):
+            raise TypeError(f"expected {np.dtype(dtype)}, got {x.dtype}")
+        return x.ctypes.data
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        if dtype is not None and str(x.dtype).replace("torch.", "") != np.dtype(dtype).name:
+            raise TypeError(f"expected {np.dtype(dtype)}, got {x.dtype}")
+        return x.data_ptr()
+    raise TypeError(f"unsupported array argument {type(x)}")
+
+
+def _stream(s):
+    if s is None:
+        return None
+    if isinstance(s, int):
+        return s
+    return int(s.cuda_stream)
+
+
+def _len(x) -> int:
+    return int(x.shape[0]) if x is not None else 0
+
+
+# ---------------------------------------------------------------------------
+# context
+# ---------------------------------------------------------------------------
+
+def are_create(device: int = 0, mem_budget_bytes: int = 0):
+    out = C.c_void_p()
+    _check(None, lib().are_create(C.byref(out), int(device), int(mem_budget_bytes)))
+    return out
+
+
+def are_destroy(ctx) -> None:
+    _check(None, lib().are_destroy(ctx))
+
+
+def are_last_error(ctx) -> str:
+    return (lib().are_last_error(ctx) or b"").decode(errors="replace")
+
+
+def are_memory_used(ctx) -> int:
+    n = C.c_size_t()
+    _check(ctx, lib().are_memory_used(ctx, C.byref(n)))
+    return int(n.value)
+
+
+def are_launch_count(ctx) -> int:
+    n = C.c_uint64()
+    _check(ctx, lib().are_launch_count(ctx, C.byref(n)))
+    return int(n.value)
+
+
+# ---------------------------------------------------------------------------
+# inputs
+# ---------------------------------------------------------------------------
+
+def are_load_yet(ctx, catalog_size: int, n_trials: int, offsets, events_per_trial: int,
+                 event_ids, timestamps=None) -> int:
+    h = C.c_int32()
+    _check(ctx, lib().are_load_yet(ctx, int(catalog_size), int(n_trials),
+                                   _addr(offsets, np.int64), int(events_per_trial or 0),
+                                   _addr(event_ids, np.int32), _addr(timestamps, np.float32),
+                                   C.byref(h)))
+    return h.value
+
+
+def are_load_elt(ctx, event_ids, losses, fx: float = 1.0, deductible: float = 0.0,
+                 limit: float = math.inf, share: float = 1.0) -> int:
+    n = _len(event_ids)
+    if _len(losses) != n:
+        raise ValueError("event_ids and losses differ in length")
+    t = FinTerms(fx, deductible, limit, share)
+    h = C.c_int32()
+    _check(ctx, lib().are_load_elt(ctx, n, _addr(event_ids, np.int32), _addr(losses, np.float64),
+                                   C.byref(t), C.byref(h)))
+    return h.value
+
+
+def are_define_layer(ctx, elt_handles: Sequence[int], occ_ret: float = 0.0,
+                     occ_lim: float = math.inf, agg_ret: float = 0.0,
+                     agg_lim: float = math.inf) -> int:
+    hs = np.ascontiguousarray(elt_handles, dtype=np.int32)
+    t = LayerTerms(occ_ret, occ_lim, agg_ret, agg_lim)
+    h = C.c_int32()
+    _check(ctx, lib().are_define_layer(ctx, hs.ctypes.data, hs.shape[0], C.byref(t), C.byref(h)))
+    return h.value
+
+
+def are_free_yet(ctx, h: int) -> None:
+    _check(ctx, lib().are_free_yet(ctx, int(h)))
+
+
+def are_free_elt(ctx, h: int) -> None:
+    _check(ctx, lib().are_free_elt(ctx, int(h)))
+
+
+def are_free_layer(ctx, h: int) -> None:
+    _check(ctx, lib().are_free_layer(ctx, int(h)))
+
+
+# ---------------------------------------------------------------------------
+# analysis stage and filters
+# ---------------------------------------------------------------------------
+
+def are_prepare(ctx, layer: int, yet: int, precision: int = ARE_FP64, stream=None) -> None:
+    _check(ctx, lib().are_prepare(ctx, int(layer), int(yet), int(precision), _stream(stream)))
+
+
+def are_simulate(ctx, layer: int, yet: int, trial_begin: int, n_trials: int,
+                 precision: int, ylt, stream=None) -> None:
+    _check(ctx, lib().are_simulate(ctx, int(layer), int(yet), int(trial_begin), int(n_trials),
+                                   int(precision), _addr(ylt, np.float64), _stream(stream)))
+
+
+def are_risk_measures(ctx, ylt, n: Optional[int] = None,
+                      return_periods: Sequence[float] = (100.0, 250.0),
+                      tvar_levels: Sequence[float] = (0.99,), stream=None):
+    """Returns (pml, tvar) as numpy float64 arrays."""
+    n = _len(ylt) if n is None else int(n)
+    rp = np.ascontiguousarray(return_periods, dtype=np.float64)
+    lv = np.ascontiguousarray(tvar_levels, dtype=np.float64)
+    pml = np.empty(rp.shape[0], np.float64)
+    tv = np.empty(lv.shape[0], np.float64)
+    _check(ctx, lib().are_risk_measures(ctx, _addr(ylt, np.float64), n, rp.ctypes.data,
+                                        rp.shape[0], pml.ctypes.data, lv.ctypes.data, lv.shape[0],
+                                        tv.ctypes.data, _stream(stream)))
+    return pml, tv

@@ -1,0 +1,176 @@
+// are_internal.cuh -- context state and kernel entry points shared by the
+// translation units of libare.  Not part of the public ABI (include/are.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "are.h"
+
+namespace are {
+
+constexpr int kMaxElts = ARE_MAX_ELTS_PER_LAYER;
+constexpr int kMaxTargets = 8;  // PML/TVaR ranks selected in one pass
+
+// ---------------------------------------------------------------------------
+// status helpers
+// ---------------------------------------------------------------------------
+
+void set_error(const are_ctx *ctx, const std::string &msg);
+
+struct Error {
+    are_status code;
+    std::string msg;
+};
+
+#define ARE_CUDA_TRY(expr)                                                          \
+    do {                                                                            \
+        cudaError_t e__ = (expr);                                                   \
+        if (e__ != cudaSuccess)                                                     \
+            throw ::are::Error{e__ == cudaErrorMemoryAllocation ? ARE_ENOMEM        \
+                                                                : ARE_ECUDA,        \
+                               std::string(#expr) + ": " + cudaGetErrorString(e__)}; \
+    } while (0)
+
+#define ARE_CHECK(cond, code, msg)                      \
+    do {                                                \
+        if (!(cond)) throw ::are::Error{(code), (msg)}; \
+    } while (0)
+
+// ---------------------------------------------------------------------------
+// device-resident inputs
+// ---------------------------------------------------------------------------
+
+struct Yet {
+    int32_t catalog = 0;
+    int64_t n_trials = 0;
+    int32_t k = 0;                 // events per trial when fixed, else 0
+    int64_t n_events = 0;
+    int64_t *d_off = nullptr;      // n_trials + 1 (ragged only)
+    int32_t *d_ids = nullptr;      // n_events, padded by kIdPad zero ids
+    size_t bytes = 0;
+};
+constexpr int64_t kIdPad = 64;     // zero ids after the last event (vector over-read)
+
+struct Elt {
+    int32_t n = 0;
+    int32_t max_id = -1;
+    int32_t *d_ids = nullptr;
+    double *d_loss = nullptr;
+    are_fin_terms terms{};
+    size_t bytes = 0;
+    int users = 0;                 // layers referring to it
+};
+
+// Event-major direct-access table of one layer: row e holds the converted
+// losses of event e in the layer's ELTs, jp columns (j >= J are zero).
+struct Table {
+    int32_t catalog = -1;
+    int jp = 0;
+    void *d = nullptr;
+    size_t bytes = 0;
+};
+
+struct Layer {
+    std::vector<int32_t> elts;
+    are_layer_terms terms{};
+    Table t32, t64;
+};
+
+// ---------------------------------------------------------------------------
+// kernel parameter blocks (passed by value; they live in the constant bank)
+// ---------------------------------------------------------------------------
+
+struct TermsF32 {
+    float ded[kMaxElts], lim[kMaxElts], share[kMaxElts];
+    float occ_r, occ_l;
+};
+struct TermsF64 {
+    double ded[kMaxElts], lim[kMaxElts], share[kMaxElts];
+    double occ_r, occ_l;
+};
+
+struct SimArgs {
+    const int32_t *ids;      // YET event ids
+    const int64_t *off;      // ragged offsets or nullptr
+    int32_t k;               // fixed events per trial
+    int64_t trial_begin;
+    int64_t n_trials;
+    const void *table;       // [catalog][jp]
+    double agg_r, agg_l;
+    int any_share;           // some ELT has share != 1
+    double *ylt;             // n_trials
+};
+
+struct ScatterArgs {
+    const int32_t *ids[kMaxElts];
+    const double *loss[kMaxElts];
+    int32_t n[kMaxElts];
+    double fx[kMaxElts];
+    int32_t n_elts;
+    int32_t jp;
+};
+
+// ---------------------------------------------------------------------------
+// launchers (one per translation unit); each returns the number of kernels
+// it launched, which the context adds to its launch count
+// ---------------------------------------------------------------------------
+
+// repack.cu
+int launch_scatter_table(void *table, bool fp32, const ScatterArgs &a, cudaStream_t s);
+int table_jp(int n_elts, bool fp32);
+
+// validate.cu: each sets *flag (device int, zeroed by the caller) non-zero on a violation
+int launch_check_ids(const int32_t *ids, int64_t n, int32_t catalog, int *flag, cudaStream_t s);
+int launch_check_offsets(const int64_t *off, int64_t n_trials, int64_t n_events, int *flag,
+                          cudaStream_t s);
+int launch_check_timestamps(const float *ts, const int64_t *off, int64_t n_trials, int32_t k,
+                             int *flag, cudaStream_t s);
+
+// simulate.cu
+int launch_simulate(const SimArgs &a, are_precision prec, int jp, const TermsF32 *t32,
+                     const TermsF64 *t64, int num_sms, cudaStream_t s);
+
+// select.cu
+struct SelectScratch {
+    uint32_t *hist = nullptr;       // kMaxTargets * 256
+    unsigned long long *state = nullptr;  // per target: prefix, remaining rank, ...
+    double *partial = nullptr;      // per block per target: sum hi, sum lo, count
+    double *result = nullptr;       // per target: value, tail mean
+    int max_blocks = 0;
+};
+void select_alloc(SelectScratch &s, int num_sms);
+void select_free(SelectScratch &s);
+// ranks[t] (1-based, descending order) for n_targets <= kMaxTargets; writes
+// result[2*t] = m-th largest value, result[2*t+1] = mean of the m largest.
+int launch_select(const double *ylt, int64_t n, const int64_t *ranks, int n_targets,
+                   SelectScratch &s, int num_sms, cudaStream_t st);
+
+}  // namespace are
+
+// ---------------------------------------------------------------------------
+// context
+// ---------------------------------------------------------------------------
+
+struct are_ctx {
+    int device = 0;
+    int num_sms = 0;
+    size_t budget = 0;
+    size_t used = 0;
+    cudaStream_t stream = nullptr;
+    std::recursive_mutex mu;
+    int32_t next_handle = 1;
+    std::map<int32_t, are::Yet> yets;
+    std::map<int32_t, are::Elt> elts;
+    std::map<int32_t, are::Layer> layers;
+    int *d_flag = nullptr;   // validation flag
+    int *h_flag = nullptr;   // pinned mirror
+    are::SelectScratch sel;
+    double *h_result = nullptr;  // pinned, 2 * kMaxTargets
+    uint64_t launches = 0;       // kernels launched by this context
+};

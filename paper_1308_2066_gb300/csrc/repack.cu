@@ -1,0 +1,55 @@
+// repack.cu -- preprocessing (Section II-B, stage 1): the layer's ELTs become
+// one event-major direct-access table.
+//
+// The paper keeps one catalog-sized loss array per ELT (Section III-B: a
+// 2M-event catalog and 15 ELTs give 30M event-loss pairs), so an event costs
+// one random access per ELT.  Here row e of a single table holds event e's
+// losses in all J ELTs of the layer, in layer order, padded to a whole number
+// of 32-byte sectors (jp columns, zeros past J): one event's lookups in every
+// ELT become one row read.  Each loss is stored as fx * loss, the ELT's
+// currency conversion, computed in FP64 and rounded once to the table type.
+#include <cuda_runtime.h>
+
+#include "are_internal.cuh"
+
+namespace are {
+namespace {
+
+template <typename T>
+__global__ void k_scatter(T *__restrict__ tab, const ScatterArgs a)
+{
+    const int j = blockIdx.y;
+    const int32_t n = a.n[j];
+    const int32_t *ids = a.ids[j];
+    const double *loss = a.loss[j];
+    const double fx = a.fx[j];
+    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        tab[(size_t)ids[i] * a.jp + j] = (T)__dmul_rn(fx, loss[i]);
+}
+
+}  // namespace
+
+// Columns per row: J rounded up so a row fills whole 32-byte sectors.
+int table_jp(int n_elts, bool fp32)
+{
+    const int per_sector = fp32 ? 8 : 4;
+    int jp = (n_elts + per_sector - 1) / per_sector * per_sector;
+    return jp < per_sector ? per_sector : jp;
+}
+
+int launch_scatter_table(void *table, bool fp32, const ScatterArgs &a, cudaStream_t s)
+{
+    int32_t nmax = 0;
+    for (int j = 0; j < a.n_elts; ++j) nmax = a.n[j] > nmax ? a.n[j] : nmax;
+    if (nmax == 0 || a.n_elts == 0) return 0;
+    dim3 grid((unsigned)((nmax + 255) / 256), (unsigned)a.n_elts);
+    if (grid.x > 4096) grid.x = 4096;
+    if (fp32)
+        k_scatter<float><<<grid, 256, 0, s>>>(static_cast<float *>(table), a);
+    else
+        k_scatter<double><<<grid, 256, 0, s>>>(static_cast<double *>(table), a);
+    ARE_CUDA_TRY(cudaGetLastError());
+    return 1;
+}
+
+}  // namespace are

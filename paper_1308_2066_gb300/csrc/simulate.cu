@@ -1,0 +1,393 @@
+// simulate.cu -- the analysis stage (Basic Algorithm, Section II-B) for one
+// layer over a range of trials, reading the layer's event-major
+// direct-access table built by repack.cu.
+//
+// Mapping (GB300): one warp per trial.  The warp walks the trial's events in
+// steps; in a step each event's table row (J losses, 32-byte aligned) is read
+// by R lanes with one 16-byte load each, so a warp load instruction fetches
+// 32/R whole rows.  Each lane applies the financial terms (step 2) to the
+// columns it holds, the R lanes of a row add their parts by shuffles (the sum
+// over ELTs, lines 8-9), the row's first lane applies the occurrence terms
+// (step 3, lines 10-11) and adds the occurrence loss to its running sum.  At
+// the end of the trial the warp adds the lanes' sums and applies the
+// aggregate terms (step 4).  The trial loss is the aggregate-clamped total:
+// with non-negative occurrence losses the de-cumulated marginals of lines
+// 16-19 telescope to it, so the YLT needs no per-event scan.
+//
+// FP64 on GB300 runs at a small fraction of the FP32 rate, so the FP64 path
+// takes every decision it can on bit patterns: for non-negative doubles the
+// integer order of the bits is the numeric order, so "x <= deductible",
+// "v > limit" and the zero tests are integer compares.  A subtraction or an
+// addition is issued only when some lane of the warp needs one (adding an
+// exact zero or clamping a non-positive value changes nothing), which keeps
+// the FP64 pipe for the few occurrences that carry a loss.
+#include <cuda_runtime.h>
+
+#include <type_traits>
+
+#include "are_internal.cuh"
+
+namespace are {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+template <typename T>
+struct VecOf;
+template <>
+struct VecOf<float> {
+    using type = float4;
+    static constexpr int n = 4;
+};
+template <>
+struct VecOf<double> {
+    using type = double2;
+    static constexpr int n = 2;
+};
+
+__device__ __forceinline__ float comp(const float4 &v, int c)
+{
+    return c == 0 ? v.x : c == 1 ? v.y : c == 2 ? v.z : v.w;
+}
+__device__ __forceinline__ double comp(const double2 &v, int c) { return c == 0 ? v.x : v.y; }
+
+__device__ __forceinline__ uint64_t bits(double x) { return (uint64_t)__double_as_longlong(x); }
+__device__ __forceinline__ double dbl(uint64_t b) { return __longlong_as_double((long long)b); }
+
+// FP64 add/sub/mul that the compiler may not hoist out of the warp-uniform
+// branches below (it would otherwise compute them speculatively, and on this
+// chip every FP64 instruction is expensive).
+__device__ __forceinline__ double vadd(double a, double b)
+{
+    double r;
+    asm volatile("add.rn.f64 %0, %1, %2;" : "=d"(r) : "d"(a), "d"(b));
+    return r;
+}
+__device__ __forceinline__ double vsub(double a, double b)
+{
+    double r;
+    asm volatile("sub.rn.f64 %0, %1, %2;" : "=d"(r) : "d"(a), "d"(b));
+    return r;
+}
+__device__ __forceinline__ double vmul(double a, double b)
+{
+    double r;
+    asm volatile("mul.rn.f64 %0, %1, %2;" : "=d"(r) : "d"(a), "d"(b));
+    return r;
+}
+
+// a + b for non-negative doubles, issuing the FP64 add only when some lane of
+// the warp has two non-zero operands (x + 0 = x exactly).  All lanes call it.
+__device__ __forceinline__ double add_nn(double a, double b)
+{
+    const bool both = bits(a) != 0 && bits(b) != 0;
+    double r = bits(a) == 0 ? b : a;
+    if (__any_sync(kFull, both)) {
+        const double s = vadd(a, b);
+        if (both) r = s;
+    }
+    return r;
+}
+
+// min(max(x - r, 0), l) for x, r >= 0 and l >= 0 (+inf allowed).  The
+// subtraction is issued only when some lane has x > r.  All lanes call it.
+__device__ __forceinline__ double net_nn(double x, uint64_t r_bits, double r, uint64_t l_bits)
+{
+    const bool need = bits(x) > r_bits;
+    double out = 0.0;
+    if (__any_sync(kFull, need)) {
+        const double d = vsub(x, r);
+        const uint64_t db = bits(d);
+        if (need) out = dbl(db < l_bits ? db : l_bits);
+    }
+    return out;
+}
+
+template <typename T>
+struct LaneTerms;
+
+template <>
+struct LaneTerms<float> {
+    float ded[4], lim[4], share[4];
+    float occ_r, occ_l;
+    __device__ void load(const TermsF32 &t, int col)
+    {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const int j = col * 4 + c;
+            ded[c] = j < kMaxElts ? t.ded[j] : 0.f;
+            lim[c] = j < kMaxElts ? t.lim[j] : 0.f;
+            share[c] = j < kMaxElts ? t.share[j] : 1.f;
+        }
+        occ_r = t.occ_r;
+        occ_l = t.occ_l;
+    }
+    // sum over this lane's columns of share * min(max(x - D, 0), Lim)
+    __device__ __forceinline__ float part(const float4 &v, bool any_share) const
+    {
+        float p = 0.f;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            float n = fminf(fmaxf(__fsub_rn(comp(v, c), ded[c]), 0.f), lim[c]);
+            if (any_share) n = __fmul_rn(n, share[c]);
+            p = __fadd_rn(p, n);
+        }
+        return p;
+    }
+};
+
+template <>
+struct LaneTerms<double> {
+    double ded[2], share[2];
+    uint64_t ded_b[2], lim_b[2], share_b[2];
+    double occ_r;
+    uint64_t occ_r_b, occ_l_b;
+    __device__ void load(const TermsF64 &t, int col)
+    {
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            const int j = col * 2 + c;
+            ded[c] = j < kMaxElts ? t.ded[j] : 0.0;
+            share[c] = j < kMaxElts ? t.share[j] : 1.0;
+            ded_b[c] = bits(ded[c]);
+            share_b[c] = bits(share[c]);
+            lim_b[c] = bits(j < kMaxElts ? t.lim[j] : 0.0);
+        }
+        occ_r = t.occ_r;
+        occ_r_b = bits(t.occ_r);
+        occ_l_b = bits(t.occ_l);
+    }
+    __device__ __forceinline__ double part(const double2 &v, bool any_share) const
+    {
+        double p = 0.0;
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            double n = net_nn(comp(v, c), ded_b[c], ded[c], lim_b[c]);
+            if (any_share) {
+                const bool need = bits(n) != 0 && share_b[c] != bits(1.0);
+                if (__any_sync(kFull, need)) {
+                    const double m = vmul(n, share[c]);
+                    if (need) n = m;
+                }
+            }
+            p = add_nn(p, n);
+        }
+        return p;
+    }
+};
+
+// Sum of the R lanes of a row into its first lane (col == 0), pairing
+// neighbours first.  Works for any R <= 32; every lane calls it.
+template <int R>
+__device__ __forceinline__ float row_sum(float v, int col)
+{
+#pragma unroll
+    for (int off = 1; off < R; off <<= 1) {
+        const float o = __shfl_down_sync(kFull, v, off);
+        if ((col & (2 * off - 1)) == 0 && col + off < R) v = __fadd_rn(v, o);
+    }
+    return v;
+}
+template <int R>
+__device__ __forceinline__ double row_sum(double v, int col)
+{
+#pragma unroll
+    for (int off = 1; off < R; off <<= 1) {
+        double o = __shfl_down_sync(kFull, v, off);
+        if (!((col & (2 * off - 1)) == 0 && col + off < R)) o = 0.0;
+        v = add_nn(v, o);
+    }
+    return v;
+}
+
+// Per-lane running sums of occurrence losses (step 4, lines 12-13), one
+// flavour per precision mode.
+struct AccF64 {
+    double s = 0.0;
+    __device__ __forceinline__ void add(double o) { s = add_nn(s, o); }
+    __device__ __forceinline__ double total() const { return s; }
+};
+struct AccKahan {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float o)
+    {
+        const float y = __fsub_rn(o, c);
+        const float t = __fadd_rn(s, y);
+        c = __fsub_rn(__fsub_rn(t, s), y);
+        s = t;
+    }
+    // s - c exactly in double: c is within a few ulps of s's last bit
+    __device__ __forceinline__ double total() const { return (double)s - (double)c; }
+};
+struct AccF32F64 {
+    double s = 0.0;
+    __device__ __forceinline__ void add(float o)
+    {
+        const bool need = o != 0.f;
+        if (__any_sync(kFull, need)) {
+            const double t = vadd(s, (double)o);
+            if (need) s = t;
+        }
+    }
+    __device__ __forceinline__ double total() const { return s; }
+};
+
+__device__ __forceinline__ double warp_total(double v)
+{
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v = __dadd_rn(v, __shfl_xor_sync(kFull, v, off));
+    return v;
+}
+
+__device__ __forceinline__ double net_d(double v, double r, double l)
+{
+    double a = v - r;
+    a = a > 0.0 ? a : 0.0;
+    return a < l ? a : l;
+}
+
+template <typename T, int JP, int ACC, bool FIXED>
+struct Config {
+    static constexpr int VPL = VecOf<T>::n;
+    static constexpr int R = JP / VPL;         // lanes per row
+    static constexpr int RPW = 32 / R;         // rows per warp load
+    static constexpr int U = RPW >= 16 ? 4 : 8;  // rows per lane in flight
+    static constexpr int B = RPW * U;          // events per warp step
+    static_assert(JP % VPL == 0 && R >= 1 && R <= 32, "row layout");
+};
+
+template <typename T, int JP, int ACC, bool FIXED>
+__global__ void __launch_bounds__(256) k_simulate(const SimArgs a,
+                                                  const typename std::conditional<
+                                                      sizeof(T) == 4, TermsF32, TermsF64>::type terms)
+{
+    using Cfg = Config<T, JP, ACC, FIXED>;
+    using V = typename VecOf<T>::type;
+    constexpr int R = Cfg::R, RPW = Cfg::RPW, U = Cfg::U, B = Cfg::B;
+
+    const int lane = threadIdx.x & 31;
+    const int row = lane / R, col = lane % R;
+    const bool lane_on = row < RPW;
+    LaneTerms<T> lt;
+    lt.load(terms, col);
+    const bool any_share = a.any_share != 0;
+    const T *tab = static_cast<const T *>(a.table);
+
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t n_warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+
+    for (int64_t t = warp; t < a.n_trials; t += n_warps) {
+        const int64_t tt = a.trial_begin + t;
+        const int64_t beg = FIXED ? tt * (int64_t)a.k : a.off[tt];
+        const int64_t end = FIXED ? beg + a.k : a.off[tt + 1];
+
+        typename std::conditional<ACC == ARE_FP64, AccF64,
+                                  typename std::conditional<ACC == ARE_FP32_KAHAN, AccKahan,
+                                                            AccF32F64>::type>::type acc;
+
+        int32_t nid[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t e = beg + u * RPW + row;
+            nid[u] = (lane_on && e < end) ? __ldcs(a.ids + e) : -1;
+        }
+        for (int64_t s = beg; s < end; s += B) {
+            int32_t id[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) id[u] = nid[u];
+            if (s + B < end) {
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int64_t e = s + B + u * RPW + row;
+                    nid[u] = (lane_on && e < end) ? __ldcs(a.ids + e) : -1;
+                }
+            }
+            V v[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                if (id[u] >= 0)
+                    v[u] = __ldg(reinterpret_cast<const V *>(tab + (size_t)id[u] * JP) + col);
+                else
+                    v[u] = V{};
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const T g = row_sum<R>(lt.part(v[u], any_share), col);
+                const bool lead = col == 0 && id[u] >= 0;
+                if constexpr (sizeof(T) == 4) {
+                    const float o = lead ? fminf(fmaxf(__fsub_rn(g, lt.occ_r), 0.f), lt.occ_l) : 0.f;
+                    acc.add(o);
+                } else {
+                    const double o = net_nn(lead ? g : 0.0, lt.occ_r_b, lt.occ_r, lt.occ_l_b);
+                    acc.add(o);
+                }
+            }
+        }
+        const double S = warp_total(acc.total());
+        if (lane == 0) a.ylt[t] = net_d(S, a.agg_r, a.agg_l);
+    }
+}
+
+template <typename T, int JP, int ACC, bool FIXED, typename TT>
+void launch_one(const SimArgs &a, const TT &terms, int num_sms, cudaStream_t s)
+{
+    auto kern = k_simulate<T, JP, ACC, FIXED>;
+    static int per_sm = 0;
+    if (per_sm == 0) {
+        ARE_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, 0));
+        if (per_sm < 1) per_sm = 1;
+    }
+    const int64_t warps_needed = a.n_trials;
+    int64_t blocks = (warps_needed + 7) / 8;
+    const int64_t cap = (int64_t)num_sms * per_sm;
+    if (blocks > cap) blocks = cap;
+    if (blocks < 1) blocks = 1;
+    kern<<<(unsigned)blocks, 256, 0, s>>>(a, terms);
+    ARE_CUDA_TRY(cudaGetLastError());
+}
+
+template <typename T, int JP, int ACC, typename TT>
+void launch_fx(const SimArgs &a, const TT &terms, int num_sms, cudaStream_t s)
+{
+    if (a.off)
+        launch_one<T, JP, ACC, false>(a, terms, num_sms, s);
+    else
+        launch_one<T, JP, ACC, true>(a, terms, num_sms, s);
+}
+
+}  // namespace
+
+int launch_simulate(const SimArgs &a, are_precision prec, int jp, const TermsF32 *t32,
+                     const TermsF64 *t64, int num_sms, cudaStream_t s)
+{
+    if (a.n_trials <= 0) return 0;
+    if (prec == ARE_FP64) {
+        switch (jp) {
+        case 4: return launch_fx<double, 4, ARE_FP64>(a, *t64, num_sms, s), 1;
+        case 8: return launch_fx<double, 8, ARE_FP64>(a, *t64, num_sms, s), 1;
+        case 12: return launch_fx<double, 12, ARE_FP64>(a, *t64, num_sms, s), 1;
+        case 16: return launch_fx<double, 16, ARE_FP64>(a, *t64, num_sms, s), 1;
+        case 20: return launch_fx<double, 20, ARE_FP64>(a, *t64, num_sms, s), 1;
+        case 24: return launch_fx<double, 24, ARE_FP64>(a, *t64, num_sms, s), 1;
+        case 28: return launch_fx<double, 28, ARE_FP64>(a, *t64, num_sms, s), 1;
+        case 32: return launch_fx<double, 32, ARE_FP64>(a, *t64, num_sms, s), 1;
+        }
+    } else if (prec == ARE_FP32_KAHAN) {
+        switch (jp) {
+        case 8: return launch_fx<float, 8, ARE_FP32_KAHAN>(a, *t32, num_sms, s), 1;
+        case 16: return launch_fx<float, 16, ARE_FP32_KAHAN>(a, *t32, num_sms, s), 1;
+        case 24: return launch_fx<float, 24, ARE_FP32_KAHAN>(a, *t32, num_sms, s), 1;
+        case 32: return launch_fx<float, 32, ARE_FP32_KAHAN>(a, *t32, num_sms, s), 1;
+        }
+    } else if (prec == ARE_FP32_FP64AGG) {
+        switch (jp) {
+        case 8: return launch_fx<float, 8, ARE_FP32_FP64AGG>(a, *t32, num_sms, s), 1;
+        case 16: return launch_fx<float, 16, ARE_FP32_FP64AGG>(a, *t32, num_sms, s), 1;
+        case 24: return launch_fx<float, 24, ARE_FP32_FP64AGG>(a, *t32, num_sms, s), 1;
+        case 32: return launch_fx<float, 32, ARE_FP32_FP64AGG>(a, *t32, num_sms, s), 1;
+        }
+    }
+    throw Error{ARE_EINVAL, "no simulate kernel for this precision and table width"};
+}
+
+}  // namespace are

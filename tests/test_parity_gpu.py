@@ -1,0 +1,330 @@
+"""GPU path (libare through its C ABI) against the FP64 CPU oracle.
+
+Every comparison is element by element on the same seeded inputs.  FP64
+results must agree within 1e-12 and the FP32 paths within 1e-5, relative to
+the oracle's value or, for trial losses, to the trial's gross loss (see
+gpu_support.mixed_check).  Ids, counts and selected order statistics are
+exact."""
+import math
+
+import numpy as np
+import pytest
+
+import workloads as W
+from gpu_support import Loaded, RTOL, mixed_check, rel_close, tail_candidates
+
+pytestmark = pytest.mark.gpu
+INF = math.inf
+PRECISIONS = [0, 1, 2]
+
+
+@pytest.fixture(scope="module")
+def are():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    import paper_1308_2066_gb300 as are
+    are.lib()
+    return are
+
+
+@pytest.fixture(scope="module")
+def ctx(are):
+    c = are.are_create(0)
+    yield c
+    are.are_destroy(c)
+
+
+@pytest.fixture(scope="module")
+def tiny(are, ctx):
+    wl = W.plain_tiny()
+    wl.layers.append(W.Layer(elts=[0, 1, 2, 3], occ_r=5e4, occ_l=2e6, agg_r=1e5, agg_l=INF))
+    L = Loaded(are, ctx, wl)
+    yield L
+    L.release()
+
+
+@pytest.fixture(scope="module")
+def tiny_oracle(orc, tiny):
+    return [orc.simulate_layer(tiny.wl, i) for i in range(len(tiny.wl.layers))]
+
+
+# ---------------------------------------------------------------------------
+# the 10,000 x 100 workload, every trial
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+@pytest.mark.parametrize("layer", [0, 1])
+def test_tiny_workload_every_trial(tiny, tiny_oracle, precision, layer):
+    ref = tiny_oracle[layer]
+    got = tiny.simulate(layer, precision)
+    ok, st = mixed_check(got, ref.ylt, ref.gross, RTOL[precision])
+    assert ok, st
+    assert np.all(got >= 0) and np.all(got <= tiny.wl.layers[layer].agg_l)
+    at_cap = ref.ylt == tiny.wl.layers[layer].agg_l
+    np.testing.assert_array_equal(got[at_cap], ref.ylt[at_cap])
+    capped = float(np.mean(at_cap))
+    if layer == 0:
+        assert capped > 0.3      # the recipe's aggregate limit binds often
+    else:
+        assert capped == 0.0
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_tiny_workload_risk_measures(are, ctx, orc, tiny, tiny_oracle, precision):
+    rps, lv = [100.0, 250.0, 10.0, 2.0], [0.99, 0.9, 0.5]
+    for layer in (0, 1):
+        got_ylt = tiny.simulate(layer, precision)
+        pml, tv = are.are_risk_measures(ctx, got_ylt, None, rps, lv)
+        rpml, rtv = orc.risk_measures(tiny_oracle[layer].ylt, rps, lv)
+        assert rel_close(pml, rpml, RTOL[precision]), (pml, rpml)
+        assert rel_close(tv, rtv, RTOL[precision]), (tv, rtv)
+        if layer == 1:
+            assert len(set(pml)) == len(pml)   # the uncapped variant is not degenerate
+
+
+# ---------------------------------------------------------------------------
+# PML / TVaR selection on given YLTs
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n", [1, 2, 3, 100, 4097, 100_000, 1_000_003])
+def test_risk_measures_on_oracle_ylt(are, ctx, orc, n):
+    import torch
+    g = np.random.default_rng(n)
+    y = np.round(g.lognormal(13, 2.5, n), 2)
+    y[g.random(n) < 0.2] = 0.0
+    y[g.random(n) < 0.05] = 1e7
+    rps = [1.0, 1.5, 2.0, 10.0, 100.0, 250.0, 500.0, 1000.0, 10000.0]
+    lv = [0.5, 0.9, 0.99, 0.995, 0.999]
+    rpml, rtv = orc.risk_measures(y, rps, lv)
+    for src in (y, torch.from_numpy(y).cuda()):
+        pml, tv = are.are_risk_measures(ctx, src, n, rps, lv)
+        np.testing.assert_array_equal(pml, rpml)
+        assert rel_close(tv, rtv, 1e-13), (tv, rtv)
+
+
+def test_risk_measures_negative_and_tied_values(are, ctx, orc):
+    y = np.array([-5.0, 3.0, 3.0, 3.0, -0.0, 0.0, 2.5, -1e300, 1e300, 7.0])
+    rps, lv = [1.0, 2.0, 3.0, 10.0], [0.5, 0.7, 0.95]
+    rpml, rtv = orc.risk_measures(y, rps, lv)
+    pml, tv = are.are_risk_measures(ctx, y, None, rps, lv)
+    np.testing.assert_array_equal(pml, rpml)
+    assert rel_close(tv, rtv, 1e-13)
+
+
+def test_risk_measure_arguments_rejected(are, ctx):
+    y = np.ones(10)
+    for rps, lv in (([0.5], []), ([], [1.0]), ([], [0.0]), ([float("nan")], [])):
+        with pytest.raises(are.AreError) as e:
+            are.are_risk_measures(ctx, y, None, rps, lv)
+        assert e.value.status == are.ARE_EINVAL
+    with pytest.raises(are.AreError):
+        are.are_risk_measures(ctx, y, 0, [2.0], [])
+
+
+# ---------------------------------------------------------------------------
+# ragged YETs, every table width, financial-term variety
+# ---------------------------------------------------------------------------
+
+def ragged_workload(seed, J, n_trials=3000, mean=60, catalog=5000, nnz=300):
+    g = np.random.Generator(np.random.PCG64(1000 + seed))
+    yet = W.yet_poisson(g, n_trials, mean, catalog)
+    elts = []
+    for j in range(J):
+        e = W.percentile_terms(W.elt_lognormal(g, catalog, nnz), int(g.integers(0, 300)),
+                               int(g.integers(900, 1001)))
+        e.fx = float(g.choice([1.0, 1.0, 0.83, 1.27]))
+        e.share = float(g.choice([1.0, 1.0, 0.5, 0.35]))
+        if j % 5 == 4:
+            e.lim = INF
+        elts.append(e)
+    pooled = np.concatenate([e.losses for e in elts])
+    occ_r = W.nearest_rank(pooled, 300)
+    layer = W.Layer(list(range(J)), occ_r, W.nearest_rank(pooled, 995) * 3,
+                    occ_r * 4, [INF, occ_r * 40][seed % 2])
+    return W.Workload(f"ragged_j{J}", yet, elts, [layer])
+
+
+@pytest.mark.parametrize("J", [1, 3, 4, 5, 8, 9, 12, 16, 17, 20, 24, 25, 31, 32])
+def test_ragged_every_table_width(are, ctx, orc, J):
+    wl = ragged_workload(J, J)
+    L = Loaded(are, ctx, wl, device_inputs=bool(J % 2))
+    try:
+        ref = orc.simulate_layer(wl)
+        for p in PRECISIONS:
+            got = L.simulate(0, p)
+            ok, st = mixed_check(got, ref.ylt, ref.gross, RTOL[p])
+            assert ok, (p, st)
+            assert np.all(got[ref.n_events == 0] == 0)
+    finally:
+        L.release()
+
+
+def test_empty_trials_and_short_tails(are, ctx, orc):
+    g = np.random.Generator(np.random.PCG64(77))
+    yet = W.yet_poisson(g, 4000, 3, 300)         # many empty and 1-2 event trials
+    elts = [W.percentile_terms(W.elt_lognormal(g, 300, 100)) for _ in range(6)]
+    wl = W.Workload("short", yet, elts, [W.Layer(list(range(6)), 1e4, 5e5, 2e4, 1e6)])
+    L = Loaded(are, ctx, wl)
+    try:
+        ref = orc.simulate_layer(wl)
+        assert np.sum(ref.n_events == 0) > 100
+        for p in PRECISIONS:
+            ok, st = mixed_check(L.simulate(0, p), ref.ylt, ref.gross, RTOL[p])
+            assert ok, (p, st)
+    finally:
+        L.release()
+
+
+def test_trial_ranges_and_host_buffers(are, ctx, tiny):
+    for p in PRECISIONS:
+        whole = tiny.simulate(0, p)
+        parts = [tiny.simulate(0, p, a, b - a) for a, b in ((0, 1), (1, 4093), (4093, 10_000))]
+        np.testing.assert_array_equal(np.concatenate(parts), whole)
+        np.testing.assert_array_equal(tiny.simulate(0, p, 17, 5000, device=False), whole[17:5017])
+
+
+def test_single_trial_single_event(are, ctx, orc, golden):
+    """The hand-worked cases of tests/golden through the GPU, every precision."""
+    spec = golden["layers"]["two_elts"]
+    cases = [c for c in golden["trials"] if c["layer"] == "two_elts"]
+    counts = [len(c["events"]) for c in cases]
+    off = np.zeros(len(cases) + 1, np.int64)
+    off[1:] = np.cumsum(counts)
+    ids = np.array([e for c in cases for e in c["events"]], np.int32)
+    yet = W.YET(12, len(cases), ids, offsets=off)
+    elts = [W.ELT(np.array(e["ids"], np.int32), np.array(e["losses"]), e["ded"],
+                  INF if e["lim"] == "inf" else e["lim"], e["fx"], e["share"]) for e in spec["elts"]]
+    wl = W.Workload("hand", yet, elts, [W.Layer([0, 1], spec["occ_r"], spec["occ_l"],
+                                                 spec["agg_r"], spec["agg_l"])])
+    L = Loaded(are, ctx, wl, timestamps=False)
+    try:
+        for p in PRECISIONS:
+            np.testing.assert_array_equal(L.simulate(0, p), [c["ylt"] for c in cases])
+    finally:
+        L.release()
+
+
+# ---------------------------------------------------------------------------
+# input validation through the boundary
+# ---------------------------------------------------------------------------
+
+def test_invalid_inputs_rejected(are, ctx):
+    E = are.AreError
+    ids = np.array([0, 1, 2, 3], np.int32)
+    with pytest.raises(E) as e:
+        are.are_load_yet(ctx, 3, 2, None, 2, ids)          # id 3 outside catalog of 3
+    assert e.value.status == are.ARE_EINVAL
+    with pytest.raises(E):
+        are.are_load_yet(ctx, 4, 2, np.array([0, 3, 2], np.int64), 0, ids[:2])
+    with pytest.raises(E):
+        are.are_load_yet(ctx, 4, 2, np.array([0, 2, 4], np.int64), 0, ids,
+                         np.array([0.1, 0.2, 0.9, 0.3], np.float32))
+    with pytest.raises(E):
+        are.are_load_yet(ctx, 4, 1, None, 0, ids)
+    with pytest.raises(E):
+        are.are_load_elt(ctx, np.array([1, 1], np.int32), np.array([1.0, 2.0]))
+    with pytest.raises(E):
+        are.are_load_elt(ctx, np.array([1], np.int32), np.array([-1.0]))
+    with pytest.raises(E):
+        are.are_load_elt(ctx, np.array([1], np.int32), np.array([1.0]), share=1.5)
+    with pytest.raises(E):
+        are.are_load_elt(ctx, np.array([1], np.int32), np.array([1.0]), deductible=INF)
+    h = are.are_load_elt(ctx, np.array([1, 7], np.int32), np.array([1.0, 2.0]))
+    with pytest.raises(E):
+        are.are_define_layer(ctx, [h, h])
+    with pytest.raises(E):
+        are.are_define_layer(ctx, [h], occ_ret=-1.0)
+    with pytest.raises(E):
+        are.are_define_layer(ctx, [h] * 0)
+    with pytest.raises(E) as e:
+        are.are_define_layer(ctx, [h, 99999])
+    assert e.value.status == are.ARE_ENOTFOUND
+    lay = are.are_define_layer(ctx, [h])
+    y = are.are_load_yet(ctx, 5, 2, None, 2, ids)
+    with pytest.raises(E):          # ELT id 7 outside the YET's 5-event catalog
+        are.are_simulate(ctx, lay, y, 0, 2, 0, np.zeros(2))
+    with pytest.raises(E):
+        are.are_simulate(ctx, lay, y, 1, 2, 0, np.zeros(2))
+    with pytest.raises(E):
+        are.are_simulate(ctx, lay, y, 0, 2, 7, np.zeros(2))
+    with pytest.raises(E):
+        are.are_free_elt(ctx, h)    # still used by the layer
+    are.are_free_layer(ctx, lay)
+    are.are_free_elt(ctx, h)
+    are.are_free_yet(ctx, y)
+    with pytest.raises(E) as e:
+        are.are_free_yet(ctx, y)
+    assert e.value.status == are.ARE_ENOTFOUND
+
+
+def test_memory_budget(are):
+    c = are.are_create(0, 1 << 20)
+    try:
+        before = are.are_memory_used(c)
+        with pytest.raises(are.AreError) as e:
+            are.are_load_yet(c, 10, 1000, None, 1000, np.zeros(10**6, np.int32))
+        assert e.value.status == are.ARE_ENOMEM
+        assert are.are_memory_used(c) == before
+        y = are.are_load_yet(c, 10, 10, None, 10, np.zeros(100, np.int32))
+        assert are.are_memory_used(c) > before
+        are.are_free_yet(c, y)
+        assert are.are_memory_used(c) == before
+    finally:
+        are.are_destroy(c)
+
+
+# ---------------------------------------------------------------------------
+# full-size workloads, in the launch configuration the benchmark times:
+# sampled trials one by one, and PML/TVaR through their tail trials
+# ---------------------------------------------------------------------------
+
+def check_full_size(are, ctx, orc, wl, precisions, n_sample=1500, seed=0):
+    rps, lv = [100.0, 250.0], [0.99]
+    n = wl.yet.n_trials
+    m_max = max(orc.rank_for_return_period(n, r) for r in rps)
+    m_max = max(m_max, max(orc.rank_for_level(n, a) for a in lv))
+    sample = np.sort(np.random.default_rng(seed).choice(n, n_sample, replace=False))
+    L = Loaded(are, ctx, wl, timestamps=False)
+    report = {}
+    try:
+        for p in precisions:
+            got = L.simulate(0, p)
+            assert np.all(np.isfinite(got)) and np.all(got >= 0)
+            ref = orc.simulate_layer(wl, trials=sample)
+            ok, st = mixed_check(got[sample], ref.ylt, ref.gross, RTOL[p])
+            assert ok, (p, st)
+            np.testing.assert_array_equal(ref.n_events, wl.yet.counts()[sample])
+            # tail: the m_max + margin largest GPU losses hold every trial the
+            # oracle can rank in its top m_max, unless an error exceeds the gap
+            cand = tail_candidates(got, m_max, margin=m_max // 5 + 100)
+            rc = orc.simulate_layer(wl, trials=cand)
+            err = np.abs(got[cand] - rc.ylt)
+            gap = np.sort(rc.ylt)[::-1][m_max - 1] - got[cand[-1]]
+            assert err.max() < gap, (p, err.max(), gap)
+            full = np.zeros(n)
+            full[cand] = rc.ylt
+            rpml, rtv = orc.risk_measures(full, rps, lv)
+            pml, tv = are.are_risk_measures(ctx, got, None, rps, lv)
+            assert rel_close(pml, rpml, RTOL[p]), (p, pml, rpml)
+            assert rel_close(tv, rtv, RTOL[p]), (p, tv, rtv)
+            report[p] = {"ylt": st, "pml": list(pml), "pml_ref": list(rpml), "tvar": list(tv),
+                         "tvar_ref": list(rtv)}
+    finally:
+        L.release()
+    return report
+
+
+def test_paper_scale_full_size(are, ctx, orc):
+    """1,000,000 trials x 1000 events, 16 ELTs: every precision."""
+    wl = W.paper_scale()
+    rep = check_full_size(are, ctx, orc, wl, PRECISIONS)
+    print("paper_scale", rep)
+
+
+def test_precision_stress_full_size(are, ctx, orc):
+    """1,000,000 ragged trials (Poisson 1000, <= 3000), 2,000,000-event
+    catalog, 32 Pareto ELTs, neutral terms: whole-trial sums reach the YLT."""
+    wl = W.precision_stress()
+    assert wl.yet.counts().max() <= 3000
+    rep = check_full_size(are, ctx, orc, wl, PRECISIONS, n_sample=1000, seed=3)
+    print("precision_stress", rep)

@@ -5,7 +5,7 @@ published (Section III-C says the parameter ranges come from discussions with
 practitioners).  This module builds stand-ins with the shapes the paper gives:
 trials of 800-1500 events (Section II-A, item 1), ELTs of 10,000-30,000 nonzero
 losses (item 2), layers of 3-30 ELTs (item 3), and the 1M-trial x 1000-event,
-one-layer workload of the experiments (Section III-D).
+one-layer workload of the experiments (Section III-C).
 
 It holds no arithmetic of the method: it draws event ids, loss values and term
 values, and nothing else.  Both the GPU library's tests and the CPU oracle take
@@ -203,12 +203,14 @@ def plain_tiny(n_trials: int = 10_000, k: int = 100, catalog: int = 10_000,
 
 
 def paper_scale(n_trials: int = 1_000_000, k: int = 1000, catalog: int = 1_000_000,
-                n_elts: int = 16, nnz: int = 20_000, timestamps: bool = False) -> Workload:
+                n_elts: int = 16, nnz: int = 20_000, timestamps: bool = False,
+                shard: int = 0) -> Workload:
     """1,000,000 trials x 1000 events over a 1,000,000-event catalog; one layer
     of 16 lognormal ELTs of 20,000 entries; per-ELT terms at p10/p99; layer
     terms ten times those of the tiny workload.  Timestamps are off by default
-    at this size: the method reads only the stored order."""
-    g = rng(1)
+    at this size: the method reads only the stored order.  ``shard`` > 0 draws
+    another block of trials of the same recipe (the ELTs stay the same)."""
+    g = rng(1) if shard == 0 else rng(1, 1000 + shard)
     yet = yet_fixed(g, n_trials, k, catalog, timestamps=timestamps)
     elts = [percentile_terms(elt_lognormal(rng(1, 1 + j), catalog, nnz)) for j in range(n_elts)]
     layer = Layer(elts=list(range(n_elts)), occ_r=5e5, occ_l=2e7, agg_r=1e6, agg_l=1e8)
