@@ -115,7 +115,8 @@ ARE_API are_status are_create(are_ctx **out, int device, size_t mem_budget_bytes
 ARE_API are_status are_destroy(are_ctx *ctx);
 
 /* Message of the last failed call made by the calling thread on `ctx`
- * ("" if none).  The string stays valid until that thread's next call. */
+ * ("" if none); with ctx NULL, of its last failed are_risk_measures_static
+ * call.  The string stays valid until that thread's next call. */
 ARE_API const char *are_last_error(const are_ctx *ctx);
 
 /* Device memory the context holds now, in bytes (budget accounting). */
@@ -209,6 +210,41 @@ ARE_API are_status are_risk_measures(are_ctx *ctx, const double *ylt, int64_t n,
                              const double *return_periods, int32_t n_rp, double *pml_out,
                              const double *tvar_levels, int32_t n_tv, double *tvar_out,
                              void *stream);
+
+/* ------------------------------------------------------------------------ */
+/* Allocation-free PML/TVaR                                                  */
+/* ------------------------------------------------------------------------ */
+
+/* Size of the device scratch array behind are_risk_measures_static. */
+#define ARE_STATIC_SCRATCH_BYTES (256u * 1024u)
+
+/* PML and TVaR of a device-resident YLT without a context and without any
+ * allocation.  The paper has no counterpart: this exists for callers that
+ * cannot allocate device memory -- code running under another framework's
+ * memory pool or a fixed memory reservation (a real-time pricing service
+ * that sizes everything up front), or code that must not create a context.
+ *
+ * Same definitions and results as are_risk_measures, with these limits:
+ *   - ylt must be device memory of the current CUDA device (host memory is
+ *     ARE_EINVAL: copying it in would need a device buffer);
+ *   - n_rp + n_tv <= 8 (more is ARE_EINVAL); n < 2^32 - 1;
+ *   - pml_out and tvar_out are host arrays; the call synchronises `stream`
+ *     (NULL = the legacy default stream) before returning.
+ * The kernels' scratch (histograms, selection state, per-block partial sums,
+ * results) is one file-scope device array of ARE_STATIC_SCRATCH_BYTES
+ * (256 KiB) that every GPU loading the library holds until the process
+ * exits.  The first call on a device looks up that array's device address
+ * (cudaGetSymbolAddress, with the device current) and caches it: make that
+ * first call before any stream capture.  Every call shares the one array and
+ * reinitialises what must start at zero; calls whose work overlaps on the
+ * GPU (other streams or other threads on the same device) race on it and
+ * must be serialised by the caller.  Nothing is allocated: no cudaMalloc,
+ * no cudaFree, no allocating library routine.  On failure, are_last_error(NULL)
+ * returns the calling thread's message. */
+ARE_API are_status are_risk_measures_static(const double *ylt, int64_t n,
+                                            const double *return_periods, int32_t n_rp,
+                                            double *pml_out, const double *tvar_levels,
+                                            int32_t n_tv, double *tvar_out, void *stream);
 
 #ifdef __cplusplus
 }

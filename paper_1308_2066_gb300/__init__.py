@@ -67,6 +67,8 @@ _SIGS = {
                                  _P]),
     "are_risk_measures": (C.c_int32, [_P, _P, C.c_int64, _P, C.c_int32, _P, _P, C.c_int32, _P,
                                       _P]),
+    "are_risk_measures_static": (C.c_int32, [_P, C.c_int64, _P, C.c_int32, _P, _P, C.c_int32,
+                                             _P, _P]),
 }
 
 
@@ -88,7 +90,7 @@ def lib():
 
 def _check(ctx, status: int):
     if status != ARE_OK:
-        msg = lib().are_last_error(ctx) if ctx else b""
+        msg = lib().are_last_error(ctx)
         raise AreError(status, (msg or b"").decode(errors="replace"))
 
 
@@ -229,4 +231,19 @@ def are_risk_measures(ctx, ylt, n: Optional[int] = None,
     _check(ctx, lib().are_risk_measures(ctx, _addr(ylt, np.float64), n, rp.ctypes.data,
                                         rp.shape[0], pml.ctypes.data, lv.ctypes.data, lv.shape[0],
                                         tv.ctypes.data, _stream(stream)))
+    return pml, tv
+
+
+def are_risk_measures_static(ylt, n: Optional[int] = None,
+                             return_periods: Sequence[float] = (100.0, 250.0),
+                             tvar_levels: Sequence[float] = (0.99,), stream=None):
+    """Context-free, allocation-free PML/TVaR of a device YLT (see are.h)."""
+    n = _len(ylt) if n is None else int(n)
+    rp = np.ascontiguousarray(return_periods, dtype=np.float64)
+    lv = np.ascontiguousarray(tvar_levels, dtype=np.float64)
+    pml = np.empty(rp.shape[0], np.float64)
+    tv = np.empty(lv.shape[0], np.float64)
+    _check(None, lib().are_risk_measures_static(_addr(ylt, np.float64), n, rp.ctypes.data,
+                                                rp.shape[0], pml.ctypes.data, lv.ctypes.data,
+                                                lv.shape[0], tv.ctypes.data, _stream(stream)))
     return pml, tv

@@ -218,23 +218,37 @@ void fill_terms(are_ctx *ctx, const Layer &L, TermsF32 &t32, TermsF64 &t64, int 
     t32.occ_l = (float)L.terms.occ_lim;
 }
 
-// Integer ranks of the risk measures (the definitions in include/are.h).
 int64_t rank_rp(int64_t n, double rp)
 {
-    ARE_CHECK(std::isfinite(rp), ARE_EINVAL, "return period must be finite");
-    const long long micro = std::llround(rp * 1e6);
-    ARE_CHECK(micro >= 1000000, ARE_EINVAL, "return period must be >= 1");
-    return (n * 1000000 + micro - 1) / micro;
+    const int64_t m = rank_for_return_period(n, rp);
+    ARE_CHECK(m >= 1, ARE_EINVAL, "return period must be finite and >= 1");
+    return m;
 }
 int64_t rank_level(int64_t n, double a)
 {
-    ARE_CHECK(std::isfinite(a), ARE_EINVAL, "TVaR level must be finite");
-    const long long nano = std::llround(a * 1e9);
-    ARE_CHECK(nano > 0 && nano < 1000000000, ARE_EINVAL, "TVaR level must lie in (0, 1)");
-    return (n * (1000000000 - nano) + 999999999) / 1000000000;
+    const int64_t m = rank_for_level(n, a);
+    ARE_CHECK(m >= 1, ARE_EINVAL, "TVaR level must be finite and lie in (0, 1)");
+    return m;
 }
 
 }  // namespace
+
+// Integer ranks of the risk measures (the definitions in include/are.h).
+int64_t rank_for_return_period(int64_t n, double rp)
+{
+    if (!std::isfinite(rp) || rp > 1e12) return -1;
+    const long long micro = std::llround(rp * 1e6);
+    if (micro < 1000000) return -1;
+    return (n * 1000000 + micro - 1) / micro;
+}
+int64_t rank_for_level(int64_t n, double a)
+{
+    if (!std::isfinite(a)) return -1;
+    const long long nano = std::llround(a * 1e9);
+    if (nano <= 0 || nano >= 1000000000) return -1;
+    return (n * (1000000000 - nano) + 999999999) / 1000000000;
+}
+
 }  // namespace are
 
 using namespace are;
@@ -302,6 +316,7 @@ are_status are_destroy(are_ctx *ctx)
 
 const char *are_last_error(const are_ctx *ctx)
 {
+    if (!ctx) return static_last_error();
     auto it = t_errors.find(ctx);
     return it == t_errors.end() ? "" : it->second.c_str();
 }

@@ -145,9 +145,19 @@ struct SelectScratch {
     int max_blocks = 0;
 };
 void select_alloc(SelectScratch &s, int num_sms);
+// Ranks of the risk measures (definitions in include/are.h); -1 when the
+// return period or level is out of range.
+int64_t rank_for_return_period(int64_t n, double rp);
+int64_t rank_for_level(int64_t n, double a);
+// Message of the calling thread's last failed are_risk_measures_static call.
+const char *static_last_error();
 void select_free(SelectScratch &s);
+constexpr int kSelectLaunches = 2 + 2 * 8 + 2;
+inline int select_max_blocks(int num_sms) { return num_sms * 4; }
 // ranks[t] (1-based, descending order) for n_targets <= kMaxTargets; writes
 // result[2*t] = m-th largest value, result[2*t+1] = mean of the m largest.
+cudaError_t select_enqueue(const double *ylt, int64_t n, const int64_t *ranks, int nt,
+                           const SelectScratch &s, cudaStream_t st);
 int launch_select(const double *ylt, int64_t n, const int64_t *ranks, int n_targets,
                    SelectScratch &s, int num_sms, cudaStream_t st);
 

@@ -12,6 +12,9 @@
 // in device memory, so the host waits only for the final values.
 #include <cuda_runtime.h>
 
+#include <cstdio>
+#include <mutex>
+
 #include "are_internal.cuh"
 
 namespace are {
@@ -237,7 +240,7 @@ __global__ void k_final(const unsigned long long *state, const double *partial, 
 
 void select_alloc(SelectScratch &s, int num_sms)
 {
-    s.max_blocks = num_sms * 4;
+    s.max_blocks = select_max_blocks(num_sms);
     ARE_CUDA_TRY(cudaMalloc(&s.hist, sizeof(uint32_t) * kMaxTargets * kBins));
     ARE_CUDA_TRY(cudaMalloc(&s.state, sizeof(unsigned long long) * 2 * kMaxTargets));
     ARE_CUDA_TRY(cudaMalloc(&s.partial, sizeof(double) * 3 * kMaxTargets * s.max_blocks));
@@ -253,15 +256,15 @@ void select_free(SelectScratch &s)
     s = SelectScratch{};
 }
 
-int launch_select(const double *ylt, int64_t n, const int64_t *ranks, int nt, SelectScratch &s,
-                   int num_sms, cudaStream_t st)
+// Enqueues the selection kernels; reports launch errors instead of throwing.
+cudaError_t select_enqueue(const double *ylt, int64_t n, const int64_t *ranks, int nt,
+                           const SelectScratch &s, cudaStream_t st)
 {
     Ranks r{};
     for (int t = 0; t < nt; ++t) r.m[t] = ranks[t];
     int64_t blocks = (n + kThreads * 8 - 1) / (kThreads * 8);
     if (blocks > s.max_blocks) blocks = s.max_blocks;
     if (blocks < 1) blocks = 1;
-    (void)num_sms;
     k_init<<<1, kThreads, 0, st>>>(s.state, s.hist, r, nt);
     for (int pass = 0; pass < 8; ++pass) {
         k_hist<<<(unsigned)blocks, kThreads, 0, st>>>(ylt, n, s.state, nt, pass, s.hist);
@@ -269,8 +272,138 @@ int launch_select(const double *ylt, int64_t n, const int64_t *ranks, int nt, Se
     }
     k_tail<<<(unsigned)blocks, kThreads, 0, st>>>(ylt, n, s.state, nt, s.partial);
     k_final<<<1, 32 * kMaxTargets, 0, st>>>(s.state, s.partial, (int)blocks, r, nt, s.result);
-    ARE_CUDA_TRY(cudaGetLastError());
-    return 2 + 2 * 8 + 2;
+    return cudaGetLastError();
+}
+
+int launch_select(const double *ylt, int64_t n, const int64_t *ranks, int nt, SelectScratch &s,
+                  int num_sms, cudaStream_t st)
+{
+    (void)num_sms;
+    ARE_CUDA_TRY(select_enqueue(ylt, n, ranks, nt, s, st));
+    return kSelectLaunches;
 }
 
 }  // namespace are
+
+// ---------------------------------------------------------------------------
+// Allocation-free PML/TVaR: the same kernels, with their scratch in a
+// fixed-size array that lives in the library's device image.
+// ---------------------------------------------------------------------------
+
+namespace {
+
+constexpr size_t kStaticHist = 0;                                    // 8 x 256 words
+constexpr size_t kStaticState = kStaticHist + sizeof(uint32_t) * are::kMaxTargets * 256;
+constexpr size_t kStaticResult = kStaticState + 256;                 // 2 x 8 words
+constexpr size_t kStaticPartial = kStaticResult + 256;               // blocks x 8 x 3 doubles
+constexpr int kStaticMaxBlocks = 1024;
+static_assert(kStaticPartial + sizeof(double) * 3 * are::kMaxTargets * kStaticMaxBlocks <=
+                  ARE_STATIC_SCRATCH_BYTES,
+              "static scratch too small for its block limit");
+
+// Every GPU that loads the library holds this array until the process exits.
+static __device__ __align__(256) unsigned char g_static_scratch[ARE_STATIC_SCRATCH_BYTES];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mu;
+void *g_static_addr[kMaxDevices];   // device address of g_static_scratch, per device
+int g_static_sms[kMaxDevices];
+thread_local char t_static_error[192];
+
+are_status static_fail(are_status code, const char *msg)
+{
+    std::snprintf(t_static_error, sizeof t_static_error, "%s", msg);
+    return code;
+}
+
+}  // namespace
+
+namespace are {
+const char *static_last_error() { return t_static_error; }
+}
+
+extern "C" are_status are_risk_measures_static(const double *ylt, int64_t n,
+                                               const double *return_periods, int32_t n_rp,
+                                               double *pml_out, const double *tvar_levels,
+                                               int32_t n_tv, double *tvar_out, void *stream)
+{
+    using namespace are;
+    t_static_error[0] = '\0';
+    if (!ylt || n <= 0) return static_fail(ARE_EINVAL, "need a device YLT of n > 0 losses");
+    if (n >= (int64_t)UINT32_MAX)
+        return static_fail(ARE_EINVAL, "YLT too long for the selection counters");
+    if (n_rp < 0 || n_tv < 0 || (n_rp > 0 && (!return_periods || !pml_out)) ||
+        (n_tv > 0 && (!tvar_levels || !tvar_out)))
+        return static_fail(ARE_EINVAL, "bad PML or TVaR arrays");
+    if (n_rp + n_tv > kMaxTargets)
+        return static_fail(ARE_EINVAL,
+                           "at most 8 return periods and TVaR levels together per call");
+    if (n_rp + n_tv == 0) return ARE_OK;
+    int64_t ranks[kMaxTargets];
+    for (int32_t r = 0; r < n_rp; ++r)
+        if ((ranks[r] = rank_for_return_period(n, return_periods[r])) < 1)
+            return static_fail(ARE_EINVAL, "return period must be finite and >= 1");
+    for (int32_t r = 0; r < n_tv; ++r)
+        if ((ranks[n_rp + r] = rank_for_level(n, tvar_levels[r])) < 1)
+            return static_fail(ARE_EINVAL, "TVaR level must lie in (0, 1)");
+
+    int dev = 0;
+    cudaPointerAttributes attr;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+        cudaGetLastError();
+        return static_fail(ARE_ECUDA, "no usable current CUDA device");
+    }
+    if (cudaPointerGetAttributes(&attr, ylt) != cudaSuccess) {
+        cudaGetLastError();
+        return static_fail(ARE_EINVAL, "ylt is not a CUDA pointer");
+    }
+    if (attr.type != cudaMemoryTypeDevice && attr.type != cudaMemoryTypeManaged)
+        return static_fail(ARE_EINVAL, "ylt must be device memory of the current device");
+    if (attr.type == cudaMemoryTypeDevice && attr.device != dev)
+        return static_fail(ARE_EINVAL, "ylt must be device memory of the current device");
+
+    // Set-up, once per device with that device current: the device address
+    // of the scratch array (its name is only a host-side stand-in).
+    {
+        std::lock_guard<std::mutex> lock(g_static_mu);
+        if (!g_static_addr[dev]) {
+            void *p = nullptr;
+            if (cudaGetSymbolAddress(&p, g_static_scratch) != cudaSuccess || !p) {
+                cudaGetLastError();
+                return static_fail(ARE_ECUDA, "cudaGetSymbolAddress of the static scratch failed");
+            }
+            int sms = 0;
+            if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+                cudaGetLastError();
+                return static_fail(ARE_ECUDA, "cannot query the SM count");
+            }
+            g_static_sms[dev] = sms;
+            g_static_addr[dev] = p;
+        }
+    }
+    unsigned char *base = static_cast<unsigned char *>(g_static_addr[dev]);
+    SelectScratch sc;
+    sc.hist = reinterpret_cast<uint32_t *>(base + kStaticHist);
+    sc.state = reinterpret_cast<unsigned long long *>(base + kStaticState);
+    sc.result = reinterpret_cast<double *>(base + kStaticResult);
+    sc.partial = reinterpret_cast<double *>(base + kStaticPartial);
+    sc.max_blocks = select_max_blocks(g_static_sms[dev]);
+    if (sc.max_blocks > kStaticMaxBlocks) sc.max_blocks = kStaticMaxBlocks;
+
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int nt = n_rp + n_tv;
+    double res[2 * kMaxTargets];
+    cudaError_t e = select_enqueue(ylt, n, ranks, nt, sc, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(res, sc.result, sizeof(double) * 2 * nt, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        std::snprintf(t_static_error, sizeof t_static_error, "CUDA error: %s",
+                      cudaGetErrorString(e));
+        return ARE_ECUDA;
+    }
+    for (int32_t r = 0; r < n_rp; ++r) pml_out[r] = res[2 * r];
+    for (int32_t r = 0; r < n_tv; ++r) tvar_out[r] = res[2 * (n_rp + r) + 1];
+    return ARE_OK;
+}
