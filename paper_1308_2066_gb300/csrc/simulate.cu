@@ -23,6 +23,7 @@
 // the FP64 pipe for the few occurrences that carry a loss.
 #include <cuda_runtime.h>
 
+#include <cstdlib>
 #include <type_traits>
 
 #include "are_internal.cuh"
@@ -328,6 +329,225 @@ __global__ void __launch_bounds__(256) k_simulate(const SimArgs a,
     }
 }
 
+// ---------------------------------------------------------------------------
+// FP32 paths, staged: one event per lane.
+//
+// A warp takes its trials in batches of up to 32 events (a batch never spans
+// two trials).  The 32 table rows of a batch are copied global -> shared with
+// cp.async in a coalesced pattern (the lanes of one copy instruction cover
+// 32/CH whole rows, so each row costs one L1 wavefront), then every lane
+// reads its own event's row from shared memory and does all of the event's
+// arithmetic: financial terms per ELT, the sum over ELTs in layer order, the
+// occurrence terms and the compensated running sum.  Row chunks are rotated
+// per row so the lanes' 16-byte shared reads hit distinct banks.  Event ids
+// are loaded three batches ahead and rows one batch ahead (double buffer).
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, int src_bytes)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src),
+                 "r"(src_bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+__device__ __forceinline__ void cp_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// Physical slot of 16-byte chunk c of row r (CH chunks per row): a rotation
+// that gives the 8 lanes of each shared-memory phase 8 distinct bank groups.
+template <int CH>
+__device__ __forceinline__ int chunk_slot(int c, int r)
+{
+    const int rot = CH == 2 ? (r >> 2) & 1 : CH == 4 ? (r >> 1) & 3 : CH == 6 ? (r >> 2) & 1 : r & 7;
+    const int p = c + rot;
+    return p >= CH ? p - CH : p;
+}
+
+struct Batch {
+    int64_t t = -1;    // trial (index into the launch's range)
+    int64_t pos = 0;   // first event
+    int cnt = 0;       // events in the batch, 0 = no more work
+    bool last = false; // last batch of its trial
+};
+struct Cursor {
+    int64_t t, pos, end;
+};
+
+template <bool FIXED>
+__device__ __forceinline__ void trial_bounds(const SimArgs &a, int64_t t, int64_t &b, int64_t &e)
+{
+    const int64_t tt = a.trial_begin + t;
+    if (FIXED) {
+        b = tt * (int64_t)a.k;
+        e = b + a.k;
+    } else {
+        b = a.off[tt];
+        e = a.off[tt + 1];
+    }
+}
+
+// The warp's next batch; trials without events get their loss written here.
+template <bool FIXED>
+__device__ __forceinline__ Batch next_batch(const SimArgs &a, Cursor &c, int64_t step, int lane,
+                                            double empty_loss)
+{
+    Batch b;
+    while (c.t < a.n_trials) {
+        if (c.pos < c.end) {
+            b.t = c.t;
+            b.pos = c.pos;
+            const int64_t left = c.end - c.pos;
+            b.cnt = left < 32 ? (int)left : 32;
+            c.pos += 32;
+            if (c.pos >= c.end) {
+                b.last = true;
+                c.t += step;
+                if (c.t < a.n_trials) trial_bounds<FIXED>(a, c.t, c.pos, c.end);
+            }
+            return b;
+        }
+        if (lane == 0) a.ylt[c.t] = empty_loss;
+        c.t += step;
+        if (c.t < a.n_trials) trial_bounds<FIXED>(a, c.t, c.pos, c.end);
+    }
+    return b;
+}
+
+constexpr int kStagedWarps = 8;
+
+template <int JP>
+constexpr int staged_smem_bytes()
+{
+    return kStagedWarps * 2 * 32 * JP * 4;
+}
+
+template <int JP, int ACC, bool FIXED>
+__global__ void __launch_bounds__(kStagedWarps * 32) k_simulate_staged(const SimArgs a, const TermsF32 tm)
+{
+    constexpr int CH = JP / 4;
+    extern __shared__ float4 stage[];
+    const int lane = threadIdx.x & 31;
+    float4 *buf0 = stage + (size_t)(threadIdx.x >> 5) * 2 * 32 * CH;
+    float4 *buf1 = buf0 + 32 * CH;
+    const float *tab = static_cast<const float *>(a.table);
+    const bool any_share = a.any_share != 0;
+
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t step = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const double empty_loss = net_d(0.0, a.agg_r, a.agg_l);
+    Cursor cur{warp, 0, 0};
+    if (cur.t < a.n_trials) trial_bounds<FIXED>(a, cur.t, cur.pos, cur.end);
+
+    auto load_ids = [&](const Batch &b) -> int32_t {
+        return lane < b.cnt ? __ldcs(a.ids + b.pos + lane) : 0;
+    };
+    auto issue_rows = [&](const Batch &b, int32_t idv, float4 *buf) {
+#pragma unroll
+        for (int i = 0; i < CH; ++i) {
+            const int q = lane + 32 * i, r = q / CH, c = q % CH;
+            const int32_t id = __shfl_sync(kFull, idv, r);
+            const bool ok = r < b.cnt;
+            const float *src = ok ? tab + (size_t)id * JP + c * 4 : tab;
+            cp_async16(smem_addr(buf + r * CH + chunk_slot<CH>(c, r)), src, ok ? 16 : 0);
+        }
+        cp_commit();
+    };
+
+    typename std::conditional<ACC == ARE_FP32_KAHAN, AccKahan, AccF32F64>::type acc;
+    auto compute = [&](const Batch &b, const float4 *buf) {
+        float4 v[CH];
+#pragma unroll
+        for (int c = 0; c < CH; ++c) v[c] = buf[lane * CH + chunk_slot<CH>(c, lane)];
+        float g = 0.f;
+#pragma unroll
+        for (int c = 0; c < CH; ++c)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int j = c * 4 + e;
+                float n = fminf(fmaxf(__fsub_rn(comp(v[c], e), tm.ded[j]), 0.f), tm.lim[j]);
+                if (any_share) n = __fmul_rn(n, tm.share[j]);
+                g = __fadd_rn(g, n);
+            }
+        acc.add(fminf(fmaxf(__fsub_rn(g, tm.occ_r), 0.f), tm.occ_l));
+        if (b.last) {
+            const double S = warp_total(acc.total());
+            if (lane == 0) a.ylt[b.t] = net_d(S, a.agg_r, a.agg_l);
+            acc = decltype(acc){};
+        }
+    };
+
+    Batch q0 = next_batch<FIXED>(a, cur, step, lane, empty_loss);
+    int32_t i0 = load_ids(q0);
+    Batch q1 = next_batch<FIXED>(a, cur, step, lane, empty_loss);
+    int32_t i1 = load_ids(q1);
+    Batch q2 = next_batch<FIXED>(a, cur, step, lane, empty_loss);
+    int32_t i2 = load_ids(q2);
+    Batch q3;
+    int32_t i3 = 0;
+    issue_rows(q0, i0, buf0);
+
+    // Each stage: ids three batches ahead, rows one batch ahead, compute.
+#define ARE_STAGE(QC, QN, IN, QF, IF, BC, BN)                      \
+    if (QC.cnt == 0) break;                                        \
+    QF = next_batch<FIXED>(a, cur, step, lane, empty_loss);        \
+    IF = load_ids(QF);                                             \
+    issue_rows(QN, IN, BN);                                        \
+    cp_wait1();                                                    \
+    __syncwarp();                                                  \
+    compute(QC, BC);                                               \
+    __syncwarp();
+    while (true) {
+        ARE_STAGE(q0, q1, i1, q3, i3, buf0, buf1)
+        ARE_STAGE(q1, q2, i2, q0, i0, buf1, buf0)
+        ARE_STAGE(q2, q3, i3, q1, i1, buf0, buf1)
+        ARE_STAGE(q3, q0, i0, q2, i2, buf1, buf0)
+    }
+#undef ARE_STAGE
+    cp_wait0();
+}
+
+template <int JP, int ACC, bool FIXED>
+void launch_staged(const SimArgs &a, const TermsF32 &terms, int num_sms, cudaStream_t s)
+{
+    auto kern = k_simulate_staged<JP, ACC, FIXED>;
+    constexpr int smem = staged_smem_bytes<JP>();
+    static int per_sm = 0;
+    if (per_sm == 0) {
+        ARE_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        ARE_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern,
+                                                                   kStagedWarps * 32, smem));
+        if (per_sm < 1) per_sm = 1;
+    }
+    int64_t blocks = (a.n_trials + kStagedWarps - 1) / kStagedWarps;
+    const int64_t cap = (int64_t)num_sms * per_sm;
+    if (blocks > cap) blocks = cap;
+    if (blocks < 1) blocks = 1;
+    kern<<<(unsigned)blocks, kStagedWarps * 32, smem, s>>>(a, terms);
+    ARE_CUDA_TRY(cudaGetLastError());
+}
+
+template <int JP, int ACC>
+void launch_staged_fx(const SimArgs &a, const TermsF32 &terms, int num_sms, cudaStream_t s)
+{
+    if (a.off)
+        launch_staged<JP, ACC, false>(a, terms, num_sms, s);
+    else
+        launch_staged<JP, ACC, true>(a, terms, num_sms, s);
+}
+
+bool use_register_kernel()
+{
+    static const bool reg = [] {
+        const char *v = getenv("ARE_SIM_KERNEL");
+        return v && v[0] == 'r';
+    }();
+    return reg;
+}
+
 template <typename T, int JP, int ACC, bool FIXED, typename TT>
 void launch_one(const SimArgs &a, const TT &terms, int num_sms, cudaStream_t s)
 {
@@ -371,6 +591,20 @@ int launch_simulate(const SimArgs &a, are_precision prec, int jp, const TermsF32
         case 24: return launch_fx<double, 24, ARE_FP64>(a, *t64, num_sms, s), 1;
         case 28: return launch_fx<double, 28, ARE_FP64>(a, *t64, num_sms, s), 1;
         case 32: return launch_fx<double, 32, ARE_FP64>(a, *t64, num_sms, s), 1;
+        }
+    } else if (!use_register_kernel() && prec == ARE_FP32_KAHAN) {
+        switch (jp) {
+        case 8: return launch_staged_fx<8, ARE_FP32_KAHAN>(a, *t32, num_sms, s), 1;
+        case 16: return launch_staged_fx<16, ARE_FP32_KAHAN>(a, *t32, num_sms, s), 1;
+        case 24: return launch_staged_fx<24, ARE_FP32_KAHAN>(a, *t32, num_sms, s), 1;
+        case 32: return launch_staged_fx<32, ARE_FP32_KAHAN>(a, *t32, num_sms, s), 1;
+        }
+    } else if (!use_register_kernel() && prec == ARE_FP32_FP64AGG) {
+        switch (jp) {
+        case 8: return launch_staged_fx<8, ARE_FP32_FP64AGG>(a, *t32, num_sms, s), 1;
+        case 16: return launch_staged_fx<16, ARE_FP32_FP64AGG>(a, *t32, num_sms, s), 1;
+        case 24: return launch_staged_fx<24, ARE_FP32_FP64AGG>(a, *t32, num_sms, s), 1;
+        case 32: return launch_staged_fx<32, ARE_FP32_FP64AGG>(a, *t32, num_sms, s), 1;
         }
     } else if (prec == ARE_FP32_KAHAN) {
         switch (jp) {
