@@ -193,6 +193,48 @@ ARE_API are_status are_simulate(are_ctx *ctx, int32_t layer, int32_t yet, int64_
                         int64_t n_trials, are_precision precision, double *ylt,
                         void *stream);
 
+/* Analysis stage for n_layers layers over the same trials (the Basic
+ * Algorithm's outer loop over layers; the portfolio analysis of Section IV).
+ * ylts[i] (device memory, double[n_trials]) receives layer layers[i]'s YLT.
+ * FP32 precisions run as persistent launches (one per table width) whose
+ * warps claim (layer, trial tile) work items layer by layer; FP64 runs one
+ * launch per layer.  The first call with a given set of layers, YET, trial
+ * range, precision, output pointers and tuned configuration builds the
+ * layers' tables, a work list and a CUDA graph; identical later calls replay
+ * the graph.  Replays of one plan must not overlap on the GPU. */
+ARE_API are_status are_simulate_portfolio(are_ctx *ctx, const int32_t *layers, int32_t n_layers,
+                                          int32_t yet, int64_t trial_begin, int64_t n_trials,
+                                          are_precision precision, double *const *ylts,
+                                          void *stream);
+
+/* ------------------------------------------------------------------------ */
+/* Launch tuning                                                             */
+/* ------------------------------------------------------------------------ */
+
+/* The launch configuration the autotuner picked for one kind of work. */
+typedef struct {
+    int32_t kernel;          /* 0 persistent work items, 1 staged rows, 2 register rows */
+    int32_t rows_in_flight;  /* table rows each lane keeps in flight (persistent kernel) */
+    int32_t trials_per_item; /* trials per work item (persistent kernel) */
+    int32_t blocks_per_sm;   /* 0 = as many as fit */
+    double ms;               /* measured time of one pass */
+} are_tune_result;
+
+/* Time every candidate launch configuration on these layers and this YET
+ * (one layer: the single-layer kernels and persistent-kernel settings;
+ * several: the persistent kernel's rows in flight and trials per work item)
+ * and keep the fastest for this kind of work: precision, YET layout, widest
+ * table row, mean events per trial and one layer vs several.  Later
+ * are_simulate and are_simulate_portfolio calls of that kind use it.
+ * *best (may be NULL) receives the winner.  Runs on `stream` and waits. */
+ARE_API are_status are_autotune(are_ctx *ctx, const int32_t *layers, int32_t n_layers,
+                                int32_t yet, are_precision precision, void *stream,
+                                are_tune_result *best);
+
+/* Write / read the context's tuning table (one JSON object per line). */
+ARE_API are_status are_tune_save(are_ctx *ctx, const char *path);
+ARE_API are_status are_tune_load(are_ctx *ctx, const char *path);
+
 /* ------------------------------------------------------------------------ */
 /* Filters on the YLT (Section II-C): PML and TVaR                           */
 /* ------------------------------------------------------------------------ */
@@ -210,6 +252,14 @@ ARE_API are_status are_risk_measures(are_ctx *ctx, const double *ylt, int64_t n,
                              const double *return_periods, int32_t n_rp, double *pml_out,
                              const double *tvar_levels, int32_t n_tv, double *tvar_out,
                              void *stream);
+
+/* are_risk_measures for n_ylt YLTs of n losses each (ylts: host array of
+ * device pointers), selected together: pml_out[y * n_rp + r] and
+ * tvar_out[y * n_tv + r] are host arrays.  Synchronises `stream`. */
+ARE_API are_status are_risk_measures_batch(are_ctx *ctx, const double *const *ylts, int32_t n_ylt,
+                                           int64_t n, const double *return_periods, int32_t n_rp,
+                                           double *pml_out, const double *tvar_levels,
+                                           int32_t n_tv, double *tvar_out, void *stream);
 
 /* ------------------------------------------------------------------------ */
 /* Allocation-free PML/TVaR                                                  */

@@ -40,6 +40,11 @@ class FinTerms(C.Structure):
                 ("share", C.c_double)]
 
 
+class TuneResult(C.Structure):
+    _fields_ = [("kernel", C.c_int32), ("rows_in_flight", C.c_int32),
+                ("trials_per_item", C.c_int32), ("blocks_per_sm", C.c_int32), ("ms", C.c_double)]
+
+
 class LayerTerms(C.Structure):
     _fields_ = [("occ_ret", C.c_double), ("occ_lim", C.c_double), ("agg_ret", C.c_double),
                 ("agg_lim", C.c_double)]
@@ -69,6 +74,14 @@ _SIGS = {
                                       _P]),
     "are_risk_measures_static": (C.c_int32, [_P, C.c_int64, _P, C.c_int32, _P, _P, C.c_int32,
                                              _P, _P]),
+    "are_simulate_portfolio": (C.c_int32, [_P, _P, C.c_int32, C.c_int32, C.c_int64, C.c_int64,
+                                           C.c_int, _P, _P]),
+    "are_risk_measures_batch": (C.c_int32, [_P, _P, C.c_int32, C.c_int64, _P, C.c_int32, _P, _P,
+                                            C.c_int32, _P, _P]),
+    "are_autotune": (C.c_int32, [_P, _P, C.c_int32, C.c_int32, C.c_int, _P,
+                                 C.POINTER(TuneResult)]),
+    "are_tune_save": (C.c_int32, [_P, C.c_char_p]),
+    "are_tune_load": (C.c_int32, [_P, C.c_char_p]),
 }
 
 
@@ -247,3 +260,48 @@ def are_risk_measures_static(ylt, n: Optional[int] = None,
                                                 rp.shape[0], pml.ctypes.data, lv.ctypes.data,
                                                 lv.shape[0], tv.ctypes.data, _stream(stream)))
     return pml, tv
+
+
+def are_simulate_portfolio(ctx, layers: Sequence[int], yet: int, trial_begin: int, n_trials: int,
+                           precision: int, ylts: Sequence, stream=None) -> None:
+    """Analysis stage for several layers in one persistent, graph-replayed launch."""
+    hs = np.ascontiguousarray(layers, dtype=np.int32)
+    ptrs = (C.c_void_p * len(ylts))(*[_addr(y, np.float64) for y in ylts])
+    if len(ylts) != hs.shape[0]:
+        raise ValueError("one YLT per layer")
+    _check(ctx, lib().are_simulate_portfolio(ctx, hs.ctypes.data, hs.shape[0], int(yet),
+                                             int(trial_begin), int(n_trials), int(precision),
+                                             C.cast(ptrs, C.c_void_p), _stream(stream)))
+
+
+def are_risk_measures_batch(ctx, ylts: Sequence, n: int,
+                            return_periods: Sequence[float] = (100.0, 250.0),
+                            tvar_levels: Sequence[float] = (0.99,), stream=None):
+    """(pml[n_ylt, n_rp], tvar[n_ylt, n_tv]) for several device YLTs."""
+    ptrs = (C.c_void_p * len(ylts))(*[_addr(y, np.float64) for y in ylts])
+    rp = np.ascontiguousarray(return_periods, dtype=np.float64)
+    lv = np.ascontiguousarray(tvar_levels, dtype=np.float64)
+    pml = np.empty((len(ylts), rp.shape[0]), np.float64)
+    tv = np.empty((len(ylts), lv.shape[0]), np.float64)
+    _check(ctx, lib().are_risk_measures_batch(ctx, C.cast(ptrs, C.c_void_p), len(ylts), int(n),
+                                              rp.ctypes.data, rp.shape[0], pml.ctypes.data,
+                                              lv.ctypes.data, lv.shape[0], tv.ctypes.data,
+                                              _stream(stream)))
+    return pml, tv
+
+
+def are_autotune(ctx, layers: Sequence[int], yet: int, precision: int, stream=None) -> dict:
+    """Time the candidate launch configurations and keep the fastest."""
+    hs = np.ascontiguousarray(layers, dtype=np.int32)
+    r = TuneResult()
+    _check(ctx, lib().are_autotune(ctx, hs.ctypes.data, hs.shape[0], int(yet), int(precision),
+                                   _stream(stream), C.byref(r)))
+    return {f: getattr(r, f) for f, _ in TuneResult._fields_}
+
+
+def are_tune_save(ctx, path: str) -> None:
+    _check(ctx, lib().are_tune_save(ctx, os.fsencode(path)))
+
+
+def are_tune_load(ctx, path: str) -> None:
+    _check(ctx, lib().are_tune_load(ctx, os.fsencode(path)))

@@ -5,6 +5,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <unordered_map>
 
@@ -151,6 +152,7 @@ Table &build_table(are_ctx *ctx, Layer &L, int32_t catalog, bool fp32, cudaStrea
     const size_t bytes = (size_t)catalog * jp * (fp32 ? 4 : 8);
     if (t.d && (t.catalog != catalog || t.jp != jp)) free_table(ctx, t);
     if (!t.d) {
+        ++L.generation;
         t.d = dalloc(ctx, bytes);
         t.bytes = bytes;
         t.catalog = catalog;
@@ -218,6 +220,89 @@ void fill_terms(are_ctx *ctx, const Layer &L, TermsF32 &t32, TermsF64 &t64, int 
     t32.occ_l = (float)L.terms.occ_lim;
 }
 
+void fill_layer_f32(are_ctx *ctx, const Layer &L, LayerF32 &o)
+{
+    std::memset(&o, 0, sizeof o);
+    o.table = static_cast<const float *>(L.t32.d);
+    o.jp = L.t32.jp;
+    for (int j = 0; j < kMaxElts; ++j) o.share[j] = 1.f;
+    for (size_t j = 0; j < L.elts.size(); ++j) {
+        const are_fin_terms &f = ctx->elts.at(L.elts[j]).terms;
+        o.ded[j] = (float)f.deductible;
+        o.lim[j] = (float)f.limit;
+        o.share[j] = (float)f.share;
+        o.any_share |= f.share != 1.0;
+    }
+    o.occ_r = (float)L.terms.occ_ret;
+    o.occ_l = (float)L.terms.occ_lim;
+    o.agg_r = L.terms.agg_ret;
+    o.agg_l = L.terms.agg_lim;
+}
+
+// Key of the tuning table: precision, YET layout, widest table row, mean
+// events per trial (power-of-two bucket) and one layer vs several.
+std::string tune_key(are_precision p, const Yet &y, int jp, bool multi)
+{
+    const double mean = y.n_trials ? (double)y.n_events / (double)y.n_trials : 0.0;
+    int bucket = 1;
+    while (bucket < mean && bucket < (1 << 20)) bucket <<= 1;
+    return "p" + std::to_string((int)p) + (y.d_off ? "_ragged" : "_fixed") + "_jp" +
+           std::to_string(jp) + "_ev" + std::to_string(bucket) + (multi ? "_multi" : "_single");
+}
+
+ItemWork item_work(const Yet &y, int64_t trial_begin, int64_t n_trials, const ItemConfig &cfg)
+{
+    ItemWork w;
+    std::memset(&w, 0, sizeof w);
+    w.ids = y.d_ids;
+    w.off = y.d_off;
+    w.k = y.k;
+    w.trial_begin = trial_begin;
+    w.n_trials = n_trials;
+    w.trials_per_item = cfg.trials_per_item > 0 ? cfg.trials_per_item : 8;
+    return w;
+}
+
+// One layer's analysis stage with a given kernel choice.
+int run_single(are_ctx *ctx, const Layer &L, const Yet &y, int64_t trial_begin, int64_t n_trials,
+               are_precision precision, double *d_out, const TuneEntry &te, cudaStream_t s)
+{
+    const bool fp32 = precision != ARE_FP64;
+    if (fp32 && te.kernel == 0) {
+        ItemWork w = item_work(y, trial_begin, n_trials, te.cfg);
+        fill_layer_f32(ctx, L, w.one);
+        w.one.ylt = d_out;
+        w.n_layers = 1;
+        w.n_items = (n_trials + w.trials_per_item - 1) / w.trials_per_item;
+        return launch_items(w, L.t32.jp, te.cfg, precision, ctx->num_sms, s);
+    }
+    const Table &t = fp32 ? L.t32 : L.t64;
+    SimArgs a{};
+    a.ids = y.d_ids;
+    a.off = y.d_off;
+    a.k = y.k;
+    a.trial_begin = trial_begin;
+    a.n_trials = n_trials;
+    a.table = t.d;
+    a.agg_r = L.terms.agg_ret;
+    a.agg_l = L.terms.agg_lim;
+    a.ylt = d_out;
+    a.kernel = te.kernel;
+    TermsF32 t32;
+    TermsF64 t64;
+    fill_terms(ctx, L, t32, t64, a.any_share);
+    return launch_simulate(a, precision, t.jp, &t32, &t64, ctx->num_sms, s);
+}
+
+TuneEntry tuned(are_ctx *ctx, are_precision p, const Yet &y, int jp, bool multi)
+{
+    auto it = ctx->tune.find(tune_key(p, y, jp, multi));
+    if (it != ctx->tune.end()) return it->second;
+    TuneEntry d;
+    d.kernel = multi ? 0 : (p == ARE_FP64 ? 2 : 1);
+    return d;
+}
+
 int64_t rank_rp(int64_t n, double rp)
 {
     const int64_t m = rank_for_return_period(n, rp);
@@ -249,6 +334,119 @@ int64_t rank_for_level(int64_t n, double a)
     return (n * (1000000000 - nano) + 999999999) / 1000000000;
 }
 
+namespace {
+
+void free_plan(are_ctx *ctx, Plan &p)
+{
+    if (p.exec) cudaGraphExecDestroy(p.exec);
+    if (p.graph) cudaGraphDestroy(p.graph);
+    dfree(ctx, p.d_work, p.work_bytes);
+    p = Plan{};
+}
+
+constexpr int kWidths[3] = {8, 16, 32};
+
+// Layers of a multi-layer launch grouped by FP32 table width: group g holds
+// the LayerF32 records of width kWidths[g] at d_work + offset[g].
+struct Groups {
+    std::vector<LayerF32> rec[3];
+    size_t offset[3] = {0, 0, 0};
+    size_t counters = 0;
+    size_t bytes = 0;
+};
+
+Groups group_layers(are_ctx *ctx, const std::vector<int32_t> &layers,
+                    const std::vector<double *> &ylts, int64_t n_trials, int tpi)
+{
+    Groups g;
+    for (size_t i = 0; i < layers.size(); ++i) {
+        const Layer &L = ctx->layers.at(layers[i]);
+        LayerF32 r;
+        fill_layer_f32(ctx, L, r);
+        r.ylt = ylts[i];
+        const int gi = r.jp == 8 ? 0 : r.jp == 16 ? 1 : 2;
+        r.item_begin = 0;
+        g.rec[gi].push_back(r);
+    }
+    const int64_t per_layer = (n_trials + tpi - 1) / tpi;
+    size_t off = 0;
+    for (int gi = 0; gi < 3; ++gi) {
+        int64_t next = 0;
+        for (LayerF32 &r : g.rec[gi]) {
+            r.item_begin = next;
+            next += per_layer;
+        }
+        g.offset[gi] = off;
+        off += (sizeof(LayerF32) * g.rec[gi].size() + 255) / 256 * 256;
+    }
+    g.counters = off;
+    g.bytes = off + 3 * sizeof(unsigned long long);
+    return g;
+}
+
+// Enqueues the analysis stage of several layers.  FP32: one persistent
+// launch per table width over a device work list at d_work (which must hold
+// the Groups layout); FP64: one launch per layer.
+int enqueue_multi(are_ctx *ctx, const std::vector<int32_t> &layers,
+                  const std::vector<double *> &ylts, const Yet &y, int64_t trial_begin,
+                  int64_t n_trials, are_precision prec, const TuneEntry &te, const Groups *g,
+                  void *d_work, cudaStream_t s)
+{
+    int launches = 0;
+    if (prec == ARE_FP64) {
+        for (size_t i = 0; i < layers.size(); ++i)
+            launches += run_single(ctx, ctx->layers.at(layers[i]), y, trial_begin, n_trials, prec,
+                                   ylts[i], te, s);
+        return launches;
+    }
+    unsigned char *base = static_cast<unsigned char *>(d_work);
+    for (int gi = 0; gi < 3; ++gi) {
+        if (g->rec[gi].empty()) continue;
+        ItemWork w = item_work(y, trial_begin, n_trials, te.cfg);
+        w.layers = reinterpret_cast<const LayerF32 *>(base + g->offset[gi]);
+        w.n_layers = (int32_t)g->rec[gi].size();
+        w.n_items = (int64_t)g->rec[gi].size() * ((n_trials + w.trials_per_item - 1) / w.trials_per_item);
+        w.counter = reinterpret_cast<unsigned long long *>(base + g->counters) + gi;
+        ARE_CUDA_TRY(cudaMemsetAsync(w.counter, 0, sizeof(unsigned long long), s));
+        launches += launch_items(w, kWidths[gi], te.cfg, prec, ctx->num_sms, s);
+    }
+    return launches;
+}
+
+void check_multi_args(are_ctx *ctx, const int32_t *layers, int32_t n_layers, const Yet &y,
+                      int64_t trial_begin, int64_t n_trials, double *const *ylts)
+{
+    ARE_CHECK(layers && n_layers >= 1, ARE_EINVAL, "need at least one layer");
+    ARE_CHECK(trial_begin >= 0 && n_trials >= 1 && trial_begin + n_trials <= y.n_trials, ARE_EINVAL,
+              "trial range outside the YET");
+    for (int32_t i = 0; i < n_layers; ++i) {
+        layer_of(ctx, layers[i]);
+        if (ylts) {
+            ARE_CHECK(ylts[i] && is_device_ptr(ylts[i]), ARE_EINVAL,
+                      "every YLT of a multi-layer launch must be device memory");
+        }
+    }
+}
+
+void ensure_tables(are_ctx *ctx, const int32_t *layers, int32_t n_layers, const Yet &y, bool fp32,
+                   cudaStream_t s)
+{
+    for (int32_t i = 0; i < n_layers; ++i) {
+        Layer &L = layer_of(ctx, layers[i]);
+        const Table &t = fp32 ? L.t32 : L.t64;
+        if (!t.d || t.catalog != y.catalog) build_table(ctx, L, y.catalog, fp32, s);
+    }
+}
+
+int max_width(are_ctx *ctx, const int32_t *layers, int32_t n_layers, bool fp32)
+{
+    int jp = 0;
+    for (int32_t i = 0; i < n_layers; ++i)
+        jp = std::max(jp, table_jp((int)layer_of(ctx, layers[i]).elts.size(), fp32));
+    return jp;
+}
+
+}  // namespace
 }  // namespace are
 
 using namespace are;
@@ -271,6 +469,7 @@ are_status are_create(are_ctx **out, int device, size_t mem_budget_bytes)
     are_status st = guarded(ctx, [&] {
         ARE_CUDA_TRY(cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device));
         ARE_CUDA_TRY(cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking));
+        ARE_CUDA_TRY(cudaStreamCreateWithFlags(&ctx->capture, cudaStreamNonBlocking));
         ARE_CUDA_TRY(cudaMalloc(&ctx->d_flag, sizeof(int)));
         ARE_CUDA_TRY(cudaMallocHost(&ctx->h_flag, sizeof(int)));
         ARE_CUDA_TRY(cudaMallocHost(&ctx->h_result, sizeof(double) * 2 * kMaxTargets));
@@ -303,6 +502,11 @@ are_status are_destroy(are_ctx *ctx)
             dfree(ctx, kv.second.d_ids, 0);
             dfree(ctx, kv.second.d_off, 0);
         }
+        for (auto &p : ctx->plans) free_plan(ctx, p);
+        ctx->plans.clear();
+        if (ctx->d_multi) cudaFree(ctx->d_multi);
+        if (ctx->h_multi) cudaFreeHost(ctx->h_multi);
+        if (ctx->capture) cudaStreamDestroy(ctx->capture);
         select_free(ctx->sel);
         if (ctx->d_flag) cudaFree(ctx->d_flag);
         if (ctx->h_flag) cudaFreeHost(ctx->h_flag);
@@ -552,20 +756,8 @@ are_status are_simulate(are_ctx *ctx, int32_t layer, int32_t yet, int64_t trial_
         double *d_out = ylt;
         if (!dev_out) d_out = (double *)dalloc(ctx, sizeof(double) * n_trials);
         try {
-            SimArgs a{};
-            a.ids = y.d_ids;
-            a.off = y.d_off;
-            a.k = y.k;
-            a.trial_begin = trial_begin;
-            a.n_trials = n_trials;
-            a.table = t.d;
-            a.agg_r = L.terms.agg_ret;
-            a.agg_l = L.terms.agg_lim;
-            a.ylt = d_out;
-            TermsF32 t32;
-            TermsF64 t64;
-            fill_terms(ctx, L, t32, t64, a.any_share);
-            ctx->launches += launch_simulate(a, precision, t.jp, &t32, &t64, ctx->num_sms, s);
+            const TuneEntry te = tuned(ctx, precision, y, t.jp, false);
+            ctx->launches += run_single(ctx, L, y, trial_begin, n_trials, precision, d_out, te, s);
             if (!dev_out) {
                 ARE_CUDA_TRY(cudaMemcpyAsync(ylt, d_out, sizeof(double) * n_trials,
                                              cudaMemcpyDeviceToHost, s));
@@ -622,6 +814,308 @@ are_status are_risk_measures(are_ctx *ctx, const double *ylt, int64_t n,
         dfree(ctx, tmp, sizeof(double) * n);
         for (int32_t r = 0; r < n_rp; ++r) pml_out[r] = res[2 * r];
         for (int32_t r = 0; r < n_tv; ++r) tvar_out[r] = res[2 * (n_rp + r) + 1];
+    });
+}
+
+are_status are_simulate_portfolio(are_ctx *ctx, const int32_t *layers, int32_t n_layers,
+                                  int32_t yet, int64_t trial_begin, int64_t n_trials,
+                                  are_precision precision, double *const *ylts, void *stream)
+{
+    return guarded(ctx, [&] {
+        check_precision(precision);
+        Yet &y = yet_of(ctx, yet);
+        ARE_CHECK(ylts, ARE_EINVAL, "ylts is NULL");
+        check_multi_args(ctx, layers, n_layers, y, trial_begin, n_trials, ylts);
+        CallStream cs(ctx, stream);
+        const bool fp32 = precision != ARE_FP64;
+        ensure_tables(ctx, layers, n_layers, y, fp32, cs.s);
+        const std::vector<int32_t> lv(layers, layers + n_layers);
+        const std::vector<double *> yv(ylts, ylts + n_layers);
+        std::vector<uint64_t> gens;
+        for (int32_t h : lv) gens.push_back(ctx->layers.at(h).generation);
+        const TuneEntry te = tuned(ctx, precision, y, max_width(ctx, layers, n_layers, fp32), true);
+
+        Plan *plan = nullptr;
+        for (Plan &p : ctx->plans)
+            if (p.layers == lv && p.ylts == yv && p.generations == gens && p.yet == yet &&
+                p.trial_begin == trial_begin && p.n_trials == n_trials &&
+                p.precision == (int)precision && p.kernel == te.kernel &&
+                p.cfg.rows_in_flight == te.cfg.rows_in_flight &&
+                p.cfg.trials_per_item == te.cfg.trials_per_item &&
+                p.cfg.blocks_per_sm == te.cfg.blocks_per_sm)
+                plan = &p;
+        if (!plan) {
+            if (ctx->plans.size() >= 8) {
+                free_plan(ctx, ctx->plans.front());
+                ctx->plans.erase(ctx->plans.begin());
+            }
+            Plan p;
+            p.layers = lv;
+            p.ylts = yv;
+            p.generations = gens;
+            p.yet = yet;
+            p.trial_begin = trial_begin;
+            p.n_trials = n_trials;
+            p.precision = (int)precision;
+            p.kernel = te.kernel;
+            p.cfg = te.cfg;
+            try {
+                Groups g;
+                if (fp32) {
+                    g = group_layers(ctx, lv, yv, n_trials,
+                                     te.cfg.trials_per_item > 0 ? te.cfg.trials_per_item : 8);
+                    p.work_bytes = g.bytes;
+                    p.d_work = dalloc(ctx, g.bytes);
+                    std::vector<unsigned char> host(g.bytes, 0);
+                    for (int gi = 0; gi < 3; ++gi)
+                        if (!g.rec[gi].empty())
+                            std::memcpy(host.data() + g.offset[gi], g.rec[gi].data(),
+                                        sizeof(LayerF32) * g.rec[gi].size());
+                    ARE_CUDA_TRY(cudaMemcpyAsync(p.d_work, host.data(), g.bytes,
+                                                 cudaMemcpyHostToDevice, cs.s));
+                    ARE_CUDA_TRY(cudaStreamSynchronize(cs.s));
+                }
+                ARE_CUDA_TRY(cudaStreamBeginCapture(ctx->capture, cudaStreamCaptureModeThreadLocal));
+                int launches = 0;
+                try {
+                    launches = enqueue_multi(ctx, lv, yv, y, trial_begin, n_trials, precision, te,
+                                             fp32 ? &g : nullptr, p.d_work, ctx->capture);
+                } catch (...) {
+                    cudaGraph_t dead = nullptr;
+                    cudaStreamEndCapture(ctx->capture, &dead);
+                    if (dead) cudaGraphDestroy(dead);
+                    throw;
+                }
+                ARE_CUDA_TRY(cudaStreamEndCapture(ctx->capture, &p.graph));
+                ARE_CUDA_TRY(cudaGraphInstantiate(&p.exec, p.graph, 0));
+                p.launches = (uint64_t)launches;
+            } catch (...) {
+                free_plan(ctx, p);
+                throw;
+            }
+            ctx->plans.push_back(p);
+            plan = &ctx->plans.back();
+        }
+        ARE_CUDA_TRY(cudaGraphLaunch(plan->exec, cs.s));
+        ctx->launches += plan->launches;
+        cs.finish();
+    });
+}
+
+are_status are_risk_measures_batch(are_ctx *ctx, const double *const *ylts, int32_t n_ylt,
+                                   int64_t n, const double *return_periods, int32_t n_rp,
+                                   double *pml_out, const double *tvar_levels, int32_t n_tv,
+                                   double *tvar_out, void *stream)
+{
+    return guarded(ctx, [&] {
+        ARE_CHECK(ylts && n_ylt >= 1, ARE_EINVAL, "need at least one YLT");
+        ARE_CHECK(n > 0 && n < (int64_t)UINT32_MAX, ARE_EINVAL, "bad YLT length");
+        ARE_CHECK(n_rp >= 0 && n_tv >= 0, ARE_EINVAL, "negative count");
+        ARE_CHECK(n_rp == 0 || (return_periods && pml_out), ARE_EINVAL, "NULL PML arrays");
+        ARE_CHECK(n_tv == 0 || (tvar_levels && tvar_out), ARE_EINVAL, "NULL TVaR arrays");
+        for (int32_t i = 0; i < n_ylt; ++i)
+            ARE_CHECK(ylts[i] && is_device_ptr(ylts[i]), ARE_EINVAL, "every YLT must be device memory");
+        std::vector<int64_t> ranks;
+        for (int32_t r = 0; r < n_rp; ++r) ranks.push_back(rank_rp(n, return_periods[r]));
+        for (int32_t r = 0; r < n_tv; ++r) ranks.push_back(rank_level(n, tvar_levels[r]));
+        if (ranks.empty()) return;
+        CallStream cs(ctx, stream);
+        const size_t ptr_bytes = (sizeof(double *) * n_ylt + 255) / 256 * 256;
+        const size_t need = ptr_bytes + select_multi_bytes(n_ylt, n, ctx->num_sms);
+        if (ctx->multi_bytes < need) {
+            ARE_CUDA_TRY(cudaStreamSynchronize(cs.s));
+            dfree(ctx, ctx->d_multi, ctx->multi_bytes);
+            ctx->d_multi = nullptr;
+            ctx->multi_bytes = 0;
+            ctx->d_multi = dalloc(ctx, need);
+            ctx->multi_bytes = need;
+        }
+        const size_t count = (size_t)2 * kMaxTargets * n_ylt;
+        if (ctx->h_multi_count < count) {
+            if (ctx->h_multi) cudaFreeHost(ctx->h_multi);
+            ctx->h_multi = nullptr;
+            ctx->h_multi_count = 0;
+            ARE_CUDA_TRY(cudaMallocHost(&ctx->h_multi, sizeof(double) * count));
+            ctx->h_multi_count = count;
+        }
+        const double *const *d_ptrs = static_cast<const double *const *>(ctx->d_multi);
+        ARE_CUDA_TRY(cudaMemcpyAsync(ctx->d_multi, ylts, sizeof(double *) * n_ylt,
+                                     cudaMemcpyHostToDevice, cs.s));
+        void *scratch = static_cast<unsigned char *>(ctx->d_multi) + ptr_bytes;
+        for (size_t b = 0; b < ranks.size(); b += kMaxTargets) {
+            const int nt = (int)std::min<size_t>(kMaxTargets, ranks.size() - b);
+            double *d_res = nullptr;
+            ctx->launches += launch_select_multi(d_ptrs, n_ylt, n, ranks.data() + b, nt, scratch,
+                                                 ctx->num_sms, cs.s, &d_res);
+            ARE_CUDA_TRY(cudaMemcpyAsync(ctx->h_multi, d_res, sizeof(double) * count,
+                                         cudaMemcpyDeviceToHost, cs.s));
+            ARE_CUDA_TRY(cudaStreamSynchronize(cs.s));
+            for (int32_t y = 0; y < n_ylt; ++y)
+                for (int t = 0; t < nt; ++t) {
+                    const size_t gt = b + t;
+                    const double *res = ctx->h_multi + (size_t)y * 2 * kMaxTargets;
+                    if ((int64_t)gt < n_rp) pml_out[(size_t)y * n_rp + gt] = res[2 * t];
+                    else tvar_out[(size_t)y * n_tv + (gt - n_rp)] = res[2 * t + 1];
+                }
+        }
+        cs.finish();
+    });
+}
+
+are_status are_autotune(are_ctx *ctx, const int32_t *layers, int32_t n_layers, int32_t yet,
+                        are_precision precision, void *stream, are_tune_result *best)
+{
+    return guarded(ctx, [&] {
+        check_precision(precision);
+        Yet &y = yet_of(ctx, yet);
+        check_multi_args(ctx, layers, n_layers, y, 0, y.n_trials, nullptr);
+        CallStream cs(ctx, stream);
+        const bool fp32 = precision != ARE_FP64;
+        ensure_tables(ctx, layers, n_layers, y, fp32, cs.s);
+        const bool multi = n_layers > 1;
+        const int jp = max_width(ctx, layers, n_layers, fp32);
+        const std::string key = tune_key(precision, y, jp, multi);
+        std::vector<TuneEntry> cands;
+        if (fp32) {
+            if (!multi) {
+                TuneEntry e;
+                e.kernel = 1;
+                cands.push_back(e);
+                e.kernel = 2;
+                cands.push_back(e);
+            }
+            for (int u : {4, 8})
+                for (int tpi : multi ? std::vector<int>{2, 4, 8, 16, 32} : std::vector<int>{2, 8}) {
+                    TuneEntry e;
+                    e.kernel = 0;
+                    e.cfg.rows_in_flight = u;
+                    e.cfg.trials_per_item = tpi;
+                    cands.push_back(e);
+                }
+        } else {
+            TuneEntry e;
+            e.kernel = 2;
+            cands.push_back(e);
+        }
+        const size_t out_bytes = sizeof(double) * (size_t)y.n_trials * n_layers;
+        double *outs = (double *)dalloc(ctx, out_bytes);
+        void *work = nullptr;
+        size_t work_bytes = 0;
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        TuneEntry win;
+        win.ms = 1e300;
+        try {
+            ARE_CUDA_TRY(cudaEventCreate(&e0));
+            ARE_CUDA_TRY(cudaEventCreate(&e1));
+            std::vector<int32_t> lv(layers, layers + n_layers);
+            std::vector<double *> yv;
+            for (int32_t i = 0; i < n_layers; ++i) yv.push_back(outs + (size_t)i * y.n_trials);
+            for (TuneEntry &c : cands) {
+                Groups g;
+                if (fp32) {
+                    g = group_layers(ctx, lv, yv, y.n_trials, c.cfg.trials_per_item);
+                    if (work_bytes < g.bytes) {
+                        ARE_CUDA_TRY(cudaStreamSynchronize(cs.s));
+                        dfree(ctx, work, work_bytes);
+                        work = nullptr;
+                        work = dalloc(ctx, g.bytes);
+                        work_bytes = g.bytes;
+                    }
+                    std::vector<unsigned char> host(g.bytes, 0);
+                    for (int gi = 0; gi < 3; ++gi)
+                        if (!g.rec[gi].empty())
+                            std::memcpy(host.data() + g.offset[gi], g.rec[gi].data(),
+                                        sizeof(LayerF32) * g.rec[gi].size());
+                    ARE_CUDA_TRY(cudaMemcpyAsync(work, host.data(), g.bytes, cudaMemcpyHostToDevice, cs.s));
+                    ARE_CUDA_TRY(cudaStreamSynchronize(cs.s));
+                }
+                auto run = [&] {
+                    if (multi)
+                        ctx->launches += enqueue_multi(ctx, lv, yv, y, 0, y.n_trials, precision, c,
+                                                       fp32 ? &g : nullptr, work, cs.s);
+                    else
+                        ctx->launches += run_single(ctx, ctx->layers.at(lv[0]), y, 0, y.n_trials,
+                                                    precision, yv[0], c, cs.s);
+                };
+                run();
+                double best_ms = 1e300;
+                for (int rep = 0; rep < 3; ++rep) {
+                    ARE_CUDA_TRY(cudaEventRecord(e0, cs.s));
+                    run();
+                    ARE_CUDA_TRY(cudaEventRecord(e1, cs.s));
+                    ARE_CUDA_TRY(cudaEventSynchronize(e1));
+                    float ms = 0.f;
+                    ARE_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+                    best_ms = std::min(best_ms, (double)ms);
+                }
+                c.ms = best_ms;
+                if (best_ms < win.ms) win = c;
+            }
+        } catch (...) {
+            cudaStreamSynchronize(cs.s);
+            if (e0) cudaEventDestroy(e0);
+            if (e1) cudaEventDestroy(e1);
+            dfree(ctx, work, work_bytes);
+            dfree(ctx, outs, out_bytes);
+            throw;
+        }
+        ARE_CUDA_TRY(cudaStreamSynchronize(cs.s));
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        dfree(ctx, work, work_bytes);
+        dfree(ctx, outs, out_bytes);
+        ctx->tune[key] = win;
+        if (best) {
+            best->kernel = win.kernel;
+            best->rows_in_flight = win.cfg.rows_in_flight;
+            best->trials_per_item = win.cfg.trials_per_item;
+            best->blocks_per_sm = win.cfg.blocks_per_sm;
+            best->ms = win.ms;
+        }
+        cs.finish();
+    });
+}
+
+are_status are_tune_save(are_ctx *ctx, const char *path)
+{
+    return guarded(ctx, [&] {
+        ARE_CHECK(path, ARE_EINVAL, "path is NULL");
+        FILE *f = std::fopen(path, "w");
+        ARE_CHECK(f, ARE_EINVAL, std::string("cannot write ") + path);
+        for (const auto &kv : ctx->tune)
+            std::fprintf(f,
+                         "{\"key\": \"%s\", \"kernel\": %d, \"rows_in_flight\": %d, "
+                         "\"trials_per_item\": %d, \"blocks_per_sm\": %d, \"ms\": %.6f}\n",
+                         kv.first.c_str(), kv.second.kernel, kv.second.cfg.rows_in_flight,
+                         kv.second.cfg.trials_per_item, kv.second.cfg.blocks_per_sm, kv.second.ms);
+        std::fclose(f);
+    });
+}
+
+are_status are_tune_load(are_ctx *ctx, const char *path)
+{
+    return guarded(ctx, [&] {
+        ARE_CHECK(path, ARE_EINVAL, "path is NULL");
+        FILE *f = std::fopen(path, "r");
+        ARE_CHECK(f, ARE_ENOTFOUND, std::string("cannot read ") + path);
+        char line[512], key[256];
+        int loaded = 0;
+        while (std::fgets(line, sizeof line, f)) {
+            TuneEntry e;
+            double ms = 0;
+            if (std::sscanf(line,
+                            "{\"key\": \"%255[^\"]\", \"kernel\": %d, \"rows_in_flight\": %d, "
+                            "\"trials_per_item\": %d, \"blocks_per_sm\": %d, \"ms\": %lf}",
+                            key, &e.kernel, &e.cfg.rows_in_flight, &e.cfg.trials_per_item,
+                            &e.cfg.blocks_per_sm, &ms) == 6 &&
+                e.kernel >= 0 && e.kernel <= 2 && e.cfg.trials_per_item > 0) {
+                e.ms = ms;
+                ctx->tune[key] = e;
+                ++loaded;
+            }
+        }
+        std::fclose(f);
+        ARE_CHECK(loaded > 0, ARE_EINVAL, std::string("no tuning entries in ") + path);
     });
 }
 

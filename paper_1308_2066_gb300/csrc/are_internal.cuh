@@ -80,6 +80,7 @@ struct Layer {
     std::vector<int32_t> elts;
     are_layer_terms terms{};
     Table t32, t64;
+    uint64_t generation = 0;   // bumped whenever a table is (re)allocated or freed
 };
 
 // ---------------------------------------------------------------------------
@@ -105,6 +106,7 @@ struct SimArgs {
     double agg_r, agg_l;
     int any_share;           // some ELT has share != 1
     double *ylt;             // n_trials
+    int kernel;              // FP32 tables: 1 staged, 2 register
 };
 
 struct ScatterArgs {
@@ -114,6 +116,64 @@ struct ScatterArgs {
     double fx[kMaxElts];
     int32_t n_elts;
     int32_t jp;
+};
+
+// One layer of a persistent multi-layer launch (FP32 tables).
+struct LayerF32 {
+    const float *table;      // [catalog][jp]
+    double *ylt;             // n_trials losses
+    float ded[kMaxElts], lim[kMaxElts], share[kMaxElts];  // zero / zero / one past J
+    float occ_r, occ_l;
+    double agg_r, agg_l;
+    int32_t jp;              // 8, 16 or 32
+    int32_t any_share;
+    int64_t item_begin;      // index of the layer's first work item
+};
+
+// Work of a persistent launch: every layer's trials cut into items of
+// trials_per_item trials, numbered layer by layer.
+struct ItemWork {
+    const int32_t *ids;
+    const int64_t *off;      // ragged offsets or nullptr (k events per trial)
+    int32_t k;
+    int64_t trial_begin, n_trials;
+    int32_t trials_per_item;
+    int32_t n_layers;
+    int64_t n_items;
+    const LayerF32 *layers;            // device array of n_layers, or nullptr: use `one`
+    unsigned long long *counter;       // device, zero before the launch; nullptr: static split
+    LayerF32 one;                      // the layer when there is exactly one
+};
+
+// Tunables of the persistent kernel.
+struct ItemConfig {
+    int rows_in_flight = 8;  // U: table rows per lane in flight (4 or 8)
+    int trials_per_item = 8; // trials per work item
+    int blocks_per_sm = 0;   // 256-thread blocks per SM (0 = as many as fit)
+};
+
+// A tuned launch configuration of the analysis stage.
+struct TuneEntry {
+    int kernel = 0;            // 0 persistent items, 1 staged, 2 register
+    ItemConfig cfg;
+    double ms = 0.0;
+};
+
+// A cached multi-layer launch: work list and CUDA graph.
+struct Plan {
+    std::vector<int32_t> layers;
+    std::vector<uint64_t> generations;
+    std::vector<double *> ylts;
+    int32_t yet = 0;
+    int64_t trial_begin = 0, n_trials = 0;
+    int precision = 0;
+    int kernel = 0;
+    ItemConfig cfg;
+    void *d_work = nullptr;    // LayerF32 records by table width, then the item counters
+    size_t work_bytes = 0;
+    uint64_t launches = 0;     // kernels per replay
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
 };
 
 // ---------------------------------------------------------------------------
@@ -131,6 +191,11 @@ int launch_check_offsets(const int64_t *off, int64_t n_trials, int64_t n_events,
                           cudaStream_t s);
 int launch_check_timestamps(const float *ts, const int64_t *off, int64_t n_trials, int32_t k,
                              int *flag, cudaStream_t s);
+
+// sim_items.cu
+// All of w's layers must have table width jp (8, 16 or 32 floats).
+int launch_items(const ItemWork &w, int jp, const ItemConfig &cfg, are_precision prec,
+                 int num_sms, cudaStream_t s);
 
 // simulate.cu
 int launch_simulate(const SimArgs &a, are_precision prec, int jp, const TermsF32 *t32,
@@ -158,6 +223,11 @@ inline int select_max_blocks(int num_sms) { return num_sms * 4; }
 // result[2*t] = m-th largest value, result[2*t+1] = mean of the m largest.
 cudaError_t select_enqueue(const double *ylt, int64_t n, const int64_t *ranks, int nt,
                            const SelectScratch &s, cudaStream_t st);
+// The same for n_ylt YLTs of n losses each (device array of pointers); the
+// scratch must be sized by select_multi_bytes.  Results: result[(y*8+t)*2].
+size_t select_multi_bytes(int n_ylt, int64_t n, int num_sms);
+int launch_select_multi(const double *const *ylts, int n_ylt, int64_t n, const int64_t *ranks,
+                        int nt, void *scratch, int num_sms, cudaStream_t st, double **result);
 int launch_select(const double *ylt, int64_t n, const int64_t *ranks, int n_targets,
                    SelectScratch &s, int num_sms, cudaStream_t st);
 
@@ -183,4 +253,11 @@ struct are_ctx {
     are::SelectScratch sel;
     double *h_result = nullptr;  // pinned, 2 * kMaxTargets
     uint64_t launches = 0;       // kernels launched by this context
+    cudaStream_t capture = nullptr;           // stream used to capture plans
+    std::map<std::string, are::TuneEntry> tune;
+    std::vector<are::Plan> plans;
+    void *d_multi = nullptr;     // batched-selection scratch and pointer array
+    size_t multi_bytes = 0;
+    double *h_multi = nullptr;   // pinned results of a batched selection
+    size_t h_multi_count = 0;
 };

@@ -29,12 +29,14 @@ __global__ void k_scatter(T *__restrict__ tab, const ScatterArgs a)
 
 }  // namespace
 
-// Columns per row: J rounded up so a row fills whole 32-byte sectors.
+// Columns per row: J rounded up so a row fills whole 32-byte sectors; FP32
+// rows are 8, 16 or 32 floats (a power of two, so the lanes that share a row
+// pair up by halving), FP64 rows any multiple of 4 doubles.
 int table_jp(int n_elts, bool fp32)
 {
-    const int per_sector = fp32 ? 8 : 4;
-    int jp = (n_elts + per_sector - 1) / per_sector * per_sector;
-    return jp < per_sector ? per_sector : jp;
+    if (fp32) return n_elts <= 8 ? 8 : n_elts <= 16 ? 16 : 32;
+    int jp = (n_elts + 3) / 4 * 4;
+    return jp < 4 ? 4 : jp;
 }
 
 int launch_scatter_table(void *table, bool fp32, const ScatterArgs &a, cudaStream_t s)

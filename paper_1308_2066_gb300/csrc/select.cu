@@ -63,10 +63,30 @@ struct Ranks {
     long long m[kMaxTargets];
 };
 
+// Scratch of one selection over n_ylt YLTs (blockIdx.y or blockIdx.x picks
+// the YLT): per YLT 8 x 256 histogram words, 8 x (prefix, rank) state words,
+// blocks x 8 x 3 partial sums, 8 x 2 results.
+struct Sel {
+    const double *single;        // the YLT when there is one
+    const double *const *many;   // device array of YLT pointers, or nullptr
+    uint32_t *hist;
+    unsigned long long *state;
+    double *partial;
+    double *result;
+    int blocks;                  // blocks per YLT in the histogram and tail passes
+};
+__device__ __forceinline__ const double *ylt_of(const Sel &s, int y)
+{
+    return s.many ? s.many[y] : s.single;
+}
+
 // state[2t] = key prefix decided so far, state[2t+1] = rank still to find
 // among the keys that share the prefix (1 = the largest of them).
-__global__ void k_init(unsigned long long *state, uint32_t *hist, Ranks r, int nt)
+__global__ void k_init(Sel s, Ranks r, int nt)
 {
+    const int y = blockIdx.x;
+    uint32_t *hist = s.hist + (size_t)y * kMaxTargets * kBins;
+    unsigned long long *state = s.state + (size_t)y * 2 * kMaxTargets;
     for (int i = threadIdx.x; i < nt * kBins; i += blockDim.x) hist[i] = 0;
     if (threadIdx.x < nt) {
         state[2 * threadIdx.x] = 0ull;
@@ -74,10 +94,12 @@ __global__ void k_init(unsigned long long *state, uint32_t *hist, Ranks r, int n
     }
 }
 
-__global__ void __launch_bounds__(kThreads) k_hist(const double *__restrict__ y, int64_t n,
-                                                   const unsigned long long *__restrict__ state,
-                                                   int nt, int pass, uint32_t *hist)
+__global__ void __launch_bounds__(kThreads) k_hist(Sel s, int64_t n, int nt, int pass)
 {
+    const int y = blockIdx.y;
+    const double *__restrict__ v = ylt_of(s, y);
+    const unsigned long long *state = s.state + (size_t)y * 2 * kMaxTargets;
+    uint32_t *hist = s.hist + (size_t)y * kMaxTargets * kBins;
     __shared__ uint32_t h[kMaxTargets * kBins];
     for (int i = threadIdx.x; i < nt * kBins; i += blockDim.x) h[i] = 0;
     const int shift = 56 - 8 * pass;
@@ -87,7 +109,7 @@ __global__ void __launch_bounds__(kThreads) k_hist(const double *__restrict__ y,
     __syncthreads();
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        const uint64_t k = key_of(y[i]);
+        const uint64_t k = key_of(v[i]);
         const uint32_t d = (uint32_t)(k >> shift) & 0xffu;
 #pragma unroll
         for (int t = 0; t < kMaxTargets; ++t) {
@@ -102,12 +124,14 @@ __global__ void __launch_bounds__(kThreads) k_hist(const double *__restrict__ y,
 }
 
 // One warp per target: find the bucket that holds the wanted rank, descending.
-__global__ void k_pick(unsigned long long *state, uint32_t *hist, int nt, int pass)
+__global__ void k_pick(Sel s, int nt, int pass)
 {
+    const int y = blockIdx.x;
     const int t = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (t >= nt) return;
+    unsigned long long *state = s.state + (size_t)y * 2 * kMaxTargets;
     const int shift = 56 - 8 * pass;
-    uint32_t *h = hist + t * kBins;
+    uint32_t *h = s.hist + ((size_t)y * kMaxTargets + t) * kBins;
     uint32_t c[8];
     unsigned long long lane_sum = 0;
 #pragma unroll
@@ -144,10 +168,11 @@ __global__ void k_pick(unsigned long long *state, uint32_t *hist, int nt, int pa
 
 // Per block and target: compensated sum and count of the values whose key
 // is above the selected key.
-__global__ void __launch_bounds__(kThreads) k_tail(const double *__restrict__ y, int64_t n,
-                                                   const unsigned long long *__restrict__ state,
-                                                   int nt, double *partial)
+__global__ void __launch_bounds__(kThreads) k_tail(Sel s, int64_t n, int nt)
 {
+    const int y = blockIdx.y;
+    const double *__restrict__ v = ylt_of(s, y);
+    const unsigned long long *state = s.state + (size_t)y * 2 * kMaxTargets;
     uint64_t kt[kMaxTargets];
     DD acc[kMaxTargets];
     unsigned long long cnt[kMaxTargets];
@@ -158,12 +183,12 @@ __global__ void __launch_bounds__(kThreads) k_tail(const double *__restrict__ y,
     }
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        const double v = y[i];
-        const uint64_t k = key_of(v);
+        const double x = v[i];
+        const uint64_t k = key_of(x);
 #pragma unroll
         for (int t = 0; t < kMaxTargets; ++t)
             if (k > kt[t]) {
-                acc[t].add(v);
+                acc[t].add(x);
                 ++cnt[t];
             }
     }
@@ -187,53 +212,78 @@ __global__ void __launch_bounds__(kThreads) k_tail(const double *__restrict__ y,
     __syncthreads();
     if (threadIdx.x < nt) {
         const int t = threadIdx.x;
-        DD s;
+        DD sum;
         double c = 0.0;
         for (int i = 0; i < kThreads / 32; ++i) {
             DD o;
             o.hi = sh[i][t][0];
             o.lo = sh[i][t][1];
-            s.add(o);
+            sum.add(o);
             c += sh[i][t][2];
         }
-        double *p = partial + ((size_t)blockIdx.x * kMaxTargets + t) * 3;
-        p[0] = s.hi;
-        p[1] = s.lo;
+        double *p = s.partial + (((size_t)y * s.blocks + blockIdx.x) * kMaxTargets + t) * 3;
+        p[0] = sum.hi;
+        p[1] = sum.lo;
         p[2] = c;
     }
 }
 
 // One warp per target: adds the blocks' partial sums in block order, then
 // the ties at the selected value, and writes (value, mean of the m largest).
-__global__ void k_final(const unsigned long long *state, const double *partial, int n_blocks,
-                        Ranks r, int nt, double *result)
+__global__ void k_final(Sel s, Ranks r, int nt)
 {
+    const int y = blockIdx.x;
     const int t = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (t >= nt) return;
-    DD s;
+    const unsigned long long *state = s.state + (size_t)y * 2 * kMaxTargets;
+    DD sum;
     double c = 0.0;
-    for (int b = lane; b < n_blocks; b += 32) {
-        const double *p = partial + ((size_t)b * kMaxTargets + t) * 3;
+    for (int b = lane; b < s.blocks; b += 32) {
+        const double *p = s.partial + (((size_t)y * s.blocks + b) * kMaxTargets + t) * 3;
         DD o;
         o.hi = p[0];
         o.lo = p[1];
-        s.add(o);
+        sum.add(o);
         c += p[2];
     }
     for (int off = 16; off > 0; off >>= 1) {
         DD o;
-        o.hi = __shfl_down_sync(0xffffffffu, s.hi, off);
-        o.lo = __shfl_down_sync(0xffffffffu, s.lo, off);
+        o.hi = __shfl_down_sync(0xffffffffu, sum.hi, off);
+        o.lo = __shfl_down_sync(0xffffffffu, sum.lo, off);
         c += __shfl_down_sync(0xffffffffu, c, off);
-        s.add(o);
+        sum.add(o);
     }
     if (lane == 0) {
         const double v = value_of(state[2 * t]);
         const double m = (double)r.m[t];
-        s.add(__dmul_rn(m - c, v));
-        result[2 * t] = v;
-        result[2 * t + 1] = __ddiv_rn(__dadd_rn(s.hi, s.lo), m);
+        sum.add(__dmul_rn(m - c, v));
+        double *res = s.result + (size_t)y * 2 * kMaxTargets;
+        res[2 * t] = v;
+        res[2 * t + 1] = __ddiv_rn(__dadd_rn(sum.hi, sum.lo), m);
     }
+}
+
+cudaError_t enqueue(const Sel &s, int n_ylt, int64_t n, const int64_t *ranks, int nt,
+                    cudaStream_t st)
+{
+    Ranks r{};
+    for (int t = 0; t < nt; ++t) r.m[t] = ranks[t];
+    const dim3 grid((unsigned)s.blocks, (unsigned)n_ylt);
+    k_init<<<n_ylt, kThreads, 0, st>>>(s, r, nt);
+    for (int pass = 0; pass < 8; ++pass) {
+        k_hist<<<grid, kThreads, 0, st>>>(s, n, nt, pass);
+        k_pick<<<n_ylt, 32 * kMaxTargets, 0, st>>>(s, nt, pass);
+    }
+    k_tail<<<grid, kThreads, 0, st>>>(s, n, nt);
+    k_final<<<n_ylt, 32 * kMaxTargets, 0, st>>>(s, r, nt);
+    return cudaGetLastError();
+}
+
+int blocks_for(int64_t n, int cap)
+{
+    int64_t b = (n + kThreads * 8 - 1) / (kThreads * 8);
+    if (b > cap) b = cap;
+    return b < 1 ? 1 : (int)b;
 }
 
 }  // namespace
@@ -260,19 +310,8 @@ void select_free(SelectScratch &s)
 cudaError_t select_enqueue(const double *ylt, int64_t n, const int64_t *ranks, int nt,
                            const SelectScratch &s, cudaStream_t st)
 {
-    Ranks r{};
-    for (int t = 0; t < nt; ++t) r.m[t] = ranks[t];
-    int64_t blocks = (n + kThreads * 8 - 1) / (kThreads * 8);
-    if (blocks > s.max_blocks) blocks = s.max_blocks;
-    if (blocks < 1) blocks = 1;
-    k_init<<<1, kThreads, 0, st>>>(s.state, s.hist, r, nt);
-    for (int pass = 0; pass < 8; ++pass) {
-        k_hist<<<(unsigned)blocks, kThreads, 0, st>>>(ylt, n, s.state, nt, pass, s.hist);
-        k_pick<<<1, 32 * kMaxTargets, 0, st>>>(s.state, s.hist, nt, pass);
-    }
-    k_tail<<<(unsigned)blocks, kThreads, 0, st>>>(ylt, n, s.state, nt, s.partial);
-    k_final<<<1, 32 * kMaxTargets, 0, st>>>(s.state, s.partial, (int)blocks, r, nt, s.result);
-    return cudaGetLastError();
+    Sel sel{ylt, nullptr, s.hist, s.state, s.partial, s.result, blocks_for(n, s.max_blocks)};
+    return enqueue(sel, 1, n, ranks, nt, st);
 }
 
 int launch_select(const double *ylt, int64_t n, const int64_t *ranks, int nt, SelectScratch &s,
@@ -280,6 +319,45 @@ int launch_select(const double *ylt, int64_t n, const int64_t *ranks, int nt, Se
 {
     (void)num_sms;
     ARE_CUDA_TRY(select_enqueue(ylt, n, ranks, nt, s, st));
+    return kSelectLaunches;
+}
+
+namespace {
+int multi_blocks(int n_ylt, int64_t n, int num_sms)
+{
+    int cap = select_max_blocks(num_sms) / (n_ylt > 0 ? n_ylt : 1);
+    return blocks_for(n, cap < 1 ? 1 : cap);
+}
+size_t align256(size_t x) { return (x + 255) / 256 * 256; }
+}  // namespace
+
+size_t select_multi_bytes(int n_ylt, int64_t n, int num_sms)
+{
+    const size_t blocks = (size_t)multi_blocks(n_ylt, n, num_sms);
+    return align256(sizeof(uint32_t) * kMaxTargets * kBins * n_ylt) +
+           align256(sizeof(unsigned long long) * 2 * kMaxTargets * n_ylt) +
+           align256(sizeof(double) * 3 * kMaxTargets * blocks * n_ylt) +
+           align256(sizeof(double) * 2 * kMaxTargets * n_ylt);
+}
+
+int launch_select_multi(const double *const *ylts, int n_ylt, int64_t n, const int64_t *ranks,
+                        int nt, void *scratch, int num_sms, cudaStream_t st, double **result)
+{
+    const int blocks = multi_blocks(n_ylt, n, num_sms);
+    unsigned char *p = static_cast<unsigned char *>(scratch);
+    Sel sel;
+    sel.single = nullptr;
+    sel.many = ylts;
+    sel.blocks = blocks;
+    sel.hist = reinterpret_cast<uint32_t *>(p);
+    p += align256(sizeof(uint32_t) * kMaxTargets * kBins * n_ylt);
+    sel.state = reinterpret_cast<unsigned long long *>(p);
+    p += align256(sizeof(unsigned long long) * 2 * kMaxTargets * n_ylt);
+    sel.partial = reinterpret_cast<double *>(p);
+    p += align256(sizeof(double) * 3 * kMaxTargets * (size_t)blocks * n_ylt);
+    sel.result = reinterpret_cast<double *>(p);
+    *result = sel.result;
+    ARE_CUDA_TRY(enqueue(sel, n_ylt, n, ranks, nt, st));
     return kSelectLaunches;
 }
 

@@ -539,13 +539,14 @@ void launch_staged_fx(const SimArgs &a, const TermsF32 &terms, int num_sms, cuda
         launch_staged<JP, ACC, true>(a, terms, num_sms, s);
 }
 
-bool use_register_kernel()
+// The register kernel when asked for (kernel 2, or ARE_SIM_KERNEL=reg).
+bool use_register_kernel(const SimArgs &a)
 {
-    static const bool reg = [] {
+    static const bool env = [] {
         const char *v = getenv("ARE_SIM_KERNEL");
         return v && v[0] == 'r';
     }();
-    return reg;
+    return env || a.kernel == 2;
 }
 
 template <typename T, int JP, int ACC, bool FIXED, typename TT>
@@ -592,32 +593,28 @@ int launch_simulate(const SimArgs &a, are_precision prec, int jp, const TermsF32
         case 28: return launch_fx<double, 28, ARE_FP64>(a, *t64, num_sms, s), 1;
         case 32: return launch_fx<double, 32, ARE_FP64>(a, *t64, num_sms, s), 1;
         }
-    } else if (!use_register_kernel() && prec == ARE_FP32_KAHAN) {
+    } else if (!use_register_kernel(a) && prec == ARE_FP32_KAHAN) {
         switch (jp) {
         case 8: return launch_staged_fx<8, ARE_FP32_KAHAN>(a, *t32, num_sms, s), 1;
         case 16: return launch_staged_fx<16, ARE_FP32_KAHAN>(a, *t32, num_sms, s), 1;
-        case 24: return launch_staged_fx<24, ARE_FP32_KAHAN>(a, *t32, num_sms, s), 1;
         case 32: return launch_staged_fx<32, ARE_FP32_KAHAN>(a, *t32, num_sms, s), 1;
         }
-    } else if (!use_register_kernel() && prec == ARE_FP32_FP64AGG) {
+    } else if (!use_register_kernel(a) && prec == ARE_FP32_FP64AGG) {
         switch (jp) {
         case 8: return launch_staged_fx<8, ARE_FP32_FP64AGG>(a, *t32, num_sms, s), 1;
         case 16: return launch_staged_fx<16, ARE_FP32_FP64AGG>(a, *t32, num_sms, s), 1;
-        case 24: return launch_staged_fx<24, ARE_FP32_FP64AGG>(a, *t32, num_sms, s), 1;
         case 32: return launch_staged_fx<32, ARE_FP32_FP64AGG>(a, *t32, num_sms, s), 1;
         }
     } else if (prec == ARE_FP32_KAHAN) {
         switch (jp) {
         case 8: return launch_fx<float, 8, ARE_FP32_KAHAN>(a, *t32, num_sms, s), 1;
         case 16: return launch_fx<float, 16, ARE_FP32_KAHAN>(a, *t32, num_sms, s), 1;
-        case 24: return launch_fx<float, 24, ARE_FP32_KAHAN>(a, *t32, num_sms, s), 1;
         case 32: return launch_fx<float, 32, ARE_FP32_KAHAN>(a, *t32, num_sms, s), 1;
         }
     } else if (prec == ARE_FP32_FP64AGG) {
         switch (jp) {
         case 8: return launch_fx<float, 8, ARE_FP32_FP64AGG>(a, *t32, num_sms, s), 1;
         case 16: return launch_fx<float, 16, ARE_FP32_FP64AGG>(a, *t32, num_sms, s), 1;
-        case 24: return launch_fx<float, 24, ARE_FP32_FP64AGG>(a, *t32, num_sms, s), 1;
         case 32: return launch_fx<float, 32, ARE_FP32_FP64AGG>(a, *t32, num_sms, s), 1;
         }
     }

@@ -219,7 +219,7 @@ def paper_scale(n_trials: int = 1_000_000, k: int = 1000, catalog: int = 1_000_0
 
 def portfolio(n_trials: int = 200_000, mean_events: float = 1000.0, catalog: int = 1_000_000,
               n_layers: int = 64, pool: int = 256, max_j: int = 32,
-              timestamps: bool = False) -> Workload:
+              nnz_range: tuple = (5000, 50000), timestamps: bool = False) -> Workload:
     """Shared ragged YET (Poisson(1000) events per trial); 64 layers whose ELT
     counts are uniform on 1..32, drawn from a pool of 256 lognormal ELTs with
     5,000-50,000 entries.  Per-ELT deductible at a U(0,20) percentile and limit
@@ -231,7 +231,7 @@ def portfolio(n_trials: int = 200_000, mean_events: float = 1000.0, catalog: int
     ge = rng(2, 1)
     elts = []
     for _ in range(pool):
-        nnz = int(ge.integers(5000, 50001))
+        nnz = int(ge.integers(nnz_range[0], nnz_range[1] + 1))
         e = elt_lognormal(ge, catalog, nnz)
         percentile_terms(e, int(ge.integers(0, 201)), int(ge.integers(950, 1001)))
         elts.append(e)
