@@ -40,7 +40,8 @@ LEVELS = [0.99]
 PRECISION_NAMES = {0: "fp64", 1: "fp32_kahan", 2: "fp32_fp64agg"}
 DTYPES = {0: "f64", 1: "f32", 2: "f32"}
 FALLBACK_HBM_GBS = 6800.0
-SIM_SOURCE = os.path.join(ROOT, "paper_1308_2066_gb300", "csrc", "simulate.cu")
+SIM_SOURCES = [os.path.join(ROOT, "paper_1308_2066_gb300", "csrc", f)
+               for f in ("simulate.cu", "sim_items.cu")]
 
 
 def parse():
@@ -55,6 +56,11 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=10.0)
+    p.add_argument("--workload", choices=["paper_scale", "portfolio", "precision_stress",
+                                          "serving"], default="paper_scale")
+    p.add_argument("--rates", default="50,200,1000")
+    p.add_argument("--seconds-per-rate", type=float, default=8.0)
+    p.add_argument("--no-tune", action="store_true")
     return p.parse_args()
 
 
@@ -76,19 +82,23 @@ def hbm_peak():
 
 
 def sim_source_sha():
-    with open(SIM_SOURCE, "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()[:16]
+    """Hash of the analysis-stage kernel sources (ncu counters go stale with them)."""
+    h = hashlib.sha256()
+    for path in SIM_SOURCES:
+        with open(path, "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
 
 
 def ncu_traffic(kernel_key: str):
     """DRAM bytes per launch from a committed ncu summary, if it was taken on
-    the current simulate.cu (else None)."""
+    the current kernel sources (else None)."""
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
             rec = json.load(f).get(kernel_key)
     except (OSError, ValueError):
         return None
-    if not rec or rec.get("simulate_cu_sha") != sim_source_sha():
+    if not rec or rec.get("kernel_sources_sha") != sim_source_sha():
         return None
     return rec.get("dram_bytes_per_launch")
 
@@ -163,9 +173,23 @@ def algorithmic_bytes(n_events: int, n_trials: int, J: int, elem: int) -> int:
     return n_events * (4 + row) + 8 * n_trials
 
 
-def kernel_key(prec: int, J: int) -> str:
-    jp = math.ceil(J * (8 if prec == 0 else 4) / 32) * 32 // (8 if prec == 0 else 4)
-    return f"k_simulate<{'double' if prec == 0 else 'float'},{jp},{prec},fixed>"
+def items_bytes(wl) -> int:
+    """Algorithmic bytes of one pass over every layer of a workload."""
+    y = wl.yet
+    return sum(algorithmic_bytes(y.n_events, y.n_trials, len(L.elts), 4) for L in wl.layers)
+
+
+def kernel_key(prec: int, J: int, tuned=None) -> str:
+    """Name of the kernel that runs the analysis stage for this precision."""
+    if prec == 0:
+        return f"k_simulate<double,{math.ceil(J / 4) * 4},0,fixed>"
+    jp = 8 if J <= 8 else 16 if J <= 16 else 32
+    kind = (tuned or {}).get("kernel", 1)
+    if kind == 0:
+        return f"k_sim_items<{jp},{tuned.get('rows_in_flight')},{prec},fixed>"
+    if kind == 2:
+        return f"k_simulate<float,{jp},{prec},fixed>"
+    return f"k_simulate_staged<{jp},{prec},fixed>"
 
 
 class Resident:
@@ -241,15 +265,15 @@ def max_over_ranks(x: float, world: int, torch) -> float:
     return float(t.item())
 
 
-def roofline(n_events, n_trials, J, prec, sim_ms):
+def roofline(n_events, n_trials, J, prec, sim_ms, tuned=None):
     peak, src = hbm_peak()
     elem = 8 if prec == 0 else 4
     bytes_ = algorithmic_bytes(n_events, n_trials, J, elem)
     achieved = bytes_ / (sim_ms * 1e-3) / 1e9
-    traffic = ncu_traffic(kernel_key(prec, J))
+    traffic = ncu_traffic(kernel_key(prec, J, tuned))
     return {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
             "frac": round(achieved / peak, 4), "traffic": traffic,
-            "kernel": kernel_key(prec, J), "algorithmic_bytes_per_launch": bytes_,
+            "kernel": kernel_key(prec, J, tuned), "algorithmic_bytes_per_launch": bytes_,
             "peak_source": f"{src} HBM copy bandwidth",
             "note": ("algorithmic bytes = per event 4 B id + the event's table row in whole "
                      "32-B sectors, + 8 B per trial; the table rows are gathered from L2")}
@@ -355,11 +379,267 @@ def run_e2e(are, torch, ctx, wl, prec, steps, warmup, world):
 
 
 # ---------------------------------------------------------------------------
+# portfolio batching: 64 uneven layers over one ragged YET
+# ---------------------------------------------------------------------------
+
+def run_portfolio(args):
+    import torch
+    import paper_1308_2066_gb300 as are
+    rank, local_rank, world = dist_env()
+    torch.cuda.set_device(local_rank)
+    prec = {v: k for k, v in PRECISION_NAMES.items()}[args.precision]
+    wl = W.portfolio(n_trials=min(args.trials, 200_000))
+    y = wl.yet
+    ctx = are.are_create(local_rank)
+    ids = torch.from_numpy(y.ids).cuda()
+    off = torch.from_numpy(y.offsets).cuda()
+    yet = are.are_load_yet(ctx, y.catalog, y.n_trials, off, 0, ids)
+    del ids, off
+    elts = [are.are_load_elt(ctx, e.ids, e.losses, e.fx, e.ded, e.lim, e.share) for e in wl.elts]
+    layers = [are.are_define_layer(ctx, [elts[m] for m in L.elts], L.occ_r, L.occ_l, L.agg_r,
+                                   L.agg_l) for L in wl.layers]
+    n = y.n_trials
+    stream = torch.cuda.Stream()
+    outs = [torch.empty(n, dtype=torch.float64, device="cuda") for _ in layers]
+    tuned = None if args.no_tune else are.are_autotune(ctx, layers, yet, prec, stream)
+    lookups = sum(y.n_events * len(L.elts) for L in wl.layers)
+
+    def batched():
+        for h in layers:
+            are.are_prepare(ctx, h, yet, prec, stream)
+        are.are_simulate_portfolio(ctx, layers, yet, 0, n, prec, outs, stream)
+        return are.are_risk_measures_batch(ctx, outs, n, RPS, LEVELS, stream)
+
+    def plain():
+        for h, o in zip(layers, outs):
+            are.are_prepare(ctx, h, yet, prec, stream)
+            are.are_simulate(ctx, h, yet, 0, n, prec, o, stream)
+            are.are_risk_measures(ctx, o, n, RPS, LEVELS, stream)
+
+    def timed(fn, steps):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        l0 = are.are_launch_count(ctx)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with ClockSampler(local_rank) as clk:
+            a.record(stream)
+            for _ in range(steps):
+                fn()
+            b.record(stream)
+            b.synchronize()
+        return a.elapsed_time(b) / steps, are.are_launch_count(ctx) - l0, clk.summary()
+
+    # the persistent kernel alone (for the roofline)
+    sim = []
+    for _ in range(args.warmup + args.steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        are.are_simulate_portfolio(ctx, layers, yet, 0, n, prec, outs, stream)
+        e1.record(stream)
+        sim.append((e0, e1))
+    torch.cuda.synchronize()
+    sim_ms = float(np.mean([a.elapsed_time(b) for a, b in sim[args.warmup:]]))
+    ms_b, launches, clocks = timed(batched, args.steps)
+    ms_p, launches_p, _ = timed(plain, max(1, args.steps // 2))
+    pml, tv = batched()
+    peak, src = hbm_peak()
+    bytes_ = items_bytes(wl)
+    line = {
+        "metric": METRIC, "value": round(lookups / (ms_b * 1e-3) / 1e9, 3), "unit": UNIT,
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(ms_b, 4), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": DTYPES[prec],
+        "data": "synthetic: seeded ragged Poisson(1000) YET, lognormal ELT pool",
+        "config": {"workload": wl.name, "trials": n, "events": y.n_events, "layers": len(layers),
+                   "elts_per_layer": [len(L.elts) for L in wl.layers],
+                   "precision": PRECISION_NAMES[prec],
+                   "step": "repack 64 tables + one graph-replayed persistent launch + batched PML/TVaR",
+                   "l2": "inputs larger than L2 (0.8 GB YET streamed once per layer)"},
+        "roofline": {"bound": "hbm", "achieved": round(bytes_ / (sim_ms * 1e-3) / 1e9, 1),
+                     "peak": peak, "unit": "GB/s",
+                     "frac": round(bytes_ / (sim_ms * 1e-3) / 1e9 / peak, 4), "traffic": None,
+                     "kernel": "k_sim_items (all layers)", "algorithmic_bytes_per_launch": bytes_,
+                     "peak_source": f"{src} HBM copy bandwidth", "sim_ms": round(sim_ms, 4)},
+        "plain": {"ms_per_step": round(ms_p, 4),
+                  "value": round(lookups / (ms_p * 1e-3) / 1e9, 3),
+                  "gpu_launches": launches_p,
+                  "how": "64 x (repack + are_simulate + are_risk_measures)"},
+        "speedup_vs_plain": round(ms_p / ms_b, 3),
+        "tuned": tuned, "gpu_launches": launches, "clocks": clocks,
+        "pml_layer0": [float(x) for x in pml[0]], "tvar_layer0": [float(x) for x in tv[0]],
+    }
+    are.are_destroy(ctx)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# precision modes: 32 Pareto ELTs, long ragged trials, errors vs the oracle
+# ---------------------------------------------------------------------------
+
+def run_precision_stress(args):
+    import torch
+    import oracle
+    import paper_1308_2066_gb300 as are
+    torch.cuda.set_device(0)
+    wl = W.precision_stress(n_trials=min(args.trials, 1_000_000))
+    y = wl.yet
+    ctx = are.are_create(0)
+    ids = torch.from_numpy(y.ids).cuda()
+    off = torch.from_numpy(y.offsets).cuda()
+    yet = are.are_load_yet(ctx, y.catalog, y.n_trials, off, 0, ids)
+    del ids, off
+    elts = [are.are_load_elt(ctx, e.ids, e.losses, e.fx, e.ded, e.lim, e.share) for e in wl.elts]
+    L = wl.layers[0]
+    layer = are.are_define_layer(ctx, elts, L.occ_r, L.occ_l, L.agg_r, L.agg_l)
+    n = y.n_trials
+    stream = torch.cuda.Stream()
+    out = torch.empty(n, dtype=torch.float64, device="cuda")
+    sample = np.sort(np.random.default_rng(7).choice(n, 2000, replace=False))
+    ref = oracle.simulate_layer(wl, trials=sample)
+    rows = {}
+    for p in (0, 2, 1):
+        if not args.no_tune:
+            are.are_autotune(ctx, [layer], yet, p, stream)
+        evs = []
+        for _ in range(args.warmup + args.steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            are.are_simulate(ctx, layer, yet, 0, n, p, out, stream)
+            e1.record(stream)
+            evs.append((e0, e1))
+        torch.cuda.synchronize()
+        ms = float(np.mean([a.elapsed_time(b) for a, b in evs[args.warmup:]]))
+        got = out.cpu().numpy()
+        d = np.abs(got[sample] - ref.ylt)
+        rel = d / np.maximum(np.abs(ref.ylt), 1e-300)
+        pml, tv = are.are_risk_measures(ctx, out, n, RPS, LEVELS, stream)
+        # PML/TVaR of the oracle over the GPU's tail trials (the top 1.25 m)
+        m_max = oracle.rank_for_level(n, LEVELS[0])
+        cand = np.argsort(-got)[: m_max + m_max // 4]
+        rc = oracle.simulate_layer(wl, trials=np.sort(cand))
+        full = np.zeros(n)
+        full[np.sort(cand)] = rc.ylt
+        rp, rt = oracle.risk_measures(full, RPS, LEVELS)
+        rows[PRECISION_NAMES[p]] = {
+            "sim_ms": round(ms, 4),
+            "value": round(y.n_events * len(L.elts) / (ms * 1e-3) / 1e9, 3),
+            "ylt_rel_err_max": float(rel.max()), "ylt_rel_err_median": float(np.median(rel)),
+            "ylt_err_over_gross_max": float((d / ref.gross).max()),
+            "pml": [float(x) for x in pml], "pml_oracle": [float(x) for x in rp],
+            "pml_rel_err": [float(abs(a - b) / b) for a, b in zip(pml, rp)],
+            "tvar": [float(x) for x in tv], "tvar_oracle": [float(x) for x in rt],
+            "tvar_rel_err": [float(abs(a - b) / b) for a, b in zip(tv, rt)]}
+    head = rows[args.precision]
+    line = {"metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["sim_ms"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": DTYPES[{v: k for k, v in PRECISION_NAMES.items()}[args.precision]],
+            "data": "synthetic: ragged Poisson(1000)<=3000 YET over 2M events, 32 Pareto(1.3) ELTs",
+            "config": {"workload": wl.name, "trials": n, "events": y.n_events, "elts": len(L.elts),
+                       "sample_trials": int(sample.size)},
+            "precisions": rows}
+    are.are_destroy(ctx)
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# serving: Poisson stream of pricing requests over a resident YET and ELT pool
+# ---------------------------------------------------------------------------
+
+def serve_stream(are, ctx, hs, reqs, one_at_a_time, prec, k):
+    """Submit each request at its arrival time, collect every result; returns
+    per-request latencies (ms) and the wall time from first submit to last result."""
+    import queue
+    tickets = queue.Queue()
+    out = []
+    are.are_server_start(ctx, hs["yet"], max_inflight=32, max_pending=100000,
+                         arena_bytes=6 << 30, one_at_a_time=one_at_a_time, precision=prec)
+
+    def collect():
+        while True:
+            item = tickets.get()
+            if item is None:
+                return
+            r, t = item
+            res = are.are_wait(ctx, t, 600_000_000)
+            out.append((res["total_us"] / 1e3, res["status"], r, res))
+
+    th = threading.Thread(target=collect)
+    th.start()
+    t0 = time.perf_counter()
+    for r in reqs:
+        delay = r.arrival_s - (time.perf_counter() - t0)
+        if delay > 0:
+            time.sleep(delay)
+        L = r.layer
+        t = are.are_submit(ctx, [hs["elts"][m] for m in L.elts], L.occ_r, L.occ_l, L.agg_r,
+                           L.agg_l, r.n_trials, RPS, LEVELS)
+        tickets.put((r, t))
+    tickets.put(None)
+    th.join()
+    wall = time.perf_counter() - t0
+    are.are_server_stop(ctx)
+    lat = np.array([o[0] for o in out])
+    assert all(o[1] == 0 for o in out), "a request failed"
+    lookups = sum(r.n_trials * k * len(r.layer.elts) for r in reqs)
+    return {"requests": len(reqs), "p50_ms": round(float(np.percentile(lat, 50)), 3),
+            "p99_ms": round(float(np.percentile(lat, 99)), 3),
+            "mean_ms": round(float(lat.mean()), 3),
+            "throughput_req_s": round(len(reqs) / wall, 2),
+            "g_lookups_s": round(lookups / wall / 1e9, 2)}, out
+
+
+def run_serving(args):
+    import torch
+    import paper_1308_2066_gb300 as are
+    torch.cuda.set_device(0)
+    prec = {v: k for k, v in PRECISION_NAMES.items()}[args.precision]
+    wl = W.serving_pool(n_trials=min(args.trials, 1_000_000))
+    y = wl.yet
+    ctx = are.are_create(0)
+    ids = torch.from_numpy(y.ids).cuda()
+    hs = {"yet": are.are_load_yet(ctx, y.catalog, y.n_trials, None, y.k, ids)}
+    del ids
+    hs["elts"] = [are.are_load_elt(ctx, e.ids, e.losses, e.fx, e.ded, e.lim, e.share)
+                  for e in wl.elts]
+    pooled = np.concatenate([e.losses for e in wl.elts[:16]])
+    rows = {}
+    for i, rate in enumerate(float(x) for x in args.rates.split(",")):
+        n_req = int(min(2000, max(200, rate * args.seconds_per_rate)))
+        reqs = W.pricing_requests(n_req, rate, pool=len(wl.elts), max_trials=y.n_trials,
+                                  stream=10 + i, pooled_losses=pooled)
+        l0 = are.are_launch_count(ctx)
+        batched, _ = serve_stream(are, ctx, hs, reqs, False, prec, y.k)
+        batched["gpu_launches"] = are.are_launch_count(ctx) - l0
+        single, _ = serve_stream(are, ctx, hs, reqs, True, prec, y.k)
+        rows[str(int(rate))] = {"continuous_batching": batched, "one_request_per_launch": single}
+    head = rows.get("200", next(iter(rows.values())))["continuous_batching"]
+    line = {"metric": "p99 pricing latency", "value": head["p99_ms"], "unit": "ms",
+            "n_gpus": 1, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": DTYPES[prec],
+            "data": "synthetic: resident 1M x 1000 YET, 256 lognormal ELTs, Poisson arrivals",
+            "config": {"workload": wl.name, "request_trials": "log-uniform 1e4..1e6 (YET prefix)",
+                       "request_elts": "1..16 of the pool", "measures": "PML 100/250, TVaR 99",
+                       "precision": PRECISION_NAMES[prec], "headline_rate_req_s": 200},
+            "rates": rows}
+    are.are_destroy(ctx)
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
 
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "portfolio":
+        return run_portfolio(args)
+    if args.workload == "precision_stress":
+        return run_precision_stress(args)
+    if args.workload == "serving":
+        return run_serving(args)
     import torch
     import paper_1308_2066_gb300 as are
 
@@ -387,6 +667,10 @@ def main():
             return full
 
     paths = [prec] + ([] if args.no_variants else [p for p in (0, 2, 1) if p != prec])
+    tuned = {}
+    if not args.no_tune:
+        for p in paths:
+            tuned[PRECISION_NAMES[p]] = are.are_autotune(ctx, [res.layer], res.yet, p, stream)
     results = {}
     for p in paths:
         r = time_path(are, torch, res, p, args.steps, args.warmup, stream, ylt, gather, world)
@@ -416,7 +700,9 @@ def main():
                    "step": "repack table + simulate all trials + PML 100/250 + TVaR 99 readback",
                    "l2": "inputs larger than L2 (4 GB YET streamed every step)",
                    "parallelism": f"trial blocks per GPU x{world}"},
-        "roofline": roofline(y.n_events, y.n_trials, J, prec, head["sim_ms"]),
+        "roofline": roofline(y.n_events, y.n_trials, J, prec, head["sim_ms"],
+                             tuned.get(PRECISION_NAMES[prec])),
+        "tuned": tuned,
         "gpu_launches": head["launches"],
         "clocks": head["clocks"],
         "pml": head["pml"], "tvar": head["tvar"],
@@ -425,7 +711,8 @@ def main():
         PRECISION_NAMES[p]: {"ms_per_step": round(r["ms"] / args.steps, 4),
                              "sim_ms": round(r["sim_ms"], 4),
                              "value": round(lookups / (r["ms"] / args.steps * 1e-3) / 1e9, 3),
-                             "roofline": roofline(y.n_events, y.n_trials, J, p, r["sim_ms"]),
+                             "roofline": roofline(y.n_events, y.n_trials, J, p, r["sim_ms"],
+                                                  tuned.get(PRECISION_NAMES[p])),
                              "pml": r["pml"], "tvar": r["tvar"], "clocks": r["clocks"]}
         for p, r in results.items() if p != prec}
 

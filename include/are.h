@@ -196,9 +196,10 @@ ARE_API are_status are_simulate(are_ctx *ctx, int32_t layer, int32_t yet, int64_
 /* Analysis stage for n_layers layers over the same trials (the Basic
  * Algorithm's outer loop over layers; the portfolio analysis of Section IV).
  * ylts[i] (device memory, double[n_trials]) receives layer layers[i]'s YLT.
- * FP32 precisions run as persistent launches (one per table width) whose
- * warps claim (layer, trial tile) work items layer by layer; FP64 runs one
- * launch per layer.  The first call with a given set of layers, YET, trial
+ * With FP32 tables the tuned configuration decides between persistent
+ * launches (one per table width) whose warps claim (layer, trial tile) work
+ * items layer by layer, and one single-layer launch per layer, back to back;
+ * FP64 runs one launch per layer.  The first call with a given set of layers, YET, trial
  * range, precision, output pointers and tuned configuration builds the
  * layers' tables, a work list and a CUDA graph; identical later calls replay
  * the graph.  Replays of one plan must not overlap on the GPU. */
@@ -222,7 +223,8 @@ typedef struct {
 
 /* Time every candidate launch configuration on these layers and this YET
  * (one layer: the single-layer kernels and persistent-kernel settings;
- * several: the persistent kernel's rows in flight and trials per work item)
+ * several: back-to-back single-layer launches, or the persistent kernel with
+ * its rows in flight and trials per work item)
  * and keep the fastest for this kind of work: precision, YET layout, widest
  * table row, mean events per trial and one layer vs several.  Later
  * are_simulate and are_simulate_portfolio calls of that kind use it.
@@ -260,6 +262,73 @@ ARE_API are_status are_risk_measures_batch(are_ctx *ctx, const double *const *yl
                                            int64_t n, const double *return_periods, int32_t n_rp,
                                            double *pml_out, const double *tvar_levels,
                                            int32_t n_tv, double *tvar_out, void *stream);
+
+/* ------------------------------------------------------------------------ */
+/* Pricing server: continuous batching of requests                           */
+/* ------------------------------------------------------------------------ */
+
+/* The paper's real-time pricing scenario (Section I, Section IV: an
+ * underwriter prices a contract while on the phone) as a server over one
+ * resident YET and the context's resident ELTs.  A scheduler thread inside
+ * the library admits queued requests while request slots and arena memory
+ * are free, hands each iteration's budget of events_per_launch to the
+ * admitted requests in order of least remaining work (so few tables are
+ * live per launch and short requests overtake long ones), and runs all
+ * slices of an iteration in one persistent launch; a request arriving while
+ * others run joins at the next iteration.  When a request's last slice is done its PML/TVaR are
+ * selected and its result posted.  All device waits are bounded. */
+typedef struct {
+    int32_t max_inflight;      /* requests admitted at once, 1..256 */
+    int32_t max_pending;       /* queued requests; a submit beyond is ARE_EBUSY */
+    size_t arena_bytes;        /* device memory for admitted requests' tables and YLTs */
+    int64_t events_per_launch; /* events of one batched launch (0 = 2e8) */
+    int32_t trials_per_item;   /* trials per work item (0 = 8) */
+    int32_t one_at_a_time;     /* 1: no batching; each request runs alone, whole, in order */
+    are_precision precision;   /* ARE_FP32_KAHAN or ARE_FP32_FP64AGG */
+    int64_t stall_us;          /* test hook: the scheduler sleeps this long before each launch */
+} are_server_cfg;
+
+/* One pricing request: a layer of the context's ELTs with its own layer terms,
+ * priced over trials 0 .. n_trials-1 of the server's YET.  Everything is
+ * copied at submission. */
+typedef struct {
+    const int32_t *elt_handles;
+    int32_t n_elts;               /* 1 .. ARE_MAX_ELTS_PER_LAYER */
+    are_layer_terms terms;
+    int64_t n_trials;             /* 1 .. trials in the YET */
+    const double *return_periods; /* PML return periods, n_rp of them */
+    int32_t n_rp;
+    const double *tvar_levels;    /* TVaR levels, n_tv of them; n_rp + n_tv <= 8 */
+    int32_t n_tv;
+} are_request;
+
+typedef struct {
+    are_status status;   /* ARE_OK, or why the request failed */
+    int32_t n_rp, n_tv;
+    double pml[8];
+    double tvar[8];
+    int64_t n_trials;
+    double queue_us;     /* submission -> admission */
+    double run_us;       /* admission -> result posted */
+    double total_us;     /* submission -> result posted */
+} are_result;
+
+/* Start the server on `yet` (ARE_EBUSY if one runs).  While it runs the YET
+ * and every ELT cannot be freed. */
+ARE_API are_status are_server_start(are_ctx *ctx, int32_t yet, const are_server_cfg *cfg);
+/* Queue a request; *ticket identifies it.  ARE_EBUSY when max_pending
+ * requests are queued. */
+ARE_API are_status are_submit(are_ctx *ctx, const are_request *req, int64_t *ticket);
+/* Wait up to timeout_us (< 0: no limit) for a request's result and hand it
+ * over (a ticket's result can be taken once).  ARE_ETIMEOUT if it is not
+ * ready in time; ARE_ENOTFOUND for an unknown, taken or cancelled ticket. */
+ARE_API are_status are_wait(are_ctx *ctx, int64_t ticket, int64_t timeout_us, are_result *out);
+/* Cancel a queued or running request; its slot and memory are freed at the
+ * next launch boundary. */
+ARE_API are_status are_cancel(are_ctx *ctx, int64_t ticket);
+/* Finish the admitted requests, cancel the queued ones, stop the scheduler
+ * and free the server's memory. */
+ARE_API are_status are_server_stop(are_ctx *ctx);
 
 /* ------------------------------------------------------------------------ */
 /* Allocation-free PML/TVaR                                                  */

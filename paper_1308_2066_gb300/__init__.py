@@ -50,6 +50,25 @@ class LayerTerms(C.Structure):
                 ("agg_lim", C.c_double)]
 
 
+class ServerCfg(C.Structure):
+    _fields_ = [("max_inflight", C.c_int32), ("max_pending", C.c_int32),
+                ("arena_bytes", C.c_size_t), ("events_per_launch", C.c_int64),
+                ("trials_per_item", C.c_int32), ("one_at_a_time", C.c_int32),
+                ("precision", C.c_int), ("stall_us", C.c_int64)]
+
+
+class Request(C.Structure):
+    _fields_ = [("elt_handles", C.c_void_p), ("n_elts", C.c_int32), ("terms", LayerTerms),
+                ("n_trials", C.c_int64), ("return_periods", C.c_void_p), ("n_rp", C.c_int32),
+                ("tvar_levels", C.c_void_p), ("n_tv", C.c_int32)]
+
+
+class Result(C.Structure):
+    _fields_ = [("status", C.c_int32), ("n_rp", C.c_int32), ("n_tv", C.c_int32),
+                ("pml", C.c_double * 8), ("tvar", C.c_double * 8), ("n_trials", C.c_int64),
+                ("queue_us", C.c_double), ("run_us", C.c_double), ("total_us", C.c_double)]
+
+
 _lib = None
 _P = C.c_void_p
 _SIGS = {
@@ -82,6 +101,11 @@ _SIGS = {
                                  C.POINTER(TuneResult)]),
     "are_tune_save": (C.c_int32, [_P, C.c_char_p]),
     "are_tune_load": (C.c_int32, [_P, C.c_char_p]),
+    "are_server_start": (C.c_int32, [_P, C.c_int32, C.POINTER(ServerCfg)]),
+    "are_submit": (C.c_int32, [_P, C.POINTER(Request), C.POINTER(C.c_int64)]),
+    "are_wait": (C.c_int32, [_P, C.c_int64, C.c_int64, C.POINTER(Result)]),
+    "are_cancel": (C.c_int32, [_P, C.c_int64]),
+    "are_server_stop": (C.c_int32, [_P]),
 }
 
 
@@ -305,3 +329,46 @@ def are_tune_save(ctx, path: str) -> None:
 
 def are_tune_load(ctx, path: str) -> None:
     _check(ctx, lib().are_tune_load(ctx, os.fsencode(path)))
+
+
+# ---------------------------------------------------------------------------
+# pricing server
+# ---------------------------------------------------------------------------
+
+def are_server_start(ctx, yet: int, max_inflight: int = 32, max_pending: int = 4096,
+                     arena_bytes: int = 4 << 30, events_per_launch: int = 0,
+                     trials_per_item: int = 0, one_at_a_time: bool = False,
+                     precision: int = ARE_FP32_KAHAN, stall_us: int = 0) -> None:
+    cfg = ServerCfg(max_inflight, max_pending, arena_bytes, events_per_launch, trials_per_item,
+                    int(bool(one_at_a_time)), precision, stall_us)
+    _check(ctx, lib().are_server_start(ctx, int(yet), C.byref(cfg)))
+
+
+def are_submit(ctx, elt_handles: Sequence[int], occ_ret: float, occ_lim: float, agg_ret: float,
+               agg_lim: float, n_trials: int, return_periods: Sequence[float] = (100.0, 250.0),
+               tvar_levels: Sequence[float] = (0.99,)) -> int:
+    hs = np.ascontiguousarray(elt_handles, dtype=np.int32)
+    rp = np.ascontiguousarray(return_periods, dtype=np.float64)
+    lv = np.ascontiguousarray(tvar_levels, dtype=np.float64)
+    req = Request(hs.ctypes.data, hs.shape[0], LayerTerms(occ_ret, occ_lim, agg_ret, agg_lim),
+                  int(n_trials), rp.ctypes.data, rp.shape[0], lv.ctypes.data, lv.shape[0])
+    t = C.c_int64()
+    _check(ctx, lib().are_submit(ctx, C.byref(req), C.byref(t)))
+    return t.value
+
+
+def are_wait(ctx, ticket: int, timeout_us: int = -1) -> dict:
+    """The request's result: status, pml, tvar, n_trials and its timings (us)."""
+    r = Result()
+    _check(ctx, lib().are_wait(ctx, int(ticket), int(timeout_us), C.byref(r)))
+    return {"status": r.status, "pml": list(r.pml[: r.n_rp]), "tvar": list(r.tvar[: r.n_tv]),
+            "n_trials": r.n_trials, "queue_us": r.queue_us, "run_us": r.run_us,
+            "total_us": r.total_us}
+
+
+def are_cancel(ctx, ticket: int) -> None:
+    _check(ctx, lib().are_cancel(ctx, int(ticket)))
+
+
+def are_server_stop(ctx) -> None:
+    _check(ctx, lib().are_server_stop(ctx))

@@ -272,6 +272,8 @@ int run_single(are_ctx *ctx, const Layer &L, const Yet &y, int64_t trial_begin, 
         ItemWork w = item_work(y, trial_begin, n_trials, te.cfg);
         fill_layer_f32(ctx, L, w.one);
         w.one.ylt = d_out;
+        w.one.t0 = 0;
+        w.one.nt = n_trials;
         w.n_layers = 1;
         w.n_items = (n_trials + w.trials_per_item - 1) / w.trials_per_item;
         return launch_items(w, L.t32.jp, te.cfg, precision, ctx->num_sms, s);
@@ -374,6 +376,8 @@ Groups group_layers(are_ctx *ctx, const std::vector<int32_t> &layers,
         int64_t next = 0;
         for (LayerF32 &r : g.rec[gi]) {
             r.item_begin = next;
+            r.t0 = 0;
+            r.nt = n_trials;
             next += per_layer;
         }
         g.offset[gi] = off;
@@ -393,7 +397,8 @@ int enqueue_multi(are_ctx *ctx, const std::vector<int32_t> &layers,
                   void *d_work, cudaStream_t s)
 {
     int launches = 0;
-    if (prec == ARE_FP64) {
+    if (prec == ARE_FP64 || te.kernel != 0) {
+        // one single-layer launch per layer, back to back (one table hot in L2 at a time)
         for (size_t i = 0; i < layers.size(); ++i)
             launches += run_single(ctx, ctx->layers.at(layers[i]), y, trial_begin, n_trials, prec,
                                    ylts[i], te, s);
@@ -447,6 +452,10 @@ int max_width(are_ctx *ctx, const int32_t *layers, int32_t n_layers, bool fp32)
 }
 
 }  // namespace
+
+void *ctx_alloc(are_ctx *ctx, size_t bytes) { return dalloc(ctx, bytes); }
+void ctx_free(are_ctx *ctx, void *p, size_t bytes) { dfree(ctx, p, bytes); }
+
 }  // namespace are
 
 using namespace are;
@@ -486,6 +495,7 @@ are_status are_create(are_ctx **out, int device, size_t mem_budget_bytes)
 are_status are_destroy(are_ctx *ctx)
 {
     if (!ctx) return ARE_OK;
+    server_destroy(ctx);   // before taking the lock: its thread may be waiting for it
     {
         std::lock_guard<std::recursive_mutex> lock(ctx->mu);
         cudaSetDevice(ctx->device);
@@ -692,6 +702,7 @@ are_status are_free_yet(are_ctx *ctx, int32_t h)
 {
     return guarded(ctx, [&] {
         Yet &y = yet_of(ctx, h);
+        ARE_CHECK(!ctx->server, ARE_EBUSY, "a pricing server is running on this context");
         ARE_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
         dfree(ctx, y.d_ids, y.bytes);
         dfree(ctx, y.d_off, y.d_off ? sizeof(int64_t) * (y.n_trials + 1) : 0);
@@ -705,6 +716,7 @@ are_status are_free_elt(are_ctx *ctx, int32_t h)
         auto it = ctx->elts.find(h);
         ARE_CHECK(it != ctx->elts.end(), ARE_ENOTFOUND, "unknown ELT handle " + std::to_string(h));
         ARE_CHECK(it->second.users == 0, ARE_EINVAL, "ELT is used by a layer");
+        ARE_CHECK(!ctx->server, ARE_EBUSY, "a pricing server is running on this context");
         dfree(ctx, it->second.d_ids, sizeof(int32_t) * it->second.n);
         dfree(ctx, it->second.d_loss, sizeof(double) * it->second.n);
         ctx->elts.erase(it);
@@ -861,7 +873,7 @@ are_status are_simulate_portfolio(are_ctx *ctx, const int32_t *layers, int32_t n
             p.cfg = te.cfg;
             try {
                 Groups g;
-                if (fp32) {
+                if (fp32 && te.kernel == 0) {
                     g = group_layers(ctx, lv, yv, n_trials,
                                      te.cfg.trials_per_item > 0 ? te.cfg.trials_per_item : 8);
                     p.work_bytes = g.bytes;
@@ -879,7 +891,7 @@ are_status are_simulate_portfolio(are_ctx *ctx, const int32_t *layers, int32_t n
                 int launches = 0;
                 try {
                     launches = enqueue_multi(ctx, lv, yv, y, trial_begin, n_trials, precision, te,
-                                             fp32 ? &g : nullptr, p.d_work, ctx->capture);
+                                             &g, p.d_work, ctx->capture);
                 } catch (...) {
                     cudaGraph_t dead = nullptr;
                     cudaStreamEndCapture(ctx->capture, &dead);
@@ -984,8 +996,13 @@ are_status are_autotune(are_ctx *ctx, const int32_t *layers, int32_t n_layers, i
                 e.kernel = 2;
                 cands.push_back(e);
             }
+            if (multi) {
+                TuneEntry e;
+                e.kernel = 1;
+                cands.push_back(e);
+            }
             for (int u : {4, 8})
-                for (int tpi : multi ? std::vector<int>{2, 4, 8, 16, 32} : std::vector<int>{2, 8}) {
+                for (int tpi : multi ? std::vector<int>{2, 4, 8, 16} : std::vector<int>{2, 8}) {
                     TuneEntry e;
                     e.kernel = 0;
                     e.cfg.rows_in_flight = u;
@@ -1012,7 +1029,7 @@ are_status are_autotune(are_ctx *ctx, const int32_t *layers, int32_t n_layers, i
             for (int32_t i = 0; i < n_layers; ++i) yv.push_back(outs + (size_t)i * y.n_trials);
             for (TuneEntry &c : cands) {
                 Groups g;
-                if (fp32) {
+                if (fp32 && c.kernel == 0) {
                     g = group_layers(ctx, lv, yv, y.n_trials, c.cfg.trials_per_item);
                     if (work_bytes < g.bytes) {
                         ARE_CUDA_TRY(cudaStreamSynchronize(cs.s));
@@ -1032,7 +1049,7 @@ are_status are_autotune(are_ctx *ctx, const int32_t *layers, int32_t n_layers, i
                 auto run = [&] {
                     if (multi)
                         ctx->launches += enqueue_multi(ctx, lv, yv, y, 0, y.n_trials, precision, c,
-                                                       fp32 ? &g : nullptr, work, cs.s);
+                                                       &g, work, cs.s);
                     else
                         ctx->launches += run_single(ctx, ctx->layers.at(lv[0]), y, 0, y.n_trials,
                                                     precision, yv[0], c, cs.s);

@@ -23,6 +23,12 @@ constexpr int kMaxTargets = 8;  // PML/TVaR ranks selected in one pass
 
 void set_error(const are_ctx *ctx, const std::string &msg);
 
+struct Server;
+// Device allocation charged to the context's budget (throws Error).
+void *ctx_alloc(are_ctx *ctx, size_t bytes);
+void ctx_free(are_ctx *ctx, void *p, size_t bytes);
+void server_destroy(are_ctx *ctx);   // stops and frees a running server
+
 struct Error {
     are_status code;
     std::string msg;
@@ -128,6 +134,7 @@ struct LayerF32 {
     int32_t jp;              // 8, 16 or 32
     int32_t any_share;
     int64_t item_begin;      // index of the layer's first work item
+    int64_t t0, nt;          // the layer's trials: t0 .. t0 + nt - 1 (ylt indexed by trial)
 };
 
 // Work of a persistent launch: every layer's trials cut into items of
@@ -260,4 +267,5 @@ struct are_ctx {
     size_t multi_bytes = 0;
     double *h_multi = nullptr;   // pinned results of a batched selection
     size_t h_multi_count = 0;
+    are::Server *server = nullptr;  // running pricing server, if any
 };

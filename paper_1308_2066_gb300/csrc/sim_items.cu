@@ -239,9 +239,9 @@ __global__ void __launch_bounds__(256) k_sim_items(const __grid_constant__ ItemW
             }
         }
         const LayerF32 &L = w.layers ? w.layers[lo] : w.one;
-        const int64_t t0 = (int64_t)(item - L.item_begin) * w.trials_per_item;
+        const int64_t t0 = L.t0 + (int64_t)(item - L.item_begin) * w.trials_per_item;
         int64_t t1 = t0 + w.trials_per_item;
-        if (t1 > w.n_trials) t1 = w.n_trials;
+        if (t1 > L.t0 + L.nt) t1 = L.t0 + L.nt;
         run_item<JP, U, ACC, FIXED>(w, L, t0, t1, lane);
     }
 }

@@ -79,3 +79,31 @@ def test_missing_library_fails_loudly(tmp_path, monkeypatch):
     monkeypatch.setattr(are, "LIB_PATH", str(tmp_path / "libare.so"))
     with pytest.raises(RuntimeError, match="missing"):
         are.lib()
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """Compile a C program that prints sizeof/offsetof of every public struct
+    and compare with the binding's ctypes definitions."""
+    import paper_1308_2066_gb300 as are
+    if shutil.which("gcc") is None:
+        pytest.skip("gcc not available")
+    structs = {"are_fin_terms": are.FinTerms, "are_layer_terms": are.LayerTerms,
+               "are_tune_result": are.TuneResult, "are_server_cfg": are.ServerCfg,
+               "are_request": are.Request, "are_result": are.Result}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "are.h"', "int main(void){"]
+    for cname, cls in structs.items():
+        lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f, _ in cls._fields_:
+            lines.append(f'printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
+    lines.append("return 0;}")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    import subprocess
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    out = subprocess.check_output([str(exe)], text=True).split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for cname, cls in structs.items():
+        assert got[(cname, "size")] == C.sizeof(cls), cname
+        for f, _ in cls._fields_:
+            assert got[(cname, f)] == getattr(cls, f).offset, (cname, f)

@@ -118,7 +118,7 @@ def test_autotune_and_tuning_file(are, ctx, loaded, tmp_path, precision):
     L, refs = loaded
     n = L.wl.yet.n_trials
     multi = are.are_autotune(ctx, L.layers, L.yet, precision)
-    assert multi["kernel"] == 0 and multi["ms"] > 0 and multi["trials_per_item"] > 0
+    assert multi["kernel"] in (0, 1) and multi["ms"] > 0 and multi["trials_per_item"] > 0
     single = are.are_autotune(ctx, L.layers[:1], L.yet, precision)
     assert single["kernel"] in (0, 1, 2) and single["ms"] > 0
     outs = device_ylts(len(L.layers), n)

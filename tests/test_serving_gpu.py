@@ -1,0 +1,187 @@
+"""The pricing server (continuous batching) through the C ABI: results
+against the oracle, the same alone and in a mix, memory-based admission,
+one-at-a-time mode, bounded waits, cancellation, a full queue and argument
+errors.  Faults are injected on the host only (a stalled scheduler, a
+cancelled request); nothing here makes the GPU fault or hang."""
+import math
+import time
+
+import numpy as np
+import pytest
+
+import workloads as W
+from gpu_support import rel_close
+
+pytestmark = pytest.mark.gpu
+N_TRIALS, K, CATALOG = 20_000, 100, 20_000
+RPS, LEVELS = (100.0, 250.0, 20.0), (0.99, 0.9)
+
+
+@pytest.fixture(scope="module")
+def are():
+    import torch
+    assert torch.cuda.is_available()
+    import paper_1308_2066_gb300 as are
+    are.lib()
+    return are
+
+
+@pytest.fixture(scope="module")
+def pool():
+    g = np.random.Generator(np.random.PCG64(44))
+    yet = W.yet_fixed(g, N_TRIALS, K, CATALOG, timestamps=False)
+    elts = [W.percentile_terms(W.elt_lognormal(g, CATALOG, int(g.integers(300, 1500))))
+            for _ in range(24)]
+    return yet, elts
+
+
+@pytest.fixture()
+def served(are, pool):
+    """A context with the pool loaded; yields (ctx, yet handle, elt handles)."""
+    yet, elts = pool
+    ctx = are.are_create(0)
+    y = are.are_load_yet(ctx, CATALOG, N_TRIALS, None, K, yet.ids)
+    hs = [are.are_load_elt(ctx, e.ids, e.losses, e.fx, e.ded, e.lim, e.share) for e in elts]
+    yield ctx, y, hs
+    are.are_destroy(ctx)
+
+
+def requests(seed, n, max_j=16):
+    g = np.random.default_rng(seed)
+    out = []
+    for _ in range(n):
+        j = int(g.integers(1, max_j + 1))
+        members = [int(x) for x in g.choice(24, j, replace=False)]
+        occ_r = float(g.uniform(1e4, 1e5))
+        out.append(dict(members=members, occ_r=occ_r, occ_l=occ_r * float(g.uniform(5, 50)),
+                        agg_r=occ_r * float(g.uniform(1, 4)),
+                        agg_l=float(g.choice([math.inf, occ_r * 200])),
+                        n_trials=int(g.integers(500, N_TRIALS + 1))))
+    return out
+
+
+def submit(are, ctx, hs, r):
+    return are.are_submit(ctx, [hs[m] for m in r["members"]], r["occ_r"], r["occ_l"], r["agg_r"],
+                          r["agg_l"], r["n_trials"], RPS, LEVELS)
+
+
+def oracle_measures(orc, pool, r):
+    yet, elts = pool
+    wl = W.Workload("req", yet, elts, [W.Layer(r["members"], r["occ_r"], r["occ_l"], r["agg_r"],
+                                               r["agg_l"])])
+    res = orc.simulate_layer(wl, trials=np.arange(r["n_trials"]))
+    return orc.risk_measures(res.ylt, RPS, LEVELS)
+
+
+def test_results_match_oracle_in_a_mix(are, orc, pool, served):
+    ctx, y, hs = served
+    are.are_server_start(ctx, y, max_inflight=8, events_per_launch=3_000_000)
+    reqs = requests(1, 30)
+    tickets = [submit(are, ctx, hs, r) for r in reqs]
+    for r, t in zip(reqs, tickets):
+        res = are.are_wait(ctx, t, 60_000_000)
+        assert res["status"] == are.ARE_OK and res["n_trials"] == r["n_trials"]
+        pml, tv = oracle_measures(orc, pool, r)
+        assert rel_close(res["pml"], pml, 1e-5), (res["pml"], pml)
+        assert rel_close(res["tvar"], tv, 1e-5), (res["tvar"], tv)
+        assert res["total_us"] >= res["run_us"] >= 0 and res["queue_us"] >= 0
+    are.are_server_stop(ctx)
+
+
+def test_same_result_alone_and_in_the_mix(are, served):
+    ctx, y, hs = served
+    probe = requests(7, 1)[0]
+    are.are_server_start(ctx, y, max_inflight=1)
+    alone = are.are_wait(ctx, submit(are, ctx, hs, probe), 60_000_000)
+    are.are_server_stop(ctx)
+    # many small launches, the probe surrounded by other requests
+    are.are_server_start(ctx, y, max_inflight=16, events_per_launch=400_000, trials_per_item=4)
+    others = requests(8, 40)
+    tickets = [submit(are, ctx, hs, r) for r in others[:20]]
+    tp = submit(are, ctx, hs, probe)
+    tickets += [submit(are, ctx, hs, r) for r in others[20:]]
+    mixed = are.are_wait(ctx, tp, 60_000_000)
+    for t in tickets:
+        assert are.are_wait(ctx, t, 60_000_000)["status"] == are.ARE_OK
+    are.are_server_stop(ctx)
+    assert alone["pml"] == mixed["pml"] and alone["tvar"] == mixed["tvar"]
+    # and the same again when every request runs alone, whole, in order
+    are.are_server_start(ctx, y, max_inflight=4, one_at_a_time=True)
+    seq = are.are_wait(ctx, submit(are, ctx, hs, probe), 60_000_000)
+    are.are_server_stop(ctx)
+    assert seq["pml"] == alone["pml"] and seq["tvar"] == alone["tvar"]
+
+
+def test_admission_by_memory(are, served):
+    ctx, y, hs = served
+    table16 = CATALOG * 16 * 4
+    # room for one 16-wide table and its YLT at a time
+    are.are_server_start(ctx, y, max_inflight=8, arena_bytes=table16 + 8 * N_TRIALS + 4096)
+    reqs = [dict(r, members=r["members"][:16]) for r in requests(3, 6)]
+    tickets = [submit(are, ctx, hs, r) for r in reqs]
+    out = [are.are_wait(ctx, t, 60_000_000) for t in tickets]
+    assert all(o["status"] == are.ARE_OK for o in out)
+    are.are_server_stop(ctx)
+
+
+def test_bounded_wait_cancel_and_full_queue(are, served):
+    ctx, y, hs = served
+    are.are_server_start(ctx, y, max_inflight=2, max_pending=3, stall_us=300_000)
+    r = requests(5, 6)
+    t0 = submit(are, ctx, hs, r[0])
+    with pytest.raises(are.AreError) as e:
+        are.are_wait(ctx, t0, 1000)                     # the scheduler stalls: times out
+    assert e.value.status == are.ARE_ETIMEOUT
+    t1, t2, t3 = (submit(are, ctx, hs, x) for x in r[1:4])
+    busy = None
+    for x in r[4:]:
+        try:
+            submit(are, ctx, hs, x)
+        except are.AreError as err:
+            busy = err
+    assert busy is not None and busy.status == are.ARE_EBUSY
+    are.are_cancel(ctx, t3)
+    with pytest.raises(are.AreError) as e:
+        are.are_wait(ctx, t3, 0)
+    assert e.value.status == are.ARE_ENOTFOUND
+    for t in (t0, t1, t2):
+        assert are.are_wait(ctx, t, 120_000_000)["status"] == are.ARE_OK
+    with pytest.raises(are.AreError):
+        are.are_wait(ctx, t0, 0)                        # a result is handed over once
+    are.are_server_stop(ctx)
+
+
+def test_server_argument_errors(are, served):
+    ctx, y, hs = served
+    with pytest.raises(are.AreError):
+        are.are_submit(ctx, [hs[0]], 0, 1, 0, 1, 10)   # no server yet
+    are.are_server_start(ctx, y, max_inflight=2)
+    with pytest.raises(are.AreError) as e:
+        are.are_server_start(ctx, y)
+    assert e.value.status == are.ARE_EBUSY
+    for bad in (dict(elts=[hs[0]], n=N_TRIALS + 1), dict(elts=[hs[0], hs[0]], n=10),
+                dict(elts=[999999], n=10)):
+        with pytest.raises(are.AreError):
+            are.are_submit(ctx, bad["elts"], 0, math.inf, 0, math.inf, bad["n"])
+    with pytest.raises(are.AreError):
+        are.are_submit(ctx, [hs[0]], 0, 1, 0, 1, 10, [2.0] * 5, [0.5] * 4)
+    with pytest.raises(are.AreError) as e:
+        are.are_free_yet(ctx, y)
+    assert e.value.status == are.ARE_EBUSY
+    t = are.are_submit(ctx, [hs[1]], 0, math.inf, 0, math.inf, 5000)
+    assert are.are_wait(ctx, t, 60_000_000)["status"] == are.ARE_OK
+    are.are_server_stop(ctx)
+    are.are_free_yet(ctx, y)
+
+
+def test_stop_drops_queued_requests(are, served):
+    ctx, y, hs = served
+    are.are_server_start(ctx, y, max_inflight=1, stall_us=200_000)
+    tickets = [submit(are, ctx, hs, r) for r in requests(9, 5)]
+    time.sleep(0.05)
+    are.are_server_stop(ctx)           # finishes what was admitted, drops the queue
+    are.are_server_start(ctx, y, max_inflight=2)
+    with pytest.raises(are.AreError) as e:
+        are.are_wait(ctx, tickets[-1], 0)
+    assert e.value.status == are.ARE_ENOTFOUND
+    are.are_server_stop(ctx)
