@@ -214,7 +214,8 @@ ARE_API are_status are_simulate_portfolio(are_ctx *ctx, const int32_t *layers, i
 
 /* The launch configuration the autotuner picked for one kind of work. */
 typedef struct {
-    int32_t kernel;          /* 0 persistent work items, 1 staged rows, 2 register rows */
+    int32_t kernel;          /* 0 persistent work items, 1 staged rows (one event per lane),
+                                2 register rows */
     int32_t rows_in_flight;  /* table rows each lane keeps in flight (persistent kernel) */
     int32_t trials_per_item; /* trials per work item (persistent kernel) */
     int32_t blocks_per_sm;   /* 0 = as many as fit */
@@ -236,6 +237,22 @@ ARE_API are_status are_autotune(are_ctx *ctx, const int32_t *layers, int32_t n_l
 /* Write / read the context's tuning table (one JSON object per line). */
 ARE_API are_status are_tune_save(are_ctx *ctx, const char *path);
 ARE_API are_status are_tune_load(are_ctx *ctx, const char *path);
+
+/* The same analysis stage with per-occurrence outputs (step 4 of the
+ * Basic Algorithm before its final sum): for every event occurrence of the
+ * trials, in stored order, marginals[e - first] = m_d = A_d - A_{d-1}, the
+ * aggregate-clamped running total's increment at that occurrence (the
+ * year-event loss table of the layer), where `first` is the first event of
+ * trial trial_begin; occ_max[i] (may be NULL) = the largest occurrence loss
+ * (after occurrence terms) of trial trial_begin + i, the input of an
+ * occurrence-exceedance PML; ylt[i] (may be NULL) = the trial loss.  All
+ * three are device memory.  The running totals come from warp-shuffle
+ * prefix scans; the precision argument selects the table and term
+ * arithmetic as for are_simulate, the running totals are FP64. */
+ARE_API are_status are_simulate_occurrences(are_ctx *ctx, int32_t layer, int32_t yet,
+                                            int64_t trial_begin, int64_t n_trials,
+                                            are_precision precision, double *marginals,
+                                            double *occ_max, double *ylt, void *stream);
 
 /* ------------------------------------------------------------------------ */
 /* Filters on the YLT (Section II-C): PML and TVaR                           */

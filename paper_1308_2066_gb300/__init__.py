@@ -101,6 +101,8 @@ _SIGS = {
                                  C.POINTER(TuneResult)]),
     "are_tune_save": (C.c_int32, [_P, C.c_char_p]),
     "are_tune_load": (C.c_int32, [_P, C.c_char_p]),
+    "are_simulate_occurrences": (C.c_int32, [_P, C.c_int32, C.c_int32, C.c_int64, C.c_int64,
+                                             C.c_int, _P, _P, _P, _P]),
     "are_server_start": (C.c_int32, [_P, C.c_int32, C.POINTER(ServerCfg)]),
     "are_submit": (C.c_int32, [_P, C.POINTER(Request), C.POINTER(C.c_int64)]),
     "are_wait": (C.c_int32, [_P, C.c_int64, C.c_int64, C.POINTER(Result)]),
@@ -254,6 +256,17 @@ def are_simulate(ctx, layer: int, yet: int, trial_begin: int, n_trials: int,
                  precision: int, ylt, stream=None) -> None:
     _check(ctx, lib().are_simulate(ctx, int(layer), int(yet), int(trial_begin), int(n_trials),
                                    int(precision), _addr(ylt, np.float64), _stream(stream)))
+
+
+def are_simulate_occurrences(ctx, layer: int, yet: int, trial_begin: int, n_trials: int,
+                             precision: int, marginals, occ_max=None, ylt=None,
+                             stream=None) -> None:
+    """Per-occurrence marginals, per-trial occurrence maxima and the YLT."""
+    _check(ctx, lib().are_simulate_occurrences(ctx, int(layer), int(yet), int(trial_begin),
+                                               int(n_trials), int(precision),
+                                               _addr(marginals, np.float64),
+                                               _addr(occ_max, np.float64),
+                                               _addr(ylt, np.float64), _stream(stream)))
 
 
 def are_risk_measures(ctx, ylt, n: Optional[int] = None,

@@ -293,6 +293,7 @@ int run_single(are_ctx *ctx, const Layer &L, const Yet &y, int64_t trial_begin, 
     TermsF32 t32;
     TermsF64 t64;
     fill_terms(ctx, L, t32, t64, a.any_share);
+    if (!fp32 && te.kernel == 1) return launch_staged64(a, t.jp, t64, false, ctx->num_sms, s);
     return launch_simulate(a, precision, t.jp, &t32, &t64, ctx->num_sms, s);
 }
 
@@ -301,7 +302,7 @@ TuneEntry tuned(are_ctx *ctx, are_precision p, const Yet &y, int jp, bool multi)
     auto it = ctx->tune.find(tune_key(p, y, jp, multi));
     if (it != ctx->tune.end()) return it->second;
     TuneEntry d;
-    d.kernel = multi ? 0 : (p == ARE_FP64 ? 2 : 1);
+    d.kernel = (multi && p != ARE_FP64) ? 0 : 1;
     return d;
 }
 
@@ -784,6 +785,53 @@ are_status are_simulate(are_ctx *ctx, int32_t layer, int32_t yet, int64_t trial_
     });
 }
 
+are_status are_simulate_occurrences(are_ctx *ctx, int32_t layer, int32_t yet, int64_t trial_begin,
+                                    int64_t n_trials, are_precision precision, double *marginals,
+                                    double *occ_max, double *ylt, void *stream)
+{
+    return guarded(ctx, [&] {
+        check_precision(precision);
+        Layer &L = layer_of(ctx, layer);
+        Yet &y = yet_of(ctx, yet);
+        ARE_CHECK(trial_begin >= 0 && n_trials >= 0 && trial_begin + n_trials <= y.n_trials,
+                  ARE_EINVAL, "trial range outside the YET");
+        ARE_CHECK(marginals && is_device_ptr(marginals), ARE_EINVAL,
+                  "marginals must be device memory");
+        ARE_CHECK(!occ_max || is_device_ptr(occ_max), ARE_EINVAL, "occ_max must be device memory");
+        ARE_CHECK(!ylt || is_device_ptr(ylt), ARE_EINVAL, "ylt must be device memory");
+        if (n_trials == 0) return;
+        CallStream cs(ctx, stream);
+        const bool fp32 = precision != ARE_FP64;
+        Table &t = fp32 ? L.t32 : L.t64;
+        if (!t.d || t.catalog != y.catalog) build_table(ctx, L, y.catalog, fp32, cs.s);
+        SimArgs a{};
+        a.ids = y.d_ids;
+        a.off = y.d_off;
+        a.k = y.k;
+        a.trial_begin = trial_begin;
+        a.n_trials = n_trials;
+        a.table = t.d;
+        a.agg_r = L.terms.agg_ret;
+        a.agg_l = L.terms.agg_lim;
+        a.ylt = ylt;
+        a.marg = marginals;
+        a.occ_max = occ_max;
+        if (y.d_off) {
+            ARE_CUDA_TRY(cudaMemcpyAsync(&a.marg_base, y.d_off + trial_begin, sizeof(int64_t),
+                                         cudaMemcpyDeviceToHost, cs.s));
+            ARE_CUDA_TRY(cudaStreamSynchronize(cs.s));
+        } else {
+            a.marg_base = trial_begin * (int64_t)y.k;
+        }
+        TermsF32 t32;
+        TermsF64 t64;
+        fill_terms(ctx, L, t32, t64, a.any_share);
+        ctx->launches += fp32 ? launch_staged32_occ(a, t.jp, t32, ctx->num_sms, cs.s)
+                              : launch_staged64(a, t.jp, t64, true, ctx->num_sms, cs.s);
+        cs.finish();
+    });
+}
+
 are_status are_risk_measures(are_ctx *ctx, const double *ylt, int64_t n,
                              const double *return_periods, int32_t n_rp, double *pml_out,
                              const double *tvar_levels, int32_t n_tv, double *tvar_out,
@@ -1011,6 +1059,8 @@ are_status are_autotune(are_ctx *ctx, const int32_t *layers, int32_t n_layers, i
                 }
         } else {
             TuneEntry e;
+            e.kernel = 1;
+            cands.push_back(e);
             e.kernel = 2;
             cands.push_back(e);
         }

@@ -111,8 +111,11 @@ struct SimArgs {
     const void *table;       // [catalog][jp]
     double agg_r, agg_l;
     int any_share;           // some ELT has share != 1
-    double *ylt;             // n_trials
-    int kernel;              // FP32 tables: 1 staged, 2 register
+    double *ylt;             // n_trials (may be null when occurrences are written)
+    int kernel;              // 1 staged, 2 register
+    double *marg;            // per-occurrence marginals, or null
+    double *occ_max;         // largest occurrence loss per trial, or null
+    int64_t marg_base;       // event index of marg[0]
 };
 
 struct ScatterArgs {
@@ -203,6 +206,12 @@ int launch_check_timestamps(const float *ts, const int64_t *off, int64_t n_trial
 // All of w's layers must have table width jp (8, 16 or 32 floats).
 int launch_items(const ItemWork &w, int jp, const ItemConfig &cfg, are_precision prec,
                  int num_sms, cudaStream_t s);
+
+// staged64.cu / staged_occ.cu: one event per lane, rows staged in shared
+// memory; `occ` also writes per-occurrence marginals and occurrence maxima.
+int launch_staged64(const SimArgs &a, int jp, const TermsF64 &t, bool occ, int num_sms,
+                    cudaStream_t s);
+int launch_staged32_occ(const SimArgs &a, int jp, const TermsF32 &t, int num_sms, cudaStream_t s);
 
 // simulate.cu
 int launch_simulate(const SimArgs &a, are_precision prec, int jp, const TermsF32 *t32,
