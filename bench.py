@@ -40,8 +40,9 @@ LEVELS = [0.99]
 PRECISION_NAMES = {0: "fp64", 1: "fp32_kahan", 2: "fp32_fp64agg"}
 DTYPES = {0: "f64", 1: "f32", 2: "f32"}
 FALLBACK_HBM_GBS = 6800.0
-SIM_SOURCES = [os.path.join(ROOT, "paper_1308_2066_gb300", "csrc", f)
-               for f in ("simulate.cu", "sim_items.cu")]
+CSRC = os.path.join(ROOT, "paper_1308_2066_gb300", "csrc")
+SIM_SOURCES = sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC)
+                     if f.endswith((".cu", ".cuh")))
 
 
 def parse():
@@ -82,7 +83,7 @@ def hbm_peak():
 
 
 def sim_source_sha():
-    """Hash of the analysis-stage kernel sources (ncu counters go stale with them)."""
+    """Hash of the kernel sources (ncu counters go stale when they change)."""
     h = hashlib.sha256()
     for path in SIM_SOURCES:
         with open(path, "rb") as f:
@@ -182,7 +183,10 @@ def items_bytes(wl) -> int:
 def kernel_key(prec: int, J: int, tuned=None) -> str:
     """Name of the kernel that runs the analysis stage for this precision."""
     if prec == 0:
-        return f"k_simulate<double,{math.ceil(J / 4) * 4},0,fixed>"
+        jp = math.ceil(J / 4) * 4
+        if (tuned or {}).get("kernel", 1) == 1:
+            return f"k_staged<double,{jp},fixed,ylt>"
+        return f"k_simulate<double,{jp},0,fixed>"
     jp = 8 if J <= 8 else 16 if J <= 16 else 32
     kind = (tuned or {}).get("kernel", 1)
     if kind == 0:
@@ -659,12 +663,8 @@ def main():
     ylt = torch.empty(y.n_trials, dtype=torch.float64, device="cuda")
     gather = None
     if world > 1:
-        import torch.distributed as dist
-        full = torch.empty(world * y.n_trials, dtype=torch.float64, device="cuda")
-
-        def gather(local):
-            dist.all_gather_into_tensor(full, local)
-            return full
+        from paper_1308_2066_gb300.sharding import gather_ylt
+        gather = gather_ylt
 
     paths = [prec] + ([] if args.no_variants else [p for p in (0, 2, 1) if p != prec])
     tuned = {}

@@ -216,7 +216,8 @@ ARE_API are_status are_simulate_portfolio(are_ctx *ctx, const int32_t *layers, i
 typedef struct {
     int32_t kernel;          /* 0 persistent work items, 1 staged rows (one event per lane),
                                 2 register rows */
-    int32_t rows_in_flight;  /* table rows each lane keeps in flight (persistent kernel) */
+    int32_t rows_in_flight;  /* table rows each lane keeps in flight (persistent kernel: 4 or
+                                8; staged kernel: events per lane per batch, 1 or 2) */
     int32_t trials_per_item; /* trials per work item (persistent kernel) */
     int32_t blocks_per_sm;   /* 0 = as many as fit */
     double ms;               /* measured time of one pass */

@@ -290,6 +290,7 @@ int run_single(are_ctx *ctx, const Layer &L, const Yet &y, int64_t trial_begin, 
     a.agg_l = L.terms.agg_lim;
     a.ylt = d_out;
     a.kernel = te.kernel;
+    a.epl = te.cfg.rows_in_flight == 2 ? 2 : 1;
     TermsF32 t32;
     TermsF64 t64;
     fill_terms(ctx, L, t32, t64, a.any_share);
@@ -301,8 +302,9 @@ TuneEntry tuned(are_ctx *ctx, are_precision p, const Yet &y, int jp, bool multi)
 {
     auto it = ctx->tune.find(tune_key(p, y, jp, multi));
     if (it != ctx->tune.end()) return it->second;
-    TuneEntry d;
-    d.kernel = (multi && p != ARE_FP64) ? 0 : 1;
+    TuneEntry d;   // untuned: the staged kernel (two events per lane for FP32+Kahan)
+    d.kernel = 1;
+    d.cfg.rows_in_flight = p == ARE_FP32_KAHAN ? 2 : 1;
     return d;
 }
 
@@ -557,7 +559,8 @@ are_status are_load_yet(are_ctx *ctx, int32_t catalog_size, int64_t n_trials,
     return guarded(ctx, [&] {
         ARE_CHECK(yet_handle, ARE_EINVAL, "yet_handle is NULL");
         ARE_CHECK(catalog_size > 0, ARE_EINVAL, "catalog_size must be > 0");
-        ARE_CHECK(n_trials >= 0, ARE_EINVAL, "n_trials must be >= 0");
+        ARE_CHECK(n_trials >= 0 && n_trials < (int64_t)INT32_MAX, ARE_EINVAL,
+                  "n_trials must lie in 0 .. 2^31 - 2");
         ARE_CHECK(offsets || events_per_trial > 0, ARE_EINVAL,
                   "need offsets or events_per_trial > 0");
         fence_device_inputs({offsets, event_ids, timestamps});
@@ -1037,16 +1040,15 @@ are_status are_autotune(are_ctx *ctx, const int32_t *layers, int32_t n_layers, i
         const std::string key = tune_key(precision, y, jp, multi);
         std::vector<TuneEntry> cands;
         if (fp32) {
-            if (!multi) {
+            for (int epl : {1, 2}) {          // staged rows, one or two events per lane
                 TuneEntry e;
                 e.kernel = 1;
-                cands.push_back(e);
-                e.kernel = 2;
+                e.cfg.rows_in_flight = epl;
                 cands.push_back(e);
             }
-            if (multi) {
+            if (!multi) {
                 TuneEntry e;
-                e.kernel = 1;
+                e.kernel = 2;
                 cands.push_back(e);
             }
             for (int u : {4, 8})

@@ -113,6 +113,7 @@ struct SimArgs {
     int any_share;           // some ELT has share != 1
     double *ylt;             // n_trials (may be null when occurrences are written)
     int kernel;              // 1 staged, 2 register
+    int epl;                 // staged FP32 kernel: events per lane per batch (1 or 2)
     double *marg;            // per-occurrence marginals, or null
     double *occ_max;         // largest occurrence loss per trial, or null
     int64_t marg_base;       // event index of marg[0]

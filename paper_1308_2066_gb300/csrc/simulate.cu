@@ -52,6 +52,28 @@ __device__ __forceinline__ float comp(const float4 &v, int c)
 }
 __device__ __forceinline__ double comp(const double2 &v, int c) { return c == 0 ? v.x : v.y; }
 
+// Two FP32 operations in one packed instruction (sm_100 and later).
+__device__ __forceinline__ float2 sub2(float2 a, float2 b)
+{
+    unsigned long long ra, rb, rd;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(ra) : "f"(a.x), "f"(a.y));
+    asm("mov.b64 %0, {%1, %2};" : "=l"(rb) : "f"(b.x), "f"(b.y));
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(rd) : "l"(ra), "l"(rb));
+    float2 d;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(d.x), "=f"(d.y) : "l"(rd));
+    return d;
+}
+__device__ __forceinline__ float2 add2(float2 a, float2 b)
+{
+    unsigned long long ra, rb, rd;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(ra) : "f"(a.x), "f"(a.y));
+    asm("mov.b64 %0, {%1, %2};" : "=l"(rb) : "f"(b.x), "f"(b.y));
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(rd) : "l"(ra), "l"(rb));
+    float2 d;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(d.x), "=f"(d.y) : "l"(rd));
+    return d;
+}
+
 __device__ __forceinline__ uint64_t bits(double x) { return (uint64_t)__double_as_longlong(x); }
 __device__ __forceinline__ double dbl(uint64_t b) { return __longlong_as_double((long long)b); }
 
@@ -367,154 +389,182 @@ __device__ __forceinline__ int chunk_slot(int c, int r)
     return p >= CH ? p - CH : p;
 }
 
+// A batch in the pipeline: its trial (index into the launch's range) and a
+// packed count of events (bits 0-6, 0 = no more work) and last-of-trial flag
+// (bit 7).  Kept small: four of them live in registers.
 struct Batch {
-    int64_t t = -1;    // trial (index into the launch's range)
-    int64_t pos = 0;   // first event
-    int cnt = 0;       // events in the batch, 0 = no more work
-    bool last = false; // last batch of its trial
+    int32_t t = -1;
+    int32_t info = 0;
+    __device__ __forceinline__ int cnt() const { return info & 127; }
+    __device__ __forceinline__ bool last() const { return (info & 128) != 0; }
 };
+
+// Where a warp is in its trials: current trial, its next event and the
+// number of its events not yet handed out.
 struct Cursor {
-    int64_t t, pos, end;
+    int32_t t;
+    int32_t rem;
+    int64_t pos;
 };
 
 template <bool FIXED>
-__device__ __forceinline__ void trial_bounds(const SimArgs &a, int64_t t, int64_t &b, int64_t &e)
+__device__ __forceinline__ void trial_start(const SimArgs &a, Cursor &c)
 {
-    const int64_t tt = a.trial_begin + t;
+    const int64_t tt = a.trial_begin + c.t;
     if (FIXED) {
-        b = tt * (int64_t)a.k;
-        e = b + a.k;
+        c.pos = tt * (int64_t)a.k;
+        c.rem = a.k;
     } else {
-        b = a.off[tt];
-        e = a.off[tt + 1];
+        c.pos = a.off[tt];
+        c.rem = (int32_t)(a.off[tt + 1] - c.pos);
     }
 }
 
-// The warp's next batch; trials without events get their loss written here.
-template <bool FIXED>
-__device__ __forceinline__ Batch next_batch(const SimArgs &a, Cursor &c, int64_t step, int lane,
-                                            double empty_loss)
+// The warp's next batch of up to BS events of one trial (its first event in
+// *pos); trials without events get their loss written here.
+template <bool FIXED, int BS>
+__device__ __forceinline__ Batch next_batch(const SimArgs &a, Cursor &c, int32_t step, int lane,
+                                            double empty_loss, int64_t &pos)
 {
     Batch b;
     while (c.t < a.n_trials) {
-        if (c.pos < c.end) {
+        if (c.rem > 0) {
             b.t = c.t;
-            b.pos = c.pos;
-            const int64_t left = c.end - c.pos;
-            b.cnt = left < 32 ? (int)left : 32;
-            c.pos += 32;
-            if (c.pos >= c.end) {
-                b.last = true;
+            pos = c.pos;
+            b.info = c.rem < BS ? c.rem : BS;
+            c.pos += BS;
+            c.rem -= BS;
+            if (c.rem <= 0) {
+                b.info |= 128;
                 c.t += step;
-                if (c.t < a.n_trials) trial_bounds<FIXED>(a, c.t, c.pos, c.end);
+                if (c.t < a.n_trials) trial_start<FIXED>(a, c);
             }
             return b;
         }
         if (lane == 0) a.ylt[c.t] = empty_loss;
         c.t += step;
-        if (c.t < a.n_trials) trial_bounds<FIXED>(a, c.t, c.pos, c.end);
+        if (c.t < a.n_trials) trial_start<FIXED>(a, c);
     }
     return b;
 }
 
 constexpr int kStagedWarps = 8;
 
-template <int JP>
+template <int JP, int EPL>
 constexpr int staged_smem_bytes()
 {
-    return kStagedWarps * 2 * 32 * JP * 4;
+    return kStagedWarps * 2 * 32 * EPL * JP * 4;
 }
 
-template <int JP, int ACC, bool FIXED>
-__global__ void __launch_bounds__(kStagedWarps * 32) k_simulate_staged(const SimArgs a, const TermsF32 tm)
+template <int EPL>
+struct Ids {
+    int32_t v[EPL];
+};
+
+// EPL = events per lane in a batch (a batch is 32 * EPL events of a trial).
+template <int JP, int ACC, bool FIXED, int EPL>
+__global__ void __launch_bounds__(kStagedWarps * 32)
+    k_simulate_staged(const SimArgs a, const TermsF32 tm)
 {
-    constexpr int CH = JP / 4;
+    constexpr int CH = JP / 4;              // 16-byte chunks per row
+    constexpr int ROWS = 32 * EPL;          // rows per batch
+    constexpr int NC = CH * EPL;            // row chunks each lane copies per batch
     extern __shared__ float4 stage[];
     const int lane = threadIdx.x & 31;
-    float4 *buf0 = stage + (size_t)(threadIdx.x >> 5) * 2 * 32 * CH;
-    float4 *buf1 = buf0 + 32 * CH;
-    const float *tab = static_cast<const float *>(a.table);
+    float4 *buf0 = stage + (size_t)(threadIdx.x >> 5) * 2 * ROWS * CH;
+    float4 *buf1 = buf0 + ROWS * CH;
+    const uint32_t sbuf0 = smem_addr(buf0), sbuf1 = smem_addr(buf1);
+    const char *tab = static_cast<const char *>(a.table);
     const bool any_share = a.any_share != 0;
 
-    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t step = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int32_t warp = (int32_t)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int32_t step = (int32_t)((gridDim.x * blockDim.x) >> 5);
     const double empty_loss = net_d(0.0, a.agg_r, a.agg_l);
     Cursor cur{warp, 0, 0};
-    if (cur.t < a.n_trials) trial_bounds<FIXED>(a, cur.t, cur.pos, cur.end);
+    if (cur.t < a.n_trials) trial_start<FIXED>(a, cur);
 
-    auto load_ids = [&](const Batch &b) -> int32_t {
-        return lane < b.cnt ? __ldcs(a.ids + b.pos + lane) : 0;
-    };
-    auto issue_rows = [&](const Batch &b, int32_t idv, float4 *buf) {
+    auto load_ids = [&](const Batch &b, int64_t pos) {
+        Ids<EPL> r;
 #pragma unroll
-        for (int i = 0; i < CH; ++i) {
+        for (int e = 0; e < EPL; ++e)
+            r.v[e] = 32 * e + lane < b.cnt() ? __ldcs(a.ids + pos + 32 * e + lane) : 0;
+        return r;
+    };
+    // copy i of a lane moves chunk (lane + 32 i) % CH of row (lane + 32 i) / CH
+    auto issue_rows = [&](const Batch &b, const Ids<EPL> &idv, uint32_t sbuf) {
+#pragma unroll
+        for (int i = 0; i < NC; ++i) {
             const int q = lane + 32 * i, r = q / CH, c = q % CH;
-            const int32_t id = __shfl_sync(kFull, idv, r);
-            const bool ok = r < b.cnt;
-            const float *src = ok ? tab + (size_t)id * JP + c * 4 : tab;
-            cp_async16(smem_addr(buf + r * CH + chunk_slot<CH>(c, r)), src, ok ? 16 : 0);
+            const int32_t id = __shfl_sync(kFull, idv.v[i / CH], r & 31);
+            const bool ok = r < b.cnt();
+            const char *src = tab + (ok ? (size_t)(uint32_t)id * (JP * 4) + c * 16 : 0);
+            cp_async16(sbuf + (uint32_t)(r * CH + chunk_slot<CH>(c, r)) * 16u, src, ok ? 16 : 0);
         }
         cp_commit();
     };
 
     typename std::conditional<ACC == ARE_FP32_KAHAN, AccKahan, AccF32F64>::type acc;
     auto compute = [&](const Batch &b, const float4 *buf) {
-        float4 v[CH];
 #pragma unroll
-        for (int c = 0; c < CH; ++c) v[c] = buf[lane * CH + chunk_slot<CH>(c, lane)];
-        float g = 0.f;
+        for (int e = 0; e < EPL; ++e) {
+            const int r = lane + 32 * e;
+            float g = 0.f;
 #pragma unroll
-        for (int c = 0; c < CH; ++c)
+            for (int c = 0; c < CH; ++c) {
+                const float4 v = buf[r * CH + chunk_slot<CH>(c, r)];
 #pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const int j = c * 4 + e;
-                float n = fminf(fmaxf(__fsub_rn(comp(v[c], e), tm.ded[j]), 0.f), tm.lim[j]);
-                if (any_share) n = __fmul_rn(n, tm.share[j]);
-                g = __fadd_rn(g, n);
+                for (int k = 0; k < 4; ++k) {
+                    const int j = c * 4 + k;
+                    float n = fminf(fmaxf(__fsub_rn(comp(v, k), tm.ded[j]), 0.f), tm.lim[j]);
+                    if (any_share) n = __fmul_rn(n, tm.share[j]);
+                    g = __fadd_rn(g, n);
+                }
             }
-        acc.add(fminf(fmaxf(__fsub_rn(g, tm.occ_r), 0.f), tm.occ_l));
-        if (b.last) {
+            acc.add(fminf(fmaxf(__fsub_rn(g, tm.occ_r), 0.f), tm.occ_l));
+        }
+        if (b.last()) {
             const double S = warp_total(acc.total());
             if (lane == 0) a.ylt[b.t] = net_d(S, a.agg_r, a.agg_l);
             acc = decltype(acc){};
         }
     };
 
-    Batch q0 = next_batch<FIXED>(a, cur, step, lane, empty_loss);
-    int32_t i0 = load_ids(q0);
-    Batch q1 = next_batch<FIXED>(a, cur, step, lane, empty_loss);
-    int32_t i1 = load_ids(q1);
-    Batch q2 = next_batch<FIXED>(a, cur, step, lane, empty_loss);
-    int32_t i2 = load_ids(q2);
+    int64_t pos = 0;
+    Batch q0 = next_batch<FIXED, ROWS>(a, cur, step, lane, empty_loss, pos);
+    Ids<EPL> i0 = load_ids(q0, pos);
+    Batch q1 = next_batch<FIXED, ROWS>(a, cur, step, lane, empty_loss, pos);
+    Ids<EPL> i1 = load_ids(q1, pos);
+    Batch q2 = next_batch<FIXED, ROWS>(a, cur, step, lane, empty_loss, pos);
+    Ids<EPL> i2 = load_ids(q2, pos);
     Batch q3;
-    int32_t i3 = 0;
-    issue_rows(q0, i0, buf0);
+    Ids<EPL> i3{};
+    issue_rows(q0, i0, sbuf0);
 
     // Each stage: ids three batches ahead, rows one batch ahead, compute.
-#define ARE_STAGE(QC, QN, IN, QF, IF, BC, BN)                      \
-    if (QC.cnt == 0) break;                                        \
-    QF = next_batch<FIXED>(a, cur, step, lane, empty_loss);        \
-    IF = load_ids(QF);                                             \
-    issue_rows(QN, IN, BN);                                        \
-    cp_wait1();                                                    \
-    __syncwarp();                                                  \
-    compute(QC, BC);                                               \
+#define ARE_STAGE(QC, QN, IN, QF, IF, BC, BN, SN)                         \
+    if (QC.cnt() == 0) break;                                             \
+    QF = next_batch<FIXED, ROWS>(a, cur, step, lane, empty_loss, pos);    \
+    IF = load_ids(QF, pos);                                               \
+    issue_rows(QN, IN, SN);                                               \
+    cp_wait1();                                                           \
+    __syncwarp();                                                         \
+    compute(QC, BC);                                                      \
     __syncwarp();
     while (true) {
-        ARE_STAGE(q0, q1, i1, q3, i3, buf0, buf1)
-        ARE_STAGE(q1, q2, i2, q0, i0, buf1, buf0)
-        ARE_STAGE(q2, q3, i3, q1, i1, buf0, buf1)
-        ARE_STAGE(q3, q0, i0, q2, i2, buf1, buf0)
+        ARE_STAGE(q0, q1, i1, q3, i3, buf0, buf1, sbuf1)
+        ARE_STAGE(q1, q2, i2, q0, i0, buf1, buf0, sbuf0)
+        ARE_STAGE(q2, q3, i3, q1, i1, buf0, buf1, sbuf1)
+        ARE_STAGE(q3, q0, i0, q2, i2, buf1, buf0, sbuf0)
     }
 #undef ARE_STAGE
     cp_wait0();
 }
 
-template <int JP, int ACC, bool FIXED>
+template <int JP, int ACC, bool FIXED, int EPL>
 void launch_staged(const SimArgs &a, const TermsF32 &terms, int num_sms, cudaStream_t s)
 {
-    auto kern = k_simulate_staged<JP, ACC, FIXED>;
-    constexpr int smem = staged_smem_bytes<JP>();
+    auto kern = k_simulate_staged<JP, ACC, FIXED, EPL>;
+    constexpr int smem = staged_smem_bytes<JP, EPL>();
     static int per_sm = 0;
     if (per_sm == 0) {
         ARE_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
@@ -533,10 +583,13 @@ void launch_staged(const SimArgs &a, const TermsF32 &terms, int num_sms, cudaStr
 template <int JP, int ACC>
 void launch_staged_fx(const SimArgs &a, const TermsF32 &terms, int num_sms, cudaStream_t s)
 {
+    const bool two = a.epl == 2;
     if (a.off)
-        launch_staged<JP, ACC, false>(a, terms, num_sms, s);
+        two ? launch_staged<JP, ACC, false, 2>(a, terms, num_sms, s)
+            : launch_staged<JP, ACC, false, 1>(a, terms, num_sms, s);
     else
-        launch_staged<JP, ACC, true>(a, terms, num_sms, s);
+        two ? launch_staged<JP, ACC, true, 2>(a, terms, num_sms, s)
+            : launch_staged<JP, ACC, true, 1>(a, terms, num_sms, s);
 }
 
 // The register kernel when asked for (kernel 2, or ARE_SIM_KERNEL=reg).
