@@ -181,7 +181,11 @@ def items_bytes(wl) -> int:
 
 
 def kernel_key(prec: int, J: int, tuned=None) -> str:
-    """Name of the kernel that runs the analysis stage for this precision."""
+    """Name of the kernel that runs the analysis stage for this precision
+    (the untuned default: the staged kernel, two events per lane for FP32 +
+    Kahan, one for FP32 + FP64 sum)."""
+    if prec == "folded":
+        return "k_folded<fixed,smem_bits>"
     if prec == 0:
         jp = math.ceil(J / 4) * 4
         if (tuned or {}).get("kernel", 1) == 1:
@@ -193,7 +197,15 @@ def kernel_key(prec: int, J: int, tuned=None) -> str:
         return f"k_sim_items<{jp},{tuned.get('rows_in_flight')},{prec},fixed>"
     if kind == 2:
         return f"k_simulate<float,{jp},{prec},fixed>"
-    return f"k_simulate_staged<{jp},{prec},fixed>"
+    epl = (tuned or {}).get("rows_in_flight", 2 if prec == 1 else 1)
+    return f"k_simulate_staged<{jp},{prec},fixed,epl{2 if epl == 2 else 1}>"
+
+
+def row_bytes(J: int, prec) -> int:
+    """Bytes of one table row as the analysis kernels read it."""
+    if prec == 0:
+        return math.ceil(J / 4) * 32
+    return 32 if J <= 8 else 64 if J <= 16 else 128
 
 
 class Resident:
@@ -254,6 +266,49 @@ def time_path(are, torch, res, prec, steps, warmup, stream, ylt, gather=None, wo
             "pml": [float(x) for x in out["pml"]], "tvar": [float(x) for x in out["tvar"]]}
 
 
+def time_folded(are, torch, res, steps, warmup, stream, ylt, gather=None, world=1):
+    """The folded-table variant: rebuild the folded table, one trial pass,
+    PML/TVaR, per step."""
+    ctx, wl = res.ctx, res.wl
+    n = wl.yet.n_trials
+    sim_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(steps)]
+    out = {}
+
+    def step(i=None):
+        are.are_prepare_folded(ctx, res.layer, res.yet, stream)
+        if i is not None:
+            sim_ev[i][0].record(stream)
+        are.are_simulate_folded(ctx, res.layer, res.yet, 0, n, ylt, stream)
+        if i is not None:
+            sim_ev[i][1].record(stream)
+        if gather is not None:
+            with torch.cuda.stream(stream):
+                full = gather(ylt)
+            out["pml"], out["tvar"] = are.are_risk_measures(ctx, full, None, RPS, LEVELS, stream)
+        else:
+            out["pml"], out["tvar"] = are.are_risk_measures(ctx, ylt, n, RPS, LEVELS, stream)
+
+    for _ in range(warmup):
+        step()
+    barrier(world)
+    torch.cuda.synchronize()
+    l0 = are.are_launch_count(ctx)
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        start.record(stream)
+        for i in range(steps):
+            step(i)
+        end.record(stream)
+        end.synchronize()
+    torch.cuda.synchronize()
+    barrier(world)
+    return {"ms": start.elapsed_time(end),
+            "sim_ms": float(np.mean([a.elapsed_time(b) for a, b in sim_ev])),
+            "launches": are.are_launch_count(ctx) - l0, "clocks": clk.summary(),
+            "pml": [float(x) for x in out["pml"]], "tvar": [float(x) for x in out["tvar"]]}
+
+
 def barrier(world):
     if world > 1:
         import torch.distributed as dist
@@ -269,18 +324,45 @@ def max_over_ranks(x: float, world: int, torch) -> float:
     return float(t.item())
 
 
-def roofline(n_events, n_trials, J, prec, sim_ms, tuned=None):
+def roofline(n_events, n_trials, J, prec, sim_ms, tuned=None, ceiling=None):
+    """Memory roofline of the analysis kernel: YET bytes plus table-row
+    sectors over the measured HBM copy bandwidth; beside it the fraction of
+    the measured gather ceiling (the same id stream and row reads with no
+    arithmetic), the bound that the L2-resident row reads actually set."""
     peak, src = hbm_peak()
     elem = 8 if prec == 0 else 4
     bytes_ = algorithmic_bytes(n_events, n_trials, J, elem)
     achieved = bytes_ / (sim_ms * 1e-3) / 1e9
     traffic = ncu_traffic(kernel_key(prec, J, tuned))
+    out = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+           "frac": round(achieved / peak, 4), "traffic": traffic,
+           "kernel": kernel_key(prec, J, tuned), "algorithmic_bytes_per_launch": bytes_,
+           "peak_source": f"{src} HBM copy bandwidth",
+           "note": ("algorithmic bytes = per event 4 B id + the event's table row in whole "
+                    "32-B sectors, + 8 B per trial; the rows are gathered from the L2-resident "
+                    "table, so frac can exceed 1: l2_gather gives the fraction of the "
+                    "measured gather ceiling")}
+    if ceiling:
+        rate = n_events / (sim_ms * 1e-3)
+        out["l2_gather"] = {"row_bytes": row_bytes(J, prec),
+                            "achieved_rows_per_s": round(rate, 1),
+                            "ceiling_rows_per_s": round(ceiling, 1),
+                            "frac": round(rate / ceiling, 4),
+                            "ceiling_source": "measured live: are_gather_ceiling on this YET"}
+    return out
+
+
+def folded_roofline(n_events, n_trials, sim_ms):
+    """The folded table's trial pass: HBM traffic is the id stream and the
+    YLT; the values of the few events with h > 0 come from L2."""
+    peak, src = hbm_peak()
+    bytes_ = 4 * n_events + 8 * n_trials
+    achieved = bytes_ / (sim_ms * 1e-3) / 1e9
     return {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-            "frac": round(achieved / peak, 4), "traffic": traffic,
-            "kernel": kernel_key(prec, J, tuned), "algorithmic_bytes_per_launch": bytes_,
+            "frac": round(achieved / peak, 4), "traffic": ncu_traffic(kernel_key("folded", 0)),
+            "kernel": kernel_key("folded", 0), "algorithmic_bytes_per_launch": bytes_,
             "peak_source": f"{src} HBM copy bandwidth",
-            "note": ("algorithmic bytes = per event 4 B id + the event's table row in whole "
-                     "32-B sectors, + 8 B per trial; the table rows are gathered from L2")}
+            "note": "algorithmic bytes = 4 B id per event + 8 B per trial"}
 
 
 # ---------------------------------------------------------------------------
@@ -677,6 +759,17 @@ def main():
         r["ms"] = max_over_ranks(r["ms"], world, torch)
         r["sim_ms"] = max_over_ranks(r["sim_ms"], world, torch)
         results[p] = r
+    folded = None
+    if not args.no_variants:
+        folded = time_folded(are, torch, res, args.steps, args.warmup, stream, ylt, gather, world)
+        folded["ms"] = max_over_ranks(folded["ms"], world, torch)
+        folded["sim_ms"] = max_over_ranks(folded["sim_ms"], world, torch)
+    # the gather ceiling for each row size timed (same YET, no arithmetic)
+    ceilings = {}
+    for p in paths:
+        rb = row_bytes(J, p)
+        if rb not in ceilings:
+            ceilings[rb] = are.are_gather_ceiling(ctx, res.yet, rb, 0, y.n_trials, reps=3)
 
     head = results[prec]
     lookups = world * y.n_events * J
@@ -701,7 +794,7 @@ def main():
                    "l2": "inputs larger than L2 (4 GB YET streamed every step)",
                    "parallelism": f"trial blocks per GPU x{world}"},
         "roofline": roofline(y.n_events, y.n_trials, J, prec, head["sim_ms"],
-                             tuned.get(PRECISION_NAMES[prec])),
+                             tuned.get(PRECISION_NAMES[prec]), ceilings[row_bytes(J, prec)]),
         "tuned": tuned,
         "gpu_launches": head["launches"],
         "clocks": head["clocks"],
@@ -712,9 +805,23 @@ def main():
                              "sim_ms": round(r["sim_ms"], 4),
                              "value": round(lookups / (r["ms"] / args.steps * 1e-3) / 1e9, 3),
                              "roofline": roofline(y.n_events, y.n_trials, J, p, r["sim_ms"],
-                                                  tuned.get(PRECISION_NAMES[p])),
+                                                  tuned.get(PRECISION_NAMES[p]),
+                                                  ceilings[row_bytes(J, p)]),
                              "pml": r["pml"], "tvar": r["tvar"], "clocks": r["clocks"]}
         for p, r in results.items() if p != prec}
+    if folded is not None:
+        ms_f = folded["ms"] / args.steps
+        line["variants"]["fp64_folded"] = {
+            "what": ("one lookup per occurrence: the layer's FP64 occurrence loss per catalog "
+                     "event, built every step, then exact per-trial sums; not the per-ELT "
+                     "lookups of the headline"),
+            "ms_per_step": round(ms_f, 4), "sim_ms": round(folded["sim_ms"], 4),
+            "value": round(lookups / (ms_f * 1e-3) / 1e9, 3),
+            "value_unit": "G event-ELT lookups/s equivalent (events x J / step time)",
+            "events_per_s": round(world * y.n_events / (ms_f * 1e-3), 1),
+            "roofline": folded_roofline(y.n_events, y.n_trials, folded["sim_ms"]),
+            "pml": folded["pml"], "tvar": folded["tvar"], "clocks": folded["clocks"],
+            "gpu_launches": folded["launches"]}
 
     if not args.no_e2e:
         line["e2e"] = run_e2e(are, torch, ctx, wl, prec, max(1, min(args.steps, 10)), 1, world)

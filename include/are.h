@@ -255,6 +255,43 @@ ARE_API are_status are_simulate_occurrences(are_ctx *ctx, int32_t layer, int32_t
                                             are_precision precision, double *marginals,
                                             double *occ_max, double *ylt, void *stream);
 
+/* Folded layer table -- a variant of the analysis stage, not the per-ELT
+ * lookup of the Basic Algorithm.  Steps 1-3 of Section II-B (lookup,
+ * financial terms, sum over ELTs, occurrence terms) depend on the event and
+ * the layer only, since occurrence terms apply to each occurrence on its
+ * own.  are_prepare_folded computes, once per catalog event e and in FP64,
+ * the occurrence loss h[e] (the same operations in the same ELT order as
+ * are_simulate's FP64 path, so equal to it bit for bit), a bitmap of
+ * h[e] > 0 and the largest h, from the ELTs' entries (one pass per ELT, in
+ * layer order).  Memory: 8 B per catalog event + catalog / 8 B, held until
+ * the layer is freed.  Enqueued on `stream`. */
+ARE_API are_status are_prepare_folded(are_ctx *ctx, int32_t layer, int32_t yet, void *stream);
+
+/* Trial pass over the folded table: ylt[i] (double[n_trials], host or
+ * device) = min(max(S - AggR, 0), AggL) for trial trial_begin + i, with S the
+ * sum of h over the trial's occurrences.  S is formed exactly (h scaled by
+ * a power of two taken from the largest h and added as integers; any h of at
+ * least 2^-52 of the largest converts without error) and rounded to double
+ * once, so it does not depend on the order of the occurrences or on how the
+ * trials are split.  Builds the folded table on first use.  Same stream and
+ * host-memory rules as are_simulate. */
+ARE_API are_status are_simulate_folded(are_ctx *ctx, int32_t layer, int32_t yet,
+                                       int64_t trial_begin, int64_t n_trials, double *ylt,
+                                       void *stream);
+
+/* Gather ceiling -- a measurement helper, not a step of the method.  Reads,
+ * for every event occurrence of trials trial_begin .. trial_begin +
+ * n_trials - 1 of the YET, its id and one row of row_bytes bytes (32, 64 or
+ * 128) of a zero table with one row per catalog event, as the analysis
+ * kernels do, and nothing else; the table is allocated and freed inside the
+ * call (against the memory budget).  *rows_per_s receives the best rate over
+ * `reps` timed passes (1..100) and two launch shapes each: the bound that
+ * the table-row reads put on any analysis kernel for this YET and row size.
+ * Blocks the caller. */
+ARE_API are_status are_gather_ceiling(are_ctx *ctx, int32_t yet, int32_t row_bytes,
+                                      int64_t trial_begin, int64_t n_trials, int32_t reps,
+                                      double *rows_per_s);
+
 /* ------------------------------------------------------------------------ */
 /* Filters on the YLT (Section II-C): PML and TVaR                           */
 /* ------------------------------------------------------------------------ */

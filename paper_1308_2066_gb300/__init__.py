@@ -103,6 +103,10 @@ _SIGS = {
     "are_tune_load": (C.c_int32, [_P, C.c_char_p]),
     "are_simulate_occurrences": (C.c_int32, [_P, C.c_int32, C.c_int32, C.c_int64, C.c_int64,
                                              C.c_int, _P, _P, _P, _P]),
+    "are_prepare_folded": (C.c_int32, [_P, C.c_int32, C.c_int32, _P]),
+    "are_simulate_folded": (C.c_int32, [_P, C.c_int32, C.c_int32, C.c_int64, C.c_int64, _P, _P]),
+    "are_gather_ceiling": (C.c_int32, [_P, C.c_int32, C.c_int32, C.c_int64, C.c_int64,
+                                       C.c_int32, C.POINTER(C.c_double)]),
     "are_server_start": (C.c_int32, [_P, C.c_int32, C.POINTER(ServerCfg)]),
     "are_submit": (C.c_int32, [_P, C.POINTER(Request), C.POINTER(C.c_int64)]),
     "are_wait": (C.c_int32, [_P, C.c_int64, C.c_int64, C.POINTER(Result)]),
@@ -267,6 +271,30 @@ def are_simulate_occurrences(ctx, layer: int, yet: int, trial_begin: int, n_tria
                                                _addr(marginals, np.float64),
                                                _addr(occ_max, np.float64),
                                                _addr(ylt, np.float64), _stream(stream)))
+
+
+def are_prepare_folded(ctx, layer: int, yet: int, stream=None) -> None:
+    """Build the layer's folded table (FP64 occurrence loss per catalog event)."""
+    _check(ctx, lib().are_prepare_folded(ctx, int(layer), int(yet), _stream(stream)))
+
+
+def are_simulate_folded(ctx, layer: int, yet: int, trial_begin: int, n_trials: int, ylt,
+                        stream=None) -> None:
+    """YLT from the folded table: one lookup per occurrence, exact trial sums."""
+    _check(ctx, lib().are_simulate_folded(ctx, int(layer), int(yet), int(trial_begin),
+                                          int(n_trials), _addr(ylt, np.float64),
+                                          _stream(stream)))
+
+
+def are_gather_ceiling(ctx, yet: int, row_bytes: int, trial_begin: int = 0,
+                       n_trials: Optional[int] = None, reps: int = 3) -> float:
+    """Rows per second of a pure id-stream + table-row gather over the YET."""
+    if n_trials is None:
+        raise ValueError("n_trials is required")
+    out = C.c_double()
+    _check(ctx, lib().are_gather_ceiling(ctx, int(yet), int(row_bytes), int(trial_begin),
+                                         int(n_trials), int(reps), C.byref(out)))
+    return out.value
 
 
 def are_risk_measures(ctx, ylt, n: Optional[int] = None,

@@ -144,6 +144,12 @@ void free_table(are_ctx *ctx, Table &t)
     t = Table{};
 }
 
+void free_folded(are_ctx *ctx, Folded &f)
+{
+    dfree(ctx, f.d, f.bytes);
+    f = Folded{};
+}
+
 // Build (or rebuild) the layer's table for `catalog` in fp32 or fp64.
 Table &build_table(are_ctx *ctx, Layer &L, int32_t catalog, bool fp32, cudaStream_t s)
 {
@@ -218,6 +224,38 @@ void fill_terms(are_ctx *ctx, const Layer &L, TermsF32 &t32, TermsF64 &t64, int 
     t64.occ_l = L.terms.occ_lim;
     t32.occ_r = (float)L.terms.occ_ret;
     t32.occ_l = (float)L.terms.occ_lim;
+}
+
+// (Re)build the layer's folded table for `catalog` from its ELTs.
+Folded &build_folded(are_ctx *ctx, Layer &L, int32_t catalog, cudaStream_t s)
+{
+    Folded &f = L.fold;
+    const int32_t words = folded_words(catalog);
+    if (f.d && f.catalog != catalog) free_folded(ctx, f);
+    if (!f.d) {
+        f.words = words;
+        f.bytes = 256 + (((size_t)words * 4 + 255) & ~(size_t)255) + (size_t)catalog * 16;
+        f.d = dalloc(ctx, f.bytes);
+        f.catalog = catalog;
+    }
+    ScatterArgs a{};
+    a.n_elts = (int32_t)L.elts.size();
+    for (size_t j = 0; j < L.elts.size(); ++j) {
+        const Elt &e = ctx->elts.at(L.elts[j]);
+        ARE_CHECK(e.max_id < catalog, ARE_EINVAL,
+                  "ELT " + std::to_string(L.elts[j]) + " holds event id " + std::to_string(e.max_id) +
+                      " outside the YET's catalog of " + std::to_string(catalog));
+        a.ids[j] = e.d_ids;
+        a.loss[j] = e.d_loss;
+        a.n[j] = e.n;
+        a.fx[j] = e.terms.fx;
+    }
+    TermsF32 t32;
+    TermsF64 t64;
+    int any_share = 0;
+    fill_terms(ctx, L, t32, t64, any_share);
+    ctx->launches += launch_fold(a, t64, catalog, f.F(), f.bits(), f.hmax(), ctx->num_sms, s);
+    return f;
 }
 
 void fill_layer_f32(are_ctx *ctx, const Layer &L, LayerF32 &o)
@@ -506,6 +544,7 @@ are_status are_destroy(are_ctx *ctx)
         for (auto &kv : ctx->layers) {
             free_table(ctx, kv.second.t32);
             free_table(ctx, kv.second.t64);
+            free_folded(ctx, kv.second.fold);
         }
         for (auto &kv : ctx->elts) {
             dfree(ctx, kv.second.d_ids, 0);
@@ -734,6 +773,7 @@ are_status are_free_layer(are_ctx *ctx, int32_t h)
         ARE_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
         free_table(ctx, L.t32);
         free_table(ctx, L.t64);
+        free_folded(ctx, L.fold);
         for (int32_t e : L.elts) ctx->elts[e].users--;
         ctx->layers.erase(h);
     });
@@ -785,6 +825,106 @@ are_status are_simulate(are_ctx *ctx, int32_t layer, int32_t yet, int64_t trial_
             throw;
         }
         if (!dev_out) dfree(ctx, d_out, sizeof(double) * n_trials);
+    });
+}
+
+are_status are_prepare_folded(are_ctx *ctx, int32_t layer, int32_t yet, void *stream)
+{
+    return guarded(ctx, [&] {
+        Layer &L = layer_of(ctx, layer);
+        Yet &y = yet_of(ctx, yet);
+        CallStream cs(ctx, stream);
+        build_folded(ctx, L, y.catalog, cs.s);
+        cs.finish();
+    });
+}
+
+are_status are_simulate_folded(are_ctx *ctx, int32_t layer, int32_t yet, int64_t trial_begin,
+                               int64_t n_trials, double *ylt, void *stream)
+{
+    return guarded(ctx, [&] {
+        Layer &L = layer_of(ctx, layer);
+        Yet &y = yet_of(ctx, yet);
+        ARE_CHECK(trial_begin >= 0 && n_trials >= 0 && trial_begin + n_trials <= y.n_trials,
+                  ARE_EINVAL, "trial range outside the YET");
+        ARE_CHECK(n_trials == 0 || ylt, ARE_EINVAL, "ylt is NULL");
+        if (n_trials == 0) return;
+        CallStream cs(ctx, stream);
+        cudaStream_t s = cs.s;
+        Folded &f = L.fold;
+        if (!f.d || f.catalog != y.catalog) build_folded(ctx, L, y.catalog, s);
+        const bool dev_out = is_device_ptr(ylt);
+        double *d_out = dev_out ? ylt : (double *)dalloc(ctx, sizeof(double) * n_trials);
+        try {
+            FoldArgs a{};
+            a.ids = y.d_ids;
+            a.off = y.d_off;
+            a.k = y.k;
+            a.trial_begin = trial_begin;
+            a.n_trials = n_trials;
+            a.n_events = y.n_events;
+            a.F = f.F();
+            a.bits = f.bits();
+            a.words = f.words;
+            a.hmax = f.hmax();
+            a.agg_r = L.terms.agg_ret;
+            a.agg_l = L.terms.agg_lim;
+            a.ylt = d_out;
+            ctx->launches += launch_folded(a, ctx->num_sms, s);
+            if (!dev_out) {
+                ARE_CUDA_TRY(cudaMemcpyAsync(ylt, d_out, sizeof(double) * n_trials,
+                                             cudaMemcpyDeviceToHost, s));
+                ARE_CUDA_TRY(cudaStreamSynchronize(s));
+            }
+            cs.finish();
+        } catch (...) {
+            if (!dev_out) dfree(ctx, d_out, sizeof(double) * n_trials);
+            throw;
+        }
+        if (!dev_out) dfree(ctx, d_out, sizeof(double) * n_trials);
+    });
+}
+
+are_status are_gather_ceiling(are_ctx *ctx, int32_t yet, int32_t row_bytes, int64_t trial_begin,
+                              int64_t n_trials, int32_t reps, double *rows_per_s)
+{
+    return guarded(ctx, [&] {
+        Yet &y = yet_of(ctx, yet);
+        ARE_CHECK(row_bytes == 32 || row_bytes == 64 || row_bytes == 128, ARE_EINVAL,
+                  "row_bytes must be 32, 64 or 128");
+        ARE_CHECK(reps >= 1 && reps <= 100, ARE_EINVAL, "reps must lie in 1 .. 100");
+        ARE_CHECK(trial_begin >= 0 && n_trials >= 1 && trial_begin + n_trials <= y.n_trials,
+                  ARE_EINVAL, "trial range outside the YET (or empty)");
+        ARE_CHECK(rows_per_s, ARE_EINVAL, "rows_per_s is NULL");
+        CallStream cs(ctx, nullptr);
+        int64_t first, last;
+        if (y.d_off) {
+            ARE_CUDA_TRY(cudaMemcpy(&first, y.d_off + trial_begin, sizeof first, cudaMemcpyDeviceToHost));
+            ARE_CUDA_TRY(cudaMemcpy(&last, y.d_off + trial_begin + n_trials, sizeof last,
+                                    cudaMemcpyDeviceToHost));
+        } else {
+            first = trial_begin * y.k;
+            last = (trial_begin + n_trials) * y.k;
+        }
+        ARE_CHECK(last > first, ARE_EINVAL, "the trial range holds no events");
+        const size_t tab_bytes = (size_t)y.catalog * row_bytes;
+        const size_t out_bytes = sizeof(float) * (size_t)ctx->num_sms * 8 * 256;
+        void *tab = dalloc(ctx, tab_bytes);
+        float *out = nullptr;
+        try {
+            out = (float *)dalloc(ctx, out_bytes);
+            ARE_CUDA_TRY(cudaMemsetAsync(tab, 0, tab_bytes, cs.s));
+            const float ms = gather_ceiling_ms(y.d_ids + first, last - first, row_bytes, reps,
+                                               ctx->num_sms, tab, out, cs.s, ctx->launches);
+            *rows_per_s = (double)(last - first) / ((double)ms * 1e-3);
+            cs.finish();
+        } catch (...) {
+            if (out) dfree(ctx, out, out_bytes);
+            dfree(ctx, tab, tab_bytes);
+            throw;
+        }
+        dfree(ctx, out, out_bytes);
+        dfree(ctx, tab, tab_bytes);
     });
 }
 

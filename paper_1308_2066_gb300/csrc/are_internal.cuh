@@ -82,10 +82,29 @@ struct Table {
     size_t bytes = 0;
 };
 
+// Folded table of one layer: the FP64 occurrence loss h[e] of every catalog
+// event as a 128-bit fixed-point integer F[e] = h[e] * 2^s (s from the
+// largest h), a bitmap of h > 0 and the largest h (its bits), in one
+// allocation laid out [hmax | 248 B pad][bits: words x 4 B][F: catalog x 16 B].
+struct Folded {
+    int32_t catalog = -1;
+    int32_t words = 0;
+    void *d = nullptr;
+    size_t bytes = 0;
+    unsigned long long *hmax() const { return static_cast<unsigned long long *>(d); }
+    uint32_t *bits() const { return reinterpret_cast<uint32_t *>(static_cast<char *>(d) + 256); }
+    ulonglong2 *F() const
+    {
+        return reinterpret_cast<ulonglong2 *>(static_cast<char *>(d) + 256 +
+                                              (((size_t)words * 4 + 255) & ~(size_t)255));
+    }
+};
+
 struct Layer {
     std::vector<int32_t> elts;
     are_layer_terms terms{};
     Table t32, t64;
+    Folded fold;
     uint64_t generation = 0;   // bumped whenever a table is (re)allocated or freed
 };
 
@@ -117,6 +136,22 @@ struct SimArgs {
     double *marg;            // per-occurrence marginals, or null
     double *occ_max;         // largest occurrence loss per trial, or null
     int64_t marg_base;       // event index of marg[0]
+};
+
+// The trial pass over a folded table.
+struct FoldArgs {
+    const int32_t *ids;
+    const int64_t *off;      // ragged offsets or nullptr
+    int32_t k;
+    int64_t trial_begin;
+    int64_t n_trials;
+    int64_t n_events;        // of the whole YET (the id array's extent)
+    const ulonglong2 *F;     // [catalog] occurrence losses h * 2^s, 128-bit (x low, y high)
+    const uint32_t *bits;    // [words] bit e set iff h[e] > 0
+    int32_t words;
+    const unsigned long long *hmax;   // bits of the largest h
+    double agg_r, agg_l;
+    double *ylt;             // n_trials
 };
 
 struct ScatterArgs {
@@ -194,6 +229,13 @@ struct Plan {
 
 // repack.cu
 int launch_scatter_table(void *table, bool fp32, const ScatterArgs &a, cudaStream_t s);
+int32_t folded_words(int32_t catalog);
+bool folded_bits_in_smem(int32_t words);
+int launch_fold(const ScatterArgs &elts, const TermsF64 &tm, int32_t catalog, ulonglong2 *F,
+                uint32_t *bits, unsigned long long *hmax, int num_sms, cudaStream_t s);
+int launch_folded(const FoldArgs &a, int num_sms, cudaStream_t s);
+float gather_ceiling_ms(const int32_t *ids, int64_t n, int row_bytes, int reps, int num_sms,
+                        const void *table, float *out, cudaStream_t s, uint64_t &launches);
 int table_jp(int n_elts, bool fp32);
 
 // validate.cu: each sets *flag (device int, zeroed by the caller) non-zero on a violation

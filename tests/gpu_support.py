@@ -8,7 +8,8 @@ import numpy as np
 
 import workloads as W
 
-RTOL = {0: 1e-12, 1: 1e-5, 2: 1e-5}   # by precision: FP64, FP32+Kahan, FP32+FP64 sum
+# by precision: FP64, FP32+Kahan, FP32+FP64 sum; "folded": the FP64 folded table
+RTOL = {0: 1e-12, 1: 1e-5, 2: 1e-5, "folded": 1e-12}
 
 
 class Loaded:
@@ -50,6 +51,25 @@ class Loaded:
         out = np.full(n, -1.0)
         self.are.are_simulate(self.ctx, h, self.yet, begin, n, precision, out)
         return out
+
+    def folded(self, layer: int, begin: int = 0, n: int | None = None,
+               device: bool = True) -> np.ndarray:
+        import torch
+        y = self.wl.yet
+        n = y.n_trials - begin if n is None else n
+        if device:
+            out = torch.full((n,), -1.0, dtype=torch.float64, device="cuda")
+            self.are.are_simulate_folded(self.ctx, self.layers[layer], self.yet, begin, n, out)
+            return out.cpu().numpy()
+        out = np.full(n, -1.0)
+        self.are.are_simulate_folded(self.ctx, self.layers[layer], self.yet, begin, n, out)
+        return out
+
+    def run(self, layer: int, precision, begin: int = 0, n: int | None = None) -> np.ndarray:
+        """are_simulate in a precision, or the folded table for "folded"."""
+        if precision == "folded":
+            return self.folded(layer, begin, n)
+        return self.simulate(layer, precision, begin, n)
 
     def release(self):
         for h in self.layers:

@@ -288,7 +288,7 @@ def check_full_size(are, ctx, orc, wl, precisions, n_sample=1500, seed=0):
     report = {}
     try:
         for p in precisions:
-            got = L.simulate(0, p)
+            got = L.run(0, p)
             assert np.all(np.isfinite(got)) and np.all(got >= 0)
             ref = orc.simulate_layer(wl, trials=sample)
             ok, st = mixed_check(got[sample], ref.ylt, ref.gross, RTOL[p])
@@ -315,9 +315,10 @@ def check_full_size(are, ctx, orc, wl, precisions, n_sample=1500, seed=0):
 
 
 def test_paper_scale_full_size(are, ctx, orc):
-    """1,000,000 trials x 1000 events, 16 ELTs: every precision."""
+    """1,000,000 trials x 1000 events, 16 ELTs: every precision and the
+    folded table."""
     wl = W.paper_scale()
-    rep = check_full_size(are, ctx, orc, wl, PRECISIONS)
+    rep = check_full_size(are, ctx, orc, wl, PRECISIONS + ["folded"])
     print("paper_scale", rep)
 
 
@@ -326,5 +327,5 @@ def test_precision_stress_full_size(are, ctx, orc):
     catalog, 32 Pareto ELTs, neutral terms: whole-trial sums reach the YLT."""
     wl = W.precision_stress()
     assert wl.yet.counts().max() <= 3000
-    rep = check_full_size(are, ctx, orc, wl, PRECISIONS, n_sample=1000, seed=3)
+    rep = check_full_size(are, ctx, orc, wl, PRECISIONS + ["folded"], n_sample=1000, seed=3)
     print("precision_stress", rep)
