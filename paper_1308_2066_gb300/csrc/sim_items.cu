@@ -9,7 +9,7 @@
 // of an event (jp floats, jp/4 16-byte chunks) is read by R = jp/4 lanes with
 // one 16-byte load each, every lane holding U rows in flight.  Each lane
 // applies the financial terms of its 4 columns (step 2); a reduce-scatter
-// across the R lanes of a row sums the ELTs (lines 8-9) and leaves each lane
+// across the R lanes of a row sums the ELTs (end of step 2) and leaves each lane
 // with whole events, whose occurrence terms (step 3) and compensated running
 // sum (step 4) it then does alone.  At the end of a trial the warp adds its
 // lanes' sums and applies the aggregate terms.

@@ -7,12 +7,12 @@
 // by R lanes with one 16-byte load each, so a warp load instruction fetches
 // 32/R whole rows.  Each lane applies the financial terms (step 2) to the
 // columns it holds, the R lanes of a row add their parts by shuffles (the sum
-// over ELTs, lines 8-9), the row's first lane applies the occurrence terms
-// (step 3, lines 10-11) and adds the occurrence loss to its running sum.  At
+// over ELTs that closes step 2), the row's first lane applies the occurrence
+// terms (step 3) and adds the occurrence loss to its running sum.  At
 // the end of the trial the warp adds the lanes' sums and applies the
 // aggregate terms (step 4).  The trial loss is the aggregate-clamped total:
-// with non-negative occurrence losses the de-cumulated marginals of lines
-// 16-19 telescope to it, so the YLT needs no per-event scan.
+// with non-negative occurrence losses the de-cumulated marginals of step 4
+// telescope to it, so the YLT needs no per-event scan.
 //
 // FP64 on GB300 runs at a small fraction of the FP32 rate, so the FP64 path
 // takes every decision it can on bit patterns: for non-negative doubles the
@@ -223,7 +223,7 @@ __device__ __forceinline__ double row_sum(double v, int col)
     return v;
 }
 
-// Per-lane running sums of occurrence losses (step 4, lines 12-13), one
+// Per-lane running sums of occurrence losses (step 4), one
 // flavour per precision mode.
 struct AccF64 {
     double s = 0.0;

@@ -15,7 +15,7 @@
 // exactly 0 and adding an exact 0 changes nothing, so the event loss is the
 // sum over ELTs of step 2 in layer order, as the paper's loop forms it.
 //
-// Per-occurrence outputs (step 4, lines 12-17 of the Basic Algorithm): a
+// Per-occurrence outputs (step 4 of the Basic Algorithm, before its final sum): a
 // warp-shuffle inclusive scan of the batch's occurrence losses plus the
 // running total carried from the previous batch gives S_d, the aggregate
 // terms give A_d and the marginal m_d = A_d - A_{d-1} takes A_{d-1} from the
