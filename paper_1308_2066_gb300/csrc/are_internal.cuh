@@ -263,8 +263,9 @@ int launch_simulate(const SimArgs &a, are_precision prec, int jp, const TermsF32
 // select.cu
 struct SelectScratch {
     uint32_t *hist = nullptr;       // kMaxTargets * 256
-    unsigned long long *state = nullptr;  // per target: prefix, remaining rank, ...
-    double *partial = nullptr;      // per block per target: sum hi, sum lo, count
+    unsigned long long *state = nullptr;  // per target: prefix, remaining rank
+    unsigned int *ctrl = nullptr;   // 4 words: blocks arrived, top word of the largest |value|
+    unsigned long long *acc = nullptr;    // per target: integer tail sums and count (7 words)
     double *result = nullptr;       // per target: value, tail mean
     int max_blocks = 0;
 };
@@ -276,7 +277,7 @@ int64_t rank_for_level(int64_t n, double a);
 // Message of the calling thread's last failed are_risk_measures_static call.
 const char *static_last_error();
 void select_free(SelectScratch &s);
-constexpr int kSelectLaunches = 2 + 2 * 8 + 2;
+constexpr int kSelectLaunches = 1 + 8 + 1;
 inline int select_max_blocks(int num_sms) { return num_sms * 4; }
 // ranks[t] (1-based, descending order) for n_targets <= kMaxTargets; writes
 // result[2*t] = m-th largest value, result[2*t+1] = mean of the m largest.

@@ -7,9 +7,17 @@
 // above it, so no sort is done: an MSB-first radix select over an
 // order-preserving 64-bit key of each double finds the m-th largest key
 // exactly (8 passes of 8 bits, every target rank in the same pass), then one
-// more pass adds the values above it with compensated (two-sum) FP64
-// arithmetic.  Everything is enqueued on one stream with the per-pass state
-// in device memory, so the host waits only for the final values.
+// more pass adds the values above it.
+//
+// GB300 choices.  Each histogram pass ends with the pick of the next digit,
+// done by whichever block of the pass finishes last (a counter and memory
+// fences, no waiting), so a selection is 10 launches.  Histogram counts are
+// aggregated per warp (lanes with the digit of the warp's first active lane
+// add once), since early passes send most values to one or two bins.  The tail sum avoids FP64
+// arithmetic, which GB300 issues at a small fraction of its integer rate:
+// each value above the selected one is scaled by a power of two taken from
+// the largest magnitude of the YLT and added as 32-bit limbs to integer
+// accumulators, so the sum is exact, and it is rounded to double once.
 #include <cuda_runtime.h>
 
 #include <cstdio>
@@ -20,8 +28,12 @@
 namespace are {
 namespace {
 
+constexpr unsigned kFull = 0xffffffffu;
 constexpr int kBins = 256;
 constexpr int kThreads = 256;
+constexpr int kLimbs = 3;                      // 32-bit limbs of one scaled value (< 2^96)
+constexpr int kAccWords = 2 * kLimbs + 1;      // per target: positive limbs, negative limbs, count
+constexpr int kCtrlWords = 4;                  // blocks arrived, top word of the largest |value|
 
 __device__ __forceinline__ uint64_t key_of(double x)
 {
@@ -34,51 +46,124 @@ __device__ __forceinline__ double value_of(uint64_t k)
     return __longlong_as_double((long long)b);
 }
 
-// Error-free sum of two doubles (Knuth's TwoSum).
-__device__ __forceinline__ void two_sum(double a, double b, double &s, double &e)
-{
-    s = __dadd_rn(a, b);
-    const double bb = __dsub_rn(s, a);
-    e = __dadd_rn(__dsub_rn(a, __dsub_rn(s, bb)), __dsub_rn(b, bb));
-}
-struct DD {
-    double hi = 0.0, lo = 0.0;
-    __device__ __forceinline__ void add(double x)
-    {
-        double s, e;
-        two_sum(hi, x, s, e);
-        hi = s;
-        lo = __dadd_rn(lo, e);
-    }
-    __device__ __forceinline__ void add(const DD &o)
-    {
-        double s, e;
-        two_sum(hi, o.hi, s, e);
-        hi = s;
-        lo = __dadd_rn(lo, __dadd_rn(e, o.lo));
-    }
-};
-
 struct Ranks {
     long long m[kMaxTargets];
 };
 
 // Scratch of one selection over n_ylt YLTs (blockIdx.y or blockIdx.x picks
-// the YLT): per YLT 8 x 256 histogram words, 8 x (prefix, rank) state words,
-// blocks x 8 x 3 partial sums, 8 x 2 results.
+// the YLT).
 struct Sel {
     const double *single;        // the YLT when there is one
     const double *const *many;   // device array of YLT pointers, or nullptr
-    uint32_t *hist;
-    unsigned long long *state;
-    double *partial;
-    double *result;
+    uint32_t *hist;              // per YLT: kMaxTargets x 256 counts
+    unsigned long long *state;   // per YLT: kMaxTargets x (key prefix, rank left)
+    unsigned int *ctrl;          // per YLT: kCtrlWords
+    unsigned long long *acc;     // per YLT: kMaxTargets x kAccWords
+    double *result;              // per YLT: kMaxTargets x (m-th largest, mean of the m largest)
     int blocks;                  // blocks per YLT in the histogram and tail passes
 };
 __device__ __forceinline__ const double *ylt_of(const Sel &s, int y)
 {
     return s.many ? s.many[y] : s.single;
 }
+
+// ---------------------------------------------------------------------------
+// multi-word integers
+// ---------------------------------------------------------------------------
+
+struct U192 {
+    unsigned long long w0 = 0, w1 = 0, w2 = 0;
+};
+__device__ __forceinline__ void add192(U192 &a, unsigned long long b0, unsigned long long b1,
+                                       unsigned long long b2)
+{
+    asm("add.cc.u64 %0, %0, %3;\n\t"
+        "addc.cc.u64 %1, %1, %4;\n\t"
+        "addc.u64 %2, %2, %5;"
+        : "+l"(a.w0), "+l"(a.w1), "+l"(a.w2)
+        : "l"(b0), "l"(b1), "l"(b2));
+}
+__device__ __forceinline__ void sub192(U192 &a, const U192 &b)
+{
+    asm("sub.cc.u64 %0, %0, %3;\n\t"
+        "subc.cc.u64 %1, %1, %4;\n\t"
+        "subc.u64 %2, %2, %5;"
+        : "+l"(a.w0), "+l"(a.w1), "+l"(a.w2)
+        : "l"(b.w0), "l"(b.w1), "l"(b.w2));
+}
+__device__ __forceinline__ bool less192(const U192 &a, const U192 &b)
+{
+    if (a.w2 != b.w2) return a.w2 < b.w2;
+    if (a.w1 != b.w1) return a.w1 < b.w1;
+    return a.w0 < b.w0;
+}
+
+// |x| * 2^s as a 96-bit integer (lo 64 bits, hi 32 bits), rounding half up
+// below the last bit; |x| < 2^(95 - s) keeps it below 2^96.
+__device__ __forceinline__ void scaled(double x, int s, unsigned long long &lo, unsigned long long &hi)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
+    const int be = (int)(b >> 52);
+    unsigned long long m = b & ((1ull << 52) - 1);
+    if (be) m |= 1ull << 52;
+    const int sh = (be ? be : 1) - 1075 + s;   // |x| = m * 2^(sh - s)
+    lo = 0;
+    hi = 0;
+    if (sh >= 64) {
+        hi = m << (sh - 64);
+    } else if (sh > 0) {
+        lo = m << sh;
+        hi = m >> (64 - sh);
+    } else if (sh == 0) {
+        lo = m;
+    } else if (sh >= -53) {
+        const int k = -sh;
+        lo = (m >> k) + ((m >> (k - 1)) & 1ull);
+    }
+}
+
+// a * 2^-s rounded once to the nearest double.
+__device__ __forceinline__ double to_double(const U192 &a, int s)
+{
+    int L;
+    if (a.w2) L = 192 - __clzll((long long)a.w2);
+    else if (a.w1) L = 128 - __clzll((long long)a.w1);
+    else if (a.w0) L = 64 - __clzll((long long)a.w0);
+    else return 0.0;
+    if (L <= 64) return ldexp(__ull2double_rn(a.w0), -s);
+    const int r = L - 64;                      // 1 .. 128
+    unsigned long long w, sticky;
+    if (r < 64) {
+        w = (a.w0 >> r) | (a.w1 << (64 - r));
+        sticky = a.w0 & ((1ull << r) - 1);
+    } else if (r == 64) {
+        w = a.w1;
+        sticky = a.w0;
+    } else if (r < 128) {
+        const int q = r - 64;
+        w = (a.w1 >> q) | (a.w2 << (64 - q));
+        sticky = a.w0 | (a.w1 & ((1ull << q) - 1));
+    } else {
+        w = a.w2;
+        sticky = a.w0 | a.w1;
+    }
+    // w has its top bit set and a double keeps 53 of its 64 bits: a sticky
+    // bit in bit 0 makes the conversion's one rounding the right one
+    return ldexp(__ull2double_rn(w | (sticky ? 1ull : 0ull)), r - s);
+}
+
+// Scale of a YLT: s = 95 - floor(log2(largest |value|)), from the top 32
+// bits of the largest magnitude's bit pattern.
+__device__ __forceinline__ int tail_scale(unsigned int mag_hi)
+{
+    int e = (int)((mag_hi >> 20) & 0x7ff) - 1023;
+    if (e < -1022) e = -1022;
+    return 95 - e;
+}
+
+// ---------------------------------------------------------------------------
+// kernels
+// ---------------------------------------------------------------------------
 
 // state[2t] = key prefix decided so far, state[2t+1] = rank still to find
 // among the keys that share the prefix (1 = the largest of them).
@@ -87,69 +172,50 @@ __global__ void k_init(Sel s, Ranks r, int nt)
     const int y = blockIdx.x;
     uint32_t *hist = s.hist + (size_t)y * kMaxTargets * kBins;
     unsigned long long *state = s.state + (size_t)y * 2 * kMaxTargets;
+    unsigned long long *acc = s.acc + (size_t)y * kMaxTargets * kAccWords;
     for (int i = threadIdx.x; i < nt * kBins; i += blockDim.x) hist[i] = 0;
+    for (int i = threadIdx.x; i < nt * kAccWords; i += blockDim.x) acc[i] = 0;
+    if (threadIdx.x < kCtrlWords) s.ctrl[(size_t)y * kCtrlWords + threadIdx.x] = 0;
     if (threadIdx.x < nt) {
         state[2 * threadIdx.x] = 0ull;
         state[2 * threadIdx.x + 1] = (unsigned long long)r.m[threadIdx.x];
     }
 }
 
-__global__ void __launch_bounds__(kThreads) k_hist(Sel s, int64_t n, int nt, int pass)
+// Adds the lanes with `on` set to bin `bin` of h: the lanes whose bin is the
+// first active lane's add once together (the common case: early passes send
+// most values to one bin), the others one by one.  Every lane of the warp
+// must call it.
+__device__ __forceinline__ void hist_add(uint32_t *h, bool on, uint32_t bin, int lane)
 {
-    const int y = blockIdx.y;
-    const double *__restrict__ v = ylt_of(s, y);
-    const unsigned long long *state = s.state + (size_t)y * 2 * kMaxTargets;
-    uint32_t *hist = s.hist + (size_t)y * kMaxTargets * kBins;
-    __shared__ uint32_t h[kMaxTargets * kBins];
-    for (int i = threadIdx.x; i < nt * kBins; i += blockDim.x) h[i] = 0;
-    const int shift = 56 - 8 * pass;
-    uint64_t pre[kMaxTargets];
-#pragma unroll
-    for (int t = 0; t < kMaxTargets; ++t) pre[t] = t < nt ? state[2 * t] : 0ull;
-    __syncthreads();
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        const uint64_t k = key_of(v[i]);
-        const uint32_t d = (uint32_t)(k >> shift) & 0xffu;
-#pragma unroll
-        for (int t = 0; t < kMaxTargets; ++t) {
-            if (t >= nt) break;
-            const bool match = pass == 0 || (k >> (shift + 8)) == (pre[t] >> (shift + 8));
-            if (match) atomicAdd(&h[t * kBins + d], 1u);
-        }
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < nt * kBins; i += blockDim.x)
-        if (h[i]) atomicAdd(&hist[i], h[i]);
+    const unsigned act = __ballot_sync(kFull, on);
+    if (!act) return;
+    const int leader = __ffs(act) - 1;
+    const uint32_t b0 = __shfl_sync(kFull, bin, leader);
+    const unsigned same = __ballot_sync(kFull, on && bin == b0);
+    if (lane == leader) atomicAdd(h + b0, (uint32_t)__popc(same));
+    else if (on && bin != b0) atomicAdd(h + bin, 1u);
 }
 
-// One warp per target: find the bucket that holds the wanted rank, descending.
-__global__ void k_pick(Sel s, int nt, int pass)
+// One warp: find the bucket of h (256 counts) that holds the wanted rank,
+// counting down from the top bucket, and extend the target's prefix.
+__device__ __forceinline__ void pick(const uint32_t *h, unsigned long long *st, int shift, int lane)
 {
-    const int y = blockIdx.x;
-    const int t = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (t >= nt) return;
-    unsigned long long *state = s.state + (size_t)y * 2 * kMaxTargets;
-    const int shift = 56 - 8 * pass;
-    uint32_t *h = s.hist + ((size_t)y * kMaxTargets + t) * kBins;
     uint32_t c[8];
     unsigned long long lane_sum = 0;
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
-        c[i] = h[kBins - 1 - (lane * 8 + i)];  // lane 0 holds the top buckets
+        c[i] = __ldcg(h + kBins - 1 - (lane * 8 + i));   // lane 0 holds the top buckets
         lane_sum += c[i];
     }
     unsigned long long incl = lane_sum;
 #pragma unroll
     for (int off = 1; off < 32; off <<= 1) {
-        const unsigned long long o = __shfl_up_sync(0xffffffffu, incl, off);
+        const unsigned long long o = __shfl_up_sync(kFull, incl, off);
         if (lane >= off) incl += o;
     }
     const unsigned long long excl = incl - lane_sum;
-    const unsigned long long r = state[2 * t + 1];
-    __syncwarp();
-#pragma unroll
-    for (int i = 0; i < 8; ++i) h[kBins - 1 - (lane * 8 + i)] = 0;
+    const unsigned long long r = st[1];
     if (excl < r && r <= incl) {
         unsigned long long above = excl;
         int b = 0;
@@ -161,106 +227,172 @@ __global__ void k_pick(Sel s, int nt, int pass)
             }
             above += c[i];
         }
-        state[2 * t] |= (unsigned long long)b << shift;
-        state[2 * t + 1] = r - above;
+        st[0] |= (unsigned long long)b << shift;
+        st[1] = r - above;
     }
 }
 
-// Per block and target: compensated sum and count of the values whose key
-// is above the selected key.
-__global__ void __launch_bounds__(kThreads) k_tail(Sel s, int64_t n, int nt)
+// Histogram pass `pass` (digit bits 56 - 8 pass .. 63 - 8 pass) over the keys
+// that share each target's prefix; pass 0 counts every key once for all
+// targets and records the largest magnitude.  The last block to finish picks
+// every target's digit and clears the histogram for the next pass.
+__global__ void __launch_bounds__(kThreads) k_hist(Sel s, int64_t n, int nt, int pass)
+{
+    const int y = blockIdx.y;
+    const double *__restrict__ v = ylt_of(s, y);
+    unsigned long long *state = s.state + (size_t)y * 2 * kMaxTargets;
+    uint32_t *hist = s.hist + (size_t)y * kMaxTargets * kBins;
+    unsigned int *ctrl = s.ctrl + (size_t)y * kCtrlWords;
+    __shared__ uint32_t h[kMaxTargets * kBins];
+    __shared__ unsigned int s_mag;
+    __shared__ int s_last;
+    const int rows = pass == 0 ? 1 : nt;
+    for (int i = threadIdx.x; i < rows * kBins; i += blockDim.x) h[i] = 0;
+    if (threadIdx.x == 0) s_mag = 0;
+    const int shift = 56 - 8 * pass;
+    uint64_t pre[kMaxTargets];
+#pragma unroll
+    for (int t = 0; t < kMaxTargets; ++t)   // pass 0 has no prefix yet
+        pre[t] = (pass > 0 && t < nt) ? state[2 * t] >> (shift + 8) : 0ull;
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    unsigned int mag = 0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    // warp-uniform loop: every lane takes part in the warp's histogram adds
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n;
+         base += stride) {
+        const int64_t i = base + lane;
+        const bool ok = i < n;
+        const double x = ok ? v[i] : 0.0;
+        const uint64_t k = key_of(x);
+        const uint32_t d = (uint32_t)(k >> shift) & 0xffu;
+        if (pass == 0) {
+            hist_add(h, ok, d, lane);
+            const unsigned int m32 =
+                (unsigned int)(((unsigned long long)__double_as_longlong(x) >> 32) & 0x7fffffffu);
+            mag = m32 > mag ? m32 : mag;
+        } else {
+#pragma unroll
+            for (int t = 0; t < kMaxTargets; ++t) {
+                if (t >= nt) break;
+                hist_add(h + t * kBins, ok && (k >> (shift + 8)) == pre[t], d, lane);
+            }
+        }
+    }
+    if (pass == 0) {
+#pragma unroll
+        for (int off = 16; off; off >>= 1) {
+            const unsigned int o = __shfl_xor_sync(kFull, mag, off);
+            mag = o > mag ? o : mag;
+        }
+        if (lane == 0) atomicMax(&s_mag, mag);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < rows * kBins; i += blockDim.x)
+        if (h[i]) atomicAdd(&hist[i], h[i]);
+    if (pass == 0 && threadIdx.x == 0 && s_mag) atomicMax(&ctrl[1], s_mag);
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(&ctrl[0], 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    const int t = threadIdx.x >> 5;
+    if (t < nt) pick(hist + (pass == 0 ? 0 : t) * kBins, state + 2 * t, shift, lane);
+    __syncthreads();
+    for (int i = threadIdx.x; i < rows * kBins; i += blockDim.x) hist[i] = 0;
+    if (threadIdx.x == 0) ctrl[0] = 0;
+}
+
+// Tail pass: every value whose key is above a target's selected key is
+// added, scaled, to the target's integer accumulators (positive and
+// negative values apart) and counted.  The last block to finish forms each
+// target's sum of the m largest -- the values above plus (m - count) times
+// the selected value -- and writes (value, sum / m).
+__global__ void __launch_bounds__(kThreads) k_tail(Sel s, int64_t n, int nt, Ranks r)
 {
     const int y = blockIdx.y;
     const double *__restrict__ v = ylt_of(s, y);
     const unsigned long long *state = s.state + (size_t)y * 2 * kMaxTargets;
+    unsigned int *ctrl = s.ctrl + (size_t)y * kCtrlWords;
+    unsigned long long *acc = s.acc + (size_t)y * kMaxTargets * kAccWords;
+    __shared__ unsigned long long a[kMaxTargets * kAccWords];
+    __shared__ int s_last;
+    for (int i = threadIdx.x; i < nt * kAccWords; i += blockDim.x) a[i] = 0;
     uint64_t kt[kMaxTargets];
-    DD acc[kMaxTargets];
-    unsigned long long cnt[kMaxTargets];
+    uint64_t kmin = ~0ull;
 #pragma unroll
     for (int t = 0; t < kMaxTargets; ++t) {
         kt[t] = t < nt ? state[2 * t] : ~0ull;
-        cnt[t] = 0;
+        kmin = kt[t] < kmin ? kt[t] : kmin;
     }
+    const int sc = tail_scale(ctrl[1]);
+    __syncthreads();
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
         const double x = v[i];
         const uint64_t k = key_of(x);
+        if (k > kmin) {
+            unsigned long long lo, hi;
+            scaled(x, sc, lo, hi);
+            const int sign = x < 0.0 ? kLimbs : 0;
+            const unsigned long long l0 = lo & 0xffffffffull, l1 = lo >> 32, l2 = hi;
 #pragma unroll
-        for (int t = 0; t < kMaxTargets; ++t)
-            if (k > kt[t]) {
-                acc[t].add(x);
-                ++cnt[t];
+            for (int t = 0; t < kMaxTargets; ++t) {
+                if (t < nt && k > kt[t]) {
+                    unsigned long long *p = a + t * kAccWords;
+                    atomicAdd(p + sign, l0);
+                    atomicAdd(p + sign + 1, l1);
+                    atomicAdd(p + sign + 2, l2);
+                    atomicAdd(p + 2 * kLimbs, 1ull);
+                }
             }
-    }
-    __shared__ double sh[kThreads / 32][kMaxTargets][3];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-#pragma unroll
-    for (int t = 0; t < kMaxTargets; ++t) {
-        for (int off = 16; off > 0; off >>= 1) {
-            DD o;
-            o.hi = __shfl_down_sync(0xffffffffu, acc[t].hi, off);
-            o.lo = __shfl_down_sync(0xffffffffu, acc[t].lo, off);
-            cnt[t] += __shfl_down_sync(0xffffffffu, cnt[t], off);
-            acc[t].add(o);
-        }
-        if (lane == 0) {
-            sh[w][t][0] = acc[t].hi;
-            sh[w][t][1] = acc[t].lo;
-            sh[w][t][2] = (double)cnt[t];
         }
     }
     __syncthreads();
+    for (int i = threadIdx.x; i < nt * kAccWords; i += blockDim.x)
+        if (a[i]) atomicAdd(&acc[i], a[i]);
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(&ctrl[0], 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
     if (threadIdx.x < nt) {
         const int t = threadIdx.x;
-        DD sum;
-        double c = 0.0;
-        for (int i = 0; i < kThreads / 32; ++i) {
-            DD o;
-            o.hi = sh[i][t][0];
-            o.lo = sh[i][t][1];
-            sum.add(o);
-            c += sh[i][t][2];
+        const unsigned long long *p = acc + t * kAccWords;
+        U192 pos, neg;
+        // limb sums -> 192-bit integers: sum_l A_l * 2^(32 l)
+        for (int g = 0; g < 2; ++g) {
+            U192 &z = g ? neg : pos;
+            const unsigned long long A0 = __ldcg(p + g * kLimbs), A1 = __ldcg(p + g * kLimbs + 1),
+                                     A2 = __ldcg(p + g * kLimbs + 2);
+            add192(z, A0, 0, 0);
+            add192(z, A1 << 32, A1 >> 32, 0);
+            add192(z, 0, A2, 0);
         }
-        double *p = s.partial + (((size_t)y * s.blocks + blockIdx.x) * kMaxTargets + t) * 3;
-        p[0] = sum.hi;
-        p[1] = sum.lo;
-        p[2] = c;
-    }
-}
-
-// One warp per target: adds the blocks' partial sums in block order, then
-// the ties at the selected value, and writes (value, mean of the m largest).
-__global__ void k_final(Sel s, Ranks r, int nt)
-{
-    const int y = blockIdx.x;
-    const int t = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (t >= nt) return;
-    const unsigned long long *state = s.state + (size_t)y * 2 * kMaxTargets;
-    DD sum;
-    double c = 0.0;
-    for (int b = lane; b < s.blocks; b += 32) {
-        const double *p = s.partial + (((size_t)y * s.blocks + b) * kMaxTargets + t) * 3;
-        DD o;
-        o.hi = p[0];
-        o.lo = p[1];
-        sum.add(o);
-        c += p[2];
-    }
-    for (int off = 16; off > 0; off >>= 1) {
-        DD o;
-        o.hi = __shfl_down_sync(0xffffffffu, sum.hi, off);
-        o.lo = __shfl_down_sync(0xffffffffu, sum.lo, off);
-        c += __shfl_down_sync(0xffffffffu, c, off);
-        sum.add(o);
-    }
-    if (lane == 0) {
-        const double v = value_of(state[2 * t]);
-        const double m = (double)r.m[t];
-        sum.add(__dmul_rn(m - c, v));
+        const unsigned long long c = __ldcg(p + 2 * kLimbs);
+        const double vt = value_of(kt[t]);
+        const unsigned long long q = (unsigned long long)r.m[t] - c;   // >= 1: ties at the m-th value
+        unsigned long long lo, hi;
+        scaled(vt, sc, lo, hi);
+        U192 &z = vt < 0.0 ? neg : pos;
+        // (hi:lo) * q with hi < 2^32 and q < 2^32
+        add192(z, lo * q, __umul64hi(lo, q), 0);
+        add192(z, 0, hi * q, __umul64hi(hi, q));
+        double sum;
+        if (less192(pos, neg)) {
+            sub192(neg, pos);
+            sum = -to_double(neg, sc);
+        } else {
+            sub192(pos, neg);
+            sum = to_double(pos, sc);
+        }
         double *res = s.result + (size_t)y * 2 * kMaxTargets;
-        res[2 * t] = v;
-        res[2 * t + 1] = __ddiv_rn(__dadd_rn(sum.hi, sum.lo), m);
+        res[2 * t] = vt;
+        res[2 * t + 1] = __ddiv_rn(sum, (double)r.m[t]);
     }
+    if (threadIdx.x == 0) ctrl[0] = 0;
 }
 
 cudaError_t enqueue(const Sel &s, int n_ylt, int64_t n, const int64_t *ranks, int nt,
@@ -270,12 +402,8 @@ cudaError_t enqueue(const Sel &s, int n_ylt, int64_t n, const int64_t *ranks, in
     for (int t = 0; t < nt; ++t) r.m[t] = ranks[t];
     const dim3 grid((unsigned)s.blocks, (unsigned)n_ylt);
     k_init<<<n_ylt, kThreads, 0, st>>>(s, r, nt);
-    for (int pass = 0; pass < 8; ++pass) {
-        k_hist<<<grid, kThreads, 0, st>>>(s, n, nt, pass);
-        k_pick<<<n_ylt, 32 * kMaxTargets, 0, st>>>(s, nt, pass);
-    }
-    k_tail<<<grid, kThreads, 0, st>>>(s, n, nt);
-    k_final<<<n_ylt, 32 * kMaxTargets, 0, st>>>(s, r, nt);
+    for (int pass = 0; pass < 8; ++pass) k_hist<<<grid, kThreads, 0, st>>>(s, n, nt, pass);
+    k_tail<<<grid, kThreads, 0, st>>>(s, n, nt, r);
     return cudaGetLastError();
 }
 
@@ -293,7 +421,8 @@ void select_alloc(SelectScratch &s, int num_sms)
     s.max_blocks = select_max_blocks(num_sms);
     ARE_CUDA_TRY(cudaMalloc(&s.hist, sizeof(uint32_t) * kMaxTargets * kBins));
     ARE_CUDA_TRY(cudaMalloc(&s.state, sizeof(unsigned long long) * 2 * kMaxTargets));
-    ARE_CUDA_TRY(cudaMalloc(&s.partial, sizeof(double) * 3 * kMaxTargets * s.max_blocks));
+    ARE_CUDA_TRY(cudaMalloc(&s.ctrl, sizeof(unsigned int) * kCtrlWords));
+    ARE_CUDA_TRY(cudaMalloc(&s.acc, sizeof(unsigned long long) * kMaxTargets * kAccWords));
     ARE_CUDA_TRY(cudaMalloc(&s.result, sizeof(double) * 2 * kMaxTargets));
 }
 
@@ -301,7 +430,8 @@ void select_free(SelectScratch &s)
 {
     cudaFree(s.hist);
     cudaFree(s.state);
-    cudaFree(s.partial);
+    cudaFree(s.ctrl);
+    cudaFree(s.acc);
     cudaFree(s.result);
     s = SelectScratch{};
 }
@@ -310,7 +440,7 @@ void select_free(SelectScratch &s)
 cudaError_t select_enqueue(const double *ylt, int64_t n, const int64_t *ranks, int nt,
                            const SelectScratch &s, cudaStream_t st)
 {
-    Sel sel{ylt, nullptr, s.hist, s.state, s.partial, s.result, blocks_for(n, s.max_blocks)};
+    Sel sel{ylt, nullptr, s.hist, s.state, s.ctrl, s.acc, s.result, blocks_for(n, s.max_blocks)};
     return enqueue(sel, 1, n, ranks, nt, st);
 }
 
@@ -333,28 +463,31 @@ size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 
 size_t select_multi_bytes(int n_ylt, int64_t n, int num_sms)
 {
-    const size_t blocks = (size_t)multi_blocks(n_ylt, n, num_sms);
+    (void)n;
+    (void)num_sms;
     return align256(sizeof(uint32_t) * kMaxTargets * kBins * n_ylt) +
            align256(sizeof(unsigned long long) * 2 * kMaxTargets * n_ylt) +
-           align256(sizeof(double) * 3 * kMaxTargets * blocks * n_ylt) +
+           align256(sizeof(unsigned int) * kCtrlWords * n_ylt) +
+           align256(sizeof(unsigned long long) * kMaxTargets * kAccWords * n_ylt) +
            align256(sizeof(double) * 2 * kMaxTargets * n_ylt);
 }
 
 int launch_select_multi(const double *const *ylts, int n_ylt, int64_t n, const int64_t *ranks,
                         int nt, void *scratch, int num_sms, cudaStream_t st, double **result)
 {
-    const int blocks = multi_blocks(n_ylt, n, num_sms);
     unsigned char *p = static_cast<unsigned char *>(scratch);
     Sel sel;
     sel.single = nullptr;
     sel.many = ylts;
-    sel.blocks = blocks;
+    sel.blocks = multi_blocks(n_ylt, n, num_sms);
     sel.hist = reinterpret_cast<uint32_t *>(p);
     p += align256(sizeof(uint32_t) * kMaxTargets * kBins * n_ylt);
     sel.state = reinterpret_cast<unsigned long long *>(p);
     p += align256(sizeof(unsigned long long) * 2 * kMaxTargets * n_ylt);
-    sel.partial = reinterpret_cast<double *>(p);
-    p += align256(sizeof(double) * 3 * kMaxTargets * (size_t)blocks * n_ylt);
+    sel.ctrl = reinterpret_cast<unsigned int *>(p);
+    p += align256(sizeof(unsigned int) * kCtrlWords * n_ylt);
+    sel.acc = reinterpret_cast<unsigned long long *>(p);
+    p += align256(sizeof(unsigned long long) * kMaxTargets * kAccWords * n_ylt);
     sel.result = reinterpret_cast<double *>(p);
     *result = sel.result;
     ARE_CUDA_TRY(enqueue(sel, n_ylt, n, ranks, nt, st));
@@ -372,12 +505,11 @@ namespace {
 
 constexpr size_t kStaticHist = 0;                                    // 8 x 256 words
 constexpr size_t kStaticState = kStaticHist + sizeof(uint32_t) * are::kMaxTargets * 256;
-constexpr size_t kStaticResult = kStaticState + 256;                 // 2 x 8 words
-constexpr size_t kStaticPartial = kStaticResult + 256;               // blocks x 8 x 3 doubles
-constexpr int kStaticMaxBlocks = 1024;
-static_assert(kStaticPartial + sizeof(double) * 3 * are::kMaxTargets * kStaticMaxBlocks <=
-                  ARE_STATIC_SCRATCH_BYTES,
-              "static scratch too small for its block limit");
+constexpr size_t kStaticCtrl = kStaticState + 256;                   // 4 words
+constexpr size_t kStaticAcc = kStaticCtrl + 256;                     // 8 x 7 words
+constexpr size_t kStaticResult = kStaticAcc + 512;                   // 2 x 8 words
+static_assert(kStaticResult + 256 <= ARE_STATIC_SCRATCH_BYTES, "static scratch too small");
+static_assert(sizeof(unsigned long long) * are::kMaxTargets * 7 <= 512, "accumulator slot too small");
 
 // Every GPU that loads the library holds this array until the process exits.
 static __device__ __align__(256) unsigned char g_static_scratch[ARE_STATIC_SCRATCH_BYTES];
@@ -463,10 +595,10 @@ extern "C" are_status are_risk_measures_static(const double *ylt, int64_t n,
     SelectScratch sc;
     sc.hist = reinterpret_cast<uint32_t *>(base + kStaticHist);
     sc.state = reinterpret_cast<unsigned long long *>(base + kStaticState);
+    sc.ctrl = reinterpret_cast<unsigned int *>(base + kStaticCtrl);
+    sc.acc = reinterpret_cast<unsigned long long *>(base + kStaticAcc);
     sc.result = reinterpret_cast<double *>(base + kStaticResult);
-    sc.partial = reinterpret_cast<double *>(base + kStaticPartial);
     sc.max_blocks = select_max_blocks(g_static_sms[dev]);
-    if (sc.max_blocks > kStaticMaxBlocks) sc.max_blocks = kStaticMaxBlocks;
 
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const int nt = n_rp + n_tv;

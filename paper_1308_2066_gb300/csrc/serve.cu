@@ -7,9 +7,14 @@
 //      arena memory for the request's table and YLT are free (admission by
 //      memory), building each admitted request's direct-access table;
 //   2. hands out events_per_launch to the running requests in order of
-//      least remaining work (each takes what it needs, the last one a
-//      partial slice) and runs all slices in one persistent launch of the
-//      multi-layer kernel (one launch per table width);
+//      least remaining work, less the time each has already waited
+//      (so a long request is not overtaken for ever by short ones that keep
+//      arriving); each takes what it needs, the last one a partial slice.
+//      The slices of small requests run in one persistent launch of the
+//      multi-layer kernel (one launch per table width); a request of at
+//      least kStagedSlice events runs its slices on the single-layer staged
+//      kernel, which is faster per event.  The kernel is chosen per request,
+//      so a request's result does not depend on the requests around it;
 //   3. selects PML/TVaR for the requests whose last slice was in the launch;
 //   4. waits (bounded) for the previous iteration and posts its results.
 // One iteration is always queued ahead of the one being waited for, so the
@@ -36,6 +41,8 @@ constexpr int kMaxSlots = 256;
 constexpr int kWidths3[3] = {8, 16, 32};
 constexpr size_t kAlign = 256;
 constexpr int64_t kWaitLimitUs = 120LL * 1000 * 1000;   // one iteration may not take longer
+constexpr double kStagedSlice = 32e6;         // events: a request this large runs on its own kernel
+constexpr double kEventsPerUs = 1.6e5;        // occurrences per microsecond (a table row each), for the aging
 
 size_t up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
@@ -105,6 +112,7 @@ struct Slot {
     size_t tab_off = 0, tab_bytes = 0, ylt_off = 0, ylt_bytes = 0;
     LayerF32 rec{};
     int64_t launched = 0;           // trials handed to launches so far
+    bool staged = false;            // large request: its slices run on the staged kernel
     uint64_t finish_iter = 0;       // iteration whose completion posts the result
     SelectScratch sel;
     double *h_res = nullptr;        // pinned, 2 * kMaxTargets
@@ -313,6 +321,7 @@ void scheduler(Server *SP)
                     sl.busy = true;
                     sl.cancelled = sl.finishing = false;
                     sl.launched = 0;
+                    sl.staged = (double)sl.req.n_trials * S.mean_events >= kStagedSlice;
                     sl.t_admit = Clock::now();
                     S.running[sl.req.ticket] = free_slot;
                     admitted.push_back(free_slot);
@@ -329,16 +338,19 @@ void scheduler(Server *SP)
             // Short requests overtake long ones, and a launch touches only a
             // few requests' tables, which keeps them resident in L2.
             const int buf = (int)(S.iter & 1);
-            std::vector<int> part[3];
+            std::vector<int> part[3], big;
             std::vector<int64_t> slice;
             {
                 std::lock_guard<std::mutex> lk(S.mu);
                 std::vector<std::pair<double, int>> order;
+                const Clock::time_point now = Clock::now();
                 for (int i = 0; i < (int)S.slots.size(); ++i) {
                     const Slot &sl = S.slots[i];
                     if (!sl.busy || sl.cancelled || sl.launched >= sl.req.n_trials) continue;
-                    const double work = (double)(sl.req.n_trials - sl.launched) * (double)sl.req.elts.size();
-                    order.emplace_back(work, i);
+                    // remaining GPU time (estimated: a row gather per occurrence) less
+                    // the time since the request was submitted
+                    const double work_us = (double)(sl.req.n_trials - sl.launched) * S.mean_events / kEventsPerUs;
+                    order.emplace_back(work_us - us_between(sl.req.t_submit, now), i);
                 }
                 std::sort(order.begin(), order.end());
                 slice.assign(S.slots.size(), 0);
@@ -354,7 +366,10 @@ void scheduler(Server *SP)
                     }
                     slice[o.second] = take;
                     left_budget -= (double)take;
-                    part[sl.jp == 8 ? 0 : sl.jp == 16 ? 1 : 2].push_back(o.second);
+                    if (sl.staged)
+                        big.push_back(o.second);
+                    else
+                        part[sl.jp == 8 ? 0 : sl.jp == 16 ? 1 : 2].push_back(o.second);
                 }
             }
             if (S.cfg.stall_us > 0) std::this_thread::sleep_for(std::chrono::microseconds(S.cfg.stall_us));
@@ -403,6 +418,34 @@ void scheduler(Server *SP)
                 cfg.trials_per_item = tpi;
                 cfg.rows_in_flight = 4;
                 launches += launch_items(w, kWidths3[g], cfg, S.cfg.precision, S.ctx->num_sms, S.stream);
+            }
+            // large slices, one staged single-layer launch each
+            for (int i : big) {
+                const Slot &sl = S.slots[i];
+                SimArgs sa;
+                std::memset(&sa, 0, sizeof sa);
+                sa.ids = S.y->d_ids;
+                sa.off = S.y->d_off;
+                sa.k = S.y->k;
+                sa.trial_begin = sl.launched;
+                sa.n_trials = slice[i];
+                sa.table = sl.rec.table;
+                sa.agg_r = sl.rec.agg_r;
+                sa.agg_l = sl.rec.agg_l;
+                sa.any_share = sl.rec.any_share;
+                sa.ylt = sl.rec.ylt + sl.launched;
+                sa.kernel = 1;
+                sa.epl = S.cfg.precision == ARE_FP32_KAHAN ? 2 : 1;
+                TermsF32 tm;
+                std::memset(&tm, 0, sizeof tm);
+                for (int j = 0; j < kMaxElts; ++j) {
+                    tm.ded[j] = sl.rec.ded[j];
+                    tm.lim[j] = sl.rec.lim[j];
+                    tm.share[j] = sl.rec.share[j];
+                }
+                tm.occ_r = sl.rec.occ_r;
+                tm.occ_l = sl.rec.occ_l;
+                launches += launch_simulate(sa, S.cfg.precision, sl.jp, &tm, nullptr, S.ctx->num_sms, S.stream);
             }
             // requests whose last slice is in this launch: select their risk measures
             {

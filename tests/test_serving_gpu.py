@@ -185,3 +185,48 @@ def test_stop_drops_queued_requests(are, served):
         are.are_wait(ctx, tickets[-1], 0)
     assert e.value.status == are.ARE_ENOTFOUND
     are.are_server_stop(ctx)
+
+
+def test_large_request_on_the_staged_kernel(are):
+    """A request of at least 32M events runs its slices on the single-layer
+    staged kernel: its result equals are_simulate + are_risk_measures on the
+    same layer (the same kernel and arithmetic per trial), alone and in a
+    mix of small requests, sliced into many launches."""
+    import torch
+    g = np.random.Generator(np.random.PCG64(45))
+    n, k, C = 80_000, 500, 20_000
+    yet = W.yet_fixed(g, n, k, C, timestamps=False)
+    elts = [W.percentile_terms(W.elt_lognormal(g, C, int(g.integers(300, 1500)))) for _ in range(12)]
+    ctx = are.are_create(0)
+    try:
+        y = are.are_load_yet(ctx, C, n, None, k, torch.from_numpy(yet.ids).cuda())
+        hs = [are.are_load_elt(ctx, e.ids, e.losses, e.fx, e.ded, e.lim, e.share) for e in elts]
+        members, terms = [3, 1, 4, 0, 5, 9, 2, 6], (2e4, 1e6, 5e4, 5e7)
+        layer = are.are_define_layer(ctx, [hs[m] for m in members], *terms)
+        out = torch.empty(n, dtype=torch.float64, device="cuda")
+        are.are_simulate(ctx, layer, y, 0, n, are.ARE_FP32_KAHAN, out)
+        pml, tv = are.are_risk_measures(ctx, out, n, RPS, LEVELS)
+
+        def big():
+            return are.are_submit(ctx, [hs[m] for m in members], *terms, n, RPS, LEVELS)
+
+        small = [dict(members=[int(x) for x in g.choice(12, int(g.integers(1, 9)), replace=False)],
+                      n=int(g.integers(1000, 20_000))) for _ in range(12)]
+        for mix in (False, True):
+            are.are_server_start(ctx, y, max_inflight=16, events_per_launch=10_000_000)
+            tickets = []
+            if mix:
+                tickets += [are.are_submit(ctx, [hs[m] for m in r["members"]], 1e4, 1e6, 0, math.inf,
+                                           r["n"], RPS, LEVELS) for r in small[:6]]
+            tb = big()
+            if mix:
+                tickets += [are.are_submit(ctx, [hs[m] for m in r["members"]], 1e4, 1e6, 0, math.inf,
+                                           r["n"], RPS, LEVELS) for r in small[6:]]
+            res = are.are_wait(ctx, tb, 120_000_000)
+            for t in tickets:
+                assert are.are_wait(ctx, t, 120_000_000)["status"] == are.ARE_OK
+            are.are_server_stop(ctx)
+            assert res["status"] == are.ARE_OK
+            assert list(res["pml"]) == list(pml) and list(res["tvar"]) == list(tv), (mix, res, pml, tv)
+    finally:
+        are.are_destroy(ctx)
