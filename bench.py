@@ -429,6 +429,10 @@ def run_reference(args):
 # ---------------------------------------------------------------------------
 
 def run_e2e(are, torch, ctx, wl, prec, steps, warmup, world):
+    """Per step, from pinned host memory through the public API: load the
+    ELTs, define the layer, build its table, analyse the host-resident YET
+    (its copy to the device overlapped with the analysis, chunk by chunk),
+    select PML/TVaR and read them back."""
     y = wl.yet
     ids_pinned = torch.from_numpy(y.ids).pin_memory()
     L = wl.layers[0]
@@ -437,17 +441,14 @@ def run_e2e(are, torch, ctx, wl, prec, steps, warmup, world):
     d2h = 8 * (len(RPS) + len(LEVELS))
 
     def step():
-        yet = are.are_load_yet(ctx, y.catalog, y.n_trials, None, y.k, ids_pinned)
         elts = [are.are_load_elt(ctx, e.ids, e.losses, e.fx, e.ded, e.lim, e.share)
                 for e in wl.elts]
         layer = are.are_define_layer(ctx, elts, L.occ_r, L.occ_l, L.agg_r, L.agg_l)
-        are.are_prepare(ctx, layer, yet, prec)
-        are.are_simulate(ctx, layer, yet, 0, y.n_trials, prec, ylt)
+        are.are_simulate_streamed(ctx, layer, y.catalog, y.n_trials, None, y.k, ids_pinned, prec, ylt)
         are.are_risk_measures(ctx, ylt, y.n_trials, RPS, LEVELS)
         are.are_free_layer(ctx, layer)
         for h in elts:
             are.are_free_elt(ctx, h)
-        are.are_free_yet(ctx, yet)
 
     for _ in range(warmup):
         step()
@@ -461,7 +462,9 @@ def run_e2e(are, torch, ctx, wl, prec, steps, warmup, world):
     J = len(L.elts)
     value = world * steps * y.n_events * J / dt / 1e9
     return {"value": round(value, 3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
-            "d2h_bytes_per_step": int(d2h), "ms_per_step": round(dt / steps * 1e3, 3)}
+            "d2h_bytes_per_step": int(d2h), "ms_per_step": round(dt / steps * 1e3, 3),
+            "how": "are_load_elt x J, are_define_layer, are_simulate_streamed (host YET, "
+                   "copy overlapped with the analysis), are_risk_measures, frees"}
 
 
 # ---------------------------------------------------------------------------

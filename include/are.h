@@ -279,6 +279,26 @@ ARE_API are_status are_simulate_folded(are_ctx *ctx, int32_t layer, int32_t yet,
                                        int64_t trial_begin, int64_t n_trials, double *ylt,
                                        void *stream);
 
+/* Analysis stage for one layer over a YET held in host memory (Section
+ * II-B with the YET of Section II-A item 1 left where it is): the same
+ * result as are_load_yet + are_simulate, without a device copy of the whole
+ * YET.  The trials are cut into chunks of whole trials of about
+ * chunk_events ids (0: 32M; a longer trial forms a chunk alone); the copy of
+ * each chunk to the device (the host-to-device link, pinned memory at full
+ * speed) overlaps the analysis of the one before, in two device buffers of
+ * one chunk each.  Arguments as for are_load_yet (offsets: n_trials + 1
+ * int64, host or device, or NULL with events_per_trial > 0; event_ids: host
+ * memory, read until the call returns) and are_simulate (ylt: double[n_trials],
+ * host or device).  Ids are checked on the device as they arrive: an id
+ * outside [0, catalog_size) is read as 0 and the call returns ARE_EINVAL,
+ * with ylt not valid.  Waits for completion, also with a caller stream
+ * (then it runs after the work already queued on that stream). */
+ARE_API are_status are_simulate_streamed(are_ctx *ctx, int32_t layer, int32_t catalog_size,
+                                         int64_t n_trials, const int64_t *offsets,
+                                         int32_t events_per_trial, const int32_t *event_ids,
+                                         int64_t chunk_events, are_precision precision,
+                                         double *ylt, void *stream);
+
 /* Gather ceiling -- a measurement helper, not a step of the method.  Reads,
  * for every event occurrence of trials trial_begin .. trial_begin +
  * n_trials - 1 of the YET, its id and one row of row_bytes bytes (32, 64 or

@@ -105,6 +105,8 @@ _SIGS = {
                                              C.c_int, _P, _P, _P, _P]),
     "are_prepare_folded": (C.c_int32, [_P, C.c_int32, C.c_int32, _P]),
     "are_simulate_folded": (C.c_int32, [_P, C.c_int32, C.c_int32, C.c_int64, C.c_int64, _P, _P]),
+    "are_simulate_streamed": (C.c_int32, [_P, C.c_int32, C.c_int32, C.c_int64, _P, C.c_int32, _P,
+                                          C.c_int64, C.c_int, _P, _P]),
     "are_gather_ceiling": (C.c_int32, [_P, C.c_int32, C.c_int32, C.c_int64, C.c_int64,
                                        C.c_int32, C.POINTER(C.c_double)]),
     "are_server_start": (C.c_int32, [_P, C.c_int32, C.POINTER(ServerCfg)]),
@@ -284,6 +286,18 @@ def are_simulate_folded(ctx, layer: int, yet: int, trial_begin: int, n_trials: i
     _check(ctx, lib().are_simulate_folded(ctx, int(layer), int(yet), int(trial_begin),
                                           int(n_trials), _addr(ylt, np.float64),
                                           _stream(stream)))
+
+
+def are_simulate_streamed(ctx, layer: int, catalog_size: int, n_trials: int, offsets,
+                          events_per_trial: int, event_ids, precision: int, ylt,
+                          chunk_events: int = 0, stream=None) -> None:
+    """Analysis over a host-resident YET, its copy to the device overlapped
+    with the analysis chunk by chunk."""
+    _check(ctx, lib().are_simulate_streamed(ctx, int(layer), int(catalog_size), int(n_trials),
+                                            _addr(offsets, np.int64), int(events_per_trial),
+                                            _addr(event_ids, np.int32), int(chunk_events),
+                                            int(precision), _addr(ylt, np.float64),
+                                            _stream(stream)))
 
 
 def are_gather_ceiling(ctx, yet: int, row_bytes: int, trial_begin: int = 0,

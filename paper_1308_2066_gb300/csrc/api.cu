@@ -81,30 +81,68 @@ void fence_device_inputs(std::initializer_list<const void *> ptrs)
         }
 }
 
-// Device allocation charged to the context's budget.
+// Device allocation charged to the context's budget.  Blocks the library
+// releases are kept in a per-context cache and handed out again for requests
+// of up to 5/4 of their size (cudaMalloc and cudaFree of gigabyte blocks cost
+// milliseconds and cudaFree synchronises the device); the cache is emptied
+// when an allocation fails or the budget needs the room, and at are_destroy.
+void release_cache(are_ctx *ctx)
+{
+    for (auto &kv : ctx->cache) {
+        ctx->block_size.erase(kv.second);
+        cudaFree(kv.second);
+    }
+    ctx->cache.clear();
+    ctx->cached = 0;
+}
+
 void *dalloc(are_ctx *ctx, size_t bytes)
 {
     if (bytes == 0) bytes = 16;
     ARE_CHECK(ctx->budget == 0 || ctx->used + bytes <= ctx->budget, ARE_ENOMEM,
               "memory budget exceeded: need " + std::to_string(bytes) + " bytes, " +
                   std::to_string(ctx->budget - ctx->used) + " left");
+    auto it = ctx->cache.lower_bound(bytes);
+    if (it != ctx->cache.end() && it->first <= bytes + bytes / 4) {
+        void *p = it->second;
+        ctx->cached -= it->first;
+        ctx->cache.erase(it);
+        ctx->used += bytes;
+        return p;
+    }
+    if (ctx->budget && ctx->used + ctx->cached + bytes > ctx->budget) release_cache(ctx);
     void *p = nullptr;
     cudaError_t e = cudaMalloc(&p, bytes);
+    if (e == cudaErrorMemoryAllocation && !ctx->cache.empty()) {
+        cudaGetLastError();
+        release_cache(ctx);
+        e = cudaMalloc(&p, bytes);
+    }
     if (e != cudaSuccess) {
         cudaGetLastError();
         throw Error{e == cudaErrorMemoryAllocation ? ARE_ENOMEM : ARE_ECUDA,
                     std::string("cudaMalloc: ") + cudaGetErrorString(e)};
     }
+    ctx->block_size[p] = bytes;
     ctx->used += bytes;
     return p;
 }
 
+// Returns a block to the cache once no device work can still use it (the
+// same device-wide wait that cudaFree makes).
 void dfree(are_ctx *ctx, void *p, size_t bytes)
 {
     if (!p) return;
-    cudaFree(p);
     if (bytes == 0) bytes = 16;
     ctx->used -= std::min(ctx->used, bytes);
+    auto it = ctx->block_size.find(p);
+    if (it == ctx->block_size.end()) {   // not from dalloc
+        cudaFree(p);
+        return;
+    }
+    cudaDeviceSynchronize();
+    ctx->cache.emplace(it->second, p);
+    ctx->cached += it->second;
 }
 
 // Copy n bytes from src (host or device) into device memory dst.
@@ -563,6 +601,8 @@ are_status are_destroy(are_ctx *ctx)
         if (ctx->d_flag) cudaFree(ctx->d_flag);
         if (ctx->h_flag) cudaFreeHost(ctx->h_flag);
         if (ctx->h_result) cudaFreeHost(ctx->h_result);
+        release_cache(ctx);
+        if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
         if (ctx->stream) cudaStreamDestroy(ctx->stream);
         t_errors.erase(ctx);
     }
@@ -687,10 +727,21 @@ are_status are_load_elt(are_ctx *ctx, int32_t n_entries, const int32_t *event_id
             ARE_CHECK(std::isfinite(f.fx * loss[i]), ARE_EINVAL, "fx * loss overflows");
             max_id = std::max(max_id, ids[i]);
         }
-        std::vector<int32_t> sorted(ids);
-        std::sort(sorted.begin(), sorted.end());
-        ARE_CHECK(std::adjacent_find(sorted.begin(), sorted.end()) == sorted.end(), ARE_EINVAL,
-                  "duplicate event id within one ELT");
+        bool dup = false;
+        if (max_id < (1 << 28)) {   // bitmap of the ids seen
+            std::vector<uint64_t> seen((size_t)max_id / 64 + 1, 0);
+            for (int32_t i = 0; i < n_entries && !dup; ++i) {
+                uint64_t &w = seen[(size_t)ids[i] >> 6];
+                const uint64_t b = 1ull << (ids[i] & 63);
+                dup = (w & b) != 0;
+                w |= b;
+            }
+        } else {
+            std::vector<int32_t> sorted(ids);
+            std::sort(sorted.begin(), sorted.end());
+            dup = std::adjacent_find(sorted.begin(), sorted.end()) != sorted.end();
+        }
+        ARE_CHECK(!dup, ARE_EINVAL, "duplicate event id within one ELT");
         Elt e;
         e.n = n_entries;
         e.max_id = max_id;
@@ -882,6 +933,126 @@ are_status are_simulate_folded(are_ctx *ctx, int32_t layer, int32_t yet, int64_t
             throw;
         }
         if (!dev_out) dfree(ctx, d_out, sizeof(double) * n_trials);
+    });
+}
+
+are_status are_simulate_streamed(are_ctx *ctx, int32_t layer, int32_t catalog_size, int64_t n_trials,
+                                 const int64_t *offsets, int32_t events_per_trial,
+                                 const int32_t *event_ids, int64_t chunk_events,
+                                 are_precision precision, double *ylt, void *stream)
+{
+    return guarded(ctx, [&] {
+        check_precision(precision);
+        Layer &L = layer_of(ctx, layer);
+        ARE_CHECK(catalog_size > 0, ARE_EINVAL, "catalog_size must be > 0");
+        ARE_CHECK(n_trials >= 0 && n_trials < (int64_t)INT32_MAX, ARE_EINVAL,
+                  "n_trials must lie in 0 .. 2^31 - 2");
+        ARE_CHECK(offsets || events_per_trial > 0, ARE_EINVAL, "need offsets or events_per_trial > 0");
+        ARE_CHECK(chunk_events >= 0, ARE_EINVAL, "chunk_events must be >= 0");
+        ARE_CHECK(n_trials == 0 || ylt, ARE_EINVAL, "ylt is NULL");
+        if (n_trials == 0) return;
+        ARE_CHECK(event_ids && !is_device_ptr(event_ids), ARE_EINVAL,
+                  "event_ids must be host memory (a device-resident YET goes through are_load_yet)");
+        CallStream cs(ctx, stream);
+        cudaStream_t s = cs.s;
+        if (!ctx->copy_stream) ARE_CUDA_TRY(cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking));
+        cudaStream_t cp = ctx->copy_stream;
+
+        // the trials' event ranges, on the host for the chunk plan
+        Yet v;
+        v.catalog = catalog_size;
+        v.n_trials = n_trials;
+        v.k = offsets ? 0 : events_per_trial;
+        std::vector<int64_t> hoff;
+        if (offsets) {
+            hoff = to_host(offsets, (size_t)n_trials + 1, s);
+            ARE_CHECK(hoff[0] == 0, ARE_EINVAL, "offsets must start at 0");
+            for (int64_t t = 0; t < n_trials; ++t)
+                ARE_CHECK(hoff[t + 1] >= hoff[t], ARE_EINVAL, "offsets must be non-decreasing");
+            v.n_events = hoff[n_trials];
+        } else {
+            v.n_events = n_trials * (int64_t)events_per_trial;
+        }
+        auto first_event = [&](int64_t t) { return offsets ? hoff[t] : t * (int64_t)events_per_trial; };
+        // chunks of whole trials, about chunk_events ids each (a longer trial is a chunk alone)
+        const int64_t want = chunk_events > 0 ? chunk_events : ((int64_t)32 << 20);
+        std::vector<int64_t> cut{0};
+        int64_t longest = 0;
+        for (int64_t t = 0; t < n_trials;) {
+            const int64_t b = first_event(t);
+            int64_t u = t + 1;
+            if (offsets) {
+                while (u < n_trials && hoff[u + 1] - b <= want) ++u;
+            } else {
+                const int64_t per = std::max<int64_t>(1, want / events_per_trial);
+                u = std::min(n_trials, t + per);
+            }
+            longest = std::max(longest, first_event(u) - b);
+            cut.push_back(u);
+            t = u;
+        }
+        const size_t buf_bytes = sizeof(int32_t) * (size_t)(longest + 4 + kIdPad);
+
+        const bool fp32 = precision != ARE_FP64;
+        Table &t = fp32 ? L.t32 : L.t64;
+        if (!t.d || t.catalog != catalog_size) build_table(ctx, L, catalog_size, fp32, s);
+        int64_t *d_off = nullptr;
+        int32_t *buf[2] = {nullptr, nullptr};
+        const bool dev_out = is_device_ptr(ylt);
+        double *d_out = nullptr;
+        cudaEvent_t start = nullptr, ready[2] = {nullptr, nullptr}, done[2] = {nullptr, nullptr};
+        auto cleanup = [&] {
+            for (cudaEvent_t e : {start, ready[0], ready[1], done[0], done[1]})
+                if (e) cudaEventDestroy(e);
+            if (!dev_out) dfree(ctx, d_out, sizeof(double) * n_trials);
+            for (int i = 0; i < 2; ++i) dfree(ctx, buf[i], buf_bytes);
+            dfree(ctx, d_off, d_off ? sizeof(int64_t) * (n_trials + 1) : 0);
+        };
+        try {
+            if (offsets) {
+                d_off = (int64_t *)dalloc(ctx, sizeof(int64_t) * (n_trials + 1));
+                copy_in(d_off, hoff.data(), sizeof(int64_t) * (n_trials + 1), s);
+            }
+            v.d_off = d_off;
+            for (int i = 0; i < 2; ++i) buf[i] = (int32_t *)dalloc(ctx, buf_bytes);
+            d_out = dev_out ? ylt : (double *)dalloc(ctx, sizeof(double) * n_trials);
+            for (cudaEvent_t *e : {&start, &ready[0], &ready[1], &done[0], &done[1]})
+                ARE_CUDA_TRY(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+            ARE_CUDA_TRY(cudaMemsetAsync(ctx->d_flag, 0, sizeof(int), s));
+            ARE_CUDA_TRY(cudaEventRecord(start, s));
+            ARE_CUDA_TRY(cudaStreamWaitEvent(cp, start, 0));
+            const TuneEntry te = tuned(ctx, precision, v, t.jp, false);
+            for (size_t c = 0; c + 1 < cut.size(); ++c) {
+                const int slot = (int)(c & 1);
+                const int64_t t0 = cut[c], t1 = cut[c + 1];
+                const int64_t first = first_event(t0), n = first_event(t1) - first;
+                const int64_t lead = first & 3;   // keeps 16-byte vectors of ids aligned
+                if (c >= 2) ARE_CUDA_TRY(cudaStreamWaitEvent(cp, done[slot], 0));
+                int32_t *b = buf[slot];
+                ARE_CUDA_TRY(cudaMemsetAsync(b, 0, sizeof(int32_t) * lead, cp));
+                if (n) ARE_CUDA_TRY(cudaMemcpyAsync(b + lead, event_ids + first, sizeof(int32_t) * n,
+                                                    cudaMemcpyHostToDevice, cp));
+                ARE_CUDA_TRY(cudaMemsetAsync(b + lead + n, 0, sizeof(int32_t) * kIdPad, cp));
+                ctx->launches += launch_sanitize_ids(b + lead, n, catalog_size, ctx->d_flag, cp);
+                ARE_CUDA_TRY(cudaEventRecord(ready[slot], cp));
+                ARE_CUDA_TRY(cudaStreamWaitEvent(s, ready[slot], 0));
+                Yet cv = v;
+                cv.d_ids = b + lead - first;   // indexed by the YET's own event numbers
+                ctx->launches += run_single(ctx, L, cv, t0, t1 - t0, precision, d_out + t0, te, s);
+                ARE_CUDA_TRY(cudaEventRecord(done[slot], s));
+            }
+            if (!dev_out)
+                ARE_CUDA_TRY(cudaMemcpyAsync(ylt, d_out, sizeof(double) * n_trials, cudaMemcpyDeviceToHost, s));
+            const int f = check_flag(ctx, s);
+            ARE_CHECK(!(f & 1), ARE_EINVAL, "event id outside [0, catalog_size) (results are not valid)");
+            cs.finish();
+        } catch (...) {
+            cudaStreamSynchronize(s);
+            cudaStreamSynchronize(cp);
+            cleanup();
+            throw;
+        }
+        cleanup();
     });
 }
 

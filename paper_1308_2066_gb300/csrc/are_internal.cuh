@@ -240,6 +240,7 @@ int table_jp(int n_elts, bool fp32);
 
 // validate.cu: each sets *flag (device int, zeroed by the caller) non-zero on a violation
 int launch_check_ids(const int32_t *ids, int64_t n, int32_t catalog, int *flag, cudaStream_t s);
+int launch_sanitize_ids(int32_t *ids, int64_t n, int32_t catalog, int *flag, cudaStream_t s);
 int launch_check_offsets(const int64_t *off, int64_t n_trials, int64_t n_events, int *flag,
                           cudaStream_t s);
 int launch_check_timestamps(const float *ts, const int64_t *off, int64_t n_trials, int32_t k,
@@ -321,4 +322,9 @@ struct are_ctx {
     double *h_multi = nullptr;   // pinned results of a batched selection
     size_t h_multi_count = 0;
     are::Server *server = nullptr;  // running pricing server, if any
+    // device blocks released by the library and kept for reuse: size -> block
+    std::multimap<size_t, void *> cache;
+    std::map<void *, size_t> block_size;   // every live or cached block's allocated size
+    size_t cached = 0;                     // bytes held in `cache`
+    cudaStream_t copy_stream = nullptr;    // host-to-device copies of streamed analyses
 };

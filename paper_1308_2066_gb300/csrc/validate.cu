@@ -25,6 +25,22 @@ __global__ void k_check_ids(const int32_t *__restrict__ ids, int64_t n, int32_t 
     if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(flag, 1);
 }
 
+// The same check on ids that a kernel is about to read: an id outside the
+// catalog is replaced by 0, so no table read goes out of bounds, and flagged.
+__global__ void k_sanitize_ids(int32_t *__restrict__ ids, int64_t n, int32_t catalog, int *flag)
+{
+    int bad = 0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const int32_t v = ids[i];
+        if (v < 0 || v >= catalog) {
+            ids[i] = 0;
+            bad = 1;
+        }
+    }
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(flag, 1);
+}
+
 __global__ void k_check_offsets(const int64_t *__restrict__ off, int64_t n_trials,
                                 int64_t n_events, int *flag)
 {
@@ -79,6 +95,14 @@ int launch_check_timestamps(const float *ts, const int64_t *off, int64_t n_trial
 {
     if (n_trials <= 0) return 0;
     k_check_ts<<<blocks_for(n_trials), 256, 0, s>>>(ts, off, n_trials, k, flag);
+    ARE_CUDA_TRY(cudaGetLastError());
+    return 1;
+}
+
+int launch_sanitize_ids(int32_t *ids, int64_t n, int32_t catalog, int *flag, cudaStream_t s)
+{
+    if (n <= 0) return 0;
+    k_sanitize_ids<<<blocks_for(n), 256, 0, s>>>(ids, n, catalog, flag);
     ARE_CUDA_TRY(cudaGetLastError());
     return 1;
 }

@@ -1,0 +1,104 @@
+"""are_simulate_streamed: the analysis over a host-resident YET, copied to
+the device chunk by chunk while earlier chunks are analysed.  Each trial is
+computed by the same kernel as are_simulate, so the YLTs must be equal bit
+for bit, whatever the chunking; the FP64 result is also checked against the
+oracle."""
+import math
+
+import numpy as np
+import pytest
+
+import workloads as W
+from gpu_support import Loaded, RTOL, mixed_check
+
+pytestmark = pytest.mark.gpu
+INF = math.inf
+
+
+@pytest.fixture(scope="module")
+def are():
+    import torch
+    assert torch.cuda.is_available()
+    import paper_1308_2066_gb300 as are
+    are.lib()
+    return are
+
+
+@pytest.fixture(scope="module")
+def ctx(are):
+    c = are.are_create(0)
+    yield c
+    are.are_destroy(c)
+
+
+def streamed(are, ctx, L, layer, p, chunk, pinned=True, host_out=False):
+    import torch
+    y = L.wl.yet
+    ids = torch.from_numpy(y.ids).pin_memory() if pinned else y.ids
+    off = None if y.offsets is None else y.offsets
+    if host_out:
+        out = np.full(y.n_trials, -1.0)
+    else:
+        out = torch.full((y.n_trials,), -1.0, dtype=torch.float64, device="cuda")
+    are.are_simulate_streamed(ctx, L.layers[layer], y.catalog, y.n_trials, off, y.k or 0, ids, p,
+                              out, chunk_events=chunk)
+    return out if host_out else out.cpu().numpy()
+
+
+@pytest.mark.parametrize("p", [0, 1, 2])
+def test_fixed_yet_equals_resident_analysis(are, ctx, orc, p):
+    wl = W.plain_tiny()
+    L = Loaded(are, ctx, wl, timestamps=False)
+    try:
+        ref = L.simulate(0, p)
+        for chunk, pinned, host_out in ((0, True, False), (3000, True, True), (777, False, False)):
+            np.testing.assert_array_equal(streamed(are, ctx, L, 0, p, chunk, pinned, host_out), ref)
+        if p == 0:
+            o = orc.simulate_layer(wl, 0)
+            ok, st = mixed_check(ref, o.ylt, o.gross, RTOL[0])
+            assert ok, st
+    finally:
+        L.release()
+
+
+def test_ragged_yet_with_long_and_empty_trials(are, ctx):
+    g = np.random.Generator(np.random.PCG64(12))
+    counts = g.choice([0, 1, 5, 300, 2000, 5000], size=800)
+    off = np.zeros(801, np.int64)
+    np.cumsum(counts, out=off[1:])
+    C = 6000
+    ids = g.integers(0, C, size=int(off[-1]), dtype=np.int32)
+    elts = [W.percentile_terms(W.elt_lognormal(g, C, 900)) for _ in range(11)]
+    wl = W.Workload("r", W.YET(catalog=C, n_trials=800, ids=ids, offsets=off), elts,
+                    [W.Layer(list(range(11)), 1e4, 1e6, 5e4, 5e8)])
+    L = Loaded(are, ctx, wl, timestamps=False)
+    try:
+        for p in (0, 1, 2):
+            ref = L.simulate(0, p)
+            for chunk in (0, 1000, 4096):   # 1000: trials of 2000 and 5000 ids form chunks alone
+                np.testing.assert_array_equal(streamed(are, ctx, L, 0, p, chunk), ref)
+    finally:
+        L.release()
+
+
+def test_invalid_ids_and_arguments(are, ctx):
+    import torch
+    wl = W.plain_tiny(n_trials=500)
+    L = Loaded(are, ctx, wl, timestamps=False)
+    try:
+        bad = wl.yet.ids.copy()
+        bad[12345] = wl.yet.catalog          # one id past the catalog
+        out = torch.zeros(500, dtype=torch.float64, device="cuda")
+        with pytest.raises(are.AreError) as e:
+            are.are_simulate_streamed(ctx, L.layers[0], wl.yet.catalog, 500, None, 100, bad, 1, out,
+                                      chunk_events=2000)
+        assert e.value.status == are.ARE_EINVAL
+        # the context still works
+        np.testing.assert_array_equal(streamed(are, ctx, L, 0, 1, 0), L.simulate(0, 1))
+        dev_ids = torch.from_numpy(wl.yet.ids).cuda()
+        with pytest.raises(are.AreError):
+            are.are_simulate_streamed(ctx, L.layers[0], wl.yet.catalog, 500, None, 100, dev_ids, 1, out)
+        with pytest.raises(are.AreError):
+            are.are_simulate_streamed(ctx, L.layers[0], wl.yet.catalog, 500, None, 0, wl.yet.ids, 1, out)
+    finally:
+        L.release()
