@@ -476,8 +476,16 @@ def run_portfolio(args):
     import paper_1308_2066_gb300 as are
     rank, local_rank, world = dist_env()
     torch.cuda.set_device(local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     prec = {v: k for k, v in PRECISION_NAMES.items()}[args.precision]
     wl = W.portfolio(n_trials=min(args.trials, 200_000))
+    all_layers = wl.layers
+    # under torchrun each rank analyses whole layers (no exchange in the step)
+    from paper_1308_2066_gb300.sharding import layer_shard
+    mine = layer_shard([len(L.elts) for L in all_layers], world, rank)
+    wl.layers = [all_layers[i] for i in mine]
     y = wl.yet
     ctx = are.are_create(local_rank)
     ids = torch.from_numpy(y.ids).cuda()
@@ -491,7 +499,7 @@ def run_portfolio(args):
     stream = torch.cuda.Stream()
     outs = [torch.empty(n, dtype=torch.float64, device="cuda") for _ in layers]
     tuned = None if args.no_tune else are.are_autotune(ctx, layers, yet, prec, stream)
-    lookups = sum(y.n_events * len(L.elts) for L in wl.layers)
+    lookups = sum(y.n_events * len(L.elts) for L in all_layers)   # the whole portfolio
 
     def batched():
         for h in layers:
@@ -509,6 +517,7 @@ def run_portfolio(args):
         for _ in range(args.warmup):
             fn()
         torch.cuda.synchronize()
+        barrier(world)
         l0 = are.are_launch_count(ctx)
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         with ClockSampler(local_rank) as clk:
@@ -517,7 +526,9 @@ def run_portfolio(args):
                 fn()
             b.record(stream)
             b.synchronize()
-        return a.elapsed_time(b) / steps, are.are_launch_count(ctx) - l0, clk.summary()
+        barrier(world)
+        ms = max_over_ranks(a.elapsed_time(b) / steps, world, torch)
+        return ms, are.are_launch_count(ctx) - l0, clk.summary()
 
     # the persistent kernel alone (for the roofline)
     sim = []
@@ -528,16 +539,24 @@ def run_portfolio(args):
         e1.record(stream)
         sim.append((e0, e1))
     torch.cuda.synchronize()
-    sim_ms = float(np.mean([a.elapsed_time(b) for a, b in sim[args.warmup:]]))
+    sim_ms = max_over_ranks(float(np.mean([a.elapsed_time(b) for a, b in sim[args.warmup:]])),
+                            world, torch)
     ms_b, launches, clocks = timed(batched, args.steps)
     ms_p, launches_p, _ = timed(plain, max(1, args.steps // 2))
     pml, tv = batched()
+    per_layer = {i: ([float(x) for x in pml[k]], [float(x) for x in tv[k]])
+                 for k, i in enumerate(mine)}
+    if world > 1:
+        from paper_1308_2066_gb300.sharding import gather_results
+        per_layer = dict(enumerate(gather_results(per_layer, len(all_layers))))
     peak, src = hbm_peak()
+    wl.layers = all_layers
     bytes_ = items_bytes(wl)
     line = {
         "metric": METRIC, "value": round(lookups / (ms_b * 1e-3) / 1e9, 3), "unit": UNIT,
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": round(ms_b, 4), "higher_is_better": True, "scaling": "weak",
+        "ms_per_step": round(ms_b, 4), "higher_is_better": True,
+        "scaling": "strong" if world > 1 else "weak",
         "vs_baseline": None, "dtype": DTYPES[prec],
         "data": "synthetic: seeded ragged Poisson(1000) YET, lognormal ELT pool",
         "config": {"workload": wl.name, "trials": n, "events": y.n_events, "layers": len(layers),
@@ -556,11 +575,15 @@ def run_portfolio(args):
                   "how": "64 x (repack + are_simulate + are_risk_measures)"},
         "speedup_vs_plain": round(ms_p / ms_b, 3),
         "tuned": tuned, "gpu_launches": launches, "clocks": clocks,
-        "pml_layer0": [float(x) for x in pml[0]], "tvar_layer0": [float(x) for x in tv[0]],
+        "pml_layer0": per_layer[0][0], "tvar_layer0": per_layer[0][1],
+        "parallelism": f"whole layers per GPU x{world} (greedy by ELT count)",
     }
     are.are_destroy(ctx)
     if rank == 0:
         print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
 
 
 # ---------------------------------------------------------------------------
