@@ -188,7 +188,10 @@ def kernel_key(prec: int, J: int, tuned=None) -> str:
         return "k_folded<fixed,smem_bits>"
     if prec == 0:
         jp = math.ceil(J / 4) * 4
-        if (tuned or {}).get("kernel", 1) == 1:
+        kind = (tuned or {}).get("kernel", 1)
+        if kind == 3:
+            return f"k_screen64<{8 if J <= 8 else 16 if J <= 16 else 32},fixed>"
+        if kind == 1:
             return f"k_staged<double,{jp},fixed,ylt>"
         return f"k_simulate<double,{jp},0,fixed>"
     jp = 8 if J <= 8 else 16 if J <= 16 else 32
@@ -201,9 +204,10 @@ def kernel_key(prec: int, J: int, tuned=None) -> str:
     return f"k_simulate_staged<{jp},{prec},fixed,epl{2 if epl == 2 else 1}>"
 
 
-def row_bytes(J: int, prec) -> int:
-    """Bytes of one table row as the analysis kernels read it."""
-    if prec == 0:
+def row_bytes(J: int, prec, tuned=None) -> int:
+    """Bytes of one table row as the analysis kernels read it (the screened
+    FP64 kernel reads the FP32 screen's rows)."""
+    if prec == 0 and (tuned or {}).get("kernel", 1) != 3:
         return math.ceil(J / 4) * 32
     return 32 if J <= 8 else 64 if J <= 16 else 128
 
@@ -344,7 +348,7 @@ def roofline(n_events, n_trials, J, prec, sim_ms, tuned=None, ceiling=None):
                     "measured gather ceiling")}
     if ceiling:
         rate = n_events / (sim_ms * 1e-3)
-        out["l2_gather"] = {"row_bytes": row_bytes(J, prec),
+        out["l2_gather"] = {"row_bytes": row_bytes(J, prec, tuned),
                             "achieved_rows_per_s": round(rate, 1),
                             "ceiling_rows_per_s": round(ceiling, 1),
                             "frac": round(rate / ceiling, 4),
@@ -793,7 +797,7 @@ def main():
     # the gather ceiling for each row size timed (same YET, no arithmetic)
     ceilings = {}
     for p in paths:
-        rb = row_bytes(J, p)
+        rb = row_bytes(J, p, tuned.get(PRECISION_NAMES[p]))
         if rb not in ceilings:
             ceilings[rb] = are.are_gather_ceiling(ctx, res.yet, rb, 0, y.n_trials, reps=3)
 
@@ -820,7 +824,8 @@ def main():
                    "l2": "inputs larger than L2 (4 GB YET streamed every step)",
                    "parallelism": f"trial blocks per GPU x{world}"},
         "roofline": roofline(y.n_events, y.n_trials, J, prec, head["sim_ms"],
-                             tuned.get(PRECISION_NAMES[prec]), ceilings[row_bytes(J, prec)]),
+                             tuned.get(PRECISION_NAMES[prec]),
+                             ceilings[row_bytes(J, prec, tuned.get(PRECISION_NAMES[prec]))]),
         "tuned": tuned,
         "gpu_launches": head["launches"],
         "clocks": head["clocks"],
@@ -832,7 +837,7 @@ def main():
                              "value": round(lookups / (r["ms"] / args.steps * 1e-3) / 1e9, 3),
                              "roofline": roofline(y.n_events, y.n_trials, J, p, r["sim_ms"],
                                                   tuned.get(PRECISION_NAMES[p]),
-                                                  ceilings[row_bytes(J, p)]),
+                                                  ceilings[row_bytes(J, p, tuned.get(PRECISION_NAMES[p]))]),
                              "pml": r["pml"], "tvar": r["tvar"], "clocks": r["clocks"]}
         for p, r in results.items() if p != prec}
     if folded is not None:

@@ -215,7 +215,8 @@ ARE_API are_status are_simulate_portfolio(are_ctx *ctx, const int32_t *layers, i
 /* The launch configuration the autotuner picked for one kind of work. */
 typedef struct {
     int32_t kernel;          /* 0 persistent work items, 1 staged rows (one event per lane),
-                                2 register rows */
+                                2 register rows, 3 (FP64) staged rows of an FP32 screen with
+                                the marked entries read from the FP64 table */
     int32_t rows_in_flight;  /* table rows each lane keeps in flight (persistent kernel: 4 or
                                 8; staged kernel: events per lane per batch, 1 or 2) */
     int32_t trials_per_item; /* trials per work item (persistent kernel) */

@@ -189,19 +189,8 @@ void free_folded(are_ctx *ctx, Folded &f)
 }
 
 // Build (or rebuild) the layer's table for `catalog` in fp32 or fp64.
-Table &build_table(are_ctx *ctx, Layer &L, int32_t catalog, bool fp32, cudaStream_t s)
+ScatterArgs scatter_args(are_ctx *ctx, const Layer &L, int32_t catalog, int jp)
 {
-    Table &t = fp32 ? L.t32 : L.t64;
-    const int jp = table_jp((int)L.elts.size(), fp32);
-    const size_t bytes = (size_t)catalog * jp * (fp32 ? 4 : 8);
-    if (t.d && (t.catalog != catalog || t.jp != jp)) free_table(ctx, t);
-    if (!t.d) {
-        ++L.generation;
-        t.d = dalloc(ctx, bytes);
-        t.bytes = bytes;
-        t.catalog = catalog;
-        t.jp = jp;
-    }
     ScatterArgs a{};
     a.n_elts = (int32_t)L.elts.size();
     a.jp = jp;
@@ -215,8 +204,42 @@ Table &build_table(are_ctx *ctx, Layer &L, int32_t catalog, bool fp32, cudaStrea
         a.n[j] = e.n;
         a.fx[j] = e.terms.fx;
     }
-    ARE_CUDA_TRY(cudaMemsetAsync(t.d, 0, bytes, s));
+    return a;
+}
+
+// (Re)allocate table t for catalog x jp columns of elem bytes.
+void size_table(are_ctx *ctx, Layer &L, Table &t, int32_t catalog, int jp, size_t elem)
+{
+    const size_t bytes = (size_t)catalog * jp * elem;
+    if (t.d && (t.catalog != catalog || t.jp != jp)) free_table(ctx, t);
+    if (!t.d) {
+        ++L.generation;
+        t.d = dalloc(ctx, bytes);
+        t.bytes = bytes;
+        t.catalog = catalog;
+        t.jp = jp;
+    }
+}
+
+// Build (or rebuild) the layer's table for `catalog` in fp32 or fp64.  An
+// FP64 table comes with its FP32 screen (values rounded up) for the
+// screened FP64 kernel.
+Table &build_table(are_ctx *ctx, Layer &L, int32_t catalog, bool fp32, cudaStream_t s)
+{
+    Table &t = fp32 ? L.t32 : L.t64;
+    const int jp = table_jp((int)L.elts.size(), fp32);
+    const ScatterArgs a = scatter_args(ctx, L, catalog, jp);
+    size_table(ctx, L, t, catalog, jp, fp32 ? 4 : 8);
+    ARE_CUDA_TRY(cudaMemsetAsync(t.d, 0, t.bytes, s));
     ctx->launches += launch_scatter_table(t.d, fp32, a, s);
+    if (!fp32) {
+        Table &u = L.t32u;
+        const int jpu = table_jp((int)L.elts.size(), true);
+        const ScatterArgs au = scatter_args(ctx, L, catalog, jpu);
+        size_table(ctx, L, u, catalog, jpu, 4);
+        ARE_CUDA_TRY(cudaMemsetAsync(u.d, 0, u.bytes, s));
+        ctx->launches += launch_scatter_table(u.d, true, au, s, true);
+    }
     return t;
 }
 
@@ -370,6 +393,13 @@ int run_single(are_ctx *ctx, const Layer &L, const Yet &y, int64_t trial_begin, 
     TermsF32 t32;
     TermsF64 t64;
     fill_terms(ctx, L, t32, t64, a.any_share);
+    a.n_elts = (int32_t)L.elts.size();
+    if (!fp32 && te.kernel == 3) {
+        ARE_CHECK(L.t32u.d && L.t32u.catalog == y.catalog, ARE_EINVAL, "FP32 screen not built");
+        a.table2 = L.t32u.d;
+        a.jp64 = t.jp;
+        return launch_screen64(a, L.t32u.jp, t64, ctx->num_sms, s);
+    }
     if (!fp32 && te.kernel == 1) return launch_staged64(a, t.jp, t64, false, ctx->num_sms, s);
     return launch_simulate(a, precision, t.jp, &t32, &t64, ctx->num_sms, s);
 }
@@ -582,6 +612,7 @@ are_status are_destroy(are_ctx *ctx)
         for (auto &kv : ctx->layers) {
             free_table(ctx, kv.second.t32);
             free_table(ctx, kv.second.t64);
+            free_table(ctx, kv.second.t32u);
             free_folded(ctx, kv.second.fold);
         }
         for (auto &kv : ctx->elts) {
@@ -824,6 +855,7 @@ are_status are_free_layer(are_ctx *ctx, int32_t h)
         ARE_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
         free_table(ctx, L.t32);
         free_table(ctx, L.t64);
+        free_table(ctx, L.t32u);
         free_folded(ctx, L.fold);
         for (int32_t e : L.elts) ctx->elts[e].users--;
         ctx->layers.erase(h);
@@ -1372,10 +1404,10 @@ are_status are_autotune(are_ctx *ctx, const int32_t *layers, int32_t n_layers, i
                 }
         } else {
             TuneEntry e;
-            e.kernel = 1;
-            cands.push_back(e);
-            e.kernel = 2;
-            cands.push_back(e);
+            for (int k : {1, 3, 2}) {   // staged, screened, register
+                e.kernel = k;
+                cands.push_back(e);
+            }
         }
         const size_t out_bytes = sizeof(double) * (size_t)y.n_trials * n_layers;
         double *outs = (double *)dalloc(ctx, out_bytes);
@@ -1488,7 +1520,7 @@ are_status are_tune_load(are_ctx *ctx, const char *path)
                             "\"trials_per_item\": %d, \"blocks_per_sm\": %d, \"ms\": %lf}",
                             key, &e.kernel, &e.cfg.rows_in_flight, &e.cfg.trials_per_item,
                             &e.cfg.blocks_per_sm, &ms) == 6 &&
-                e.kernel >= 0 && e.kernel <= 2 && e.cfg.trials_per_item > 0) {
+                e.kernel >= 0 && e.kernel <= 3 && e.cfg.trials_per_item > 0) {
                 e.ms = ms;
                 ctx->tune[key] = e;
                 ++loaded;

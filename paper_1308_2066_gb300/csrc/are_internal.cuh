@@ -104,6 +104,7 @@ struct Layer {
     std::vector<int32_t> elts;
     are_layer_terms terms{};
     Table t32, t64;
+    Table t32u;              // FP32 screen of t64: its values rounded up
     Folded fold;
     uint64_t generation = 0;   // bumped whenever a table is (re)allocated or freed
 };
@@ -128,6 +129,9 @@ struct SimArgs {
     int64_t trial_begin;
     int64_t n_trials;
     const void *table;       // [catalog][jp]
+    const void *table2;      // screened FP64: the FP32 screen [catalog][jp32]
+    int32_t jp64;            // screened FP64: columns of the FP64 table
+    int32_t n_elts;          // ELTs of the layer
     double agg_r, agg_l;
     int any_share;           // some ELT has share != 1
     double *ylt;             // n_trials (may be null when occurrences are written)
@@ -228,7 +232,9 @@ struct Plan {
 // ---------------------------------------------------------------------------
 
 // repack.cu
-int launch_scatter_table(void *table, bool fp32, const ScatterArgs &a, cudaStream_t s);
+int launch_scatter_table(void *table, bool fp32, const ScatterArgs &a, cudaStream_t s,
+                         bool round_up = false);
+int launch_screen64(const SimArgs &a, int jp32, const TermsF64 &t, int num_sms, cudaStream_t s);
 int32_t folded_words(int32_t catalog);
 bool folded_bits_in_smem(int32_t words);
 int launch_fold(const ScatterArgs &elts, const TermsF64 &tm, int32_t catalog, ulonglong2 *F,

@@ -15,7 +15,7 @@
 namespace are {
 namespace {
 
-template <typename T>
+template <typename T, bool RU>
 __global__ void k_scatter(T *__restrict__ tab, const ScatterArgs a)
 {
     const int j = blockIdx.y;
@@ -23,8 +23,10 @@ __global__ void k_scatter(T *__restrict__ tab, const ScatterArgs a)
     const int32_t *ids = a.ids[j];
     const double *loss = a.loss[j];
     const double fx = a.fx[j];
-    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-        tab[(size_t)ids[i] * a.jp + j] = (T)__dmul_rn(fx, loss[i]);
+    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const double x = __dmul_rn(fx, loss[i]);
+        tab[(size_t)ids[i] * a.jp + j] = RU ? (T)__double2float_ru(x) : (T)x;
+    }
 }
 
 }  // namespace
@@ -39,17 +41,21 @@ int table_jp(int n_elts, bool fp32)
     return jp < 4 ? 4 : jp;
 }
 
-int launch_scatter_table(void *table, bool fp32, const ScatterArgs &a, cudaStream_t s)
+// round_up (FP32 only): each value rounded towards +infinity -- the FP32
+// screen of an FP64 table, never below the value it stands for.
+int launch_scatter_table(void *table, bool fp32, const ScatterArgs &a, cudaStream_t s, bool round_up)
 {
     int32_t nmax = 0;
     for (int j = 0; j < a.n_elts; ++j) nmax = a.n[j] > nmax ? a.n[j] : nmax;
     if (nmax == 0 || a.n_elts == 0) return 0;
     dim3 grid((unsigned)((nmax + 255) / 256), (unsigned)a.n_elts);
     if (grid.x > 4096) grid.x = 4096;
-    if (fp32)
-        k_scatter<float><<<grid, 256, 0, s>>>(static_cast<float *>(table), a);
+    if (fp32 && round_up)
+        k_scatter<float, true><<<grid, 256, 0, s>>>(static_cast<float *>(table), a);
+    else if (fp32)
+        k_scatter<float, false><<<grid, 256, 0, s>>>(static_cast<float *>(table), a);
     else
-        k_scatter<double><<<grid, 256, 0, s>>>(static_cast<double *>(table), a);
+        k_scatter<double, false><<<grid, 256, 0, s>>>(static_cast<double *>(table), a);
     ARE_CUDA_TRY(cudaGetLastError());
     return 1;
 }

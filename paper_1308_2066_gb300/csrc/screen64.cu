@@ -1,0 +1,237 @@
+// screen64.cu -- the FP64 analysis stage with an FP32 screen.
+//
+// The FP64 table of a layer (8 bytes per event and ELT) is as large as L2 at
+// the paper's sizes (1M events x 16 ELTs = 128 MB), so the FP64 staged
+// kernel takes about half of its table rows from HBM.  Here each event's row
+// is read from an FP32 copy of the table instead (half the bytes: it stays
+// in L2), whose entries are the FP64 values rounded up, and a column is
+// marked when that copy is > 0 and >= the deductible rounded down (one
+// compare against a per-column threshold).  Rounding
+// is monotone, so every entry whose FP64 value exceeds the deductible is
+// marked (and a few that do not: their term comes out exactly 0).  Only the
+// marked entries -- a few per cent at the paper's sizes -- are read from the
+// FP64 table.  From there the work is the FP64 staged kernel's: the marked
+// (row, column) pairs are compacted across the warp and their terms
+// min(max(x - D, 0), Lim) * share formed 32 per FP64 instruction; each event
+// then adds its marked columns in column order, the first taken as is.  An
+// unmarked column's term is exactly 0 and adding an exact 0 changes nothing,
+// so the event losses equal the FP64 staged kernel's (and the oracle's) bit
+// for bit.
+#include "staged.cuh"
+
+namespace are {
+namespace {
+
+using namespace staged;
+
+constexpr int kRound = 64;   // marked entries valued per round (two per lane)
+
+template <int JP>
+__host__ __device__ constexpr int screen_smem_bytes()
+{
+    // per warp: two FP32 row buffers, the compaction list, a round of values
+    // and the batch's event ids; per block: the FP64 terms and the FP32 screen
+    return kWarps * (2 * 32 * JP * 4 + 2 * 32 * JP + kRound * 8 + 32 * 4) + 3 * kMaxElts * 8 +
+           kMaxElts * 4;
+}
+
+template <int JP, bool FIXED>
+__global__ void __launch_bounds__(kWarps * 32) k_screen64(const SimArgs a, const TermsF64 tm)
+{
+    constexpr int CH = JP / 4;   // 16-byte chunks of an FP32 row
+    extern __shared__ float4 stage[];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    // shared memory: rows | lists | values | ids | FP64 terms | FP32 screen
+    char *smem = reinterpret_cast<char *>(stage);
+    constexpr size_t kRows = (size_t)kWarps * 2 * 32 * JP * 4;
+    constexpr size_t kLists = kRows + (size_t)kWarps * 32 * JP * 2;
+    constexpr size_t kVals = kLists + (size_t)kWarps * kRound * 8;
+    constexpr size_t kIds = kVals + (size_t)kWarps * 32 * 4;
+    constexpr size_t kTerms = kIds + 3 * kMaxElts * 8;
+    static_assert(kTerms + kMaxElts * 4 == (size_t)screen_smem_bytes<JP>(), "layout");
+    float4 *buf0 = stage + (size_t)w * 2 * 32 * CH;
+    float4 *buf1 = buf0 + 32 * CH;
+    uint16_t *list = reinterpret_cast<uint16_t *>(smem + kRows) + (size_t)w * 32 * JP;
+    double *vals = reinterpret_cast<double *>(smem + kLists) + (size_t)w * kRound;
+    int32_t *sids = reinterpret_cast<int32_t *>(smem + kVals) + (size_t)w * 32;
+    double *sterms = reinterpret_cast<double *>(smem + kIds);
+    float *sd32 = reinterpret_cast<float *>(smem + kTerms);
+    for (int i = threadIdx.x; i < kMaxElts; i += blockDim.x) {
+        sterms[i] = tm.ded[i];
+        sterms[kMaxElts + i] = tm.lim[i];
+        sterms[2 * kMaxElts + i] = tm.share[i];
+        // the deductible rounded down; columns past the layer's ELTs never marked
+        sd32[i] = i < a.n_elts ? __double2float_rd(tm.ded[i]) : __int_as_float(0x7f800000);
+    }
+    __syncthreads();
+    const double *sd = sterms, *sl = sterms + kMaxElts, *ss = sterms + 2 * kMaxElts;
+    const float *tab = static_cast<const float *>(a.table2);
+    const double *t64 = static_cast<const double *>(a.table);
+    const int jp64 = a.jp64;
+    const bool any_share = a.any_share != 0;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t step = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const double empty_loss = clamp_d(0.0, a.agg_r, a.agg_l);
+    Cursor cur{warp, 0, 0};
+    if (cur.t < a.n_trials) trial_bounds<FIXED>(a, cur.t, cur.pos, cur.end);
+
+    auto load_ids = [&](const Batch &b) -> int32_t {
+        return lane < b.cnt ? __ldcs(a.ids + b.pos + lane) : 0;
+    };
+    auto issue_rows = [&](const Batch &b, int32_t idv, float4 *buf) {
+#pragma unroll
+        for (int i = 0; i < CH; ++i) {
+            const int q = lane + 32 * i, r = q / CH, c = q % CH;
+            const int32_t id = __shfl_sync(kFull, idv, r);
+            const bool ok = r < b.cnt;
+            const float4 *src = ok ? reinterpret_cast<const float4 *>(tab + (size_t)id * JP) + c
+                                   : reinterpret_cast<const float4 *>(tab);
+            cp_async16(smem_addr(buf + r * CH + chunk_slot<CH>(c, r)), src, ok ? 16 : 0);
+        }
+        cp_commit();
+    };
+
+    SumF64 sum;
+
+    // per column: the screen value at or above which an entry is marked (the
+    // deductible rounded down, or the smallest positive float when that is 0)
+    float thr[JP];
+#pragma unroll
+    for (int j = 0; j < JP; ++j) {
+        const float d = sd32[j];
+        thr[j] = d > 0.f ? d : __int_as_float(1);
+    }
+
+    auto compute = [&](const Batch &b, int32_t idv, float4 *buf) {
+        sids[lane] = idv;
+        // mark the columns that can carry a loss
+        uint32_t mask = 0;
+#pragma unroll
+        for (int c = 0; c < CH; ++c) {
+            const float4 v = buf[lane * CH + chunk_slot<CH>(c, lane)];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const float x = e == 0 ? v.x : e == 1 ? v.y : e == 2 ? v.z : v.w;
+                const int j = c * 4 + e;
+                mask |= (uint32_t)(x >= thr[j]) << j;
+            }
+        }
+        if (lane >= b.cnt) mask = 0;
+        const int cnt = __popc(mask);
+        int incl = cnt;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const int o = __shfl_up_sync(kFull, incl, off);
+            if (lane >= off) incl += o;
+        }
+        const int total = __shfl_sync(kFull, incl, 31);
+        const int start = incl - cnt;
+        int k = start;
+        for (uint32_t m = mask; m; m &= m - 1) list[k++] = (uint16_t)((lane << 5) | (__ffs(m) - 1));
+        __syncwarp();
+        // the event loss: marked columns in column order, valued a round at a time
+        double g = 0.0;
+        bool have = false;
+        for (int base = 0; base < total; base += kRound) {
+            const int top = total - base < kRound ? total - base : kRound;
+            for (int i = lane; i < top; i += 32) {
+                const int e = list[base + i], r = e >> 5, j = e & 31;
+                // evict-first: the sparse FP64 reads must not push the screen out of L2
+                const double x = __ldcs(t64 + (size_t)sids[r] * jp64 + j);
+                double n = clamp_bits(vsub(x, sd[j]), bits(sl[j]));
+                if (any_share) n = vmul(n, ss[j]);
+                vals[i] = n;
+            }
+            __syncwarp();
+            const int lo = start > base ? start : base;
+            const int hi = start + cnt < base + top ? start + cnt : base + top;
+            for (int q = lo; __any_sync(kFull, q < hi); ++q) {
+                if (q < hi) {
+                    const double v = vals[q - base];
+                    if (have) g = vadd(g, v);
+                    else g = v;
+                    have = true;
+                }
+            }
+            __syncwarp();
+        }
+        // occurrence terms and the trial's running sum
+        sum.add(occ_clamp(g, tm));
+        if (b.last) {
+            const double S = warp_sum(sum.s);
+            if (lane == 0) a.ylt[b.t] = clamp_d(S, a.agg_r, a.agg_l);
+            sum = SumF64{};
+        }
+    };
+
+    Batch q0 = next_batch<FIXED>(a, cur, step, lane, empty_loss);
+    int32_t i0 = load_ids(q0);
+    Batch q1 = next_batch<FIXED>(a, cur, step, lane, empty_loss);
+    int32_t i1 = load_ids(q1);
+    Batch q2 = next_batch<FIXED>(a, cur, step, lane, empty_loss);
+    int32_t i2 = load_ids(q2);
+    Batch q3;
+    int32_t i3 = 0;
+    issue_rows(q0, i0, buf0);
+
+#define ARE_SCREEN_STAGE(QC, IC, QN, IN, QF, IF, BC, BN)           \
+    if (QC.cnt == 0) break;                                        \
+    QF = next_batch<FIXED>(a, cur, step, lane, empty_loss);        \
+    IF = load_ids(QF);                                             \
+    issue_rows(QN, IN, BN);                                        \
+    cp_wait1();                                                    \
+    __syncwarp();                                                  \
+    compute(QC, IC, BC);                                           \
+    __syncwarp();
+    while (true) {
+        ARE_SCREEN_STAGE(q0, i0, q1, i1, q3, i3, buf0, buf1)
+        ARE_SCREEN_STAGE(q1, i1, q2, i2, q0, i0, buf1, buf0)
+        ARE_SCREEN_STAGE(q2, i2, q3, i3, q1, i1, buf0, buf1)
+        ARE_SCREEN_STAGE(q3, i3, q0, i0, q2, i2, buf1, buf0)
+    }
+#undef ARE_SCREEN_STAGE
+    cp_wait0();
+}
+
+template <int JP, bool FIXED>
+void launch_screen_t(const SimArgs &a, const TermsF64 &tm, int num_sms, cudaStream_t s)
+{
+    auto kern = k_screen64<JP, FIXED>;
+    constexpr int smem = screen_smem_bytes<JP>();
+    static int per_sm = 0;
+    if (per_sm == 0) {
+        ARE_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        ARE_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kWarps * 32, smem));
+        if (per_sm < 1) per_sm = 1;
+    }
+    int64_t blocks = (a.n_trials + kWarps - 1) / kWarps;
+    const int64_t cap = (int64_t)num_sms * per_sm;
+    if (blocks > cap) blocks = cap;
+    if (blocks < 1) blocks = 1;
+    kern<<<(unsigned)blocks, kWarps * 32, smem, s>>>(a, tm);
+    ARE_CUDA_TRY(cudaGetLastError());
+}
+
+template <int JP>
+void go(const SimArgs &a, const TermsF64 &t, int num_sms, cudaStream_t s)
+{
+    if (a.off) launch_screen_t<JP, false>(a, t, num_sms, s);
+    else launch_screen_t<JP, true>(a, t, num_sms, s);
+}
+
+}  // namespace
+
+// a.table: the FP64 table (a.jp64 columns); a.table2: the FP32 screen
+// (jp32 columns, the FP64 values rounded up).
+int launch_screen64(const SimArgs &a, int jp32, const TermsF64 &t, int num_sms, cudaStream_t s)
+{
+    if (a.n_trials <= 0) return 0;
+    switch (jp32) {
+    case 8: go<8>(a, t, num_sms, s); return 1;
+    case 16: go<16>(a, t, num_sms, s); return 1;
+    case 32: go<32>(a, t, num_sms, s); return 1;
+    }
+    throw Error{ARE_EINVAL, "no screened FP64 kernel for table width " + std::to_string(jp32)};
+}
+
+}  // namespace are

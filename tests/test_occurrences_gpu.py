@@ -146,7 +146,7 @@ def test_every_kernel_choice(are, ctx, orc, tmp_path, p):
         entries = [json.loads(l) for l in open(path) if l.strip()]
         key = [e for e in entries if e["key"].startswith(f"p{p}_") and e["key"].endswith("_single")]
         assert key
-        kinds = [1, 2] + ([0] if p != 0 else [])
+        kinds = [1, 2] + ([0] if p != 0 else [3])
         for kind in kinds:
             for u in ((4, 8) if kind == 0 else (1, 2) if kind == 1 else (8,)):
                 e = dict(key[0], kernel=kind, rows_in_flight=u, trials_per_item=3)
