@@ -174,6 +174,19 @@ ARE_API are_status are_free_layer(are_ctx *ctx, int32_t layer_handle);
 /* Analysis stage (Section II-B)                                             */
 /* ------------------------------------------------------------------------ */
 
+/* Table layout of a layer for the FP32 analysis (are_prepare, are_simulate,
+ * are_simulate_streamed).  ARE_LAYOUT_DIRECT (the default): the direct-access
+ * layout of Section III-B, one row per catalog event.  ARE_LAYOUT_COMPACT: a
+ * row index over the catalog (4 bytes per event, -1 for an event in none of
+ * the layer's ELTs) and rows only for the events present in some ELT, for
+ * large catalogs and sparse ELTs; an event without a row has a zero loss in
+ * every ELT, so its row is not read.  The results are the same bit for bit.
+ * FP64 analyses, portfolios, per-occurrence outputs and the server use the
+ * direct layout. */
+#define ARE_LAYOUT_DIRECT 0
+#define ARE_LAYOUT_COMPACT 1
+ARE_API are_status are_set_table_layout(are_ctx *ctx, int32_t layer, int32_t layout);
+
 /* Preprocessing (Section II-B, stage 1; Section III-B's direct access
  * tables): (re)build the layer's event-major direct-access table for the
  * YET's catalog in the given precision, on `stream`.  are_simulate builds

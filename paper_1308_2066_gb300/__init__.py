@@ -23,6 +23,7 @@ LIB_PATH = os.path.join(_HERE, "libare.so")
 ARE_OK, ARE_EINVAL, ARE_ENOMEM, ARE_ECUDA, ARE_ETIMEOUT, ARE_EBUSY, ARE_ENOTFOUND = range(7)
 ARE_FP64, ARE_FP32_KAHAN, ARE_FP32_FP64AGG = 0, 1, 2
 ARE_MAX_ELTS_PER_LAYER = 32
+ARE_LAYOUT_DIRECT, ARE_LAYOUT_COMPACT = 0, 1
 STATUS_NAMES = {0: "ARE_OK", 1: "ARE_EINVAL", 2: "ARE_ENOMEM", 3: "ARE_ECUDA",
                 4: "ARE_ETIMEOUT", 5: "ARE_EBUSY", 6: "ARE_ENOTFOUND"}
 PRECISIONS = {"fp64": ARE_FP64, "fp32_kahan": ARE_FP32_KAHAN, "fp32_fp64agg": ARE_FP32_FP64AGG}
@@ -103,6 +104,7 @@ _SIGS = {
     "are_tune_load": (C.c_int32, [_P, C.c_char_p]),
     "are_simulate_occurrences": (C.c_int32, [_P, C.c_int32, C.c_int32, C.c_int64, C.c_int64,
                                              C.c_int, _P, _P, _P, _P]),
+    "are_set_table_layout": (C.c_int32, [_P, C.c_int32, C.c_int32]),
     "are_prepare_folded": (C.c_int32, [_P, C.c_int32, C.c_int32, _P]),
     "are_simulate_folded": (C.c_int32, [_P, C.c_int32, C.c_int32, C.c_int64, C.c_int64, _P, _P]),
     "are_simulate_streamed": (C.c_int32, [_P, C.c_int32, C.c_int32, C.c_int64, _P, C.c_int32, _P,
@@ -273,6 +275,11 @@ def are_simulate_occurrences(ctx, layer: int, yet: int, trial_begin: int, n_tria
                                                _addr(marginals, np.float64),
                                                _addr(occ_max, np.float64),
                                                _addr(ylt, np.float64), _stream(stream)))
+
+
+def are_set_table_layout(ctx, layer: int, layout: int) -> None:
+    """ARE_LAYOUT_DIRECT (one row per catalog event) or ARE_LAYOUT_COMPACT."""
+    _check(ctx, lib().are_set_table_layout(ctx, int(layer), int(layout)))
 
 
 def are_prepare_folded(ctx, layer: int, yet: int, stream=None) -> None:

@@ -221,6 +221,43 @@ void size_table(are_ctx *ctx, Layer &L, Table &t, int32_t catalog, int jp, size_
     }
 }
 
+void free_compact(are_ctx *ctx, Compact &c)
+{
+    dfree(ctx, c.d, c.bytes);
+    c = Compact{};
+}
+
+// Build (or rebuild) the layer's compact FP32 table for `catalog`: room for
+// as many rows as the ELTs hold entries (or the catalog, if smaller).
+Compact &build_compact(are_ctx *ctx, Layer &L, int32_t catalog, cudaStream_t s)
+{
+    Compact &c = L.comp;
+    const int jp = table_jp((int)L.elts.size(), true);
+    const ScatterArgs a = scatter_args(ctx, L, catalog, jp);
+    int64_t entries = 0;
+    for (int j = 0; j < a.n_elts; ++j) entries += a.n[j];
+    const int64_t max_rows = std::max<int64_t>(1, std::min<int64_t>(catalog, entries));
+    if (c.d && (c.catalog != catalog || c.jp != jp || c.max_rows < max_rows)) free_compact(ctx, c);
+    if (!c.d) {
+        ++L.generation;
+        auto up256 = [](size_t x) { return (x + 255) & ~(size_t)255; };
+        c.counts_off = up256(sizeof(int32_t) * (size_t)catalog);
+        c.rows_off = c.counts_off + up256(sizeof(int32_t) * (size_t)compact_scan_blocks(catalog));
+        c.bytes = c.rows_off + sizeof(float) * (size_t)max_rows * jp;
+        c.d = dalloc(ctx, c.bytes);
+        c.catalog = catalog;
+        c.jp = jp;
+        c.max_rows = max_rows;
+    }
+    ctx->launches += launch_build_compact(c.row_of(), c.counts(), c.rows(),
+                                          sizeof(float) * (size_t)c.max_rows * jp, catalog, a, s);
+    return c;
+}
+
+// The tables an analysis of layer L in `precision` reads, built if missing.
+void ensure_tables(are_ctx *ctx, Layer &L, int32_t catalog, are_precision precision, cudaStream_t s,
+                   bool rebuild);
+
 // Build (or rebuild) the layer's table for `catalog` in fp32 or fp64.  An
 // FP64 table comes with its FP32 screen (values rounded up) for the
 // screened FP64 kernel.
@@ -241,6 +278,18 @@ Table &build_table(are_ctx *ctx, Layer &L, int32_t catalog, bool fp32, cudaStrea
         ctx->launches += launch_scatter_table(u.d, true, au, s, true);
     }
     return t;
+}
+
+void ensure_tables(are_ctx *ctx, Layer &L, int32_t catalog, are_precision precision, cudaStream_t s,
+                   bool rebuild)
+{
+    const bool fp32 = precision != ARE_FP64;
+    if (fp32 && L.layout == ARE_LAYOUT_COMPACT) {
+        if (rebuild || !L.comp.d || L.comp.catalog != catalog) build_compact(ctx, L, catalog, s);
+        return;
+    }
+    const Table &t = fp32 ? L.t32 : L.t64;
+    if (rebuild || !t.d || t.catalog != catalog) build_table(ctx, L, catalog, fp32, s);
 }
 
 Layer &layer_of(are_ctx *ctx, int32_t h)
@@ -377,6 +426,7 @@ int run_single(are_ctx *ctx, const Layer &L, const Yet &y, int64_t trial_begin, 
         w.n_items = (n_trials + w.trials_per_item - 1) / w.trials_per_item;
         return launch_items(w, L.t32.jp, te.cfg, precision, ctx->num_sms, s);
     }
+    const bool compact = fp32 && L.layout == ARE_LAYOUT_COMPACT && L.comp.d && L.comp.catalog == y.catalog;
     const Table &t = fp32 ? L.t32 : L.t64;
     SimArgs a{};
     a.ids = y.d_ids;
@@ -394,6 +444,12 @@ int run_single(are_ctx *ctx, const Layer &L, const Yet &y, int64_t trial_begin, 
     TermsF64 t64;
     fill_terms(ctx, L, t32, t64, a.any_share);
     a.n_elts = (int32_t)L.elts.size();
+    if (compact) {   // the staged kernel, through the row index
+        a.table = L.comp.rows();
+        a.row_of = L.comp.row_of();
+        a.kernel = 1;
+        return launch_simulate(a, precision, L.comp.jp, &t32, &t64, ctx->num_sms, s);
+    }
     if (!fp32 && te.kernel == 3) {
         ARE_CHECK(L.t32u.d && L.t32u.catalog == y.catalog, ARE_EINVAL, "FP32 screen not built");
         a.table2 = L.t32u.d;
@@ -614,6 +670,7 @@ are_status are_destroy(are_ctx *ctx)
             free_table(ctx, kv.second.t64);
             free_table(ctx, kv.second.t32u);
             free_folded(ctx, kv.second.fold);
+            free_compact(ctx, kv.second.comp);
         }
         for (auto &kv : ctx->elts) {
             dfree(ctx, kv.second.d_ids, 0);
@@ -759,7 +816,8 @@ are_status are_load_elt(are_ctx *ctx, int32_t n_entries, const int32_t *event_id
             max_id = std::max(max_id, ids[i]);
         }
         bool dup = false;
-        if (max_id < (1 << 28)) {   // bitmap of the ids seen
+        if (n_entries == 0) {
+        } else if (max_id < (1 << 28)) {   // bitmap of the ids seen
             std::vector<uint64_t> seen((size_t)max_id / 64 + 1, 0);
             for (int32_t i = 0; i < n_entries && !dup; ++i) {
                 uint64_t &w = seen[(size_t)ids[i] >> 6];
@@ -857,6 +915,7 @@ are_status are_free_layer(are_ctx *ctx, int32_t h)
         free_table(ctx, L.t64);
         free_table(ctx, L.t32u);
         free_folded(ctx, L.fold);
+        free_compact(ctx, L.comp);
         for (int32_t e : L.elts) ctx->elts[e].users--;
         ctx->layers.erase(h);
     });
@@ -870,7 +929,7 @@ are_status are_prepare(are_ctx *ctx, int32_t layer, int32_t yet, are_precision p
         Layer &L = layer_of(ctx, layer);
         Yet &y = yet_of(ctx, yet);
         CallStream cs(ctx, stream);
-        build_table(ctx, L, y.catalog, precision != ARE_FP64, cs.s);
+        ensure_tables(ctx, L, y.catalog, precision, cs.s, true);
         cs.finish();
     });
 }
@@ -889,13 +948,12 @@ are_status are_simulate(are_ctx *ctx, int32_t layer, int32_t yet, int64_t trial_
         CallStream cs(ctx, stream);
         cudaStream_t s = cs.s;
         const bool fp32 = precision != ARE_FP64;
-        Table &t = fp32 ? L.t32 : L.t64;
-        if (!t.d || t.catalog != y.catalog) build_table(ctx, L, y.catalog, fp32, s);
+        ensure_tables(ctx, L, y.catalog, precision, s, false);
         const bool dev_out = is_device_ptr(ylt);
         double *d_out = ylt;
         if (!dev_out) d_out = (double *)dalloc(ctx, sizeof(double) * n_trials);
         try {
-            const TuneEntry te = tuned(ctx, precision, y, t.jp, false);
+            const TuneEntry te = tuned(ctx, precision, y, table_jp((int)L.elts.size(), fp32), false);
             ctx->launches += run_single(ctx, L, y, trial_begin, n_trials, precision, d_out, te, s);
             if (!dev_out) {
                 ARE_CUDA_TRY(cudaMemcpyAsync(ylt, d_out, sizeof(double) * n_trials,
@@ -908,6 +966,17 @@ are_status are_simulate(are_ctx *ctx, int32_t layer, int32_t yet, int64_t trial_
             throw;
         }
         if (!dev_out) dfree(ctx, d_out, sizeof(double) * n_trials);
+    });
+}
+
+are_status are_set_table_layout(are_ctx *ctx, int32_t layer, int32_t layout)
+{
+    return guarded(ctx, [&] {
+        Layer &L = layer_of(ctx, layer);
+        ARE_CHECK(layout == ARE_LAYOUT_DIRECT || layout == ARE_LAYOUT_COMPACT, ARE_EINVAL,
+                  "layout must be ARE_LAYOUT_DIRECT or ARE_LAYOUT_COMPACT");
+        if (L.layout != layout) ++L.generation;
+        L.layout = layout;
     });
 }
 
@@ -1026,8 +1095,8 @@ are_status are_simulate_streamed(are_ctx *ctx, int32_t layer, int32_t catalog_si
         const size_t buf_bytes = sizeof(int32_t) * (size_t)(longest + 4 + kIdPad);
 
         const bool fp32 = precision != ARE_FP64;
-        Table &t = fp32 ? L.t32 : L.t64;
-        if (!t.d || t.catalog != catalog_size) build_table(ctx, L, catalog_size, fp32, s);
+        ensure_tables(ctx, L, catalog_size, precision, s, false);
+        const int jp = table_jp((int)L.elts.size(), fp32);
         int64_t *d_off = nullptr;
         int32_t *buf[2] = {nullptr, nullptr};
         const bool dev_out = is_device_ptr(ylt);
@@ -1053,7 +1122,7 @@ are_status are_simulate_streamed(are_ctx *ctx, int32_t layer, int32_t catalog_si
             ARE_CUDA_TRY(cudaMemsetAsync(ctx->d_flag, 0, sizeof(int), s));
             ARE_CUDA_TRY(cudaEventRecord(start, s));
             ARE_CUDA_TRY(cudaStreamWaitEvent(cp, start, 0));
-            const TuneEntry te = tuned(ctx, precision, v, t.jp, false);
+            const TuneEntry te = tuned(ctx, precision, v, jp, false);
             for (size_t c = 0; c + 1 < cut.size(); ++c) {
                 const int slot = (int)(c & 1);
                 const int64_t t0 = cut[c], t1 = cut[c + 1];

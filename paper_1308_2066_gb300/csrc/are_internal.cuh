@@ -100,12 +100,29 @@ struct Folded {
     }
 };
 
+// Compact FP32 table of one layer: row_of[catalog] (-1: no row) and rows
+// for the events present in some ELT, in one allocation laid out
+// [row_of | scan scratch | rows: max_rows x jp floats].
+struct Compact {
+    int32_t catalog = -1;
+    int jp = 0;
+    int64_t max_rows = 0;
+    void *d = nullptr;
+    size_t bytes = 0;
+    size_t counts_off = 0, rows_off = 0;
+    int32_t *row_of() const { return static_cast<int32_t *>(d); }
+    int32_t *counts() const { return reinterpret_cast<int32_t *>(static_cast<char *>(d) + counts_off); }
+    float *rows() const { return reinterpret_cast<float *>(static_cast<char *>(d) + rows_off); }
+};
+
 struct Layer {
     std::vector<int32_t> elts;
     are_layer_terms terms{};
     Table t32, t64;
     Table t32u;              // FP32 screen of t64: its values rounded up
     Folded fold;
+    int layout = 0;          // ARE_LAYOUT_DIRECT or ARE_LAYOUT_COMPACT (FP32 analysis)
+    Compact comp;
     uint64_t generation = 0;   // bumped whenever a table is (re)allocated or freed
 };
 
@@ -132,6 +149,7 @@ struct SimArgs {
     const void *table2;      // screened FP64: the FP32 screen [catalog][jp32]
     int32_t jp64;            // screened FP64: columns of the FP64 table
     int32_t n_elts;          // ELTs of the layer
+    const int32_t *row_of;   // compact FP32 table: row of each event (-1: none), or null
     double agg_r, agg_l;
     int any_share;           // some ELT has share != 1
     double *ylt;             // n_trials (may be null when occurrences are written)
@@ -235,6 +253,9 @@ struct Plan {
 int launch_scatter_table(void *table, bool fp32, const ScatterArgs &a, cudaStream_t s,
                          bool round_up = false);
 int launch_screen64(const SimArgs &a, int jp32, const TermsF64 &t, int num_sms, cudaStream_t s);
+int64_t compact_scan_blocks(int32_t catalog);
+int launch_build_compact(int32_t *row_of, int32_t *counts, float *rows, size_t rows_bytes,
+                         int32_t catalog, const ScatterArgs &a, cudaStream_t s);
 int32_t folded_words(int32_t catalog);
 bool folded_bits_in_smem(int32_t words);
 int launch_fold(const ScatterArgs &elts, const TermsF64 &tm, int32_t catalog, ulonglong2 *F,

@@ -462,7 +462,9 @@ struct Ids {
 };
 
 // EPL = events per lane in a batch (a batch is 32 * EPL events of a trial).
-template <int JP, int ACC, bool FIXED, int EPL>
+// CMP: compact table -- each id is turned into its row (a.row_of) one stage
+// before the row is copied, and an event without a row reads as zeros.
+template <int JP, int ACC, bool FIXED, int EPL, bool CMP = false>
 __global__ void __launch_bounds__(kStagedWarps * 32)
     k_simulate_staged(const SimArgs a, const TermsF32 tm)
 {
@@ -496,11 +498,17 @@ __global__ void __launch_bounds__(kStagedWarps * 32)
         for (int i = 0; i < NC; ++i) {
             const int q = lane + 32 * i, r = q / CH, c = q % CH;
             const int32_t id = __shfl_sync(kFull, idv.v[i / CH], r & 31);
-            const bool ok = r < b.cnt();
+            const bool ok = r < b.cnt() && (!CMP || id >= 0);
             const char *src = tab + (ok ? (size_t)(uint32_t)id * (JP * 4) + c * 16 : 0);
             cp_async16(sbuf + (uint32_t)(r * CH + chunk_slot<CH>(c, r)) * 16u, src, ok ? 16 : 0);
         }
         cp_commit();
+    };
+    auto to_rows = [&](Ids<EPL> &v) {
+        if (CMP) {
+#pragma unroll
+            for (int e = 0; e < EPL; ++e) v.v[e] = __ldg(a.row_of + v.v[e]);
+        }
     };
 
     typename std::conditional<ACC == ARE_FP32_KAHAN, AccKahan, AccF32F64>::type acc;
@@ -538,32 +546,36 @@ __global__ void __launch_bounds__(kStagedWarps * 32)
     Ids<EPL> i2 = load_ids(q2, pos);
     Batch q3;
     Ids<EPL> i3{};
+    to_rows(i0);
+    to_rows(i1);
     issue_rows(q0, i0, sbuf0);
 
-    // Each stage: ids three batches ahead, rows one batch ahead, compute.
-#define ARE_STAGE(QC, QN, IN, QF, IF, BC, BN, SN)                         \
+    // Each stage: ids three batches ahead, (compact tables) rows of the ids
+    // two batches ahead, row copies one batch ahead, compute.
+#define ARE_STAGE(QC, QN, IN, IT, QF, IF, BC, BN, SN)                     \
     if (QC.cnt() == 0) break;                                             \
     QF = next_batch<FIXED, ROWS>(a, cur, step, lane, empty_loss, pos);    \
     IF = load_ids(QF, pos);                                               \
+    to_rows(IT);                                                          \
     issue_rows(QN, IN, SN);                                               \
     cp_wait1();                                                           \
     __syncwarp();                                                         \
     compute(QC, BC);                                                      \
     __syncwarp();
     while (true) {
-        ARE_STAGE(q0, q1, i1, q3, i3, buf0, buf1, sbuf1)
-        ARE_STAGE(q1, q2, i2, q0, i0, buf1, buf0, sbuf0)
-        ARE_STAGE(q2, q3, i3, q1, i1, buf0, buf1, sbuf1)
-        ARE_STAGE(q3, q0, i0, q2, i2, buf1, buf0, sbuf0)
+        ARE_STAGE(q0, q1, i1, i2, q3, i3, buf0, buf1, sbuf1)
+        ARE_STAGE(q1, q2, i2, i3, q0, i0, buf1, buf0, sbuf0)
+        ARE_STAGE(q2, q3, i3, i0, q1, i1, buf0, buf1, sbuf1)
+        ARE_STAGE(q3, q0, i0, i1, q2, i2, buf1, buf0, sbuf0)
     }
 #undef ARE_STAGE
     cp_wait0();
 }
 
-template <int JP, int ACC, bool FIXED, int EPL>
+template <int JP, int ACC, bool FIXED, int EPL, bool CMP = false>
 void launch_staged(const SimArgs &a, const TermsF32 &terms, int num_sms, cudaStream_t s)
 {
-    auto kern = k_simulate_staged<JP, ACC, FIXED, EPL>;
+    auto kern = k_simulate_staged<JP, ACC, FIXED, EPL, CMP>;
     constexpr int smem = staged_smem_bytes<JP, EPL>();
     static int per_sm = 0;
     if (per_sm == 0) {
@@ -583,6 +595,12 @@ void launch_staged(const SimArgs &a, const TermsF32 &terms, int num_sms, cudaStr
 template <int JP, int ACC>
 void launch_staged_fx(const SimArgs &a, const TermsF32 &terms, int num_sms, cudaStream_t s)
 {
+    if (a.row_of) {   // compact table: two events per lane with Kahan sums, one with FP64 sums
+        constexpr int E = ACC == ARE_FP32_KAHAN ? 2 : 1;
+        if (a.off) launch_staged<JP, ACC, false, E, true>(a, terms, num_sms, s);
+        else launch_staged<JP, ACC, true, E, true>(a, terms, num_sms, s);
+        return;
+    }
     const bool two = a.epl == 2;
     if (a.off)
         two ? launch_staged<JP, ACC, false, 2>(a, terms, num_sms, s)
