@@ -446,8 +446,8 @@ int run_single(are_ctx *ctx, const Layer &L, const Yet &y, int64_t trial_begin, 
     a.n_elts = (int32_t)L.elts.size();
     if (compact) {   // the staged kernel, through the row index
         a.table = L.comp.rows();
-        a.row_of = L.comp.row_of();
-        a.kernel = 1;
+        a.table2 = L.comp.row_of();
+        a.kernel = 4;
         return launch_simulate(a, precision, L.comp.jp, &t32, &t64, ctx->num_sms, s);
     }
     if (!fp32 && te.kernel == 3) {

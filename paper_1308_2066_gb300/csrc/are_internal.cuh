@@ -146,10 +146,10 @@ struct SimArgs {
     int64_t trial_begin;
     int64_t n_trials;
     const void *table;       // [catalog][jp]
-    const void *table2;      // screened FP64: the FP32 screen [catalog][jp32]
+    const void *table2;      // screened FP64: the FP32 screen [catalog][jp32];
+                             // compact FP32 (kernel 4): the row index row_of[catalog]
     int32_t jp64;            // screened FP64: columns of the FP64 table
     int32_t n_elts;          // ELTs of the layer
-    const int32_t *row_of;   // compact FP32 table: row of each event (-1: none), or null
     double agg_r, agg_l;
     int any_share;           // some ELT has share != 1
     double *ylt;             // n_trials (may be null when occurrences are written)

@@ -462,7 +462,7 @@ struct Ids {
 };
 
 // EPL = events per lane in a batch (a batch is 32 * EPL events of a trial).
-// CMP: compact table -- each id is turned into its row (a.row_of) one stage
+// CMP: compact table -- each id is turned into its row (a.table2) one stage
 // before the row is copied, and an event without a row reads as zeros.
 template <int JP, int ACC, bool FIXED, int EPL, bool CMP = false>
 __global__ void __launch_bounds__(kStagedWarps * 32)
@@ -507,7 +507,7 @@ __global__ void __launch_bounds__(kStagedWarps * 32)
     auto to_rows = [&](Ids<EPL> &v) {
         if (CMP) {
 #pragma unroll
-            for (int e = 0; e < EPL; ++e) v.v[e] = __ldg(a.row_of + v.v[e]);
+            for (int e = 0; e < EPL; ++e) v.v[e] = __ldg(static_cast<const int32_t *>(a.table2) + v.v[e]);
         }
     };
 
@@ -595,7 +595,7 @@ void launch_staged(const SimArgs &a, const TermsF32 &terms, int num_sms, cudaStr
 template <int JP, int ACC>
 void launch_staged_fx(const SimArgs &a, const TermsF32 &terms, int num_sms, cudaStream_t s)
 {
-    if (a.row_of) {   // compact table: two events per lane with Kahan sums, one with FP64 sums
+    if (a.kernel == 4) {   // compact table: two events per lane with Kahan sums, one with FP64 sums
         constexpr int E = ACC == ARE_FP32_KAHAN ? 2 : 1;
         if (a.off) launch_staged<JP, ACC, false, E, true>(a, terms, num_sms, s);
         else launch_staged<JP, ACC, true, E, true>(a, terms, num_sms, s);
