@@ -41,8 +41,6 @@ PRECISION_NAMES = {0: "fp64", 1: "fp32_kahan", 2: "fp32_fp64agg"}
 DTYPES = {0: "f64", 1: "f32", 2: "f32"}
 FALLBACK_HBM_GBS = 6800.0
 CSRC = os.path.join(ROOT, "paper_1308_2066_gb300", "csrc")
-SIM_SOURCES = sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC)
-                     if f.endswith((".cu", ".cuh")))
 
 
 def parse():
@@ -82,24 +80,40 @@ def hbm_peak():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def sim_source_sha():
-    """Hash of the kernel sources (ncu counters go stale when they change)."""
+# Source files of each analysis kernel (its DRAM traffic from ncu goes stale
+# when one of them changes).
+KERNEL_SOURCES = {
+    "k_simulate_staged": ["simulate.cu", "are_internal.cuh"],
+    "k_staged": ["staged.cuh", "staged64.cu", "are_internal.cuh"],
+    "k_screen64": ["screen64.cu", "staged.cuh", "are_internal.cuh"],
+    "k_sim_items": ["sim_items.cu", "are_internal.cuh"],
+    "k_simulate": ["simulate.cu", "are_internal.cuh"],
+    "k_folded": ["folded.cu", "are_internal.cuh"],
+}
+
+
+def sources_sha(kernel_key: str):
+    """Hash of the source files of the kernel named by `kernel_key`."""
+    name = kernel_key.split("<")[0]
+    files = KERNEL_SOURCES.get(name)
+    if not files:
+        return None
     h = hashlib.sha256()
-    for path in SIM_SOURCES:
-        with open(path, "rb") as f:
-            h.update(f.read())
+    for f in files:
+        with open(os.path.join(CSRC, f), "rb") as fh:
+            h.update(fh.read())
     return h.hexdigest()[:16]
 
 
 def ncu_traffic(kernel_key: str):
-    """DRAM bytes per launch from a committed ncu summary, if it was taken on
-    the current kernel sources (else None)."""
+    """DRAM bytes per full launch from the committed ncu summary, if it was
+    taken on the kernel's current sources (else None)."""
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
             rec = json.load(f).get(kernel_key)
     except (OSError, ValueError):
         return None
-    if not rec or rec.get("kernel_sources_sha") != sim_source_sha():
+    if not rec or rec.get("sources_sha") != sources_sha(kernel_key):
         return None
     return rec.get("dram_bytes_per_launch")
 
