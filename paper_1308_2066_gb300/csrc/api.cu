@@ -255,12 +255,11 @@ Compact &build_compact(are_ctx *ctx, Layer &L, int32_t catalog, cudaStream_t s)
 }
 
 // The tables an analysis of layer L in `precision` reads, built if missing.
-void ensure_tables(are_ctx *ctx, Layer &L, int32_t catalog, are_precision precision, cudaStream_t s,
+void ensure_tables(are_ctx *ctx, Layer &L, const Yet &y, are_precision precision, cudaStream_t s,
                    bool rebuild);
+TuneEntry tuned(are_ctx *ctx, are_precision p, const Yet &y, int jp, bool multi);
 
-// Build (or rebuild) the layer's table for `catalog` in fp32 or fp64.  An
-// FP64 table comes with its FP32 screen (values rounded up) for the
-// screened FP64 kernel.
+// Build (or rebuild) the layer's table for `catalog` in fp32 or fp64.
 Table &build_table(are_ctx *ctx, Layer &L, int32_t catalog, bool fp32, cudaStream_t s)
 {
     Table &t = fp32 ? L.t32 : L.t64;
@@ -269,27 +268,38 @@ Table &build_table(are_ctx *ctx, Layer &L, int32_t catalog, bool fp32, cudaStrea
     size_table(ctx, L, t, catalog, jp, fp32 ? 4 : 8);
     ARE_CUDA_TRY(cudaMemsetAsync(t.d, 0, t.bytes, s));
     ctx->launches += launch_scatter_table(t.d, fp32, a, s);
-    if (!fp32) {
-        Table &u = L.t32u;
-        const int jpu = table_jp((int)L.elts.size(), true);
-        const ScatterArgs au = scatter_args(ctx, L, catalog, jpu);
-        size_table(ctx, L, u, catalog, jpu, 4);
-        ARE_CUDA_TRY(cudaMemsetAsync(u.d, 0, u.bytes, s));
-        ctx->launches += launch_scatter_table(u.d, true, au, s, true);
-    }
     return t;
 }
 
-void ensure_tables(are_ctx *ctx, Layer &L, int32_t catalog, are_precision precision, cudaStream_t s,
+// The FP32 screen of the layer's FP64 table (values rounded up), read by the
+// screened FP64 kernel only: built when that kernel is the tuned choice, so
+// the other FP64 kernels do not pay for it (its 64 MB would also push the
+// FP64 table out of L2 before the analysis).
+Table &build_screen(are_ctx *ctx, Layer &L, int32_t catalog, cudaStream_t s)
+{
+    Table &u = L.t32u;
+    const int jp = table_jp((int)L.elts.size(), true);
+    const ScatterArgs a = scatter_args(ctx, L, catalog, jp);
+    size_table(ctx, L, u, catalog, jp, 4);
+    ARE_CUDA_TRY(cudaMemsetAsync(u.d, 0, u.bytes, s));
+    ctx->launches += launch_scatter_table(u.d, true, a, s, true);
+    return u;
+}
+
+void ensure_tables(are_ctx *ctx, Layer &L, const Yet &y, are_precision precision, cudaStream_t s,
                    bool rebuild)
 {
     const bool fp32 = precision != ARE_FP64;
+    const int32_t catalog = y.catalog;
     if (fp32 && L.layout == ARE_LAYOUT_COMPACT) {
         if (rebuild || !L.comp.d || L.comp.catalog != catalog) build_compact(ctx, L, catalog, s);
         return;
     }
     const Table &t = fp32 ? L.t32 : L.t64;
     if (rebuild || !t.d || t.catalog != catalog) build_table(ctx, L, catalog, fp32, s);
+    if (!fp32 && tuned(ctx, precision, y, t.jp, false).kernel == 3 &&
+        (rebuild || !L.t32u.d || L.t32u.catalog != catalog))
+        build_screen(ctx, L, catalog, s);
 }
 
 Layer &layer_of(are_ctx *ctx, int32_t h)
@@ -450,13 +460,13 @@ int run_single(are_ctx *ctx, const Layer &L, const Yet &y, int64_t trial_begin, 
         a.kernel = 4;
         return launch_simulate(a, precision, L.comp.jp, &t32, &t64, ctx->num_sms, s);
     }
-    if (!fp32 && te.kernel == 3) {
-        ARE_CHECK(L.t32u.d && L.t32u.catalog == y.catalog, ARE_EINVAL, "FP32 screen not built");
+    if (!fp32 && te.kernel == 3 && L.t32u.d && L.t32u.catalog == y.catalog) {
         a.table2 = L.t32u.d;
         a.jp64 = t.jp;
         return launch_screen64(a, L.t32u.jp, t64, ctx->num_sms, s);
     }
-    if (!fp32 && te.kernel == 1) return launch_staged64(a, t.jp, t64, false, ctx->num_sms, s);
+    if (!fp32 && (te.kernel == 1 || te.kernel == 3))   // 3 without its screen: the staged kernel
+        return launch_staged64(a, t.jp, t64, false, ctx->num_sms, s);
     return launch_simulate(a, precision, t.jp, &t32, &t64, ctx->num_sms, s);
 }
 
@@ -599,12 +609,13 @@ void check_multi_args(are_ctx *ctx, const int32_t *layers, int32_t n_layers, con
 }
 
 void ensure_tables(are_ctx *ctx, const int32_t *layers, int32_t n_layers, const Yet &y, bool fp32,
-                   cudaStream_t s)
+                   cudaStream_t s, bool screens = false)
 {
     for (int32_t i = 0; i < n_layers; ++i) {
         Layer &L = layer_of(ctx, layers[i]);
         const Table &t = fp32 ? L.t32 : L.t64;
         if (!t.d || t.catalog != y.catalog) build_table(ctx, L, y.catalog, fp32, s);
+        if (!fp32 && screens && (!L.t32u.d || L.t32u.catalog != y.catalog)) build_screen(ctx, L, y.catalog, s);
     }
 }
 
@@ -929,7 +940,7 @@ are_status are_prepare(are_ctx *ctx, int32_t layer, int32_t yet, are_precision p
         Layer &L = layer_of(ctx, layer);
         Yet &y = yet_of(ctx, yet);
         CallStream cs(ctx, stream);
-        ensure_tables(ctx, L, y.catalog, precision, cs.s, true);
+        ensure_tables(ctx, L, y, precision, cs.s, true);
         cs.finish();
     });
 }
@@ -948,7 +959,7 @@ are_status are_simulate(are_ctx *ctx, int32_t layer, int32_t yet, int64_t trial_
         CallStream cs(ctx, stream);
         cudaStream_t s = cs.s;
         const bool fp32 = precision != ARE_FP64;
-        ensure_tables(ctx, L, y.catalog, precision, s, false);
+        ensure_tables(ctx, L, y, precision, s, false);
         const bool dev_out = is_device_ptr(ylt);
         double *d_out = ylt;
         if (!dev_out) d_out = (double *)dalloc(ctx, sizeof(double) * n_trials);
@@ -1095,7 +1106,7 @@ are_status are_simulate_streamed(are_ctx *ctx, int32_t layer, int32_t catalog_si
         const size_t buf_bytes = sizeof(int32_t) * (size_t)(longest + 4 + kIdPad);
 
         const bool fp32 = precision != ARE_FP64;
-        ensure_tables(ctx, L, catalog_size, precision, s, false);
+        ensure_tables(ctx, L, v, precision, s, false);
         const int jp = table_jp((int)L.elts.size(), fp32);
         int64_t *d_off = nullptr;
         int32_t *buf[2] = {nullptr, nullptr};
@@ -1303,7 +1314,9 @@ are_status are_simulate_portfolio(are_ctx *ctx, const int32_t *layers, int32_t n
         check_multi_args(ctx, layers, n_layers, y, trial_begin, n_trials, ylts);
         CallStream cs(ctx, stream);
         const bool fp32 = precision != ARE_FP64;
-        ensure_tables(ctx, layers, n_layers, y, fp32, cs.s);
+        ensure_tables(ctx, layers, n_layers, y, fp32, cs.s,
+                      !fp32 && tuned(ctx, precision, y, max_width(ctx, layers, n_layers, fp32),
+                                     n_layers > 1).kernel == 3);
         const std::vector<int32_t> lv(layers, layers + n_layers);
         const std::vector<double *> yv(ylts, ylts + n_layers);
         std::vector<uint64_t> gens;
@@ -1446,7 +1459,7 @@ are_status are_autotune(are_ctx *ctx, const int32_t *layers, int32_t n_layers, i
         check_multi_args(ctx, layers, n_layers, y, 0, y.n_trials, nullptr);
         CallStream cs(ctx, stream);
         const bool fp32 = precision != ARE_FP64;
-        ensure_tables(ctx, layers, n_layers, y, fp32, cs.s);
+        ensure_tables(ctx, layers, n_layers, y, fp32, cs.s, !fp32);   // the screened kernel is a candidate
         const bool multi = n_layers > 1;
         const int jp = max_width(ctx, layers, n_layers, fp32);
         const std::string key = tune_key(precision, y, jp, multi);

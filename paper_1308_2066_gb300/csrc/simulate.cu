@@ -52,7 +52,8 @@ __device__ __forceinline__ float comp(const float4 &v, int c)
 }
 __device__ __forceinline__ double comp(const double2 &v, int c) { return c == 0 ? v.x : v.y; }
 
-// Two FP32 operations in one packed instruction (sm_100 and later).
+// Two FP32 operations in one packed instruction (sm_100 and later), used by
+// the FP32 + Kahan staged kernel.
 __device__ __forceinline__ float2 sub2(float2 a, float2 b)
 {
     unsigned long long ra, rb, rd;
@@ -517,15 +518,42 @@ __global__ void __launch_bounds__(kStagedWarps * 32)
         for (int e = 0; e < EPL; ++e) {
             const int r = lane + 32 * e;
             float g = 0.f;
+            if constexpr (ACC == ARE_FP32_KAHAN) {
+                // column pairs in packed FP32x2 arithmetic (x - D and the
+                // running sums; min/max have no packed form): four partial
+                // sums over the columns j mod 4, added at the end
+                float2 g01 = make_float2(0.f, 0.f), g23 = make_float2(0.f, 0.f);
 #pragma unroll
-            for (int c = 0; c < CH; ++c) {
-                const float4 v = buf[r * CH + chunk_slot<CH>(c, r)];
+                for (int c = 0; c < CH; ++c) {
+                    const float4 v = buf[r * CH + chunk_slot<CH>(c, r)];
+                    const int j = c * 4;
+                    const float2 d01 = sub2(make_float2(v.x, v.y), make_float2(tm.ded[j], tm.ded[j + 1]));
+                    const float2 d23 = sub2(make_float2(v.z, v.w), make_float2(tm.ded[j + 2], tm.ded[j + 3]));
+                    float n0 = fminf(fmaxf(d01.x, 0.f), tm.lim[j]);
+                    float n1 = fminf(fmaxf(d01.y, 0.f), tm.lim[j + 1]);
+                    float n2 = fminf(fmaxf(d23.x, 0.f), tm.lim[j + 2]);
+                    float n3 = fminf(fmaxf(d23.y, 0.f), tm.lim[j + 3]);
+                    if (any_share) {
+                        n0 = __fmul_rn(n0, tm.share[j]);
+                        n1 = __fmul_rn(n1, tm.share[j + 1]);
+                        n2 = __fmul_rn(n2, tm.share[j + 2]);
+                        n3 = __fmul_rn(n3, tm.share[j + 3]);
+                    }
+                    g01 = add2(g01, make_float2(n0, n1));
+                    g23 = add2(g23, make_float2(n2, n3));
+                }
+                g = __fadd_rn(__fadd_rn(g01.x, g01.y), __fadd_rn(g23.x, g23.y));
+            } else {
 #pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    const int j = c * 4 + k;
-                    float n = fminf(fmaxf(__fsub_rn(comp(v, k), tm.ded[j]), 0.f), tm.lim[j]);
-                    if (any_share) n = __fmul_rn(n, tm.share[j]);
-                    g = __fadd_rn(g, n);
+                for (int c = 0; c < CH; ++c) {
+                    const float4 v = buf[r * CH + chunk_slot<CH>(c, r)];
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const int j = c * 4 + k;
+                        float n = fminf(fmaxf(__fsub_rn(comp(v, k), tm.ded[j]), 0.f), tm.lim[j]);
+                        if (any_share) n = __fmul_rn(n, tm.share[j]);
+                        g = __fadd_rn(g, n);
+                    }
                 }
             }
             acc.add(fminf(fmaxf(__fsub_rn(g, tm.occ_r), 0.f), tm.occ_l));
