@@ -297,7 +297,7 @@ ARE_API are_status are_simulate_folded(are_ctx *ctx, int32_t layer, int32_t yet,
  * II-B with the YET of Section II-A item 1 left where it is): the same
  * result as are_load_yet + are_simulate, without a device copy of the whole
  * YET.  The trials are cut into chunks of whole trials of about
- * chunk_events ids (0: 32M; a longer trial forms a chunk alone); the copy of
+ * chunk_events ids (0: 64M; a longer trial forms a chunk alone); the copy of
  * each chunk to the device (the host-to-device link, pinned memory at full
  * speed) overlaps the analysis of the one before, in two device buffers of
  * one chunk each.  Arguments as for are_load_yet (offsets: n_trials + 1

@@ -1087,7 +1087,7 @@ are_status are_simulate_streamed(are_ctx *ctx, int32_t layer, int32_t catalog_si
         }
         auto first_event = [&](int64_t t) { return offsets ? hoff[t] : t * (int64_t)events_per_trial; };
         // chunks of whole trials, about chunk_events ids each (a longer trial is a chunk alone)
-        const int64_t want = chunk_events > 0 ? chunk_events : ((int64_t)32 << 20);
+        const int64_t want = chunk_events > 0 ? chunk_events : ((int64_t)64 << 20);
         std::vector<int64_t> cut{0};
         int64_t longest = 0;
         for (int64_t t = 0; t < n_trials;) {
@@ -1139,15 +1139,17 @@ are_status are_simulate_streamed(are_ctx *ctx, int32_t layer, int32_t catalog_si
                 const int64_t t0 = cut[c], t1 = cut[c + 1];
                 const int64_t first = first_event(t0), n = first_event(t1) - first;
                 const int64_t lead = first & 3;   // keeps 16-byte vectors of ids aligned
+                // the copy stream only copies, back to back; the rest of a
+                // chunk's preparation runs on the analysis stream
                 if (c >= 2) ARE_CUDA_TRY(cudaStreamWaitEvent(cp, done[slot], 0));
                 int32_t *b = buf[slot];
-                ARE_CUDA_TRY(cudaMemsetAsync(b, 0, sizeof(int32_t) * lead, cp));
                 if (n) ARE_CUDA_TRY(cudaMemcpyAsync(b + lead, event_ids + first, sizeof(int32_t) * n,
                                                     cudaMemcpyHostToDevice, cp));
-                ARE_CUDA_TRY(cudaMemsetAsync(b + lead + n, 0, sizeof(int32_t) * kIdPad, cp));
-                ctx->launches += launch_sanitize_ids(b + lead, n, catalog_size, ctx->d_flag, cp);
                 ARE_CUDA_TRY(cudaEventRecord(ready[slot], cp));
                 ARE_CUDA_TRY(cudaStreamWaitEvent(s, ready[slot], 0));
+                if (lead) ARE_CUDA_TRY(cudaMemsetAsync(b, 0, sizeof(int32_t) * lead, s));
+                ARE_CUDA_TRY(cudaMemsetAsync(b + lead + n, 0, sizeof(int32_t) * kIdPad, s));
+                ctx->launches += launch_sanitize_ids(b + lead, n, catalog_size, ctx->d_flag, s);
                 Yet cv = v;
                 cv.d_ids = b + lead - first;   // indexed by the YET's own event numbers
                 ctx->launches += run_single(ctx, L, cv, t0, t1 - t0, precision, d_out + t0, te, s);
