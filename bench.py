@@ -859,7 +859,8 @@ def main():
                    "elts": J, "catalog": y.catalog, "precision": PRECISION_NAMES[prec],
                    "step": "repack table + simulate all trials + PML 100/250 + TVaR 99 readback",
                    "l2": "inputs larger than L2 (4 GB YET streamed every step)",
-                   "parallelism": f"trial blocks per GPU x{world}"},
+                   "parallelism": f"trial blocks per GPU x{world}",
+                   "gpu": torch.cuda.get_device_name()},
         "roofline": roofline(y.n_events, y.n_trials, J, prec, head["sim_ms"],
                              tuned.get(PRECISION_NAMES[prec]),
                              ceilings[row_bytes(J, prec, tuned.get(PRECISION_NAMES[prec]))]),

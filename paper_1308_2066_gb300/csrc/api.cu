@@ -9,6 +9,8 @@
 #include <cstring>
 #include <unordered_map>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "are_internal.cuh"
 
 namespace are {
@@ -56,6 +58,15 @@ bool is_device_ptr(const void *p)
 // only enqueues work.  NULL means: wait for all earlier work on the device
 // (the caller's inputs may come from any stream), run on the context's own
 // stream, and finish before returning.
+// NVTX range over one library call (named in profilers' timelines; free
+// when no profiler is attached).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
+
 struct CallStream {
     cudaStream_t s;
     bool own;
@@ -735,6 +746,7 @@ are_status are_load_yet(are_ctx *ctx, int32_t catalog_size, int64_t n_trials,
                         const int32_t *event_ids, const float *timestamps, int32_t *yet_handle)
 {
     return guarded(ctx, [&] {
+        NvtxRange nvtx("are_load_yet");
         ARE_CHECK(yet_handle, ARE_EINVAL, "yet_handle is NULL");
         ARE_CHECK(catalog_size > 0, ARE_EINVAL, "catalog_size must be > 0");
         ARE_CHECK(n_trials >= 0 && n_trials < (int64_t)INT32_MAX, ARE_EINVAL,
@@ -806,6 +818,7 @@ are_status are_load_elt(are_ctx *ctx, int32_t n_entries, const int32_t *event_id
                         const double *losses, const are_fin_terms *terms, int32_t *elt_handle)
 {
     return guarded(ctx, [&] {
+        NvtxRange nvtx("are_load_elt");
         ARE_CHECK(elt_handle && terms, ARE_EINVAL, "elt_handle and terms must not be NULL");
         ARE_CHECK(n_entries >= 0, ARE_EINVAL, "n_entries must be >= 0");
         ARE_CHECK(n_entries == 0 || (event_ids && losses), ARE_EINVAL, "event_ids/losses are NULL");
@@ -936,6 +949,7 @@ are_status are_prepare(are_ctx *ctx, int32_t layer, int32_t yet, are_precision p
                        void *stream)
 {
     return guarded(ctx, [&] {
+        NvtxRange nvtx("are_prepare");
         check_precision(precision);
         Layer &L = layer_of(ctx, layer);
         Yet &y = yet_of(ctx, yet);
@@ -949,6 +963,7 @@ are_status are_simulate(are_ctx *ctx, int32_t layer, int32_t yet, int64_t trial_
                         int64_t n_trials, are_precision precision, double *ylt, void *stream)
 {
     return guarded(ctx, [&] {
+        NvtxRange nvtx("are_simulate");
         check_precision(precision);
         Layer &L = layer_of(ctx, layer);
         Yet &y = yet_of(ctx, yet);
@@ -994,6 +1009,7 @@ are_status are_set_table_layout(are_ctx *ctx, int32_t layer, int32_t layout)
 are_status are_prepare_folded(are_ctx *ctx, int32_t layer, int32_t yet, void *stream)
 {
     return guarded(ctx, [&] {
+        NvtxRange nvtx("are_prepare_folded");
         Layer &L = layer_of(ctx, layer);
         Yet &y = yet_of(ctx, yet);
         CallStream cs(ctx, stream);
@@ -1006,6 +1022,7 @@ are_status are_simulate_folded(are_ctx *ctx, int32_t layer, int32_t yet, int64_t
                                int64_t n_trials, double *ylt, void *stream)
 {
     return guarded(ctx, [&] {
+        NvtxRange nvtx("are_simulate_folded");
         Layer &L = layer_of(ctx, layer);
         Yet &y = yet_of(ctx, yet);
         ARE_CHECK(trial_begin >= 0 && n_trials >= 0 && trial_begin + n_trials <= y.n_trials,
@@ -1054,6 +1071,7 @@ are_status are_simulate_streamed(are_ctx *ctx, int32_t layer, int32_t catalog_si
                                  are_precision precision, double *ylt, void *stream)
 {
     return guarded(ctx, [&] {
+        NvtxRange nvtx("are_simulate_streamed");
         check_precision(precision);
         Layer &L = layer_of(ctx, layer);
         ARE_CHECK(catalog_size > 0, ARE_EINVAL, "catalog_size must be > 0");
@@ -1174,6 +1192,7 @@ are_status are_gather_ceiling(are_ctx *ctx, int32_t yet, int32_t row_bytes, int6
                               int64_t n_trials, int32_t reps, double *rows_per_s)
 {
     return guarded(ctx, [&] {
+        NvtxRange nvtx("are_gather_ceiling");
         Yet &y = yet_of(ctx, yet);
         ARE_CHECK(row_bytes == 32 || row_bytes == 64 || row_bytes == 128, ARE_EINVAL,
                   "row_bytes must be 32, 64 or 128");
@@ -1218,6 +1237,7 @@ are_status are_simulate_occurrences(are_ctx *ctx, int32_t layer, int32_t yet, in
                                     double *occ_max, double *ylt, void *stream)
 {
     return guarded(ctx, [&] {
+        NvtxRange nvtx("are_simulate_occurrences");
         check_precision(precision);
         Layer &L = layer_of(ctx, layer);
         Yet &y = yet_of(ctx, yet);
@@ -1266,6 +1286,7 @@ are_status are_risk_measures(are_ctx *ctx, const double *ylt, int64_t n,
                              void *stream)
 {
     return guarded(ctx, [&] {
+        NvtxRange nvtx("are_risk_measures");
         ARE_CHECK(n > 0 && ylt, ARE_EINVAL, "need a YLT of n > 0 losses");
         ARE_CHECK(n < (int64_t)UINT32_MAX, ARE_EINVAL, "YLT too long for the selection counters");
         ARE_CHECK(n_rp >= 0 && n_tv >= 0, ARE_EINVAL, "negative count");
@@ -1310,6 +1331,7 @@ are_status are_simulate_portfolio(are_ctx *ctx, const int32_t *layers, int32_t n
                                   are_precision precision, double *const *ylts, void *stream)
 {
     return guarded(ctx, [&] {
+        NvtxRange nvtx("are_simulate_portfolio");
         check_precision(precision);
         Yet &y = yet_of(ctx, yet);
         ARE_CHECK(ylts, ARE_EINVAL, "ylts is NULL");
@@ -1398,6 +1420,7 @@ are_status are_risk_measures_batch(are_ctx *ctx, const double *const *ylts, int3
                                    double *tvar_out, void *stream)
 {
     return guarded(ctx, [&] {
+        NvtxRange nvtx("are_risk_measures_batch");
         ARE_CHECK(ylts && n_ylt >= 1, ARE_EINVAL, "need at least one YLT");
         ARE_CHECK(n > 0 && n < (int64_t)UINT32_MAX, ARE_EINVAL, "bad YLT length");
         ARE_CHECK(n_rp >= 0 && n_tv >= 0, ARE_EINVAL, "negative count");
@@ -1456,6 +1479,7 @@ are_status are_autotune(are_ctx *ctx, const int32_t *layers, int32_t n_layers, i
                         are_precision precision, void *stream, are_tune_result *best)
 {
     return guarded(ctx, [&] {
+        NvtxRange nvtx("are_autotune");
         check_precision(precision);
         Yet &y = yet_of(ctx, yet);
         check_multi_args(ctx, layers, n_layers, y, 0, y.n_trials, nullptr);
