@@ -375,6 +375,10 @@ typedef struct {
     int32_t one_at_a_time;     /* 1: no batching; each request runs alone, whole, in order */
     are_precision precision;   /* ARE_FP32_KAHAN or ARE_FP32_FP64AGG */
     int64_t stall_us;          /* test hook: the scheduler sleeps this long before each launch */
+    int32_t folded;            /* nonzero: price each request on its folded table (FP64
+                                  occurrence loss per catalog event, exact trial sums, one
+                                  lookup per occurrence -- the variant of are_simulate_folded);
+                                  precision is then not used */
 } are_server_cfg;
 
 /* One pricing request: a layer of the context's ELTs with its own layer terms,

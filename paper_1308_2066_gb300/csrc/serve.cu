@@ -19,6 +19,11 @@
 //   4. waits (bounded) for the previous iteration and posts its results.
 // One iteration is always queued ahead of the one being waited for, so the
 // GPU is not left idle while the host reacts.
+//
+// With cfg.folded set, each admitted request gets a folded table instead
+// (its FP64 occurrence loss per catalog event, as are_prepare_folded builds
+// it) and its slices run on the folded trial kernel: one lookup per
+// occurrence and exact trial sums -- the folded-table variant of the method.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -182,6 +187,18 @@ void post(Server &S, const Request &r, are_status st, const double *res, Clock::
     S.results[r.ticket] = p;
 }
 
+// A folded table in an arena block: [hmax | 248 B][bits][F].
+size_t folded_block_bytes(int32_t catalog)
+{
+    return 256 + up((size_t)folded_words(catalog) * 4) + (size_t)catalog * 16;
+}
+unsigned long long *folded_hmax(char *b) { return reinterpret_cast<unsigned long long *>(b); }
+uint32_t *folded_bits(char *b) { return reinterpret_cast<uint32_t *>(b + 256); }
+ulonglong2 *folded_F(char *b, int32_t catalog)
+{
+    return reinterpret_cast<ulonglong2 *>(b + 256 + up((size_t)folded_words(catalog) * 4));
+}
+
 // Table of an admitted request, built on the server stream in its arena block.
 void build_request_table(Server &S, Slot &sl)
 {
@@ -197,6 +214,26 @@ void build_request_table(Server &S, Slot &sl)
             a.n[j] = e.n;
             a.fx[j] = e.terms.fx;
         }
+    }
+    if (S.cfg.folded) {
+        TermsF64 tm;
+        std::memset(&tm, 0, sizeof tm);
+        {
+            std::lock_guard<std::recursive_mutex> lk(S.ctx->mu);
+            for (int j = 0; j < kMaxElts; ++j) tm.share[j] = 1.0;
+            for (size_t j = 0; j < sl.req.elts.size(); ++j) {
+                const are_fin_terms &f = S.ctx->elts.at(sl.req.elts[j]).terms;
+                tm.ded[j] = f.deductible;
+                tm.lim[j] = f.limit;
+                tm.share[j] = f.share;
+            }
+        }
+        tm.occ_r = sl.req.terms.occ_ret;
+        tm.occ_l = sl.req.terms.occ_lim;
+        char *b = S.d_arena + sl.tab_off;
+        add_launches(S, launch_fold(a, tm, S.y->catalog, folded_F(b, S.y->catalog), folded_bits(b),
+                                    folded_hmax(b), S.ctx->num_sms, S.stream));
+        return;
     }
     ARE_CUDA_TRY(cudaMemsetAsync(S.d_arena + sl.tab_off, 0, sl.tab_bytes, S.stream));
     add_launches(S, launch_scatter_table(S.d_arena + sl.tab_off, true, a, S.stream));
@@ -279,7 +316,9 @@ void scheduler(Server *SP)
 {
     Server &S = *SP;
     const int tpi = S.cfg.trials_per_item > 0 ? S.cfg.trials_per_item : 8;
-    const int64_t budget = S.cfg.events_per_launch > 0 ? S.cfg.events_per_launch : 200000000;
+    // events per iteration (a folded table's occurrence costs far less)
+    const int64_t budget = S.cfg.events_per_launch > 0 ? S.cfg.events_per_launch
+                                                       : S.cfg.folded ? 1000000000 : 200000000;
     try {
         ARE_CUDA_TRY(cudaSetDevice(S.ctx->device));
         for (;;) {
@@ -306,7 +345,8 @@ void scheduler(Server *SP)
                     Request &r = S.pending.front();
                     Slot &sl = S.slots[free_slot];
                     sl.jp = table_jp((int)r.elts.size(), true);
-                    sl.tab_bytes = (size_t)S.y->catalog * sl.jp * sizeof(float);
+                    sl.tab_bytes = S.cfg.folded ? folded_block_bytes(S.y->catalog)
+                                                : (size_t)S.y->catalog * sl.jp * sizeof(float);
                     sl.ylt_bytes = sizeof(double) * (size_t)r.n_trials;
                     size_t a = 0, b = 0;
                     if (!S.arena.take(sl.tab_bytes, a)) break;
@@ -338,7 +378,7 @@ void scheduler(Server *SP)
             // Short requests overtake long ones, and a launch touches only a
             // few requests' tables, which keeps them resident in L2.
             const int buf = (int)(S.iter & 1);
-            std::vector<int> part[3], big;
+            std::vector<int> part[3], big, fold;
             std::vector<int64_t> slice;
             {
                 std::lock_guard<std::mutex> lk(S.mu);
@@ -366,7 +406,9 @@ void scheduler(Server *SP)
                     }
                     slice[o.second] = take;
                     left_budget -= (double)take;
-                    if (sl.staged)
+                    if (S.cfg.folded)
+                        fold.push_back(o.second);
+                    else if (sl.staged)
                         big.push_back(o.second);
                     else
                         part[sl.jp == 8 ? 0 : sl.jp == 16 ? 1 : 2].push_back(o.second);
@@ -418,6 +460,26 @@ void scheduler(Server *SP)
                 cfg.trials_per_item = tpi;
                 cfg.rows_in_flight = 4;
                 launches += launch_items(w, kWidths3[g], cfg, S.cfg.precision, S.ctx->num_sms, S.stream);
+            }
+            // folded tables: one trial-pass launch per request slice
+            for (int i : fold) {
+                const Slot &sl = S.slots[i];
+                char *b = S.d_arena + sl.tab_off;
+                FoldArgs fa{};
+                fa.ids = S.y->d_ids;
+                fa.off = S.y->d_off;
+                fa.k = S.y->k;
+                fa.trial_begin = sl.launched;
+                fa.n_trials = slice[i];
+                fa.n_events = S.y->n_events;
+                fa.F = folded_F(b, S.y->catalog);
+                fa.bits = folded_bits(b);
+                fa.words = folded_words(S.y->catalog);
+                fa.hmax = folded_hmax(b);
+                fa.agg_r = sl.req.terms.agg_ret;
+                fa.agg_l = sl.req.terms.agg_lim;
+                fa.ylt = reinterpret_cast<double *>(S.d_arena + sl.ylt_off) + sl.launched;
+                launches += launch_folded(fa, S.ctx->num_sms, S.stream);
             }
             // large slices, one staged single-layer launch each
             for (int i : big) {
@@ -572,8 +634,8 @@ are_status are_server_start(are_ctx *ctx, int32_t yet, const are_server_cfg *cfg
                   "max_inflight must lie in 1..256");
         ARE_CHECK(cfg->max_pending >= 1, ARE_EINVAL, "max_pending must be >= 1");
         ARE_CHECK(cfg->arena_bytes >= 4096, ARE_EINVAL, "arena_bytes too small");
-        ARE_CHECK(cfg->precision == ARE_FP32_KAHAN || cfg->precision == ARE_FP32_FP64AGG, ARE_EINVAL,
-                  "the server runs the FP32 table paths");
+        ARE_CHECK(cfg->folded || cfg->precision == ARE_FP32_KAHAN || cfg->precision == ARE_FP32_FP64AGG,
+                  ARE_EINVAL, "the server runs the FP32 table paths (or folded tables)");
         ARE_CHECK(cfg->trials_per_item >= 0 && cfg->events_per_launch >= 0 && cfg->stall_us >= 0,
                   ARE_EINVAL, "negative server setting");
         ARE_CUDA_TRY(cudaSetDevice(ctx->device));

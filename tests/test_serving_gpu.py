@@ -230,3 +230,25 @@ def test_large_request_on_the_staged_kernel(are):
             assert list(res["pml"]) == list(pml) and list(res["tvar"]) == list(tv), (mix, res, pml, tv)
     finally:
         are.are_destroy(ctx)
+
+
+def test_folded_server_matches_oracle_alone_and_in_a_mix(are, orc, pool, served):
+    """Folded tables in the server: FP64 occurrence losses and exact trial
+    sums, so PML/TVaR agree with the oracle within the FP64 tolerance and a
+    request's result is identical alone and in a mix."""
+    ctx, y, hs = served
+    reqs = requests(11, 24)
+    are.are_server_start(ctx, y, max_inflight=8, events_per_launch=500_000, folded=True)
+    tickets = [submit(are, ctx, hs, r) for r in reqs]
+    mixed = [are.are_wait(ctx, t, 60_000_000) for t in tickets]
+    are.are_server_stop(ctx)
+    for r, res in zip(reqs, mixed):
+        assert res["status"] == are.ARE_OK
+        pml, tv = oracle_measures(orc, pool, r)
+        assert rel_close(res["pml"], pml, 1e-12), (res["pml"], pml)
+        assert rel_close(res["tvar"], tv, 1e-12), (res["tvar"], tv)
+    are.are_server_start(ctx, y, max_inflight=1, folded=True)
+    for r, res in zip(reqs[:5], mixed[:5]):
+        alone = are.are_wait(ctx, submit(are, ctx, hs, r), 60_000_000)
+        assert alone["pml"] == res["pml"] and alone["tvar"] == res["tvar"]
+    are.are_server_stop(ctx)
