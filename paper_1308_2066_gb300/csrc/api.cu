@@ -1083,6 +1083,7 @@ are_status are_simulate_streamed(are_ctx *ctx, int32_t layer, int32_t catalog_si
         if (n_trials == 0) return;
         ARE_CHECK(event_ids && !is_device_ptr(event_ids), ARE_EINVAL,
                   "event_ids must be host memory (a device-resident YET goes through are_load_yet)");
+        fence_device_inputs({offsets});
         CallStream cs(ctx, stream);
         cudaStream_t s = cs.s;
         if (!ctx->copy_stream) ARE_CUDA_TRY(cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking));

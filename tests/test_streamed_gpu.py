@@ -102,3 +102,45 @@ def test_invalid_ids_and_arguments(are, ctx):
             are.are_simulate_streamed(ctx, L.layers[0], wl.yet.catalog, 500, None, 0, wl.yet.ids, 1, out)
     finally:
         L.release()
+
+
+def test_device_offsets_and_caller_stream(are, ctx):
+    """Offsets given in device memory, the analysis enqueued after other work
+    on a caller stream: the same YLT as the resident analysis."""
+    import torch
+    g = np.random.Generator(np.random.PCG64(13))
+    yet = W.yet_poisson(g, 1500, 150, 8000, timestamps=False)
+    elts = [W.percentile_terms(W.elt_lognormal(g, 8000, 700)) for _ in range(6)]
+    wl = W.Workload("d", yet, elts, [W.Layer(list(range(6)), 1e4, 1e6, 2e4, INF)])
+    L = Loaded(are, ctx, wl, timestamps=False)
+    try:
+        ref = L.simulate(0, 1)
+        s = torch.cuda.Stream()
+        off = torch.from_numpy(yet.offsets).cuda()
+        out = torch.full((1500,), -1.0, dtype=torch.float64, device="cuda")
+        with torch.cuda.stream(s):
+            out.fill_(-2.0)                   # queued before the analysis on the same stream
+        are.are_simulate_streamed(ctx, L.layers[0], yet.catalog, 1500, off, 0, yet.ids, 1, out,
+                                  chunk_events=20_000, stream=s)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(out.cpu().numpy(), ref)
+    finally:
+        L.release()
+
+
+def test_gather_ceiling(are, ctx):
+    """The measurement helper: a positive rate for each row size, argument checks."""
+    import torch
+    g = np.random.Generator(np.random.PCG64(14))
+    yet = W.yet_fixed(g, 4000, 500, 100_000, timestamps=False)
+    h = are.are_load_yet(ctx, yet.catalog, yet.n_trials, None, yet.k, torch.from_numpy(yet.ids).cuda())
+    try:
+        for rb in (32, 64, 128):
+            rate = are.are_gather_ceiling(ctx, h, rb, 0, yet.n_trials, reps=1)
+            assert rate > 1e8
+        with pytest.raises(are.AreError):
+            are.are_gather_ceiling(ctx, h, 48, 0, yet.n_trials)
+        with pytest.raises(are.AreError):
+            are.are_gather_ceiling(ctx, h, 64, 0, yet.n_trials + 1)
+    finally:
+        are.are_free_yet(ctx, h)
