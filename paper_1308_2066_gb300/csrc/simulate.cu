@@ -494,14 +494,27 @@ __global__ void __launch_bounds__(kStagedWarps * 32)
         return r;
     };
     // copy i of a lane moves chunk (lane + 32 i) % CH of row (lane + 32 i) / CH
+    // (a full batch of a direct table copies every row unconditionally; the
+    // other batches zero-fill the rows past their events and, with compact
+    // tables, the rows of events that have none)
     auto issue_rows = [&](const Batch &b, const Ids<EPL> &idv, uint32_t sbuf) {
+        if (!CMP && b.cnt() == ROWS) {
 #pragma unroll
-        for (int i = 0; i < NC; ++i) {
-            const int q = lane + 32 * i, r = q / CH, c = q % CH;
-            const int32_t id = __shfl_sync(kFull, idv.v[i / CH], r & 31);
-            const bool ok = r < b.cnt() && (!CMP || id >= 0);
-            const char *src = tab + (ok ? (size_t)(uint32_t)id * (JP * 4) + c * 16 : 0);
-            cp_async16(sbuf + (uint32_t)(r * CH + chunk_slot<CH>(c, r)) * 16u, src, ok ? 16 : 0);
+            for (int i = 0; i < NC; ++i) {
+                const int q = lane + 32 * i, r = q / CH, c = q % CH;
+                const int32_t id = __shfl_sync(kFull, idv.v[i / CH], r & 31);
+                cp_async16(sbuf + (uint32_t)(r * CH + chunk_slot<CH>(c, r)) * 16u,
+                           tab + (size_t)(uint32_t)id * (JP * 4) + c * 16, 16);
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < NC; ++i) {
+                const int q = lane + 32 * i, r = q / CH, c = q % CH;
+                const int32_t id = __shfl_sync(kFull, idv.v[i / CH], r & 31);
+                const bool ok = r < b.cnt() && (!CMP || id >= 0);
+                const char *src = tab + (ok ? (size_t)(uint32_t)id * (JP * 4) + c * 16 : 0);
+                cp_async16(sbuf + (uint32_t)(r * CH + chunk_slot<CH>(c, r)) * 16u, src, ok ? 16 : 0);
+            }
         }
         cp_commit();
     };
