@@ -78,15 +78,27 @@ __global__ void __launch_bounds__(kWarps * 32) k_screen64(const SimArgs a, const
     auto load_ids = [&](const Batch &b) -> int32_t {
         return lane < b.cnt ? __ldcs(a.ids + b.pos + lane) : 0;
     };
+    // (a full batch copies every row unconditionally; a partial one
+    // zero-fills the rows past its events)
     auto issue_rows = [&](const Batch &b, int32_t idv, float4 *buf) {
+        if (b.cnt == 32) {
 #pragma unroll
-        for (int i = 0; i < CH; ++i) {
-            const int q = lane + 32 * i, r = q / CH, c = q % CH;
-            const int32_t id = __shfl_sync(kFull, idv, r);
-            const bool ok = r < b.cnt;
-            const float4 *src = ok ? reinterpret_cast<const float4 *>(tab + (size_t)id * JP) + c
-                                   : reinterpret_cast<const float4 *>(tab);
-            cp_async16(smem_addr(buf + r * CH + chunk_slot<CH>(c, r)), src, ok ? 16 : 0);
+            for (int i = 0; i < CH; ++i) {
+                const int q = lane + 32 * i, r = q / CH, c = q % CH;
+                const int32_t id = __shfl_sync(kFull, idv, r);
+                cp_async16(smem_addr(buf + r * CH + chunk_slot<CH>(c, r)),
+                           reinterpret_cast<const float4 *>(tab + (size_t)id * JP) + c, 16);
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < CH; ++i) {
+                const int q = lane + 32 * i, r = q / CH, c = q % CH;
+                const int32_t id = __shfl_sync(kFull, idv, r);
+                const bool ok = r < b.cnt;
+                const float4 *src = ok ? reinterpret_cast<const float4 *>(tab + (size_t)id * JP) + c
+                                       : reinterpret_cast<const float4 *>(tab);
+                cp_async16(smem_addr(buf + r * CH + chunk_slot<CH>(c, r)), src, ok ? 16 : 0);
+            }
         }
         cp_commit();
     };
