@@ -159,6 +159,28 @@ def test_ragged_every_table_width(are, ctx, orc, J):
         L.release()
 
 
+@pytest.mark.parametrize("k", [1, 31, 32, 33, 63, 64, 65, 128, 129])
+def test_fixed_trial_lengths_at_batch_edges(are, ctx, orc, k):
+    """Trials whose length is a whole number of staging batches (32 or 64
+    events), one more or one less: every batch full, or a last batch of a
+    single event, in each precision."""
+    g = np.random.Generator(np.random.PCG64(500 + k))
+    yet = W.yet_fixed(g, 600, k, 5000)
+    elts = [W.percentile_terms(W.elt_lognormal(g, 5000, 1500)) for _ in range(16)]
+    pooled = np.concatenate([e.losses for e in elts])
+    occ_r = W.nearest_rank(pooled, 200)
+    wl = W.Workload(f"edges_k{k}", yet, elts,
+                    [W.Layer(list(range(16)), occ_r, W.nearest_rank(pooled, 990) * 4, occ_r, INF)])
+    L = Loaded(are, ctx, wl)
+    try:
+        ref = orc.simulate_layer(wl)
+        for p in PRECISIONS:
+            ok, st = mixed_check(L.simulate(0, p), ref.ylt, ref.gross, RTOL[p])
+            assert ok, (p, st)
+    finally:
+        L.release()
+
+
 def test_empty_trials_and_short_tails(are, ctx, orc):
     g = np.random.Generator(np.random.PCG64(77))
     yet = W.yet_poisson(g, 4000, 3, 300)         # many empty and 1-2 event trials
