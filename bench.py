@@ -644,8 +644,7 @@ def run_precision_stress(args):
     ref = oracle.simulate_layer(wl, trials=sample)
     rows = {}
     for p in (0, 2, 1):
-        if not args.no_tune:
-            are.are_autotune(ctx, [layer], yet, p, stream)
+        tuned = are.are_autotune(ctx, [layer], yet, p, stream) if not args.no_tune else None
         evs = []
         for _ in range(args.warmup + args.steps):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -669,7 +668,7 @@ def run_precision_stress(args):
         full[np.sort(cand)] = rc.ylt
         rp, rt = oracle.risk_measures(full, RPS, LEVELS)
         rows[PRECISION_NAMES[p]] = {
-            "sim_ms": round(ms, 4),
+            "sim_ms": round(ms, 4), "tuned": tuned,
             "value": round(y.n_events * len(L.elts) / (ms * 1e-3) / 1e9, 3),
             "ylt_rel_err_max": float(rel.max()), "ylt_rel_err_median": float(np.median(rel)),
             "ylt_err_over_gross_max": float((d / ref.gross).max()),

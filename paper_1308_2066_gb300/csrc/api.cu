@@ -214,6 +214,7 @@ ScatterArgs scatter_args(are_ctx *ctx, const Layer &L, int32_t catalog, int jp)
         a.loss[j] = e.d_loss;
         a.n[j] = e.n;
         a.fx[j] = e.terms.fx;
+        a.ded[j] = e.terms.deductible;
     }
     return a;
 }

@@ -181,6 +181,7 @@ struct ScatterArgs {
     const double *loss[kMaxElts];
     int32_t n[kMaxElts];
     double fx[kMaxElts];
+    double ded[kMaxElts];    // per-ELT deductible, subtracted as the table is built
     int32_t n_elts;
     int32_t jp;
 };

@@ -6,8 +6,13 @@
 // one random access per ELT.  Here row e of a single table holds event e's
 // losses in all J ELTs of the layer, in layer order, padded to a whole number
 // of 32-byte sectors (jp columns, zeros past J): one event's lookups in every
-// ELT become one row read.  Each loss is stored as fx * loss, the ELT's
-// currency conversion, computed in FP64 and rounded once to the table type.
+// ELT become one row read.  Each entry is the loss in excess of the ELT's
+// deductible, fx * loss - D (currency conversion, then the deductible of the
+// financial terms, Section II-B step 2), computed in FP64 as the terms define
+// it and rounded once to the table type; an event the ELT does not hold
+// stores 0.  The analysis kernels then clamp an entry to [0, Lim]: a zero or
+// negative excess gives a zero term, as a loss at or below the deductible
+// does.
 #include <cuda_runtime.h>
 
 #include "are_internal.cuh"
@@ -24,7 +29,7 @@ __global__ void k_scatter(T *__restrict__ tab, const ScatterArgs a)
     const double *loss = a.loss[j];
     const double fx = a.fx[j];
     for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const double x = __dmul_rn(fx, loss[i]);
+        const double x = __dsub_rn(__dmul_rn(fx, loss[i]), a.ded[j]);
         tab[(size_t)ids[i] * a.jp + j] = RU ? (T)__double2float_ru(x) : (T)x;
     }
 }
@@ -42,7 +47,8 @@ int table_jp(int n_elts, bool fp32)
 }
 
 // round_up (FP32 only): each value rounded towards +infinity -- the FP32
-// screen of an FP64 table, never below the value it stands for.
+// screen of an FP64 table, never below the value it stands for (so positive
+// exactly where the FP64 entry is).
 int launch_scatter_table(void *table, bool fp32, const ScatterArgs &a, cudaStream_t s, bool round_up)
 {
     int32_t nmax = 0;

@@ -4,15 +4,14 @@
 // the paper's sizes (1M events x 16 ELTs = 128 MB), so the FP64 staged
 // kernel takes about half of its table rows from HBM.  Here each event's row
 // is read from an FP32 copy of the table instead (half the bytes: it stays
-// in L2), whose entries are the FP64 values rounded up, and a column is
-// marked when that copy is > 0 and >= the deductible rounded down (one
-// compare against a per-column threshold).  Rounding
-// is monotone, so every entry whose FP64 value exceeds the deductible is
-// marked (and a few that do not: their term comes out exactly 0).  Only the
-// marked entries -- a few per cent at the paper's sizes -- are read from the
-// FP64 table.  From there the work is the FP64 staged kernel's: the marked
-// (row, column) pairs are compacted across the warp and their terms
-// min(max(x - D, 0), Lim) * share formed 32 per FP64 instruction; each event
+// in L2), whose entries are the FP64 entries rounded up.  An FP64 entry is
+// e = x - D, the loss's excess over the ELT's deductible, and a column is
+// marked when its FP32 copy is > 0: rounding up keeps the sign, so exactly
+// the entries with e > 0 are marked.  Only the marked entries -- a few per
+// cent at the paper's sizes -- are read from the FP64 table.  From there the
+// work is the FP64 staged kernel's: the marked (row, column) pairs are
+// compacted across the warp and their terms min(e, Lim) * share formed 32
+// per FP64 instruction; each event
 // then adds its marked columns in column order, the first taken as is.  An
 // unmarked column's term is exactly 0 and adding an exact 0 changes nothing,
 // so the event losses equal the FP64 staged kernel's (and the oracle's) bit
@@ -30,9 +29,8 @@ template <int JP>
 __host__ __device__ constexpr int screen_smem_bytes()
 {
     // per warp: two FP32 row buffers, the compaction list, a round of values
-    // and the batch's event ids; per block: the FP64 terms and the FP32 screen
-    return kWarps * (2 * 32 * JP * 4 + 2 * 32 * JP + kRound * 8 + 32 * 4) + 3 * kMaxElts * 8 +
-           kMaxElts * 4;
+    // and the batch's event ids; per block: the FP64 terms
+    return kWarps * (2 * 32 * JP * 4 + 2 * 32 * JP + kRound * 8 + 32 * 4) + 3 * kMaxElts * 8;
 }
 
 template <int JP, bool FIXED>
@@ -41,30 +39,27 @@ __global__ void __launch_bounds__(kWarps * 32) k_screen64(const SimArgs a, const
     constexpr int CH = JP / 4;   // 16-byte chunks of an FP32 row
     extern __shared__ float4 stage[];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    // shared memory: rows | lists | values | ids | FP64 terms | FP32 screen
+    // shared memory: rows | lists | values | ids | FP64 terms
     char *smem = reinterpret_cast<char *>(stage);
     constexpr size_t kRows = (size_t)kWarps * 2 * 32 * JP * 4;
     constexpr size_t kLists = kRows + (size_t)kWarps * 32 * JP * 2;
     constexpr size_t kVals = kLists + (size_t)kWarps * kRound * 8;
     constexpr size_t kIds = kVals + (size_t)kWarps * 32 * 4;
     constexpr size_t kTerms = kIds + 3 * kMaxElts * 8;
-    static_assert(kTerms + kMaxElts * 4 == (size_t)screen_smem_bytes<JP>(), "layout");
+    static_assert(kTerms == (size_t)screen_smem_bytes<JP>(), "layout");
     float4 *buf0 = stage + (size_t)w * 2 * 32 * CH;
     float4 *buf1 = buf0 + 32 * CH;
     uint16_t *list = reinterpret_cast<uint16_t *>(smem + kRows) + (size_t)w * 32 * JP;
     double *vals = reinterpret_cast<double *>(smem + kLists) + (size_t)w * kRound;
     int32_t *sids = reinterpret_cast<int32_t *>(smem + kVals) + (size_t)w * 32;
     double *sterms = reinterpret_cast<double *>(smem + kIds);
-    float *sd32 = reinterpret_cast<float *>(smem + kTerms);
     for (int i = threadIdx.x; i < kMaxElts; i += blockDim.x) {
         sterms[i] = tm.ded[i];
         sterms[kMaxElts + i] = tm.lim[i];
         sterms[2 * kMaxElts + i] = tm.share[i];
-        // the deductible rounded down; columns past the layer's ELTs never marked
-        sd32[i] = i < a.n_elts ? __double2float_rd(tm.ded[i]) : __int_as_float(0x7f800000);
     }
     __syncthreads();
-    const double *sd = sterms, *sl = sterms + kMaxElts, *ss = sterms + 2 * kMaxElts;
+    const double *sl = sterms + kMaxElts, *ss = sterms + 2 * kMaxElts;
     const float *tab = static_cast<const float *>(a.table2);
     const double *t64 = static_cast<const double *>(a.table);
     const int jp64 = a.jp64;
@@ -105,18 +100,9 @@ __global__ void __launch_bounds__(kWarps * 32) k_screen64(const SimArgs a, const
 
     SumF64 sum;
 
-    // per column: the screen value at or above which an entry is marked (the
-    // deductible rounded down, or the smallest positive float when that is 0)
-    float thr[JP];
-#pragma unroll
-    for (int j = 0; j < JP; ++j) {
-        const float d = sd32[j];
-        thr[j] = d > 0.f ? d : __int_as_float(1);
-    }
-
     auto compute = [&](const Batch &b, int32_t idv, float4 *buf) {
         sids[lane] = idv;
-        // mark the columns that can carry a loss
+        // mark the columns that can carry a loss (padding columns hold 0)
         uint32_t mask = 0;
 #pragma unroll
         for (int c = 0; c < CH; ++c) {
@@ -125,7 +111,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_screen64(const SimArgs a, const
             for (int e = 0; e < 4; ++e) {
                 const float x = e == 0 ? v.x : e == 1 ? v.y : e == 2 ? v.z : v.w;
                 const int j = c * 4 + e;
-                mask |= (uint32_t)(x >= thr[j]) << j;
+                mask |= (uint32_t)(x > 0.f) << j;
             }
         }
         if (lane >= b.cnt) mask = 0;
@@ -150,7 +136,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_screen64(const SimArgs a, const
                 const int e = list[base + i], r = e >> 5, j = e & 31;
                 // evict-first: the sparse FP64 reads must not push the screen out of L2
                 const double x = __ldcs(t64 + (size_t)sids[r] * jp64 + j);
-                double n = clamp_bits(vsub(x, sd[j]), bits(sl[j]));
+                double n = clamp_bits(x, bits(sl[j]));
                 if (any_share) n = vmul(n, ss[j]);
                 vals[i] = n;
             }

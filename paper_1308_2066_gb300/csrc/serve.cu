@@ -213,6 +213,7 @@ void build_request_table(Server &S, Slot &sl)
             a.loss[j] = e.d_loss;
             a.n[j] = e.n;
             a.fx[j] = e.terms.fx;
+            a.ded[j] = e.terms.deductible;
         }
     }
     if (S.cfg.folded) {

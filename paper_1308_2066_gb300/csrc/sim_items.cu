@@ -25,23 +25,6 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 
-__device__ __forceinline__ float comp4(const float4 &v, int c)
-{
-    return c == 0 ? v.x : c == 1 ? v.y : c == 2 ? v.z : v.w;
-}
-
-// Two FP32 subtractions in one packed instruction.
-__device__ __forceinline__ float2 sub2(float2 a, float2 b)
-{
-    unsigned long long ra, rb, rd;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(ra) : "f"(a.x), "f"(a.y));
-    asm("mov.b64 %0, {%1, %2};" : "=l"(rb) : "f"(b.x), "f"(b.y));
-    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(rd) : "l"(ra), "l"(rb));
-    float2 d;
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(d.x), "=f"(d.y) : "l"(rd));
-    return d;
-}
-
 __device__ __forceinline__ double warp_sum(double v)
 {
 #pragma unroll
@@ -122,10 +105,9 @@ __device__ __forceinline__ void run_item(const ItemWork &w, const LayerF32 &L, i
     static_assert(U % R == 0 && (R & (R - 1)) == 0, "U must be a multiple of R, R a power of 2");
     const int row = lane / R, col = lane % R;
 
-    float ded[4], lim[4], shr[4];
+    float lim[4], shr[4];
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
-        ded[c] = L.ded[col * 4 + c];
         lim[c] = L.lim[col * 4 + c];
         shr[c] = L.share[col * 4 + c];
     }
@@ -174,16 +156,15 @@ __device__ __forceinline__ void run_item(const ItemWork &w, const LayerF32 &L, i
             v[u] = id[u] >= 0 ? __ldg(tab + (size_t)id[u] * R + col) : make_float4(0.f, 0.f, 0.f, 0.f);
         if (t < t1) load_ids(nid, pos, end);
 
-        // step 2 for this lane's 4 columns of each row in flight
+        // step 2 for this lane's 4 columns of each row in flight (the table
+        // holds each loss's excess over the deductible)
         float part[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-            const float2 d01 = sub2(make_float2(v[u].x, v[u].y), make_float2(ded[0], ded[1]));
-            const float2 d23 = sub2(make_float2(v[u].z, v[u].w), make_float2(ded[2], ded[3]));
-            float n0 = fminf(fmaxf(d01.x, 0.f), lim[0]);
-            float n1 = fminf(fmaxf(d01.y, 0.f), lim[1]);
-            float n2 = fminf(fmaxf(d23.x, 0.f), lim[2]);
-            float n3 = fminf(fmaxf(d23.y, 0.f), lim[3]);
+            float n0 = fminf(fmaxf(v[u].x, 0.f), lim[0]);
+            float n1 = fminf(fmaxf(v[u].y, 0.f), lim[1]);
+            float n2 = fminf(fmaxf(v[u].z, 0.f), lim[2]);
+            float n3 = fminf(fmaxf(v[u].w, 0.f), lim[3]);
             if (any_share) {
                 n0 = __fmul_rn(n0, shr[0]);
                 n1 = __fmul_rn(n1, shr[1]);

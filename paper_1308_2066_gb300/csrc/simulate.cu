@@ -16,8 +16,9 @@
 //
 // FP64 on GB300 runs at a small fraction of the FP32 rate, so the FP64 path
 // takes every decision it can on bit patterns: for non-negative doubles the
-// integer order of the bits is the numeric order, so "x <= deductible",
-// "v > limit" and the zero tests are integer compares.  A subtraction or an
+// integer order of the bits is the numeric order, so "excess <= 0" (a table
+// entry holds the loss less the ELT's deductible), "v > limit" and the zero
+// tests are integer compares.  A subtraction or an
 // addition is issued only when some lane of the warp needs one (adding an
 // exact zero or clamping a non-positive value changes nothing), which keeps
 // the FP64 pipe for the few occurrences that carry a loss.
@@ -52,18 +53,8 @@ __device__ __forceinline__ float comp(const float4 &v, int c)
 }
 __device__ __forceinline__ double comp(const double2 &v, int c) { return c == 0 ? v.x : v.y; }
 
-// Two FP32 operations in one packed instruction (sm_100 and later), used by
+// Two FP32 additions in one packed instruction (sm_100 and later), used by
 // the FP32 + Kahan staged kernel.
-__device__ __forceinline__ float2 sub2(float2 a, float2 b)
-{
-    unsigned long long ra, rb, rd;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(ra) : "f"(a.x), "f"(a.y));
-    asm("mov.b64 %0, {%1, %2};" : "=l"(rb) : "f"(b.x), "f"(b.y));
-    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(rd) : "l"(ra), "l"(rb));
-    float2 d;
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(d.x), "=f"(d.y) : "l"(rd));
-    return d;
-}
 __device__ __forceinline__ float2 add2(float2 a, float2 b)
 {
     unsigned long long ra, rb, rd;
@@ -113,6 +104,14 @@ __device__ __forceinline__ double add_nn(double a, double b)
     return r;
 }
 
+// min(max(e, 0), l) for any e and l >= 0 (+inf allowed), on bit patterns:
+// a table entry (the loss's excess over the deductible) clamped to the limit.
+__device__ __forceinline__ double excess_nn(double e, uint64_t l_bits)
+{
+    const uint64_t b = bits(e);
+    return (int64_t)b <= 0 ? 0.0 : dbl(b < l_bits ? b : l_bits);
+}
+
 // min(max(x - r, 0), l) for x, r >= 0 and l >= 0 (+inf allowed).  The
 // subtraction is issued only when some lane has x > r.  All lanes call it.
 __device__ __forceinline__ double net_nn(double x, uint64_t r_bits, double r, uint64_t l_bits)
@@ -132,27 +131,27 @@ struct LaneTerms;
 
 template <>
 struct LaneTerms<float> {
-    float ded[4], lim[4], share[4];
+    float lim[4], share[4];
     float occ_r, occ_l;
     __device__ void load(const TermsF32 &t, int col)
     {
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
             const int j = col * 4 + c;
-            ded[c] = j < kMaxElts ? t.ded[j] : 0.f;
             lim[c] = j < kMaxElts ? t.lim[j] : 0.f;
             share[c] = j < kMaxElts ? t.share[j] : 1.f;
         }
         occ_r = t.occ_r;
         occ_l = t.occ_l;
     }
-    // sum over this lane's columns of share * min(max(x - D, 0), Lim)
+    // sum over this lane's columns of share * min(max(x - D, 0), Lim), the
+    // table holding x - D
     __device__ __forceinline__ float part(const float4 &v, bool any_share) const
     {
         float p = 0.f;
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
-            float n = fminf(fmaxf(__fsub_rn(comp(v, c), ded[c]), 0.f), lim[c]);
+            float n = fminf(fmaxf(comp(v, c), 0.f), lim[c]);
             if (any_share) n = __fmul_rn(n, share[c]);
             p = __fadd_rn(p, n);
         }
@@ -162,8 +161,8 @@ struct LaneTerms<float> {
 
 template <>
 struct LaneTerms<double> {
-    double ded[2], share[2];
-    uint64_t ded_b[2], lim_b[2], share_b[2];
+    double share[2];
+    uint64_t lim_b[2], share_b[2];
     double occ_r;
     uint64_t occ_r_b, occ_l_b;
     __device__ void load(const TermsF64 &t, int col)
@@ -171,9 +170,7 @@ struct LaneTerms<double> {
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
             const int j = col * 2 + c;
-            ded[c] = j < kMaxElts ? t.ded[j] : 0.0;
             share[c] = j < kMaxElts ? t.share[j] : 1.0;
-            ded_b[c] = bits(ded[c]);
             share_b[c] = bits(share[c]);
             lim_b[c] = bits(j < kMaxElts ? t.lim[j] : 0.0);
         }
@@ -186,7 +183,7 @@ struct LaneTerms<double> {
         double p = 0.0;
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
-            double n = net_nn(comp(v, c), ded_b[c], ded[c], lim_b[c]);
+            double n = excess_nn(comp(v, c), lim_b[c]);
             if (any_share) {
                 const bool need = bits(n) != 0 && share_b[c] != bits(1.0);
                 if (__any_sync(kFull, need)) {
@@ -532,20 +529,18 @@ __global__ void __launch_bounds__(kStagedWarps * 32)
             const int r = lane + 32 * e;
             float g = 0.f;
             if constexpr (ACC == ARE_FP32_KAHAN) {
-                // column pairs in packed FP32x2 arithmetic (x - D and the
-                // running sums; min/max have no packed form): four partial
-                // sums over the columns j mod 4, added at the end
+                // the running column sums in packed FP32x2 pairs (min/max
+                // have no packed form): four partial sums over the columns
+                // j mod 4, added at the end.  Entries are x - D already.
                 float2 g01 = make_float2(0.f, 0.f), g23 = make_float2(0.f, 0.f);
 #pragma unroll
                 for (int c = 0; c < CH; ++c) {
                     const float4 v = buf[r * CH + chunk_slot<CH>(c, r)];
                     const int j = c * 4;
-                    const float2 d01 = sub2(make_float2(v.x, v.y), make_float2(tm.ded[j], tm.ded[j + 1]));
-                    const float2 d23 = sub2(make_float2(v.z, v.w), make_float2(tm.ded[j + 2], tm.ded[j + 3]));
-                    float n0 = fminf(fmaxf(d01.x, 0.f), tm.lim[j]);
-                    float n1 = fminf(fmaxf(d01.y, 0.f), tm.lim[j + 1]);
-                    float n2 = fminf(fmaxf(d23.x, 0.f), tm.lim[j + 2]);
-                    float n3 = fminf(fmaxf(d23.y, 0.f), tm.lim[j + 3]);
+                    float n0 = fminf(fmaxf(v.x, 0.f), tm.lim[j]);
+                    float n1 = fminf(fmaxf(v.y, 0.f), tm.lim[j + 1]);
+                    float n2 = fminf(fmaxf(v.z, 0.f), tm.lim[j + 2]);
+                    float n3 = fminf(fmaxf(v.w, 0.f), tm.lim[j + 3]);
                     if (any_share) {
                         n0 = __fmul_rn(n0, tm.share[j]);
                         n1 = __fmul_rn(n1, tm.share[j + 1]);
@@ -563,7 +558,7 @@ __global__ void __launch_bounds__(kStagedWarps * 32)
 #pragma unroll
                     for (int k = 0; k < 4; ++k) {
                         const int j = c * 4 + k;
-                        float n = fminf(fmaxf(__fsub_rn(comp(v, k), tm.ded[j]), 0.f), tm.lim[j]);
+                        float n = fminf(fmaxf(comp(v, k), 0.f), tm.lim[j]);
                         if (any_share) n = __fmul_rn(n, tm.share[j]);
                         g = __fadd_rn(g, n);
                     }

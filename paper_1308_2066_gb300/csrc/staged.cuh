@@ -5,15 +5,16 @@
 //
 // FP64 tables: GB300 issues an FP64 add at about 1/66 of the FP32 rate and a
 // warp with one active lane costs as much as a full one, so the FP64 work is
-// compacted across the warp.  Each lane marks its event's columns with
-// x > D (integer compares of the bit patterns, which order like the values
-// for non-negative doubles); the marked (row, column) pairs of the 32 events
-// go to a shared list and the warp applies min(x - D, Lim) * share to 32 of
-// them per FP64 instruction, in place.  Each lane then sums its event's
-// marked columns in column order: the first is taken as is, so an FP64 add
-// is issued only when some event has two or more.  Columns with x <= D give
-// exactly 0 and adding an exact 0 changes nothing, so the event loss is the
-// sum over ELTs of step 2 in layer order, as the paper's loop forms it.
+// compacted across the warp.  A table entry is e = x - D, the loss's excess
+// over the ELT's deductible (formed in FP64 when the table is built).  Each
+// lane marks its event's columns with e > 0 (an integer compare of the bit
+// pattern); the marked (row, column) pairs of the 32 events go to a shared
+// list and the warp applies min(e, Lim) * share to 32 of them per FP64
+// instruction, in place.  Each lane then sums its event's marked columns in
+// column order: the first is taken as is, so an FP64 add is issued only when
+// some event has two or more.  Columns with e <= 0 give exactly 0 and adding
+// an exact 0 changes nothing, so the event loss is the sum over ELTs of step
+// 2 in layer order, as the paper's loop forms it.
 //
 // Per-occurrence outputs (step 4 of the Basic Algorithm, before its final sum): a
 // warp-shuffle inclusive scan of the batch's occurrence losses plus the
@@ -204,7 +205,7 @@ __device__ __forceinline__ float event_loss(float4 *buf, int lane, const TermsF3
         for (int e = 0; e < 4; ++e) {
             const int j = c * 4 + e;
             const float x = e == 0 ? v[c].x : e == 1 ? v[c].y : e == 2 ? v[c].z : v[c].w;
-            float n = fminf(fmaxf(__fsub_rn(x, tm.ded[j]), 0.f), tm.lim[j]);
+            float n = fminf(fmaxf(x, 0.f), tm.lim[j]);
             if (any_share) n = __fmul_rn(n, tm.share[j]);
             g = __fadd_rn(g, n);
         }
@@ -222,8 +223,8 @@ __device__ __forceinline__ double event_loss(float4 *buf, int lane, const TermsF
 #pragma unroll
     for (int c = 0; c < CH; ++c) {
         const double2 v = reinterpret_cast<const double2 *>(buf)[lane * CH + chunk_slot<CH>(c, lane)];
-        if (bits(v.x) > bits(tm.ded[2 * c])) mask |= 1u << (2 * c);
-        if (bits(v.y) > bits(tm.ded[2 * c + 1])) mask |= 1u << (2 * c + 1);
+        if ((int64_t)bits(v.x) > 0) mask |= 1u << (2 * c);
+        if ((int64_t)bits(v.y) > 0) mask |= 1u << (2 * c + 1);
     }
     // warp-wide list of the marked (row, column) pairs, lane by lane
     const int cnt = __popc(mask);
@@ -237,12 +238,13 @@ __device__ __forceinline__ double event_loss(float4 *buf, int lane, const TermsF
     int k = incl - cnt;
     for (uint32_t m = mask; m; m &= m - 1) list[k++] = (uint16_t)((lane << 5) | (__ffs(m) - 1));
     __syncwarp();
-    // 32 marked entries per FP64 instruction: x <- min(x - D, Lim) * share
-    const double *sd = sterms, *sl = sterms + kMaxElts, *ss = sterms + 2 * kMaxElts;
+    // 32 marked entries per FP64 instruction: e <- min(e, Lim) * share (the
+    // table holds e = x - D; a marked entry has e > 0)
+    const double *sl = sterms + kMaxElts, *ss = sterms + 2 * kMaxElts;
     for (int i = lane; i < total; i += 32) {
         const int e = list[i], r = e >> 5, j = e & 31;
         double *p = elem<double, JP>(buf, r, j);
-        double n = clamp_bits(vsub(*p, sd[j]), bits(sl[j]));
+        double n = clamp_bits(*p, bits(sl[j]));
         if (any_share) n = vmul(n, ss[j]);
         *p = n;
     }
