@@ -91,6 +91,9 @@ typedef struct {
  *                     trial's running sum in FP32 with Kahan compensation.
  *   ARE_FP32_FP64AGG  losses and terms in FP32, the trial's running sum in
  *                     FP64.
+ * In every mode a loss enters the analysis as fx * loss - deductible, formed
+ * in FP64 when the layer's table is built and rounded once to the mode's
+ * type; the limit and share are applied in that type.
  * The paper does not state its precision; its losses are doubles
  * (Section III-B, data structure iii). */
 typedef enum {
