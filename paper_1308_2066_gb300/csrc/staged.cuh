@@ -10,9 +10,11 @@
 // lane marks its event's columns with e > 0 (an integer compare of the bit
 // pattern); the marked (row, column) pairs of the 32 events go to a shared
 // list and the warp applies min(e, Lim) * share to 32 of them per FP64
-// instruction, in place.  Each lane then sums its event's marked columns in
-// column order: the first is taken as is, so an FP64 add is issued only when
-// some event has two or more.  Columns with e <= 0 give exactly 0 and adding
+// instruction, in place.  (With every share 1 the term min(e, Lim) needs no
+// FP64 instruction, and each lane clamps its own columns instead.)  Each
+// lane then sums its event's marked columns in column order: the first is
+// taken as is, so an FP64 add is issued only when some event has two or
+// more.  Columns with e <= 0 give exactly 0 and adding
 // an exact 0 changes nothing, so the event loss is the sum over ELTs of step
 // 2 in layer order, as the paper's loop forms it.
 //
@@ -226,6 +228,27 @@ __device__ __forceinline__ double event_loss(float4 *buf, int lane, const TermsF
         if ((int64_t)bits(v.x) > 0) mask |= 1u << (2 * c);
         if ((int64_t)bits(v.y) > 0) mask |= 1u << (2 * c + 1);
     }
+    const double *sl = sterms + kMaxElts, *ss = sterms + 2 * kMaxElts;
+    if (!any_share) {
+        // no share factors: a marked entry's term min(e, Lim) is integer work
+        // on its bit pattern, so each lane takes its own columns in column
+        // order, with an FP64 add only where an event has two or more
+        double g = 0.0;
+        uint32_t m = mask;
+        if (m) {
+            const int j = __ffs(m) - 1;
+            g = clamp_bits(*elem<double, JP>(buf, lane, j), bits(sl[j]));
+            m &= m - 1;
+        }
+        while (__any_sync(kFull, m != 0)) {
+            if (m) {
+                const int j = __ffs(m) - 1;
+                g = vadd(g, clamp_bits(*elem<double, JP>(buf, lane, j), bits(sl[j])));
+                m &= m - 1;
+            }
+        }
+        return g;
+    }
     // warp-wide list of the marked (row, column) pairs, lane by lane
     const int cnt = __popc(mask);
     int incl = cnt;
@@ -240,7 +263,6 @@ __device__ __forceinline__ double event_loss(float4 *buf, int lane, const TermsF
     __syncwarp();
     // 32 marked entries per FP64 instruction: e <- min(e, Lim) * share (the
     // table holds e = x - D; a marked entry has e > 0)
-    const double *sl = sterms + kMaxElts, *ss = sterms + 2 * kMaxElts;
     for (int i = lane; i < total; i += 32) {
         const int e = list[i], r = e >> 5, j = e & 31;
         double *p = elem<double, JP>(buf, r, j);
