@@ -9,9 +9,10 @@
 // marked when its FP32 copy is > 0: rounding up keeps the sign, so exactly
 // the entries with e > 0 are marked.  Only the marked entries -- a few per
 // cent at the paper's sizes -- are read from the FP64 table.  From there the
-// work is the FP64 staged kernel's: the marked (row, column) pairs are
-// compacted across the warp and their terms min(e, Lim) * share formed 32
-// per FP64 instruction; each event
+// work is the FP64 staged kernel's: with share factors the marked (row,
+// column) pairs are compacted across the warp and their terms
+// min(e, Lim) * share formed 32 per FP64 instruction, without them each lane
+// reads and clamps its own; each event
 // then adds its marked columns in column order, the first taken as is.  An
 // unmarked column's term is exactly 0 and adding an exact 0 changes nothing,
 // so the event losses equal the FP64 staged kernel's (and the oracle's) bit
@@ -115,43 +116,65 @@ __global__ void __launch_bounds__(kWarps * 32) k_screen64(const SimArgs a, const
             }
         }
         if (lane >= b.cnt) mask = 0;
-        const int cnt = __popc(mask);
-        int incl = cnt;
-#pragma unroll
-        for (int off = 1; off < 32; off <<= 1) {
-            const int o = __shfl_up_sync(kFull, incl, off);
-            if (lane >= off) incl += o;
-        }
-        const int total = __shfl_sync(kFull, incl, 31);
-        const int start = incl - cnt;
-        int k = start;
-        for (uint32_t m = mask; m; m &= m - 1) list[k++] = (uint16_t)((lane << 5) | (__ffs(m) - 1));
-        __syncwarp();
-        // the event loss: marked columns in column order, valued a round at a time
         double g = 0.0;
-        bool have = false;
-        for (int base = 0; base < total; base += kRound) {
-            const int top = total - base < kRound ? total - base : kRound;
-            for (int i = lane; i < top; i += 32) {
-                const int e = list[base + i], r = e >> 5, j = e & 31;
-                // evict-first: the sparse FP64 reads must not push the screen out of L2
-                const double x = __ldcs(t64 + (size_t)sids[r] * jp64 + j);
-                double n = clamp_bits(x, bits(sl[j]));
-                if (any_share) n = vmul(n, ss[j]);
-                vals[i] = n;
+        if (!any_share) {
+            // no share factors: a marked entry's term min(e, Lim) is integer
+            // work, so each lane reads (evict-first, as below) and clamps its
+            // own marked columns in column order, the first two read
+            // together, with an FP64 add only where an event has two or more
+            const double *row = t64 + (size_t)(uint32_t)idv * jp64;
+            uint32_t m = mask;
+            const uint32_t m1 = m & (m - 1);
+            const int j0 = m ? __ffs(m) - 1 : 0, j1 = m1 ? __ffs(m1) - 1 : 0;
+            const double x0 = m ? __ldcs(row + j0) : 0.0, x1 = m1 ? __ldcs(row + j1) : 0.0;
+            if (m) g = clamp_bits(x0, bits(sl[j0]));
+            if (__any_sync(kFull, m1 != 0)) {
+                if (m1) g = vadd(g, clamp_bits(x1, bits(sl[j1])));
             }
-            __syncwarp();
-            const int lo = start > base ? start : base;
-            const int hi = start + cnt < base + top ? start + cnt : base + top;
-            for (int q = lo; __any_sync(kFull, q < hi); ++q) {
-                if (q < hi) {
-                    const double v = vals[q - base];
-                    if (have) g = vadd(g, v);
-                    else g = v;
-                    have = true;
+            m = m1 & (m1 - 1);
+            while (__any_sync(kFull, m != 0)) {
+                if (m) {
+                    const int j = __ffs(m) - 1;
+                    g = vadd(g, clamp_bits(__ldcs(row + j), bits(sl[j])));
+                    m &= m - 1;
                 }
             }
+        } else {
+            const int cnt = __popc(mask);
+            int incl = cnt;
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const int o = __shfl_up_sync(kFull, incl, off);
+                if (lane >= off) incl += o;
+            }
+            const int total = __shfl_sync(kFull, incl, 31);
+            const int start = incl - cnt;
+            int k = start;
+            for (uint32_t m = mask; m; m &= m - 1) list[k++] = (uint16_t)((lane << 5) | (__ffs(m) - 1));
             __syncwarp();
+            // the event loss: marked columns in column order, valued a round at a time
+            bool have = false;
+            for (int base = 0; base < total; base += kRound) {
+                const int top = total - base < kRound ? total - base : kRound;
+                for (int i = lane; i < top; i += 32) {
+                    const int e = list[base + i], r = e >> 5, j = e & 31;
+                    // evict-first: the sparse FP64 reads must not push the screen out of L2
+                    const double x = __ldcs(t64 + (size_t)sids[r] * jp64 + j);
+                    vals[i] = vmul(clamp_bits(x, bits(sl[j])), ss[j]);
+                }
+                __syncwarp();
+                const int lo = start > base ? start : base;
+                const int hi = start + cnt < base + top ? start + cnt : base + top;
+                for (int q = lo; __any_sync(kFull, q < hi); ++q) {
+                    if (q < hi) {
+                        const double v = vals[q - base];
+                        if (have) g = vadd(g, v);
+                        else g = v;
+                        have = true;
+                    }
+                }
+                __syncwarp();
+            }
         }
         // occurrence terms and the trial's running sum
         sum.add(occ_clamp(g, tm));

@@ -156,3 +156,39 @@ def test_every_kernel_choice(are, ctx, orc, tmp_path, p):
                 assert ok, (kind, u, st)
     finally:
         L.release()
+
+
+@pytest.mark.parametrize("with_share", [False, True])
+def test_fp64_kernels_with_and_without_share_factors(are, ctx, orc, tmp_path, with_share):
+    """Each FP64 kernel the tuner can pick (staged, register, screened) gives
+    the oracle's trial losses on a ragged 16-ELT layer, both when every
+    share is 1 (each lane clamps its own columns) and when some are not (the
+    warp-wide list of marked entries)."""
+    g = np.random.Generator(np.random.PCG64(41 + with_share))
+    yet = W.yet_poisson(g, 3000, 70, 4000)
+    elts = []
+    for j in range(16):
+        e = W.percentile_terms(W.elt_lognormal(g, 4000, 400), int(g.integers(0, 300)), 990)
+        if with_share:
+            e.share = float(g.choice([1.0, 0.5, 0.35]))
+        elts.append(e)
+    pooled = np.concatenate([e.losses for e in elts])
+    occ_r = W.nearest_rank(pooled, 200)
+    wl = W.Workload("fp64_kernels", yet, elts,
+                    [W.Layer(list(range(16)), occ_r, W.nearest_rank(pooled, 990) * 5, occ_r * 3, INF)])
+    L = Loaded(are, ctx, wl)
+    try:
+        ref = orc.simulate_layer(wl)
+        are.are_autotune(ctx, L.layers[:1], L.yet, 0)
+        path = tmp_path / "t.jsonl"
+        are.are_tune_save(ctx, str(path))
+        entries = [json.loads(l) for l in open(path) if l.strip()]
+        key = [e for e in entries if e["key"].startswith("p0_") and e["key"].endswith("_single")]
+        assert key
+        for kind in (1, 2, 3):
+            path.write_text(json.dumps(dict(key[0], kernel=kind)) + "\n")
+            are.are_tune_load(ctx, str(path))
+            ok, st = mixed_check(L.simulate(0, 0), ref.ylt, ref.gross, RTOL[0])
+            assert ok, (kind, st)
+    finally:
+        L.release()
