@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <tuple>
 #include <unordered_map>
 
 #include <nvtx3/nvToolsExt.h>
@@ -640,6 +641,25 @@ int max_width(are_ctx *ctx, const int32_t *layers, int32_t n_layers, bool fp32)
 }
 
 }  // namespace
+
+int fit_blocks(const void *kern, int threads, size_t smem)
+{
+    static std::mutex mu;
+    static std::map<std::tuple<const void *, int, int, size_t>, int> known;
+    int dev = 0;
+    ARE_CUDA_TRY(cudaGetDevice(&dev));
+    const auto key = std::make_tuple(kern, dev, threads, smem);
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = known.find(key);
+    if (it != known.end()) return it->second;
+    if (smem > 48 * 1024)
+        ARE_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    ARE_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem));
+    if (per_sm < 1) per_sm = 1;
+    known[key] = per_sm;
+    return per_sm;
+}
 
 void *ctx_alloc(are_ctx *ctx, size_t bytes) { return dalloc(ctx, bytes); }
 void ctx_free(are_ctx *ctx, void *p, size_t bytes) { dfree(ctx, p, bytes); }

@@ -266,6 +266,13 @@ float gather_ceiling_ms(const int32_t *ids, int64_t n, int row_bytes, int reps, 
                         const void *table, float *out, cudaStream_t s, uint64_t &launches);
 int table_jp(int n_elts, bool fp32);
 
+// api.cu: how many blocks of `kern` (threads per block, bytes of dynamic
+// shared memory) fit on one SM of the current device.  On the first call for
+// a device it also raises the kernel's dynamic shared-memory limit to `smem`
+// on that device; the answer is kept per (kernel, device, shape) under a
+// lock, so contexts on several devices and threads may share the library.
+int fit_blocks(const void *kern, int threads, size_t smem);
+
 // validate.cu: each sets *flag (device int, zeroed by the caller) non-zero on a violation
 int launch_check_ids(const int32_t *ids, int64_t n, int32_t catalog, int *flag, cudaStream_t s);
 int launch_sanitize_ids(int32_t *ids, int64_t n, int32_t catalog, int *flag, cudaStream_t s);

@@ -219,12 +219,7 @@ void launch_screen_t(const SimArgs &a, const TermsF64 &tm, int num_sms, cudaStre
 {
     auto kern = k_screen64<JP, FIXED>;
     constexpr int smem = screen_smem_bytes<JP>();
-    static int per_sm = 0;
-    if (per_sm == 0) {
-        ARE_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-        ARE_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kWarps * 32, smem));
-        if (per_sm < 1) per_sm = 1;
-    }
+    const int per_sm = fit_blocks(reinterpret_cast<const void *>(kern), kWarps * 32, smem);
     int64_t blocks = (a.n_trials + kWarps - 1) / kWarps;
     const int64_t cap = (int64_t)num_sms * per_sm;
     if (blocks > cap) blocks = cap;

@@ -243,10 +243,7 @@ const void *kernel_ptr()
 template <int JP, int U, int ACC, bool FIXED>
 int max_blocks_t()
 {
-    int per_sm = 0;
-    ARE_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sim_items<JP, U, ACC, FIXED>,
-                                                               256, 0));
-    return per_sm < 1 ? 1 : per_sm;
+    return fit_blocks(kernel_ptr<JP, U, ACC, FIXED>(), 256, 0);
 }
 
 template <int JP, int U, int ACC, bool FIXED>

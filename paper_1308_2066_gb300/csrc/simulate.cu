@@ -613,13 +613,7 @@ void launch_staged(const SimArgs &a, const TermsF32 &terms, int num_sms, cudaStr
 {
     auto kern = k_simulate_staged<JP, ACC, FIXED, EPL, CMP>;
     constexpr int smem = staged_smem_bytes<JP, EPL>();
-    static int per_sm = 0;
-    if (per_sm == 0) {
-        ARE_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-        ARE_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern,
-                                                                   kStagedWarps * 32, smem));
-        if (per_sm < 1) per_sm = 1;
-    }
+    const int per_sm = fit_blocks(reinterpret_cast<const void *>(kern), kStagedWarps * 32, smem);
     int64_t blocks = (a.n_trials + kStagedWarps - 1) / kStagedWarps;
     const int64_t cap = (int64_t)num_sms * per_sm;
     if (blocks > cap) blocks = cap;
@@ -660,11 +654,7 @@ template <typename T, int JP, int ACC, bool FIXED, typename TT>
 void launch_one(const SimArgs &a, const TT &terms, int num_sms, cudaStream_t s)
 {
     auto kern = k_simulate<T, JP, ACC, FIXED>;
-    static int per_sm = 0;
-    if (per_sm == 0) {
-        ARE_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, 0));
-        if (per_sm < 1) per_sm = 1;
-    }
+    const int per_sm = fit_blocks(reinterpret_cast<const void *>(kern), 256, 0);
     const int64_t warps_needed = a.n_trials;
     int64_t blocks = (warps_needed + 7) / 8;
     const int64_t cap = (int64_t)num_sms * per_sm;

@@ -9,7 +9,7 @@ import numpy as np
 import pytest
 
 import workloads as W
-from gpu_support import Loaded, RTOL, mixed_check
+from gpu_support import Loaded, RTOL, mixed_check, trial_bound
 
 pytestmark = pytest.mark.gpu
 INF = math.inf
@@ -52,7 +52,7 @@ def test_tiny_workload_same_as_direct_and_oracle(are, ctx, orc, p):
             direct, compact = both_layouts(are, ctx, L, layer, p)
             np.testing.assert_array_equal(compact, direct)
             ref = orc.simulate_layer(wl, layer)
-            ok, st = mixed_check(compact, ref.ylt, ref.gross, RTOL[p])
+            ok, st = mixed_check(compact, ref.ylt, trial_bound(wl, layer), RTOL[p])
             assert ok, st
     finally:
         L.release()

@@ -20,7 +20,7 @@ import numpy as np
 import pytest
 
 import workloads as W
-from gpu_support import Loaded, RTOL, mixed_check
+from gpu_support import Loaded, RTOL, mixed_check, trial_bound
 
 pytestmark = pytest.mark.gpu
 INF = math.inf
@@ -106,7 +106,7 @@ def test_folded_is_the_exact_sum_of_oracle_occurrence_losses(are, ctx, orc, J, r
         for layer in (0, 1):
             got = L.folded(layer)
             ref = orc.simulate_layer(wl, layer)
-            ok, st = mixed_check(got, ref.ylt, ref.gross, RTOL["folded"])
+            ok, st = mixed_check(got, ref.ylt, trial_bound(wl, layer), RTOL["folded"])
             assert ok, (layer, st)
             h = oracle_h(orc, wl, layer)
             pick = np.random.default_rng(J).choice(wl.yet.n_trials, 400, replace=False)
@@ -163,7 +163,7 @@ def test_large_catalog_bitmap_outside_shared_memory(are, ctx, orc):
     try:
         got = L.folded(0)
         ref = orc.simulate_layer(wl, 0)
-        ok, st = mixed_check(got, ref.ylt, ref.gross, RTOL["folded"])
+        ok, st = mixed_check(got, ref.ylt, trial_bound(wl, 0), RTOL["folded"])
         assert ok, st
         assert (got > 0).mean() > 0.2
     finally:
@@ -186,7 +186,7 @@ def test_empty_and_long_trials(are, ctx, orc):
         got = L.folded(0)
         assert np.all(got[counts == 0] == 0)
         ref = orc.simulate_layer(wl, 0)
-        ok, st = mixed_check(got, ref.ylt, ref.gross, RTOL["folded"])
+        ok, st = mixed_check(got, ref.ylt, trial_bound(wl, 0), RTOL["folded"])
         assert ok, st
         h = oracle_h(orc, wl, 0)
         np.testing.assert_array_equal(got, exact_ylt(wl, 0, h, np.arange(600)))

@@ -7,7 +7,7 @@ import numpy as np
 import pytest
 
 import workloads as W
-from gpu_support import Loaded, RTOL, mixed_check
+from gpu_support import Loaded, RTOL, mixed_check, running_bound, trial_bound
 
 pytestmark = pytest.mark.gpu
 INF = math.inf
@@ -45,14 +45,14 @@ def occurrences(are, ctx, L, layer, p, begin=0, n=None):
 
 def check_against_oracle(orc, L, layer, p, marg, omax, ylt, trials=None):
     ref = orc.simulate_layer(L.wl, layer, trials=trials, marginals=True)
-    ok, st = mixed_check(ylt, ref.ylt, ref.gross, RTOL[p])
+    bound = trial_bound(L.wl, layer, trials)
+    ok, st = mixed_check(ylt, ref.ylt, bound, RTOL[p])
     assert ok, ("ylt", p, st)
-    ok, st = mixed_check(omax, ref.occ_max, ref.gross, RTOL[p])
+    ok, st = mixed_check(omax, ref.occ_max, bound, RTOL[p])
     assert ok, ("occ_max", p, st)
     if p == 0:   # the event loss is formed in the oracle's order: occurrence losses are exact
         np.testing.assert_array_equal(omax, ref.occ_max)
-    gross_ev = np.repeat(ref.gross, ref.n_events)
-    ok, st = mixed_check(marg, ref.marginals, gross_ev, RTOL[p])
+    ok, st = mixed_check(marg, ref.marginals, running_bound(L.wl, layer, trials), RTOL[p])
     assert ok, ("marginals", p, st)
     return ref
 
@@ -152,7 +152,7 @@ def test_every_kernel_choice(are, ctx, orc, tmp_path, p):
                 e = dict(key[0], kernel=kind, rows_in_flight=u, trials_per_item=3)
                 path.write_text(json.dumps(e) + "\n")
                 are.are_tune_load(ctx, str(path))
-                ok, st = mixed_check(L.simulate(0, p), ref.ylt, ref.gross, RTOL[p])
+                ok, st = mixed_check(L.simulate(0, p), ref.ylt, trial_bound(wl, 0), RTOL[p])
                 assert ok, (kind, u, st)
     finally:
         L.release()
@@ -188,7 +188,7 @@ def test_fp64_kernels_with_and_without_share_factors(are, ctx, orc, tmp_path, wi
         for kind in (1, 2, 3):
             path.write_text(json.dumps(dict(key[0], kernel=kind)) + "\n")
             are.are_tune_load(ctx, str(path))
-            ok, st = mixed_check(L.simulate(0, 0), ref.ylt, ref.gross, RTOL[0])
+            ok, st = mixed_check(L.simulate(0, 0), ref.ylt, trial_bound(wl, 0), RTOL[0])
             assert ok, (kind, st)
     finally:
         L.release()

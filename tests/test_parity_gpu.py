@@ -2,7 +2,9 @@
 
 Every comparison is element by element on the same seeded inputs.  FP64
 results must agree within 1e-12 and the FP32 paths within 1e-5, relative to
-the oracle's value or, for trial losses, to the trial's gross loss (see
+the oracle's value or, for trial losses, to the trial's cancellation bound
+(gpu_support.trial_bound: the running total before the aggregate terms plus
+the event losses that reach the occurrence retention; see
 gpu_support.mixed_check).  Ids, counts and selected order statistics are
 exact."""
 import math
@@ -11,7 +13,7 @@ import numpy as np
 import pytest
 
 import workloads as W
-from gpu_support import Loaded, RTOL, mixed_check, rel_close, tail_candidates
+from gpu_support import Loaded, RTOL, mixed_check, rel_close, tail_candidates, trial_bound
 
 pytestmark = pytest.mark.gpu
 INF = math.inf
@@ -57,7 +59,8 @@ def tiny_oracle(orc, tiny):
 def test_tiny_workload_every_trial(tiny, tiny_oracle, precision, layer):
     ref = tiny_oracle[layer]
     got = tiny.simulate(layer, precision)
-    ok, st = mixed_check(got, ref.ylt, ref.gross, RTOL[precision])
+    ok, st = mixed_check(got, ref.ylt, trial_bound(tiny.wl, layer), RTOL[precision],
+                         min_plain=0.999)
     assert ok, st
     assert np.all(got >= 0) and np.all(got <= tiny.wl.layers[layer].agg_l)
     at_cap = ref.ylt == tiny.wl.layers[layer].agg_l
@@ -152,7 +155,7 @@ def test_ragged_every_table_width(are, ctx, orc, J):
         ref = orc.simulate_layer(wl)
         for p in PRECISIONS:
             got = L.simulate(0, p)
-            ok, st = mixed_check(got, ref.ylt, ref.gross, RTOL[p])
+            ok, st = mixed_check(got, ref.ylt, trial_bound(wl, 0), RTOL[p])
             assert ok, (p, st)
             assert np.all(got[ref.n_events == 0] == 0)
     finally:
@@ -175,7 +178,7 @@ def test_fixed_trial_lengths_at_batch_edges(are, ctx, orc, k):
     try:
         ref = orc.simulate_layer(wl)
         for p in PRECISIONS:
-            ok, st = mixed_check(L.simulate(0, p), ref.ylt, ref.gross, RTOL[p])
+            ok, st = mixed_check(L.simulate(0, p), ref.ylt, trial_bound(wl, 0), RTOL[p])
             assert ok, (p, st)
     finally:
         L.release()
@@ -191,7 +194,7 @@ def test_empty_trials_and_short_tails(are, ctx, orc):
         ref = orc.simulate_layer(wl)
         assert np.sum(ref.n_events == 0) > 100
         for p in PRECISIONS:
-            ok, st = mixed_check(L.simulate(0, p), ref.ylt, ref.gross, RTOL[p])
+            ok, st = mixed_check(L.simulate(0, p), ref.ylt, trial_bound(wl, 0), RTOL[p])
             assert ok, (p, st)
     finally:
         L.release()
@@ -328,6 +331,29 @@ def test_memory_budget(are):
         are.are_destroy(c)
 
 
+def test_contexts_on_two_devices(are, orc):
+    """A context on the second GPU, made after one on the first has run every
+    precision, launches the same kernels (their shared-memory limits and
+    grid sizes are kept per device) and gives the oracle's results."""
+    import torch
+    if torch.cuda.device_count() < 2:
+        pytest.skip("needs two visible GPUs")
+    wl = W.plain_tiny(n_trials=600)
+    ref = orc.simulate_layer(wl)
+    for dev in (0, 1):
+        c = are.are_create(dev)
+        try:
+            torch.cuda.set_device(dev)
+            L = Loaded(are, c, wl)
+            for p in PRECISIONS:
+                ok, st = mixed_check(L.simulate(0, p), ref.ylt, trial_bound(wl, 0), RTOL[p])
+                assert ok, (dev, p, st)
+            L.release()
+        finally:
+            are.are_destroy(c)
+            torch.cuda.set_device(0)
+
+
 # ---------------------------------------------------------------------------
 # full-size workloads, in the launch configuration the benchmark times:
 # sampled trials one by one, and PML/TVaR through their tail trials
@@ -346,7 +372,10 @@ def check_full_size(are, ctx, orc, wl, precisions, n_sample=1500, seed=0):
             got = L.run(0, p)
             assert np.all(np.isfinite(got)) and np.all(got >= 0)
             ref = orc.simulate_layer(wl, trials=sample)
-            ok, st = mixed_check(got[sample], ref.ylt, ref.gross, RTOL[p])
+            # at least 99.9% of the sampled trials pass the plain relative
+            # test; the rest pass against the trial's cancellation bound
+            ok, st = mixed_check(got[sample], ref.ylt, trial_bound(wl, 0, sample), RTOL[p],
+                                 min_plain=0.999)
             assert ok, (p, st)
             np.testing.assert_array_equal(ref.n_events, wl.yet.counts()[sample])
             # tail: the m_max + margin largest GPU losses hold every trial the

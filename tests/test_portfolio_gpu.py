@@ -9,7 +9,7 @@ import numpy as np
 import pytest
 
 import workloads as W
-from gpu_support import Loaded, RTOL, mixed_check, rel_close, tail_candidates
+from gpu_support import Loaded, RTOL, mixed_check, rel_close, tail_candidates, trial_bound
 
 pytestmark = pytest.mark.gpu
 PRECISIONS = [0, 1, 2]
@@ -62,7 +62,7 @@ def test_portfolio_matches_oracle_every_layer(are, ctx, loaded, precision):
     are.are_simulate_portfolio(ctx, L.layers, L.yet, 0, n, precision, outs)
     widths = set()
     for i, (o, ref) in enumerate(zip(outs, refs)):
-        ok, st = mixed_check(o.cpu().numpy(), ref.ylt, ref.gross, RTOL[precision])
+        ok, st = mixed_check(o.cpu().numpy(), ref.ylt, trial_bound(L.wl, i), RTOL[precision])
         assert ok, (i, st)
         widths.add(len(L.wl.layers[i].elts))
     assert min(widths) <= 8 and max(widths) > 16      # every table width is exercised
@@ -123,10 +123,11 @@ def test_autotune_and_tuning_file(are, ctx, loaded, tmp_path, precision):
     assert single["kernel"] in (0, 1, 2) and single["ms"] > 0
     outs = device_ylts(len(L.layers), n)
     are.are_simulate_portfolio(ctx, L.layers, L.yet, 0, n, precision, outs)
-    for o, ref in zip(outs, refs):
-        ok, st = mixed_check(o.cpu().numpy(), ref.ylt, ref.gross, RTOL[precision])
+    for i, (o, ref) in enumerate(zip(outs, refs)):
+        ok, st = mixed_check(o.cpu().numpy(), ref.ylt, trial_bound(L.wl, i), RTOL[precision])
         assert ok, st
-    ok, st = mixed_check(L.simulate(0, precision), refs[0].ylt, refs[0].gross, RTOL[precision])
+    ok, st = mixed_check(L.simulate(0, precision), refs[0].ylt, trial_bound(L.wl, 0),
+                         RTOL[precision])
     assert ok, st
     path = str(tmp_path / "tune.jsonl")
     are.are_tune_save(ctx, path)
@@ -176,7 +177,7 @@ def test_portfolio_full_size(are, ctx, orc):
                 assert np.all(got >= 0)
                 sample = np.sort(rng.choice(n, 60, replace=False))
                 ref = orc.simulate_layer(wl, i, trials=sample)
-                ok, st = mixed_check(got[sample], ref.ylt, ref.gross, RTOL[p])
+                ok, st = mixed_check(got[sample], ref.ylt, trial_bound(wl, i, sample), RTOL[p])
                 assert ok, (p, i, st)
                 if i % 8 == 0:
                     m_max = orc.rank_for_level(n, 0.99)
