@@ -216,6 +216,8 @@ ScatterArgs scatter_args(are_ctx *ctx, const Layer &L, int32_t catalog, int jp)
         a.n[j] = e.n;
         a.fx[j] = e.terms.fx;
         a.ded[j] = e.terms.deductible;
+        a.lim[j] = e.terms.limit;
+        a.share[j] = e.terms.share;
     }
     return a;
 }
@@ -334,25 +336,8 @@ void check_precision(are_precision p)
               "unknown precision " + std::to_string((int)p));
 }
 
-void fill_terms(are_ctx *ctx, const Layer &L, TermsF32 &t32, TermsF64 &t64, int &any_share)
+void fill_terms(const Layer &L, TermsF32 &t32, TermsF64 &t64)
 {
-    std::memset(&t32, 0, sizeof t32);
-    std::memset(&t64, 0, sizeof t64);
-    any_share = 0;
-    for (int j = 0; j < kMaxElts; ++j) {
-        t32.share[j] = 1.f;
-        t64.share[j] = 1.0;
-    }
-    for (size_t j = 0; j < L.elts.size(); ++j) {
-        const are_fin_terms &f = ctx->elts.at(L.elts[j]).terms;
-        t64.ded[j] = f.deductible;
-        t64.lim[j] = f.limit;
-        t64.share[j] = f.share;
-        t32.ded[j] = (float)f.deductible;
-        t32.lim[j] = (float)f.limit;
-        t32.share[j] = (float)f.share;
-        any_share |= f.share != 1.0;
-    }
     t64.occ_r = L.terms.occ_ret;
     t64.occ_l = L.terms.occ_lim;
     t32.occ_r = (float)L.terms.occ_ret;
@@ -371,39 +356,17 @@ Folded &build_folded(are_ctx *ctx, Layer &L, int32_t catalog, cudaStream_t s)
         f.d = dalloc(ctx, f.bytes);
         f.catalog = catalog;
     }
-    ScatterArgs a{};
-    a.n_elts = (int32_t)L.elts.size();
-    for (size_t j = 0; j < L.elts.size(); ++j) {
-        const Elt &e = ctx->elts.at(L.elts[j]);
-        ARE_CHECK(e.max_id < catalog, ARE_EINVAL,
-                  "ELT " + std::to_string(L.elts[j]) + " holds event id " + std::to_string(e.max_id) +
-                      " outside the YET's catalog of " + std::to_string(catalog));
-        a.ids[j] = e.d_ids;
-        a.loss[j] = e.d_loss;
-        a.n[j] = e.n;
-        a.fx[j] = e.terms.fx;
-    }
-    TermsF32 t32;
-    TermsF64 t64;
-    int any_share = 0;
-    fill_terms(ctx, L, t32, t64, any_share);
-    ctx->launches += launch_fold(a, t64, catalog, f.F(), f.bits(), f.hmax(), ctx->num_sms, s);
+    const ScatterArgs a = scatter_args(ctx, L, catalog, 0);
+    ctx->launches += launch_fold(a, L.terms.occ_ret, L.terms.occ_lim, catalog, f.F(), f.bits(),
+                                 f.hmax(), ctx->num_sms, s);
     return f;
 }
 
-void fill_layer_f32(are_ctx *ctx, const Layer &L, LayerF32 &o)
+void fill_layer_f32(const Layer &L, LayerF32 &o)
 {
     std::memset(&o, 0, sizeof o);
     o.table = static_cast<const float *>(L.t32.d);
     o.jp = L.t32.jp;
-    for (int j = 0; j < kMaxElts; ++j) o.share[j] = 1.f;
-    for (size_t j = 0; j < L.elts.size(); ++j) {
-        const are_fin_terms &f = ctx->elts.at(L.elts[j]).terms;
-        o.ded[j] = (float)f.deductible;
-        o.lim[j] = (float)f.limit;
-        o.share[j] = (float)f.share;
-        o.any_share |= f.share != 1.0;
-    }
     o.occ_r = (float)L.terms.occ_ret;
     o.occ_l = (float)L.terms.occ_lim;
     o.agg_r = L.terms.agg_ret;
@@ -441,7 +404,7 @@ int run_single(are_ctx *ctx, const Layer &L, const Yet &y, int64_t trial_begin, 
     const bool fp32 = precision != ARE_FP64;
     if (fp32 && te.kernel == 0) {
         ItemWork w = item_work(y, trial_begin, n_trials, te.cfg);
-        fill_layer_f32(ctx, L, w.one);
+        fill_layer_f32(L, w.one);
         w.one.ylt = d_out;
         w.one.t0 = 0;
         w.one.nt = n_trials;
@@ -465,7 +428,7 @@ int run_single(are_ctx *ctx, const Layer &L, const Yet &y, int64_t trial_begin, 
     a.epl = te.cfg.rows_in_flight == 2 ? 2 : 1;
     TermsF32 t32;
     TermsF64 t64;
-    fill_terms(ctx, L, t32, t64, a.any_share);
+    fill_terms(L, t32, t64);
     a.n_elts = (int32_t)L.elts.size();
     if (compact) {   // the staged kernel, through the row index
         a.table = L.comp.rows();
@@ -487,9 +450,9 @@ TuneEntry tuned(are_ctx *ctx, are_precision p, const Yet &y, int jp, bool multi)
 {
     auto it = ctx->tune.find(tune_key(p, y, jp, multi));
     if (it != ctx->tune.end()) return it->second;
-    TuneEntry d;   // untuned: the staged kernel (two events per lane for FP32+Kahan)
-    d.kernel = 1;
-    d.cfg.rows_in_flight = p == ARE_FP32_KAHAN ? 2 : 1;
+    TuneEntry d;   // untuned: FP32, the register-rows kernel (two groups of 32 events
+    d.kernel = p == ARE_FP64 ? 1 : 2;   // per batch); FP64, the staged kernel
+    d.cfg.rows_in_flight = 2;
     return d;
 }
 
@@ -552,7 +515,7 @@ Groups group_layers(are_ctx *ctx, const std::vector<int32_t> &layers,
     for (size_t i = 0; i < layers.size(); ++i) {
         const Layer &L = ctx->layers.at(layers[i]);
         LayerF32 r;
-        fill_layer_f32(ctx, L, r);
+        fill_layer_f32(L, r);
         r.ylt = ylts[i];
         const int gi = r.jp == 8 ? 0 : r.jp == 16 ? 1 : 2;
         r.item_begin = 0;
@@ -1295,7 +1258,7 @@ are_status are_simulate_occurrences(are_ctx *ctx, int32_t layer, int32_t yet, in
         }
         TermsF32 t32;
         TermsF64 t64;
-        fill_terms(ctx, L, t32, t64, a.any_share);
+        fill_terms(L, t32, t64);
         ctx->launches += fp32 ? launch_staged32_occ(a, t.jp, t32, ctx->num_sms, cs.s)
                               : launch_staged64(a, t.jp, t64, true, ctx->num_sms, cs.s);
         cs.finish();
@@ -1513,19 +1476,20 @@ are_status are_autotune(are_ctx *ctx, const int32_t *layers, int32_t n_layers, i
         const std::string key = tune_key(precision, y, jp, multi);
         std::vector<TuneEntry> cands;
         if (fp32) {
+            for (int u : {1, 2}) {            // register rows, one or two groups of 32 events
+                TuneEntry e;
+                e.kernel = 2;
+                e.cfg.rows_in_flight = u;
+                cands.push_back(e);
+            }
             for (int epl : {1, 2}) {          // staged rows, one or two events per lane
                 TuneEntry e;
                 e.kernel = 1;
                 e.cfg.rows_in_flight = epl;
                 cands.push_back(e);
             }
-            if (!multi) {
-                TuneEntry e;
-                e.kernel = 2;
-                cands.push_back(e);
-            }
-            for (int u : {4, 8})
-                for (int tpi : multi ? std::vector<int>{2, 4, 8, 16} : std::vector<int>{2, 8}) {
+            for (int u : {1, 2})              // persistent work items
+                for (int tpi : multi ? std::vector<int>{4, 8, 16, 32} : std::vector<int>{8, 32}) {
                     TuneEntry e;
                     e.kernel = 0;
                     e.cfg.rows_in_flight = u;

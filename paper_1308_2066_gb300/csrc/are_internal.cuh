@@ -73,8 +73,10 @@ struct Elt {
     int users = 0;                 // layers referring to it
 };
 
-// Event-major direct-access table of one layer: row e holds the converted
-// losses of event e in the layer's ELTs, jp columns (j >= J are zero).
+// Event-major direct-access table of one layer: row e holds, for each of the
+// layer's ELTs in layer order, event e's financial term
+// share * min(max(fx * loss - D, 0), Lim) (zero where the ELT has no entry
+// for e), jp columns (j >= J are zero).
 struct Table {
     int32_t catalog = -1;
     int jp = 0;
@@ -130,12 +132,11 @@ struct Layer {
 // kernel parameter blocks (passed by value; they live in the constant bank)
 // ---------------------------------------------------------------------------
 
+// The layer's occurrence terms (Table I); the per-ELT terms are in the table.
 struct TermsF32 {
-    float ded[kMaxElts], lim[kMaxElts], share[kMaxElts];
     float occ_r, occ_l;
 };
 struct TermsF64 {
-    double ded[kMaxElts], lim[kMaxElts], share[kMaxElts];
     double occ_r, occ_l;
 };
 
@@ -151,10 +152,10 @@ struct SimArgs {
     int32_t jp64;            // screened FP64: columns of the FP64 table
     int32_t n_elts;          // ELTs of the layer
     double agg_r, agg_l;
-    int any_share;           // some ELT has share != 1
     double *ylt;             // n_trials (may be null when occurrences are written)
-    int kernel;              // 1 staged, 2 register
-    int epl;                 // staged FP32 kernel: events per lane per batch (1 or 2)
+    int kernel;              // 1 staged, 2 register rows
+    int epl;                 // staged FP32 kernel: events per lane per batch (1 or 2);
+                             // register-rows kernel: groups of 32 events per batch (1 or 2)
     double *marg;            // per-occurrence marginals, or null
     double *occ_max;         // largest occurrence loss per trial, or null
     int64_t marg_base;       // event index of marg[0]
@@ -176,25 +177,36 @@ struct FoldArgs {
     double *ylt;             // n_trials
 };
 
+// The layer's ELTs and their financial terms, as the table builders read them.
 struct ScatterArgs {
     const int32_t *ids[kMaxElts];
     const double *loss[kMaxElts];
     int32_t n[kMaxElts];
     double fx[kMaxElts];
-    double ded[kMaxElts];    // per-ELT deductible, subtracted as the table is built
+    double ded[kMaxElts];
+    double lim[kMaxElts];
+    double share[kMaxElts];
     int32_t n_elts;
     int32_t jp;
 };
 
+// A layer table entry: the financial term share * min(max(fx * x - D, 0), Lim)
+// of a loss x in FP64, operation by operation (Section II-B step 2).
+__device__ __forceinline__ double fin_term(double x, double fx, double ded, double lim, double share)
+{
+    double e = __dsub_rn(__dmul_rn(fx, x), ded);
+    e = e > 0.0 ? e : 0.0;
+    e = e > lim ? lim : e;
+    return __dmul_rn(share, e);
+}
+
 // One layer of a persistent multi-layer launch (FP32 tables).
 struct LayerF32 {
-    const float *table;      // [catalog][jp]
+    const float *table;      // [catalog][jp] terms
     double *ylt;             // n_trials losses
-    float ded[kMaxElts], lim[kMaxElts], share[kMaxElts];  // zero / zero / one past J
     float occ_r, occ_l;
     double agg_r, agg_l;
     int32_t jp;              // 8, 16 or 32
-    int32_t any_share;
     int64_t item_begin;      // index of the layer's first work item
     int64_t t0, nt;          // the layer's trials: t0 .. t0 + nt - 1 (ylt indexed by trial)
 };
@@ -216,7 +228,7 @@ struct ItemWork {
 
 // Tunables of the persistent kernel.
 struct ItemConfig {
-    int rows_in_flight = 8;  // U: table rows per lane in flight (4 or 8)
+    int rows_in_flight = 2;  // U: groups of 32 events per batch (1 or 2)
     int trials_per_item = 8; // trials per work item
     int blocks_per_sm = 0;   // 256-thread blocks per SM (0 = as many as fit)
 };
@@ -259,7 +271,7 @@ int launch_build_compact(int32_t *row_of, int32_t *counts, float *rows, size_t r
                          int32_t catalog, const ScatterArgs &a, cudaStream_t s);
 int32_t folded_words(int32_t catalog);
 bool folded_bits_in_smem(int32_t words);
-int launch_fold(const ScatterArgs &elts, const TermsF64 &tm, int32_t catalog, ulonglong2 *F,
+int launch_fold(const ScatterArgs &elts, double occ_r, double occ_l, int32_t catalog, ulonglong2 *F,
                 uint32_t *bits, unsigned long long *hmax, int num_sms, cudaStream_t s);
 int launch_folded(const FoldArgs &a, int num_sms, cudaStream_t s);
 float gather_ceiling_ms(const int32_t *ids, int64_t n, int row_bytes, int reps, int num_sms,

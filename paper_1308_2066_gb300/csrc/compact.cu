@@ -109,9 +109,9 @@ __global__ void k_scatter_compact(float *__restrict__ rows, const int32_t *__res
     const int j = blockIdx.y;
     const int32_t *ids = a.ids[j];
     const double *loss = a.loss[j];
-    const double fx = a.fx[j], ded = a.ded[j];
+    const double fx = a.fx[j], ded = a.ded[j], lim = a.lim[j], share = a.share[j];
     for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < a.n[j]; i += gridDim.x * blockDim.x)
-        rows[(size_t)row_of[ids[i]] * a.jp + j] = (float)__dsub_rn(__dmul_rn(fx, loss[i]), ded);
+        rows[(size_t)row_of[ids[i]] * a.jp + j] = (float)fin_term(loss[i], fx, ded, lim, share);
 }
 
 }  // namespace

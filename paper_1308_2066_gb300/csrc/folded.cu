@@ -351,7 +351,7 @@ bool folded_bits_in_smem(int32_t words)
     return (size_t)words * 4 + sizeof(uint32_t) * kFoldThreads * kSlots <= 220u * 1024u;
 }
 
-int launch_fold(const ScatterArgs &elts, const TermsF64 &tm, int32_t catalog, ulonglong2 *F,
+int launch_fold(const ScatterArgs &elts, double occ_r, double occ_l, int32_t catalog, ulonglong2 *F,
                 uint32_t *bits, unsigned long long *hmax, int num_sms, cudaStream_t s)
 {
     const int32_t words = folded_words(catalog);
@@ -364,13 +364,13 @@ int launch_fold(const ScatterArgs &elts, const TermsF64 &tm, int32_t catalog, ul
         int blocks = (elts.n[j] + 255) / 256;
         if (blocks > num_sms * 8) blocks = num_sms * 8;
         k_fold_elt<<<blocks, 256, 0, s>>>(elts.ids[j], elts.loss[j], elts.n[j], elts.fx[j],
-                                          tm.ded[j], tm.lim[j], tm.share[j], h, 2);
+                                          elts.ded[j], elts.lim[j], elts.share[j], h, 2);
         ARE_CUDA_TRY(cudaGetLastError());
         ++launches;
     }
     int64_t blocks = ((int64_t)words * 32 + 255) / 256;
     if (blocks > (int64_t)num_sms * 16) blocks = (int64_t)num_sms * 16;
-    k_fold_finish<<<(unsigned)blocks, 256, 0, s>>>(catalog, tm.occ_r, tm.occ_l, h, 2, bits, words, hmax);
+    k_fold_finish<<<(unsigned)blocks, 256, 0, s>>>(catalog, occ_r, occ_l, h, 2, bits, words, hmax);
     ARE_CUDA_TRY(cudaGetLastError());
     k_fold_fixed<<<(unsigned)blocks, 256, 0, s>>>(catalog, F, hmax);
     ARE_CUDA_TRY(cudaGetLastError());

@@ -4,15 +4,18 @@
 // The paper keeps one catalog-sized loss array per ELT (Section III-B: a
 // 2M-event catalog and 15 ELTs give 30M event-loss pairs), so an event costs
 // one random access per ELT.  Here row e of a single table holds event e's
-// losses in all J ELTs of the layer, in layer order, padded to a whole number
-// of 32-byte sectors (jp columns, zeros past J): one event's lookups in every
-// ELT become one row read.  Each entry is the loss in excess of the ELT's
-// deductible, fx * loss - D (currency conversion, then the deductible of the
-// financial terms, Section II-B step 2), computed in FP64 as the terms define
-// it and rounded once to the table type; an event the ELT does not hold
-// stores 0.  The analysis kernels then clamp an entry to [0, Lim]: a zero or
-// negative excess gives a zero term, as a loss at or below the deductible
-// does.
+// entries in all J ELTs of the layer, in layer order, padded to a whole
+// number of 32-byte sectors (jp columns, zeros past J): one event's lookups
+// in every ELT become one row read.
+//
+// Each entry is the event's financial term in that ELT (Section II-B step 2
+// before its sum over ELTs): f_j(x) = share_j * min(max(fx_j * x - D_j, 0),
+// Lim_j), formed in FP64 in exactly the operations and order the terms
+// define (fx * x, less D, clamped, times the share) and rounded once to the
+// table type.  A term depends only on the event and the ELT, never on the
+// trial, so it is formed once per ELT entry here instead of once per
+// occurrence; every occurrence still reads its event's whole row.  An event
+// the ELT does not hold has x = 0 and stores f_j(0) = 0.
 #include <cuda_runtime.h>
 
 #include "are_internal.cuh"
@@ -27,9 +30,9 @@ __global__ void k_scatter(T *__restrict__ tab, const ScatterArgs a)
     const int32_t n = a.n[j];
     const int32_t *ids = a.ids[j];
     const double *loss = a.loss[j];
-    const double fx = a.fx[j];
+    const double fx = a.fx[j], ded = a.ded[j], lim = a.lim[j], share = a.share[j];
     for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const double x = __dsub_rn(__dmul_rn(fx, loss[i]), a.ded[j]);
+        const double x = fin_term(loss[i], fx, ded, lim, share);
         tab[(size_t)ids[i] * a.jp + j] = RU ? (T)__double2float_ru(x) : (T)x;
     }
 }

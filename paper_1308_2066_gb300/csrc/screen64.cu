@@ -4,19 +4,15 @@
 // the paper's sizes (1M events x 16 ELTs = 128 MB), so the FP64 staged
 // kernel takes about half of its table rows from HBM.  Here each event's row
 // is read from an FP32 copy of the table instead (half the bytes: it stays
-// in L2), whose entries are the FP64 entries rounded up.  An FP64 entry is
-// e = x - D, the loss's excess over the ELT's deductible, and a column is
-// marked when its FP32 copy is > 0: rounding up keeps the sign, so exactly
-// the entries with e > 0 are marked.  Only the marked entries -- a few per
-// cent at the paper's sizes -- are read from the FP64 table.  From there the
-// work is the FP64 staged kernel's: with share factors the marked (row,
-// column) pairs are compacted across the warp and their terms
-// min(e, Lim) * share formed 32 per FP64 instruction, without them each lane
-// reads and clamps its own; each event
-// then adds its marked columns in column order, the first taken as is.  An
-// unmarked column's term is exactly 0 and adding an exact 0 changes nothing,
-// so the event losses equal the FP64 staged kernel's (and the oracle's) bit
-// for bit.
+// in L2), whose entries are the FP64 terms rounded up.  A term is >= 0 and
+// rounding up keeps a non-zero term non-zero, so a column is marked when its
+// FP32 copy is > 0, exactly where the FP64 term is not 0.  Only the marked
+// entries -- a few per cent at the paper's sizes -- are read from the FP64
+// table: each lane reads its own in column order (the first two together)
+// and adds them, the first taken as is, with an FP64 add only where some
+// event of the warp has two or more.  An unmarked column's term is exactly 0
+// and adding an exact 0 changes nothing, so the event losses equal the FP64
+// staged kernel's (and the oracle's) bit for bit.
 #include "staged.cuh"
 
 namespace are {
@@ -24,14 +20,10 @@ namespace {
 
 using namespace staged;
 
-constexpr int kRound = 64;   // marked entries valued per round (two per lane)
-
 template <int JP>
 __host__ __device__ constexpr int screen_smem_bytes()
 {
-    // per warp: two FP32 row buffers, the compaction list, a round of values
-    // and the batch's event ids; per block: the FP64 terms
-    return kWarps * (2 * 32 * JP * 4 + 2 * 32 * JP + kRound * 8 + 32 * 4) + 3 * kMaxElts * 8;
+    return kWarps * 2 * 32 * JP * 4;   // per warp: two FP32 row buffers
 }
 
 template <int JP, bool FIXED>
@@ -40,31 +32,11 @@ __global__ void __launch_bounds__(kWarps * 32) k_screen64(const SimArgs a, const
     constexpr int CH = JP / 4;   // 16-byte chunks of an FP32 row
     extern __shared__ float4 stage[];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    // shared memory: rows | lists | values | ids | FP64 terms
-    char *smem = reinterpret_cast<char *>(stage);
-    constexpr size_t kRows = (size_t)kWarps * 2 * 32 * JP * 4;
-    constexpr size_t kLists = kRows + (size_t)kWarps * 32 * JP * 2;
-    constexpr size_t kVals = kLists + (size_t)kWarps * kRound * 8;
-    constexpr size_t kIds = kVals + (size_t)kWarps * 32 * 4;
-    constexpr size_t kTerms = kIds + 3 * kMaxElts * 8;
-    static_assert(kTerms == (size_t)screen_smem_bytes<JP>(), "layout");
     float4 *buf0 = stage + (size_t)w * 2 * 32 * CH;
     float4 *buf1 = buf0 + 32 * CH;
-    uint16_t *list = reinterpret_cast<uint16_t *>(smem + kRows) + (size_t)w * 32 * JP;
-    double *vals = reinterpret_cast<double *>(smem + kLists) + (size_t)w * kRound;
-    int32_t *sids = reinterpret_cast<int32_t *>(smem + kVals) + (size_t)w * 32;
-    double *sterms = reinterpret_cast<double *>(smem + kIds);
-    for (int i = threadIdx.x; i < kMaxElts; i += blockDim.x) {
-        sterms[i] = tm.ded[i];
-        sterms[kMaxElts + i] = tm.lim[i];
-        sterms[2 * kMaxElts + i] = tm.share[i];
-    }
-    __syncthreads();
-    const double *sl = sterms + kMaxElts, *ss = sterms + 2 * kMaxElts;
     const float *tab = static_cast<const float *>(a.table2);
     const double *t64 = static_cast<const double *>(a.table);
     const int jp64 = a.jp64;
-    const bool any_share = a.any_share != 0;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t step = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const double empty_loss = clamp_d(0.0, a.agg_r, a.agg_l);
@@ -102,7 +74,6 @@ __global__ void __launch_bounds__(kWarps * 32) k_screen64(const SimArgs a, const
     SumF64 sum;
 
     auto compute = [&](const Batch &b, int32_t idv, float4 *buf) {
-        sids[lane] = idv;
         // mark the columns that can carry a loss (padding columns hold 0)
         uint32_t mask = 0;
 #pragma unroll
@@ -116,64 +87,24 @@ __global__ void __launch_bounds__(kWarps * 32) k_screen64(const SimArgs a, const
             }
         }
         if (lane >= b.cnt) mask = 0;
+        // the marked columns' FP64 terms in column order (evict-first: the
+        // sparse FP64 reads must not push the screen out of L2), the first
+        // two read together, an FP64 add only where an event has two or more
         double g = 0.0;
-        if (!any_share) {
-            // no share factors: a marked entry's term min(e, Lim) is integer
-            // work, so each lane reads (evict-first, as below) and clamps its
-            // own marked columns in column order, the first two read
-            // together, with an FP64 add only where an event has two or more
-            const double *row = t64 + (size_t)(uint32_t)idv * jp64;
-            uint32_t m = mask;
-            const uint32_t m1 = m & (m - 1);
-            const int j0 = m ? __ffs(m) - 1 : 0, j1 = m1 ? __ffs(m1) - 1 : 0;
-            const double x0 = m ? __ldcs(row + j0) : 0.0, x1 = m1 ? __ldcs(row + j1) : 0.0;
-            if (m) g = clamp_bits(x0, bits(sl[j0]));
-            if (__any_sync(kFull, m1 != 0)) {
-                if (m1) g = vadd(g, clamp_bits(x1, bits(sl[j1])));
-            }
-            m = m1 & (m1 - 1);
-            while (__any_sync(kFull, m != 0)) {
-                if (m) {
-                    const int j = __ffs(m) - 1;
-                    g = vadd(g, clamp_bits(__ldcs(row + j), bits(sl[j])));
-                    m &= m - 1;
-                }
-            }
-        } else {
-            const int cnt = __popc(mask);
-            int incl = cnt;
-#pragma unroll
-            for (int off = 1; off < 32; off <<= 1) {
-                const int o = __shfl_up_sync(kFull, incl, off);
-                if (lane >= off) incl += o;
-            }
-            const int total = __shfl_sync(kFull, incl, 31);
-            const int start = incl - cnt;
-            int k = start;
-            for (uint32_t m = mask; m; m &= m - 1) list[k++] = (uint16_t)((lane << 5) | (__ffs(m) - 1));
-            __syncwarp();
-            // the event loss: marked columns in column order, valued a round at a time
-            bool have = false;
-            for (int base = 0; base < total; base += kRound) {
-                const int top = total - base < kRound ? total - base : kRound;
-                for (int i = lane; i < top; i += 32) {
-                    const int e = list[base + i], r = e >> 5, j = e & 31;
-                    // evict-first: the sparse FP64 reads must not push the screen out of L2
-                    const double x = __ldcs(t64 + (size_t)sids[r] * jp64 + j);
-                    vals[i] = vmul(clamp_bits(x, bits(sl[j])), ss[j]);
-                }
-                __syncwarp();
-                const int lo = start > base ? start : base;
-                const int hi = start + cnt < base + top ? start + cnt : base + top;
-                for (int q = lo; __any_sync(kFull, q < hi); ++q) {
-                    if (q < hi) {
-                        const double v = vals[q - base];
-                        if (have) g = vadd(g, v);
-                        else g = v;
-                        have = true;
-                    }
-                }
-                __syncwarp();
+        const double *row = t64 + (size_t)(uint32_t)idv * jp64;
+        uint32_t m = mask;
+        const uint32_t m1 = m & (m - 1);
+        const int j0 = m ? __ffs(m) - 1 : 0, j1 = m1 ? __ffs(m1) - 1 : 0;
+        const double x0 = m ? __ldcs(row + j0) : 0.0, x1 = m1 ? __ldcs(row + j1) : 0.0;
+        if (m) g = x0;
+        if (__any_sync(kFull, m1 != 0)) {
+            if (m1) g = vadd(g, x1);
+        }
+        m = m1 & (m1 - 1);
+        while (__any_sync(kFull, m != 0)) {
+            if (m) {
+                g = vadd(g, __ldcs(row + __ffs(m) - 1));
+                m &= m - 1;
             }
         }
         // occurrence terms and the trial's running sum

@@ -214,26 +214,15 @@ void build_request_table(Server &S, Slot &sl)
             a.n[j] = e.n;
             a.fx[j] = e.terms.fx;
             a.ded[j] = e.terms.deductible;
+            a.lim[j] = e.terms.limit;
+            a.share[j] = e.terms.share;
         }
     }
     if (S.cfg.folded) {
-        TermsF64 tm;
-        std::memset(&tm, 0, sizeof tm);
-        {
-            std::lock_guard<std::recursive_mutex> lk(S.ctx->mu);
-            for (int j = 0; j < kMaxElts; ++j) tm.share[j] = 1.0;
-            for (size_t j = 0; j < sl.req.elts.size(); ++j) {
-                const are_fin_terms &f = S.ctx->elts.at(sl.req.elts[j]).terms;
-                tm.ded[j] = f.deductible;
-                tm.lim[j] = f.limit;
-                tm.share[j] = f.share;
-            }
-        }
-        tm.occ_r = sl.req.terms.occ_ret;
-        tm.occ_l = sl.req.terms.occ_lim;
         char *b = S.d_arena + sl.tab_off;
-        add_launches(S, launch_fold(a, tm, S.y->catalog, folded_F(b, S.y->catalog), folded_bits(b),
-                                    folded_hmax(b), S.ctx->num_sms, S.stream));
+        add_launches(S, launch_fold(a, sl.req.terms.occ_ret, sl.req.terms.occ_lim, S.y->catalog,
+                                    folded_F(b, S.y->catalog), folded_bits(b), folded_hmax(b),
+                                    S.ctx->num_sms, S.stream));
         return;
     }
     ARE_CUDA_TRY(cudaMemsetAsync(S.d_arena + sl.tab_off, 0, sl.tab_bytes, S.stream));
@@ -247,15 +236,6 @@ void fill_record(Server &S, Slot &sl)
     o.table = reinterpret_cast<const float *>(S.d_arena + sl.tab_off);
     o.ylt = reinterpret_cast<double *>(S.d_arena + sl.ylt_off);
     o.jp = sl.jp;
-    for (int j = 0; j < kMaxElts; ++j) o.share[j] = 1.f;
-    std::lock_guard<std::recursive_mutex> lk(S.ctx->mu);
-    for (size_t j = 0; j < sl.req.elts.size(); ++j) {
-        const are_fin_terms &f = S.ctx->elts.at(sl.req.elts[j]).terms;
-        o.ded[j] = (float)f.deductible;
-        o.lim[j] = (float)f.limit;
-        o.share[j] = (float)f.share;
-        o.any_share |= f.share != 1.0;
-    }
     o.occ_r = (float)sl.req.terms.occ_ret;
     o.occ_l = (float)sl.req.terms.occ_lim;
     o.agg_r = sl.req.terms.agg_ret;
@@ -459,7 +439,7 @@ void scheduler(Server *SP)
                 ARE_CUDA_TRY(cudaMemsetAsync(w.counter, 0, sizeof(unsigned long long), S.stream));
                 ItemConfig cfg;
                 cfg.trials_per_item = tpi;
-                cfg.rows_in_flight = 4;
+                cfg.rows_in_flight = 2;
                 launches += launch_items(w, kWidths3[g], cfg, S.cfg.precision, S.ctx->num_sms, S.stream);
             }
             // folded tables: one trial-pass launch per request slice
@@ -495,17 +475,10 @@ void scheduler(Server *SP)
                 sa.table = sl.rec.table;
                 sa.agg_r = sl.rec.agg_r;
                 sa.agg_l = sl.rec.agg_l;
-                sa.any_share = sl.rec.any_share;
                 sa.ylt = sl.rec.ylt + sl.launched;
-                sa.kernel = 1;
-                sa.epl = S.cfg.precision == ARE_FP32_KAHAN ? 2 : 1;
+                sa.kernel = 2;
+                sa.epl = 2;
                 TermsF32 tm;
-                std::memset(&tm, 0, sizeof tm);
-                for (int j = 0; j < kMaxElts; ++j) {
-                    tm.ded[j] = sl.rec.ded[j];
-                    tm.lim[j] = sl.rec.lim[j];
-                    tm.share[j] = sl.rec.share[j];
-                }
                 tm.occ_r = sl.rec.occ_r;
                 tm.occ_l = sl.rec.occ_l;
                 launches += launch_simulate(sa, S.cfg.precision, sl.jp, &tm, nullptr, S.ctx->num_sms, S.stream);

@@ -1,57 +1,42 @@
 // simulate.cu -- the analysis stage (Basic Algorithm, Section II-B) for one
 // layer over a range of trials, reading the layer's event-major
-// direct-access table built by repack.cu.
+// direct-access table built by repack.cu (each entry an event's financial
+// term in one ELT).  Three kernels:
 //
-// Mapping (GB300): one warp per trial.  The warp walks the trial's events in
-// steps; in a step each event's table row (J losses, 32-byte aligned) is read
-// by R lanes with one 16-byte load each, so a warp load instruction fetches
-// 32/R whole rows.  Each lane applies the financial terms (step 2) to the
-// columns it holds, the R lanes of a row add their parts by shuffles (the sum
-// over ELTs that closes step 2), the row's first lane applies the occurrence
-// terms (step 3) and adds the occurrence loss to its running sum.  At
-// the end of the trial the warp adds the lanes' sums and applies the
-// aggregate terms (step 4).  The trial loss is the aggregate-clamped total:
-// with non-negative occurrence losses the de-cumulated marginals of step 4
-// telescope to it, so the YLT needs no per-event scan.
+//  * k_rows (FP32 tables, the default): rows held in registers, see rows.cuh.
+//  * k_simulate_staged (FP32 tables, a tuning candidate and the compact
+//    layout's kernel): one event per lane, rows staged in shared memory.
+//  * k_simulate (FP64 tables, a tuning candidate): one warp per trial; in a
+//    step each event's table row is read by R lanes with one 16-byte load
+//    each, the R lanes of a row add their parts by shuffles (the sum over
+//    ELTs of step 2), the row's first lane applies the occurrence terms
+//    (step 3) and adds the occurrence loss to its running sum; at the end of
+//    the trial the warp adds the lanes' sums and applies the aggregate terms
+//    (step 4).
+//
+// The trial loss is the aggregate-clamped total: with non-negative
+// occurrence losses the de-cumulated marginals of step 4 telescope to it, so
+// the YLT needs no per-event scan.
 //
 // FP64 on GB300 runs at a small fraction of the FP32 rate, so the FP64 path
 // takes every decision it can on bit patterns: for non-negative doubles the
-// integer order of the bits is the numeric order, so "excess <= 0" (a table
-// entry holds the loss less the ELT's deductible), "v > limit" and the zero
-// tests are integer compares.  A subtraction or an
+// integer order of the bits is the numeric order, so "x > retention", the
+// limit clamp and the zero tests are integer compares.  A subtraction or an
 // addition is issued only when some lane of the warp needs one (adding an
 // exact zero or clamping a non-positive value changes nothing), which keeps
 // the FP64 pipe for the few occurrences that carry a loss.
 #include <cuda_runtime.h>
 
-#include <cstdlib>
+#include <string>
 #include <type_traits>
 
 #include "are_internal.cuh"
+#include "rows.cuh"
 
 namespace are {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
-
-template <typename T>
-struct VecOf;
-template <>
-struct VecOf<float> {
-    using type = float4;
-    static constexpr int n = 4;
-};
-template <>
-struct VecOf<double> {
-    using type = double2;
-    static constexpr int n = 2;
-};
-
-__device__ __forceinline__ float comp(const float4 &v, int c)
-{
-    return c == 0 ? v.x : c == 1 ? v.y : c == 2 ? v.z : v.w;
-}
-__device__ __forceinline__ double comp(const double2 &v, int c) { return c == 0 ? v.x : v.y; }
 
 // Two FP32 additions in one packed instruction (sm_100 and later), used by
 // the FP32 + Kahan staged kernel.
@@ -104,14 +89,6 @@ __device__ __forceinline__ double add_nn(double a, double b)
     return r;
 }
 
-// min(max(e, 0), l) for any e and l >= 0 (+inf allowed), on bit patterns:
-// a table entry (the loss's excess over the deductible) clamped to the limit.
-__device__ __forceinline__ double excess_nn(double e, uint64_t l_bits)
-{
-    const uint64_t b = bits(e);
-    return (int64_t)b <= 0 ? 0.0 : dbl(b < l_bits ? b : l_bits);
-}
-
 // min(max(x - r, 0), l) for x, r >= 0 and l >= 0 (+inf allowed).  The
 // subtraction is issued only when some lane has x > r.  All lanes call it.
 __device__ __forceinline__ double net_nn(double x, uint64_t r_bits, double r, uint64_t l_bits)
@@ -126,89 +103,22 @@ __device__ __forceinline__ double net_nn(double x, uint64_t r_bits, double r, ui
     return out;
 }
 
-template <typename T>
-struct LaneTerms;
-
-template <>
-struct LaneTerms<float> {
-    float lim[4], share[4];
-    float occ_r, occ_l;
-    __device__ void load(const TermsF32 &t, int col)
-    {
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            const int j = col * 4 + c;
-            lim[c] = j < kMaxElts ? t.lim[j] : 0.f;
-            share[c] = j < kMaxElts ? t.share[j] : 1.f;
-        }
-        occ_r = t.occ_r;
-        occ_l = t.occ_l;
-    }
-    // sum over this lane's columns of share * min(max(x - D, 0), Lim), the
-    // table holding x - D
-    __device__ __forceinline__ float part(const float4 &v, bool any_share) const
-    {
-        float p = 0.f;
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            float n = fminf(fmaxf(comp(v, c), 0.f), lim[c]);
-            if (any_share) n = __fmul_rn(n, share[c]);
-            p = __fadd_rn(p, n);
-        }
-        return p;
-    }
-};
-
-template <>
-struct LaneTerms<double> {
-    double share[2];
-    uint64_t lim_b[2], share_b[2];
+// The occurrence terms as one lane of the FP64 register kernel uses them.
+struct LaneTermsF64 {
     double occ_r;
     uint64_t occ_r_b, occ_l_b;
-    __device__ void load(const TermsF64 &t, int col)
+    __device__ void load(const TermsF64 &t)
     {
-#pragma unroll
-        for (int c = 0; c < 2; ++c) {
-            const int j = col * 2 + c;
-            share[c] = j < kMaxElts ? t.share[j] : 1.0;
-            share_b[c] = bits(share[c]);
-            lim_b[c] = bits(j < kMaxElts ? t.lim[j] : 0.0);
-        }
         occ_r = t.occ_r;
         occ_r_b = bits(t.occ_r);
         occ_l_b = bits(t.occ_l);
     }
-    __device__ __forceinline__ double part(const double2 &v, bool any_share) const
-    {
-        double p = 0.0;
-#pragma unroll
-        for (int c = 0; c < 2; ++c) {
-            double n = excess_nn(comp(v, c), lim_b[c]);
-            if (any_share) {
-                const bool need = bits(n) != 0 && share_b[c] != bits(1.0);
-                if (__any_sync(kFull, need)) {
-                    const double m = vmul(n, share[c]);
-                    if (need) n = m;
-                }
-            }
-            p = add_nn(p, n);
-        }
-        return p;
-    }
+    // sum over this lane's columns of the terms, in column order
+    __device__ __forceinline__ double part(const double2 &v) const { return add_nn(v.x, v.y); }
 };
 
 // Sum of the R lanes of a row into its first lane (col == 0), pairing
 // neighbours first.  Works for any R <= 32; every lane calls it.
-template <int R>
-__device__ __forceinline__ float row_sum(float v, int col)
-{
-#pragma unroll
-    for (int off = 1; off < R; off <<= 1) {
-        const float o = __shfl_down_sync(kFull, v, off);
-        if ((col & (2 * off - 1)) == 0 && col + off < R) v = __fadd_rn(v, o);
-    }
-    return v;
-}
 template <int R>
 __device__ __forceinline__ double row_sum(double v, int col)
 {
@@ -221,13 +131,8 @@ __device__ __forceinline__ double row_sum(double v, int col)
     return v;
 }
 
-// Per-lane running sums of occurrence losses (step 4), one
-// flavour per precision mode.
-struct AccF64 {
-    double s = 0.0;
-    __device__ __forceinline__ void add(double o) { s = add_nn(s, o); }
-    __device__ __forceinline__ double total() const { return s; }
-};
+// Per-lane running sums of occurrence losses (step 4) for the staged FP32
+// kernel, one flavour per precision mode.
 struct AccKahan {
     float s = 0.f, c = 0.f;
     __device__ __forceinline__ void add(float o)
@@ -267,32 +172,23 @@ __device__ __forceinline__ double net_d(double v, double r, double l)
     return a < l ? a : l;
 }
 
-template <typename T, int JP, int ACC, bool FIXED>
-struct Config {
-    static constexpr int VPL = VecOf<T>::n;
-    static constexpr int R = JP / VPL;         // lanes per row
-    static constexpr int RPW = 32 / R;         // rows per warp load
-    static constexpr int U = RPW >= 16 ? 4 : 8;  // rows per lane in flight
-    static constexpr int B = RPW * U;          // events per warp step
-    static_assert(JP % VPL == 0 && R >= 1 && R <= 32, "row layout");
-};
-
-template <typename T, int JP, int ACC, bool FIXED>
-__global__ void __launch_bounds__(256) k_simulate(const SimArgs a,
-                                                  const typename std::conditional<
-                                                      sizeof(T) == 4, TermsF32, TermsF64>::type terms)
+// The FP64 register kernel: R = JP / 2 lanes per row (two doubles each),
+// 32 / R rows per warp load, U rows per lane in flight.
+template <int JP, bool FIXED>
+__global__ void __launch_bounds__(256) k_simulate(const SimArgs a, const TermsF64 terms)
 {
-    using Cfg = Config<T, JP, ACC, FIXED>;
-    using V = typename VecOf<T>::type;
-    constexpr int R = Cfg::R, RPW = Cfg::RPW, U = Cfg::U, B = Cfg::B;
+    constexpr int R = JP / 2;                  // lanes per row
+    constexpr int RPW = 32 / R;                // rows per warp load
+    constexpr int U = RPW >= 16 ? 4 : 8;       // rows per lane in flight
+    constexpr int B = RPW * U;                 // events per warp step
+    static_assert(JP % 2 == 0 && R >= 1 && R <= 32, "row layout");
 
     const int lane = threadIdx.x & 31;
     const int row = lane / R, col = lane % R;
     const bool lane_on = row < RPW;
-    LaneTerms<T> lt;
-    lt.load(terms, col);
-    const bool any_share = a.any_share != 0;
-    const T *tab = static_cast<const T *>(a.table);
+    LaneTermsF64 lt;
+    lt.load(terms);
+    const double *tab = static_cast<const double *>(a.table);
 
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t n_warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -301,10 +197,7 @@ __global__ void __launch_bounds__(256) k_simulate(const SimArgs a,
         const int64_t tt = a.trial_begin + t;
         const int64_t beg = FIXED ? tt * (int64_t)a.k : a.off[tt];
         const int64_t end = FIXED ? beg + a.k : a.off[tt + 1];
-
-        typename std::conditional<ACC == ARE_FP64, AccF64,
-                                  typename std::conditional<ACC == ARE_FP32_KAHAN, AccKahan,
-                                                            AccF32F64>::type>::type acc;
+        double acc = 0.0;
 
         int32_t nid[U];
 #pragma unroll
@@ -323,28 +216,22 @@ __global__ void __launch_bounds__(256) k_simulate(const SimArgs a,
                     nid[u] = (lane_on && e < end) ? __ldcs(a.ids + e) : -1;
                 }
             }
-            V v[U];
+            double2 v[U];
 #pragma unroll
             for (int u = 0; u < U; ++u) {
                 if (id[u] >= 0)
-                    v[u] = __ldg(reinterpret_cast<const V *>(tab + (size_t)id[u] * JP) + col);
+                    v[u] = __ldg(reinterpret_cast<const double2 *>(tab + (size_t)id[u] * JP) + col);
                 else
-                    v[u] = V{};
+                    v[u] = double2{};
             }
 #pragma unroll
             for (int u = 0; u < U; ++u) {
-                const T g = row_sum<R>(lt.part(v[u], any_share), col);
+                const double g = row_sum<R>(lt.part(v[u]), col);
                 const bool lead = col == 0 && id[u] >= 0;
-                if constexpr (sizeof(T) == 4) {
-                    const float o = lead ? fminf(fmaxf(__fsub_rn(g, lt.occ_r), 0.f), lt.occ_l) : 0.f;
-                    acc.add(o);
-                } else {
-                    const double o = net_nn(lead ? g : 0.0, lt.occ_r_b, lt.occ_r, lt.occ_l_b);
-                    acc.add(o);
-                }
+                acc = add_nn(acc, net_nn(lead ? g : 0.0, lt.occ_r_b, lt.occ_r, lt.occ_l_b));
             }
         }
-        const double S = warp_total(acc.total());
+        const double S = warp_total(acc);
         if (lane == 0) a.ylt[t] = net_d(S, a.agg_r, a.agg_l);
     }
 }
@@ -357,7 +244,7 @@ __global__ void __launch_bounds__(256) k_simulate(const SimArgs a,
 // cp.async in a coalesced pattern (the lanes of one copy instruction cover
 // 32/CH whole rows, so each row costs one L1 wavefront), then every lane
 // reads its own event's row from shared memory and does all of the event's
-// arithmetic: financial terms per ELT, the sum over ELTs in layer order, the
+// arithmetic: the sum over ELTs of the row's terms, the
 // occurrence terms and the compensated running sum.  Row chunks are rotated
 // per row so the lanes' 16-byte shared reads hit distinct banks.  Event ids
 // are loaded three batches ahead and rows one batch ahead (double buffer).
@@ -475,7 +362,6 @@ __global__ void __launch_bounds__(kStagedWarps * 32)
     float4 *buf1 = buf0 + ROWS * CH;
     const uint32_t sbuf0 = smem_addr(buf0), sbuf1 = smem_addr(buf1);
     const char *tab = static_cast<const char *>(a.table);
-    const bool any_share = a.any_share != 0;
 
     const int32_t warp = (int32_t)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     const int32_t step = (int32_t)((gridDim.x * blockDim.x) >> 5);
@@ -527,43 +413,16 @@ __global__ void __launch_bounds__(kStagedWarps * 32)
 #pragma unroll
         for (int e = 0; e < EPL; ++e) {
             const int r = lane + 32 * e;
-            float g = 0.f;
-            if constexpr (ACC == ARE_FP32_KAHAN) {
-                // the running column sums in packed FP32x2 pairs (min/max
-                // have no packed form): four partial sums over the columns
-                // j mod 4, added at the end.  Entries are x - D already.
-                float2 g01 = make_float2(0.f, 0.f), g23 = make_float2(0.f, 0.f);
+            // the sum over ELTs of the row's terms in packed FP32x2 pairs:
+            // partial sums over the columns j mod 4, added at the end
+            float2 g01 = make_float2(0.f, 0.f), g23 = make_float2(0.f, 0.f);
 #pragma unroll
-                for (int c = 0; c < CH; ++c) {
-                    const float4 v = buf[r * CH + chunk_slot<CH>(c, r)];
-                    const int j = c * 4;
-                    float n0 = fminf(fmaxf(v.x, 0.f), tm.lim[j]);
-                    float n1 = fminf(fmaxf(v.y, 0.f), tm.lim[j + 1]);
-                    float n2 = fminf(fmaxf(v.z, 0.f), tm.lim[j + 2]);
-                    float n3 = fminf(fmaxf(v.w, 0.f), tm.lim[j + 3]);
-                    if (any_share) {
-                        n0 = __fmul_rn(n0, tm.share[j]);
-                        n1 = __fmul_rn(n1, tm.share[j + 1]);
-                        n2 = __fmul_rn(n2, tm.share[j + 2]);
-                        n3 = __fmul_rn(n3, tm.share[j + 3]);
-                    }
-                    g01 = add2(g01, make_float2(n0, n1));
-                    g23 = add2(g23, make_float2(n2, n3));
-                }
-                g = __fadd_rn(__fadd_rn(g01.x, g01.y), __fadd_rn(g23.x, g23.y));
-            } else {
-#pragma unroll
-                for (int c = 0; c < CH; ++c) {
-                    const float4 v = buf[r * CH + chunk_slot<CH>(c, r)];
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) {
-                        const int j = c * 4 + k;
-                        float n = fminf(fmaxf(comp(v, k), 0.f), tm.lim[j]);
-                        if (any_share) n = __fmul_rn(n, tm.share[j]);
-                        g = __fadd_rn(g, n);
-                    }
-                }
+            for (int c = 0; c < CH; ++c) {
+                const float4 v = buf[r * CH + chunk_slot<CH>(c, r)];
+                g01 = add2(g01, make_float2(v.x, v.y));
+                g23 = add2(g23, make_float2(v.z, v.w));
             }
+            const float g = __fadd_rn(__fadd_rn(g01.x, g01.y), __fadd_rn(g23.x, g23.y));
             acc.add(fminf(fmaxf(__fsub_rn(g, tm.occ_r), 0.f), tm.occ_l));
         }
         if (b.last()) {
@@ -640,23 +499,12 @@ void launch_staged_fx(const SimArgs &a, const TermsF32 &terms, int num_sms, cuda
             : launch_staged<JP, ACC, true, 1>(a, terms, num_sms, s);
 }
 
-// The register kernel when asked for (kernel 2, or ARE_SIM_KERNEL=reg).
-bool use_register_kernel(const SimArgs &a)
+template <int JP, bool FIXED>
+void launch_register64(const SimArgs &a, const TermsF64 &terms, int num_sms, cudaStream_t s)
 {
-    static const bool env = [] {
-        const char *v = getenv("ARE_SIM_KERNEL");
-        return v && v[0] == 'r';
-    }();
-    return env || a.kernel == 2;
-}
-
-template <typename T, int JP, int ACC, bool FIXED, typename TT>
-void launch_one(const SimArgs &a, const TT &terms, int num_sms, cudaStream_t s)
-{
-    auto kern = k_simulate<T, JP, ACC, FIXED>;
+    auto kern = k_simulate<JP, FIXED>;
     const int per_sm = fit_blocks(reinterpret_cast<const void *>(kern), 256, 0);
-    const int64_t warps_needed = a.n_trials;
-    int64_t blocks = (warps_needed + 7) / 8;
+    int64_t blocks = (a.n_trials + 7) / 8;
     const int64_t cap = (int64_t)num_sms * per_sm;
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
@@ -664,58 +512,109 @@ void launch_one(const SimArgs &a, const TT &terms, int num_sms, cudaStream_t s)
     ARE_CUDA_TRY(cudaGetLastError());
 }
 
-template <typename T, int JP, int ACC, typename TT>
-void launch_fx(const SimArgs &a, const TT &terms, int num_sms, cudaStream_t s)
+template <int JP>
+void launch_fx64(const SimArgs &a, const TermsF64 &terms, int num_sms, cudaStream_t s)
 {
     if (a.off)
-        launch_one<T, JP, ACC, false>(a, terms, num_sms, s);
+        launch_register64<JP, false>(a, terms, num_sms, s);
     else
-        launch_one<T, JP, ACC, true>(a, terms, num_sms, s);
+        launch_register64<JP, true>(a, terms, num_sms, s);
+}
+
+// ---------------------------------------------------------------------------
+// FP32 paths, rows in registers (rows.cuh): a warp takes a contiguous block
+// of the launch's trials.
+// ---------------------------------------------------------------------------
+
+// Blocks per SM the register budget is set for: the row pieces in flight
+// (JP * U floats per lane) decide it.
+__host__ __device__ constexpr int rows_min_blocks(int jp, int u)
+{
+    return jp * u <= 16 ? 5 : jp * u <= 32 ? 4 : 2;
+}
+
+template <int JP, int U, int ACC, bool FIXED>
+__global__ void __launch_bounds__(256, rows_min_blocks(JP, U))
+    k_rows(const rows::Trials a, const int64_t n_trials)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    rows::run_trials<JP, U, ACC, FIXED>(a, warp * n_trials / nw, (warp + 1) * n_trials / nw, lane);
+}
+
+template <int JP, int U, int ACC, bool FIXED>
+void launch_rows_t(const SimArgs &a, const TermsF32 &tm, int num_sms, cudaStream_t s)
+{
+    auto kern = k_rows<JP, U, ACC, FIXED>;
+    const int per_sm = fit_blocks(reinterpret_cast<const void *>(kern), 256, 0);
+    int64_t blocks = (a.n_trials + 7) / 8;
+    const int64_t cap = (int64_t)num_sms * per_sm;
+    if (blocks > cap) blocks = cap;
+    if (blocks < 1) blocks = 1;
+    rows::Trials t;
+    t.ids = a.ids;
+    t.off = a.off;
+    t.k = a.k;
+    t.trial_begin = a.trial_begin;
+    t.table = static_cast<const float *>(a.table);
+    t.ylt = a.ylt;
+    t.occ_r = tm.occ_r;
+    t.occ_l = tm.occ_l;
+    t.agg_r = a.agg_r;
+    t.agg_l = a.agg_l;
+    kern<<<(unsigned)blocks, 256, 0, s>>>(t, a.n_trials);
+    ARE_CUDA_TRY(cudaGetLastError());
+}
+
+template <int JP, int ACC>
+void launch_rows(const SimArgs &a, const TermsF32 &tm, int num_sms, cudaStream_t s)
+{
+    const bool two = a.epl != 1;
+    if (a.off)
+        two ? launch_rows_t<JP, 2, ACC, false>(a, tm, num_sms, s)
+            : launch_rows_t<JP, 1, ACC, false>(a, tm, num_sms, s);
+    else
+        two ? launch_rows_t<JP, 2, ACC, true>(a, tm, num_sms, s)
+            : launch_rows_t<JP, 1, ACC, true>(a, tm, num_sms, s);
+}
+
+template <int ACC>
+int launch_fp32(const SimArgs &a, int jp, const TermsF32 &tm, int num_sms, cudaStream_t s)
+{
+    const bool staged = a.kernel == 1 || a.kernel == 4;   // 4: the compact table's rows
+    switch (jp) {
+    case 8: staged ? launch_staged_fx<8, ACC>(a, tm, num_sms, s) : launch_rows<8, ACC>(a, tm, num_sms, s); return 1;
+    case 16: staged ? launch_staged_fx<16, ACC>(a, tm, num_sms, s) : launch_rows<16, ACC>(a, tm, num_sms, s); return 1;
+    case 32: staged ? launch_staged_fx<32, ACC>(a, tm, num_sms, s) : launch_rows<32, ACC>(a, tm, num_sms, s); return 1;
+    }
+    throw Error{ARE_EINVAL, "no FP32 simulate kernel for table width " + std::to_string(jp)};
 }
 
 }  // namespace
 
+// FP32: the register-rows kernel unless a.kernel names the staged one (1,
+// or 4 for the compact layout); FP64: the register kernel.
 int launch_simulate(const SimArgs &a, are_precision prec, int jp, const TermsF32 *t32,
                      const TermsF64 *t64, int num_sms, cudaStream_t s)
 {
     if (a.n_trials <= 0) return 0;
     if (prec == ARE_FP64) {
         switch (jp) {
-        case 4: return launch_fx<double, 4, ARE_FP64>(a, *t64, num_sms, s), 1;
-        case 8: return launch_fx<double, 8, ARE_FP64>(a, *t64, num_sms, s), 1;
-        case 12: return launch_fx<double, 12, ARE_FP64>(a, *t64, num_sms, s), 1;
-        case 16: return launch_fx<double, 16, ARE_FP64>(a, *t64, num_sms, s), 1;
-        case 20: return launch_fx<double, 20, ARE_FP64>(a, *t64, num_sms, s), 1;
-        case 24: return launch_fx<double, 24, ARE_FP64>(a, *t64, num_sms, s), 1;
-        case 28: return launch_fx<double, 28, ARE_FP64>(a, *t64, num_sms, s), 1;
-        case 32: return launch_fx<double, 32, ARE_FP64>(a, *t64, num_sms, s), 1;
+        case 4: return launch_fx64<4>(a, *t64, num_sms, s), 1;
+        case 8: return launch_fx64<8>(a, *t64, num_sms, s), 1;
+        case 12: return launch_fx64<12>(a, *t64, num_sms, s), 1;
+        case 16: return launch_fx64<16>(a, *t64, num_sms, s), 1;
+        case 20: return launch_fx64<20>(a, *t64, num_sms, s), 1;
+        case 24: return launch_fx64<24>(a, *t64, num_sms, s), 1;
+        case 28: return launch_fx64<28>(a, *t64, num_sms, s), 1;
+        case 32: return launch_fx64<32>(a, *t64, num_sms, s), 1;
         }
-    } else if (!use_register_kernel(a) && prec == ARE_FP32_KAHAN) {
-        switch (jp) {
-        case 8: return launch_staged_fx<8, ARE_FP32_KAHAN>(a, *t32, num_sms, s), 1;
-        case 16: return launch_staged_fx<16, ARE_FP32_KAHAN>(a, *t32, num_sms, s), 1;
-        case 32: return launch_staged_fx<32, ARE_FP32_KAHAN>(a, *t32, num_sms, s), 1;
-        }
-    } else if (!use_register_kernel(a) && prec == ARE_FP32_FP64AGG) {
-        switch (jp) {
-        case 8: return launch_staged_fx<8, ARE_FP32_FP64AGG>(a, *t32, num_sms, s), 1;
-        case 16: return launch_staged_fx<16, ARE_FP32_FP64AGG>(a, *t32, num_sms, s), 1;
-        case 32: return launch_staged_fx<32, ARE_FP32_FP64AGG>(a, *t32, num_sms, s), 1;
-        }
-    } else if (prec == ARE_FP32_KAHAN) {
-        switch (jp) {
-        case 8: return launch_fx<float, 8, ARE_FP32_KAHAN>(a, *t32, num_sms, s), 1;
-        case 16: return launch_fx<float, 16, ARE_FP32_KAHAN>(a, *t32, num_sms, s), 1;
-        case 32: return launch_fx<float, 32, ARE_FP32_KAHAN>(a, *t32, num_sms, s), 1;
-        }
-    } else if (prec == ARE_FP32_FP64AGG) {
-        switch (jp) {
-        case 8: return launch_fx<float, 8, ARE_FP32_FP64AGG>(a, *t32, num_sms, s), 1;
-        case 16: return launch_fx<float, 16, ARE_FP32_FP64AGG>(a, *t32, num_sms, s), 1;
-        case 32: return launch_fx<float, 32, ARE_FP32_FP64AGG>(a, *t32, num_sms, s), 1;
-        }
+        throw Error{ARE_EINVAL, "no FP64 simulate kernel for table width " + std::to_string(jp)};
     }
-    throw Error{ARE_EINVAL, "no simulate kernel for this precision and table width"};
+    if (prec == ARE_FP32_KAHAN) return launch_fp32<ARE_FP32_KAHAN>(a, jp, *t32, num_sms, s);
+    if (prec == ARE_FP32_FP64AGG) return launch_fp32<ARE_FP32_FP64AGG>(a, jp, *t32, num_sms, s);
+    throw Error{ARE_EINVAL, "unknown precision"};
 }
 
 }  // namespace are

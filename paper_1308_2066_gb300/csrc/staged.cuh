@@ -3,20 +3,15 @@
 // per row).  Instantiated by staged64.cu (FP64 tables) and staged_occ.cu
 // (per-occurrence outputs).
 //
-// FP64 tables: GB300 issues an FP64 add at about 1/66 of the FP32 rate and a
-// warp with one active lane costs as much as a full one, so the FP64 work is
-// compacted across the warp.  A table entry is e = x - D, the loss's excess
-// over the ELT's deductible (formed in FP64 when the table is built).  Each
-// lane marks its event's columns with e > 0 (an integer compare of the bit
-// pattern); the marked (row, column) pairs of the 32 events go to a shared
-// list and the warp applies min(e, Lim) * share to 32 of them per FP64
-// instruction, in place.  (With every share 1 the term min(e, Lim) needs no
-// FP64 instruction, and each lane clamps its own columns instead.)  Each
-// lane then sums its event's marked columns in column order: the first is
-// taken as is, so an FP64 add is issued only when some event has two or
-// more.  Columns with e <= 0 give exactly 0 and adding
-// an exact 0 changes nothing, so the event loss is the sum over ELTs of step
-// 2 in layer order, as the paper's loop forms it.
+// A table entry is the event's financial term in one ELT (formed in FP64 as
+// the table is built).  FP64 tables: GB300 issues an FP64 add at about 1/66
+// of the FP32 rate and a warp with one active lane costs as much as a full
+// one, so each lane marks its event's non-zero columns (an integer test of
+// the bit pattern) and adds them in column order: the first is taken as is,
+// so an FP64 add is issued only when some event of the warp has two or more.
+// Columns with a zero term add an exact 0, which changes nothing, so the
+// event loss is the sum over ELTs of step 2 in layer order, as the paper's
+// loop forms it.
 //
 // Per-occurrence outputs (step 4 of the Basic Algorithm, before its final sum): a
 // warp-shuffle inclusive scan of the batch's occurrence losses plus the
@@ -52,12 +47,6 @@ __device__ __forceinline__ double vsub(double a, double b)
 {
     double r;
     asm volatile("sub.rn.f64 %0, %1, %2;" : "=d"(r) : "d"(a), "d"(b));
-    return r;
-}
-__device__ __forceinline__ double vmul(double a, double b)
-{
-    double r;
-    asm volatile("mul.rn.f64 %0, %1, %2;" : "=d"(r) : "d"(a), "d"(b));
     return r;
 }
 
@@ -182,97 +171,39 @@ __device__ __forceinline__ Batch next_batch(const SimArgs &a, Cursor &c, int64_t
 template <typename T, int JP>
 constexpr int smem_bytes()
 {
-    // per warp: two row buffers, and for FP64 the compaction list; per block:
-    // the FP64 terms
-    return kWarps * (2 * 32 * JP * (int)sizeof(T) + (sizeof(T) == 8 ? 2 * 32 * JP : 0)) +
-           (sizeof(T) == 8 ? 3 * kMaxElts * 8 : 0);
+    return kWarps * 2 * 32 * JP * (int)sizeof(T);   // per warp: two row buffers
 }
 
 template <typename T>
 using TermsOf = typename std::conditional<sizeof(T) == 4, TermsF32, TermsF64>::type;
 
-// Step 2 for the lane's event: the event loss over the layer's ELTs.
+// Step 2 for the lane's event: the sum over the layer's ELTs of the terms.
 template <int JP>
-__device__ __forceinline__ float event_loss(float4 *buf, int lane, const TermsF32 &tm, bool any_share,
-                                            uint16_t *, const double *)
+__device__ __forceinline__ float event_loss(float4 *buf, int lane)
 {
     constexpr int CH = JP / 4;
-    float4 v[CH];
-#pragma unroll
-    for (int c = 0; c < CH; ++c) v[c] = buf[lane * CH + chunk_slot<CH>(c, lane)];
     float g = 0.f;
 #pragma unroll
-    for (int c = 0; c < CH; ++c)
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            const int j = c * 4 + e;
-            const float x = e == 0 ? v[c].x : e == 1 ? v[c].y : e == 2 ? v[c].z : v[c].w;
-            float n = fminf(fmaxf(x, 0.f), tm.lim[j]);
-            if (any_share) n = __fmul_rn(n, tm.share[j]);
-            g = __fadd_rn(g, n);
-        }
+    for (int c = 0; c < CH; ++c) {
+        const float4 v = buf[lane * CH + chunk_slot<CH>(c, lane)];
+        g = __fadd_rn(__fadd_rn(__fadd_rn(__fadd_rn(g, v.x), v.y), v.z), v.w);
+    }
     return g;
 }
 
-// FP64: compacted across the warp (see the file comment).  sterms holds
-// D[32], Lim bits[32], share[32] in shared memory.
+// FP64: the non-zero columns in column order, an FP64 add only where some
+// event of the warp has two or more (see the file comment).
 template <int JP>
-__device__ __forceinline__ double event_loss(float4 *buf, int lane, const TermsF64 &tm, bool any_share,
-                                             uint16_t *list, const double *sterms)
+__device__ __forceinline__ double event_loss64(float4 *buf, int lane)
 {
     constexpr int CH = JP / 2;
     uint32_t mask = 0;
 #pragma unroll
     for (int c = 0; c < CH; ++c) {
         const double2 v = reinterpret_cast<const double2 *>(buf)[lane * CH + chunk_slot<CH>(c, lane)];
-        if ((int64_t)bits(v.x) > 0) mask |= 1u << (2 * c);
-        if ((int64_t)bits(v.y) > 0) mask |= 1u << (2 * c + 1);
+        if (bits(v.x) != 0) mask |= 1u << (2 * c);
+        if (bits(v.y) != 0) mask |= 1u << (2 * c + 1);
     }
-    const double *sl = sterms + kMaxElts, *ss = sterms + 2 * kMaxElts;
-    if (!any_share) {
-        // no share factors: a marked entry's term min(e, Lim) is integer work
-        // on its bit pattern, so each lane takes its own columns in column
-        // order, with an FP64 add only where an event has two or more
-        double g = 0.0;
-        uint32_t m = mask;
-        if (m) {
-            const int j = __ffs(m) - 1;
-            g = clamp_bits(*elem<double, JP>(buf, lane, j), bits(sl[j]));
-            m &= m - 1;
-        }
-        while (__any_sync(kFull, m != 0)) {
-            if (m) {
-                const int j = __ffs(m) - 1;
-                g = vadd(g, clamp_bits(*elem<double, JP>(buf, lane, j), bits(sl[j])));
-                m &= m - 1;
-            }
-        }
-        return g;
-    }
-    // warp-wide list of the marked (row, column) pairs, lane by lane
-    const int cnt = __popc(mask);
-    int incl = cnt;
-#pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-        const int o = __shfl_up_sync(kFull, incl, off);
-        if (lane >= off) incl += o;
-    }
-    const int total = __shfl_sync(kFull, incl, 31);
-    int k = incl - cnt;
-    for (uint32_t m = mask; m; m &= m - 1) list[k++] = (uint16_t)((lane << 5) | (__ffs(m) - 1));
-    __syncwarp();
-    // 32 marked entries per FP64 instruction: e <- min(e, Lim) * share (the
-    // table holds e = x - D; a marked entry has e > 0)
-    for (int i = lane; i < total; i += 32) {
-        const int e = list[i], r = e >> 5, j = e & 31;
-        double *p = elem<double, JP>(buf, r, j);
-        double n = clamp_bits(*p, bits(sl[j]));
-        if (any_share) n = vmul(n, ss[j]);
-        *p = n;
-    }
-    __syncwarp();
-    // the event loss: marked columns in column order; FP64 adds only where
-    // an event has two or more
     double g = 0.0;
     uint32_t m = mask;
     if (m) {
@@ -342,21 +273,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_staged(const SimArgs a, const T
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     float4 *buf0 = stage + (size_t)w * 2 * 32 * CH;
     float4 *buf1 = buf0 + 32 * CH;
-    uint16_t *list = nullptr;
-    double *sterms = nullptr;
-    if constexpr (sizeof(T) == 8) {
-        uint16_t *lists = reinterpret_cast<uint16_t *>(stage + (size_t)kWarps * 2 * 32 * CH);
-        list = lists + (size_t)w * 32 * JP;          // room for every column of 32 events
-        sterms = reinterpret_cast<double *>(lists + (size_t)kWarps * 32 * JP);
-        for (int i = threadIdx.x; i < kMaxElts; i += blockDim.x) {
-            sterms[i] = tm.ded[i];
-            sterms[kMaxElts + i] = tm.lim[i];
-            sterms[2 * kMaxElts + i] = tm.share[i];
-        }
-        __syncthreads();
-    }
     const T *tab = static_cast<const T *>(a.table);
-    const bool any_share = a.any_share != 0;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t step = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const double empty_loss = clamp_d(0.0, a.agg_r, a.agg_l);
@@ -399,7 +316,9 @@ __global__ void __launch_bounds__(kWarps * 32) k_staged(const SimArgs a, const T
     const uint64_t agg_l_bits = bits(a.agg_l);
 
     auto compute = [&](const Batch &b, float4 *buf) {
-        const T g = event_loss<JP>(buf, lane, tm, any_share, list, sterms);
+        T g;
+        if constexpr (sizeof(T) == 8) g = event_loss64<JP>(buf, lane);
+        else g = event_loss<JP>(buf, lane);
         const T o = occ_clamp(g, tm);
         if constexpr (!OCC) {
             if constexpr (sizeof(T) == 8) sum.add(o);

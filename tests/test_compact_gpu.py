@@ -1,9 +1,13 @@
 """The compact layer table (are_set_table_layout ARE_LAYOUT_COMPACT): a row
 index over the catalog and rows only for the events present in some ELT.
 The staged kernel reads the same values in the same order through it, so the
-YLT must equal the direct layout's bit for bit; the FP32 results are also
-checked against the oracle."""
+YLT must equal the direct layout's on the same kernel bit for bit (the
+direct run is pinned to the staged kernel through the tuning file); the
+FP32 results are also checked against the oracle."""
+import json
 import math
+import os
+import tempfile
 
 import numpy as np
 import pytest
@@ -31,9 +35,27 @@ def ctx(are):
     are.are_destroy(c)
 
 
+def pin_staged(are, ctx, L, layer, p):
+    """Make the direct layout's analysis of this layer run on the staged
+    kernel, with the compact layout's events per lane (2 with Kahan sums,
+    1 with FP64 sums)."""
+    are.are_autotune(ctx, [L.layers[layer]], L.yet, p)
+    with tempfile.TemporaryDirectory() as d:
+        path = os.path.join(d, "t.jsonl")
+        are.are_tune_save(ctx, path)
+        entries = [json.loads(x) for x in open(path) if x.strip()]
+        key = [e for e in entries if e["key"].startswith(f"p{p}_") and e["key"].endswith("_single")]
+        assert key
+        e = dict(key[0], kernel=1, rows_in_flight=2 if p == 1 else 1)
+        with open(path, "w") as f:
+            f.write(json.dumps(e) + "\n")
+        are.are_tune_load(ctx, path)
+
+
 def both_layouts(are, ctx, L, layer, p):
     h = L.layers[layer]
     are.are_set_table_layout(ctx, h, are.ARE_LAYOUT_DIRECT)
+    pin_staged(are, ctx, L, layer, p)
     direct = L.simulate(layer, p)
     are.are_set_table_layout(ctx, h, are.ARE_LAYOUT_COMPACT)
     are.are_prepare(ctx, h, L.yet, p)

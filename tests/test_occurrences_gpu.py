@@ -148,7 +148,7 @@ def test_every_kernel_choice(are, ctx, orc, tmp_path, p):
         assert key
         kinds = [1, 2] + ([0] if p != 0 else [3])
         for kind in kinds:
-            for u in ((4, 8) if kind == 0 else (1, 2) if kind == 1 else (8,)):
+            for u in ((8,) if (p == 0 and kind == 2) else (1, 2)):
                 e = dict(key[0], kernel=kind, rows_in_flight=u, trials_per_item=3)
                 path.write_text(json.dumps(e) + "\n")
                 are.are_tune_load(ctx, str(path))

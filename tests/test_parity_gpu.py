@@ -232,10 +232,10 @@ def test_single_trial_single_event(are, ctx, orc, golden):
 @pytest.mark.parametrize("share", [1.0, 0.35])
 def test_term_arithmetic_bit_exact(are, ctx, share):
     """One event per trial, one ELT, neutral layer terms: each trial loss is
-    one financial term, which the header fixes exactly.  The loss's excess
-    over the deductible is formed in FP64 (fx * x, then - D) and rounded once
-    to the mode's type; the limit and share are applied in that type.  The
-    expected values below restate that arithmetic in numpy."""
+    one financial term, which the header fixes exactly.  The term
+    share * min(max(fx * x - D, 0), Lim) is formed in FP64 as the terms
+    define it and rounded once to the mode's type.  The expected values below
+    restate that arithmetic in numpy."""
     g = np.random.Generator(np.random.PCG64(2024))
     catalog, n = 4096, 3000
     ids = g.permutation(catalog)[:n].astype(np.int32)        # 1096 events absent
@@ -250,9 +250,7 @@ def test_term_arithmetic_bit_exact(are, ctx, share):
     present[ids] = True
     e64 = np.float64(fx) * x - ded                           # two FP64 roundings, as defined
     want64 = np.where(present, np.minimum(np.maximum(e64, 0.0), lim) * share, 0.0)
-    e32 = e64.astype(np.float32)
-    n32 = np.minimum(np.maximum(e32, np.float32(0)), np.float32(lim)) * np.float32(share)
-    want32 = np.where(present, n32.astype(np.float64), 0.0)
+    want32 = want64.astype(np.float32).astype(np.float64)    # one rounding to FP32
     L = Loaded(are, ctx, wl, timestamps=False)
     try:
         np.testing.assert_array_equal(L.simulate(0, 0), want64)
