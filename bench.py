@@ -13,6 +13,14 @@ prints one JSON line.  Under torchrun (N > 1) each rank simulates its own
 block of 1,000,000 trials (weak scaling); the ranks' YLTs are gathered once
 per step for the PML/TVaR of the whole YET.  ``--impl reference`` times the
 CPU oracle on a bounded sample of the same workload instead.
+
+At N = 1 the line also carries three bounded sub-records (skip them with
+--no-subrecords): ``portfolio`` (64 uneven layers over a ragged 200,000-trial
+YET, batched against plain), ``serving`` (2,000 pricing requests at 200 req/s,
+continuous batching against one request per launch, p50/p99) and
+``precision_stress`` (each precision mode's error against the FP64 oracle on
+the 1M-trial, 32-Pareto-ELT workload).  ``--workload portfolio|serving|
+precision_stress`` runs one of those studies alone, in full.
 """
 from __future__ import annotations
 
@@ -60,6 +68,8 @@ def parse():
     p.add_argument("--rates", default="50,200,1000")
     p.add_argument("--seconds-per-rate", type=float, default=8.0)
     p.add_argument("--no-tune", action="store_true")
+    p.add_argument("--no-subrecords", action="store_true",
+                   help="skip the portfolio, serving and precision-stress sub-records")
     return p.parse_args()
 
 
@@ -83,10 +93,11 @@ def hbm_peak():
 # Source files of each analysis kernel (its DRAM traffic from ncu goes stale
 # when one of them changes).
 KERNEL_SOURCES = {
+    "k_rows": ["simulate.cu", "rows.cuh", "are_internal.cuh"],
     "k_simulate_staged": ["simulate.cu", "are_internal.cuh"],
     "k_staged": ["staged.cuh", "staged64.cu", "are_internal.cuh"],
     "k_screen64": ["screen64.cu", "staged.cuh", "are_internal.cuh"],
-    "k_sim_items": ["sim_items.cu", "are_internal.cuh"],
+    "k_sim_items": ["sim_items.cu", "rows.cuh", "are_internal.cuh"],
     "k_simulate": ["simulate.cu", "are_internal.cuh"],
     "k_folded": ["folded.cu", "are_internal.cuh"],
 }
@@ -196,26 +207,27 @@ def items_bytes(wl) -> int:
 
 def kernel_key(prec: int, J: int, tuned=None) -> str:
     """Name of the kernel that runs the analysis stage for this precision
-    (the untuned default: the staged kernel, two events per lane for FP32 +
-    Kahan, one for FP32 + FP64 sum)."""
+    under the tuned choice (untuned: the register-rows kernel with two groups
+    of 32 events per batch for FP32, the staged kernel for FP64)."""
     if prec == "folded":
         return "k_folded<fixed,smem_bits>"
+    t = tuned or {}
     if prec == 0:
         jp = math.ceil(J / 4) * 4
-        kind = (tuned or {}).get("kernel", 1)
+        kind = t.get("kernel", 1)
         if kind == 3:
             return f"k_screen64<{8 if J <= 8 else 16 if J <= 16 else 32},fixed>"
         if kind == 1:
             return f"k_staged<double,{jp},fixed,ylt>"
-        return f"k_simulate<double,{jp},0,fixed>"
+        return f"k_simulate<{jp},fixed>"
     jp = 8 if J <= 8 else 16 if J <= 16 else 32
-    kind = (tuned or {}).get("kernel", 1)
+    kind = t.get("kernel", 2)
+    u = t.get("rows_in_flight", 2)
     if kind == 0:
-        return f"k_sim_items<{jp},{tuned.get('rows_in_flight')},{prec},fixed>"
+        return f"k_sim_items<{jp},{u},{prec},fixed>"
     if kind == 2:
-        return f"k_simulate<float,{jp},{prec},fixed>"
-    epl = (tuned or {}).get("rows_in_flight", 2 if prec == 1 else 1)
-    return f"k_simulate_staged<{jp},{prec},fixed,epl{2 if epl == 2 else 1}>"
+        return f"k_rows<{jp},{u},{prec},fixed>"
+    return f"k_simulate_staged<{jp},{prec},fixed,epl{2 if u == 2 else 1}>"
 
 
 def row_bytes(J: int, prec, tuned=None) -> int:
@@ -342,32 +354,47 @@ def max_over_ranks(x: float, world: int, torch) -> float:
     return float(t.item())
 
 
+SHAPE_NAMES = {0: "16-byte loads, lane reads its row's id",
+               1: "32-byte loads, ids shuffled from one coalesced read per 32 events",
+               2: "cp.async rows staged in shared memory"}
+
+
 def roofline(n_events, n_trials, J, prec, sim_ms, tuned=None, ceiling=None):
-    """Memory roofline of the analysis kernel: YET bytes plus table-row
-    sectors over the measured HBM copy bandwidth; beside it the fraction of
-    the measured gather ceiling (the same id stream and row reads with no
-    arithmetic), the bound that the L2-resident row reads actually set."""
-    peak, src = hbm_peak()
+    """Roofline of the analysis kernel.  Its table rows are gathered from the
+    L2-resident table, so the bound that applies is the gather ceiling: the
+    same id stream and row reads with no arithmetic, measured live in this
+    run over every launch shape of are_gather_ceiling.  achieved and peak are
+    the algorithmic bytes (4 B id + the row in whole 32-B sectors per event,
+    8 B per trial) over the kernel's time and over the ceiling's time, so
+    frac = the kernel's rows/s over the ceiling's.  hbm_formula_frac puts the
+    same bytes over the measured HBM copy bandwidth (above 1: the rows are
+    not HBM traffic); dram_frac is the ncu-measured DRAM traffic of one
+    launch over the kernel's time, over that bandwidth."""
+    hbm, src = hbm_peak()
     elem = 8 if prec == 0 else 4
     bytes_ = algorithmic_bytes(n_events, n_trials, J, elem)
-    achieved = bytes_ / (sim_ms * 1e-3) / 1e9
-    traffic = ncu_traffic(kernel_key(prec, J, tuned))
-    out = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-           "frac": round(achieved / peak, 4), "traffic": traffic,
-           "kernel": kernel_key(prec, J, tuned), "algorithmic_bytes_per_launch": bytes_,
-           "peak_source": f"{src} HBM copy bandwidth",
-           "note": ("algorithmic bytes = per event 4 B id + the event's table row in whole "
-                    "32-B sectors, + 8 B per trial; the rows are gathered from the L2-resident "
-                    "table, so frac can exceed 1: l2_gather gives the fraction of the "
-                    "measured gather ceiling")}
-    if ceiling:
-        rate = n_events / (sim_ms * 1e-3)
-        out["l2_gather"] = {"row_bytes": row_bytes(J, prec, tuned),
-                            "achieved_rows_per_s": round(rate, 1),
-                            "ceiling_rows_per_s": round(ceiling, 1),
-                            "frac": round(rate / ceiling, 4),
-                            "ceiling_source": "measured live: are_gather_ceiling on this YET"}
-    return out
+    secs = sim_ms * 1e-3
+    achieved = bytes_ / secs / 1e9
+    key = kernel_key(prec, J, tuned)
+    traffic = ncu_traffic(key)
+    best, shapes = ceiling
+    rate = n_events / secs
+    top = max(shapes, key=lambda x: x[3])
+    return {"bound": "l2_gather", "achieved": round(achieved, 1),
+            "peak": round(bytes_ / (n_events / best) / 1e9, 1), "unit": "GB/s",
+            "frac": round(rate / best, 4), "traffic": traffic, "kernel": key,
+            "algorithmic_bytes_per_launch": bytes_,
+            "peak_source": ("measured live in this run: best of %d launch shapes of the gather "
+                            "ceiling (ids + table rows, no arithmetic) on this YET" % len(shapes)),
+            "hbm_formula_frac": round(achieved / hbm, 4),
+            "dram_frac": (round(traffic / secs / 1e9 / hbm, 4) if traffic else None),
+            "hbm_peak": hbm, "hbm_peak_source": f"{src} HBM copy bandwidth (MEASURED_PEAKS.json)",
+            "l2_gather": {"row_bytes": row_bytes(J, prec, tuned),
+                          "achieved_rows_per_s": round(rate, 1),
+                          "ceiling_rows_per_s": round(best, 1),
+                          "ceiling_shape": {"kind": SHAPE_NAMES[top[0]], "in_flight": top[1],
+                                            "blocks_per_sm": top[2]},
+                          "shapes_timed": len(shapes)}}
 
 
 def folded_roofline(n_events, n_trials, sim_ms):
@@ -489,6 +516,151 @@ def run_e2e(are, torch, ctx, wl, prec, steps, warmup, world):
 # portfolio batching: 64 uneven layers over one ragged YET
 # ---------------------------------------------------------------------------
 
+def portfolio_kernel_name(tuned, prec) -> str:
+    """What runs the batched analysis under the tuned choice."""
+    kind = (tuned or {}).get("kernel", 2)
+    u = (tuned or {}).get("rows_in_flight", 2)
+    if kind == 0:
+        return (f"k_sim_items<jp,{u},{prec},ragged>: one persistent launch per table width, "
+                f"{(tuned or {}).get('trials_per_item')} trials per work item")
+    if kind == 2:
+        return f"k_rows<jp,{u},{prec},ragged>: one launch per layer, back to back in the graph"
+    return f"k_simulate_staged<jp,{prec},ragged,epl{u}>: one launch per layer, back to back in the graph"
+
+
+def portfolio_record(are, torch, prec, steps, warmup, tune=True, variants=True, rank=0, world=1,
+                     local_rank=0, n_trials=200_000):
+    """Portfolio of 64 uneven layers (1..32 ELTs from a pool of 256) over a
+    ragged 200,000-trial YET: the batched form (every table rebuilt, one
+    graph-replayed analysis of all layers, one batched PML/TVaR) against the
+    plain form (per layer: repack, are_simulate, are_risk_measures).  Under
+    torchrun each rank takes whole layers (no exchange in the step)."""
+    wl = W.portfolio(n_trials=min(n_trials, 200_000))
+    all_layers = wl.layers
+    from paper_1308_2066_gb300.sharding import layer_shard
+    mine = layer_shard([len(L.elts) for L in all_layers], world, rank)
+    wl.layers = [all_layers[i] for i in mine]
+    y = wl.yet
+    ctx = are.are_create(local_rank)
+    try:
+        ids = torch.from_numpy(y.ids).cuda()
+        off = torch.from_numpy(y.offsets).cuda()
+        yet = are.are_load_yet(ctx, y.catalog, y.n_trials, off, 0, ids)
+        del ids, off
+        elts = [are.are_load_elt(ctx, e.ids, e.losses, e.fx, e.ded, e.lim, e.share) for e in wl.elts]
+        layers = [are.are_define_layer(ctx, [elts[m] for m in L.elts], L.occ_r, L.occ_l, L.agg_r,
+                                       L.agg_l) for L in wl.layers]
+        n = y.n_trials
+        stream = torch.cuda.Stream()
+        outs = [torch.empty(n, dtype=torch.float64, device="cuda") for _ in layers]
+        tuned = are.are_autotune(ctx, layers, yet, prec, stream) if tune else None
+        lookups = sum(y.n_events * len(L.elts) for L in all_layers)   # the whole portfolio
+
+        def batched():
+            for h in layers:
+                are.are_prepare(ctx, h, yet, prec, stream)
+            are.are_simulate_portfolio(ctx, layers, yet, 0, n, prec, outs, stream)
+            return are.are_risk_measures_batch(ctx, outs, n, RPS, LEVELS, stream)
+
+        def plain():
+            for h, o in zip(layers, outs):
+                are.are_prepare(ctx, h, yet, prec, stream)
+                are.are_simulate(ctx, h, yet, 0, n, prec, o, stream)
+                are.are_risk_measures(ctx, o, n, RPS, LEVELS, stream)
+
+        def timed(fn, k):
+            for _ in range(warmup):
+                fn()
+            torch.cuda.synchronize()
+            barrier(world)
+            l0 = are.are_launch_count(ctx)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            with ClockSampler(local_rank) as clk:
+                a.record(stream)
+                for _ in range(k):
+                    fn()
+                b.record(stream)
+                b.synchronize()
+            barrier(world)
+            ms = max_over_ranks(a.elapsed_time(b) / k, world, torch)
+            return ms, are.are_launch_count(ctx) - l0, clk.summary()
+
+        # the analysis alone (one graph replay of every layer), for the roofline
+        sim = []
+        for _ in range(warmup + steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            are.are_simulate_portfolio(ctx, layers, yet, 0, n, prec, outs, stream)
+            e1.record(stream)
+            sim.append((e0, e1))
+        torch.cuda.synchronize()
+        sim_ms = max_over_ranks(float(np.mean([a.elapsed_time(b) for a, b in sim[warmup:]])),
+                                world, torch)
+        ms_b, launches, clocks = timed(batched, steps)
+        ms_p, launches_p, _ = timed(plain, max(1, steps // 2))
+        folded = None
+        if variants:
+            def folded_fn():   # each layer's folded table, one exact pass per layer
+                for h, o in zip(layers, outs):
+                    are.are_prepare_folded(ctx, h, yet, stream)
+                    are.are_simulate_folded(ctx, h, yet, 0, n, o, stream)
+                return are.are_risk_measures_batch(ctx, outs, n, RPS, LEVELS, stream)
+            ms_f, launches_f, _ = timed(folded_fn, max(1, steps // 2))
+            folded = {"ms_per_step": round(ms_f, 4),
+                      "value": round(lookups / (ms_f * 1e-3) / 1e9, 3),
+                      "value_unit": "G event-ELT lookups/s equivalent", "gpu_launches": launches_f,
+                      "what": ("per layer: FP64 folded table (one lookup per occurrence) and one "
+                               "exact trial pass; batched PML/TVaR")}
+        pml, tv = batched()
+        per_layer = {i: ([float(x) for x in pml[k]], [float(x) for x in tv[k]])
+                     for k, i in enumerate(mine)}
+        if world > 1:
+            from paper_1308_2066_gb300.sharding import gather_results
+            per_layer = dict(enumerate(gather_results(per_layer, len(all_layers))))
+        # the gather ceiling of every row size on this YET: the time it would
+        # take for every layer's rows, against the analysis' time
+        ceil = {}
+        t_ceil = 0.0
+        for L in wl.layers:
+            rb = row_bytes(len(L.elts), prec, tuned)
+            if rb not in ceil:
+                ceil[rb] = are.are_gather_ceiling(ctx, yet, rb, 0, n, reps=2)
+            t_ceil += y.n_events / ceil[rb]
+        hbm, src = hbm_peak()
+        mine_bytes = sum(algorithmic_bytes(y.n_events, y.n_trials, len(L.elts), 4 if prec else 8)
+                         for L in wl.layers)
+        roof = {"bound": "l2_gather", "achieved": round(mine_bytes / (sim_ms * 1e-3) / 1e9, 1),
+                "peak": round(mine_bytes / t_ceil / 1e9, 1), "unit": "GB/s",
+                "frac": round(t_ceil / (sim_ms * 1e-3), 4), "traffic": None,
+                "kernel": portfolio_kernel_name(tuned, prec),
+                "algorithmic_bytes_per_launch": mine_bytes, "sim_ms": round(sim_ms, 4),
+                "peak_source": "measured live: the gather ceiling of each layer's row size on this YET",
+                "hbm_formula_frac": round(mine_bytes / (sim_ms * 1e-3) / 1e9 / hbm, 4)}
+        return {
+            "metric": METRIC, "value": round(lookups / (ms_b * 1e-3) / 1e9, 3), "unit": UNIT,
+            "n_gpus": world, "steps": steps, "warmup": warmup, "ms_per_step": round(ms_b, 4),
+            "higher_is_better": True, "scaling": "strong" if world > 1 else "weak",
+            "vs_baseline": None, "dtype": DTYPES[prec],
+            "data": "synthetic: seeded ragged Poisson(1000) YET, lognormal ELT pool",
+            "config": {"workload": wl.name, "trials": n, "events": y.n_events,
+                       "layers": len(all_layers), "elts_per_layer": [len(L.elts) for L in all_layers],
+                       "precision": PRECISION_NAMES[prec],
+                       "step": "repack every table + one graph-replayed analysis of every layer + "
+                               "batched PML/TVaR",
+                       "l2": "inputs larger than L2 (0.8 GB YET streamed once per layer)",
+                       "parallelism": f"whole layers per GPU x{world} (greedy by ELT count)"},
+            "roofline": roof,
+            "plain": {"ms_per_step": round(ms_p, 4), "value": round(lookups / (ms_p * 1e-3) / 1e9, 3),
+                      "gpu_launches": launches_p,
+                      "how": "64 x (repack + are_simulate + are_risk_measures)"},
+            "speedup_vs_plain": round(ms_p / ms_b, 3),
+            "folded_variant": folded, "tuned": tuned, "kernel": portfolio_kernel_name(tuned, prec),
+            "gpu_launches": launches, "clocks": clocks,
+            "pml_layer0": per_layer[0][0], "tvar_layer0": per_layer[0][1]}
+    finally:
+        are.are_destroy(ctx)
+
+
 def run_portfolio(args):
     import torch
     import paper_1308_2066_gb300 as are
@@ -498,119 +670,9 @@ def run_portfolio(args):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     prec = {v: k for k, v in PRECISION_NAMES.items()}[args.precision]
-    wl = W.portfolio(n_trials=min(args.trials, 200_000))
-    all_layers = wl.layers
-    # under torchrun each rank analyses whole layers (no exchange in the step)
-    from paper_1308_2066_gb300.sharding import layer_shard
-    mine = layer_shard([len(L.elts) for L in all_layers], world, rank)
-    wl.layers = [all_layers[i] for i in mine]
-    y = wl.yet
-    ctx = are.are_create(local_rank)
-    ids = torch.from_numpy(y.ids).cuda()
-    off = torch.from_numpy(y.offsets).cuda()
-    yet = are.are_load_yet(ctx, y.catalog, y.n_trials, off, 0, ids)
-    del ids, off
-    elts = [are.are_load_elt(ctx, e.ids, e.losses, e.fx, e.ded, e.lim, e.share) for e in wl.elts]
-    layers = [are.are_define_layer(ctx, [elts[m] for m in L.elts], L.occ_r, L.occ_l, L.agg_r,
-                                   L.agg_l) for L in wl.layers]
-    n = y.n_trials
-    stream = torch.cuda.Stream()
-    outs = [torch.empty(n, dtype=torch.float64, device="cuda") for _ in layers]
-    tuned = None if args.no_tune else are.are_autotune(ctx, layers, yet, prec, stream)
-    lookups = sum(y.n_events * len(L.elts) for L in all_layers)   # the whole portfolio
-
-    def batched():
-        for h in layers:
-            are.are_prepare(ctx, h, yet, prec, stream)
-        are.are_simulate_portfolio(ctx, layers, yet, 0, n, prec, outs, stream)
-        return are.are_risk_measures_batch(ctx, outs, n, RPS, LEVELS, stream)
-
-    def plain():
-        for h, o in zip(layers, outs):
-            are.are_prepare(ctx, h, yet, prec, stream)
-            are.are_simulate(ctx, h, yet, 0, n, prec, o, stream)
-            are.are_risk_measures(ctx, o, n, RPS, LEVELS, stream)
-
-    def timed(fn, steps):
-        for _ in range(args.warmup):
-            fn()
-        torch.cuda.synchronize()
-        barrier(world)
-        l0 = are.are_launch_count(ctx)
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        with ClockSampler(local_rank) as clk:
-            a.record(stream)
-            for _ in range(steps):
-                fn()
-            b.record(stream)
-            b.synchronize()
-        barrier(world)
-        ms = max_over_ranks(a.elapsed_time(b) / steps, world, torch)
-        return ms, are.are_launch_count(ctx) - l0, clk.summary()
-
-    # the persistent kernel alone (for the roofline)
-    sim = []
-    for _ in range(args.warmup + args.steps):
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        are.are_simulate_portfolio(ctx, layers, yet, 0, n, prec, outs, stream)
-        e1.record(stream)
-        sim.append((e0, e1))
-    torch.cuda.synchronize()
-    sim_ms = max_over_ranks(float(np.mean([a.elapsed_time(b) for a, b in sim[args.warmup:]])),
-                            world, torch)
-    ms_b, launches, clocks = timed(batched, args.steps)
-    ms_p, launches_p, _ = timed(plain, max(1, args.steps // 2))
-
-    def folded():   # variant: each layer's folded table, one exact pass per layer
-        for h, o in zip(layers, outs):
-            are.are_prepare_folded(ctx, h, yet, stream)
-            are.are_simulate_folded(ctx, h, yet, 0, n, o, stream)
-        return are.are_risk_measures_batch(ctx, outs, n, RPS, LEVELS, stream)
-
-    ms_f, launches_f, _ = timed(folded, max(1, args.steps // 2))
-    pml, tv = batched()
-    per_layer = {i: ([float(x) for x in pml[k]], [float(x) for x in tv[k]])
-                 for k, i in enumerate(mine)}
-    if world > 1:
-        from paper_1308_2066_gb300.sharding import gather_results
-        per_layer = dict(enumerate(gather_results(per_layer, len(all_layers))))
-    peak, src = hbm_peak()
-    wl.layers = all_layers
-    bytes_ = items_bytes(wl)
-    line = {
-        "metric": METRIC, "value": round(lookups / (ms_b * 1e-3) / 1e9, 3), "unit": UNIT,
-        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": round(ms_b, 4), "higher_is_better": True,
-        "scaling": "strong" if world > 1 else "weak",
-        "vs_baseline": None, "dtype": DTYPES[prec],
-        "data": "synthetic: seeded ragged Poisson(1000) YET, lognormal ELT pool",
-        "config": {"workload": wl.name, "trials": n, "events": y.n_events, "layers": len(layers),
-                   "elts_per_layer": [len(L.elts) for L in wl.layers],
-                   "precision": PRECISION_NAMES[prec],
-                   "step": "repack 64 tables + one graph-replayed persistent launch + batched PML/TVaR",
-                   "l2": "inputs larger than L2 (0.8 GB YET streamed once per layer)"},
-        "roofline": {"bound": "hbm", "achieved": round(bytes_ / (sim_ms * 1e-3) / 1e9, 1),
-                     "peak": peak, "unit": "GB/s",
-                     "frac": round(bytes_ / (sim_ms * 1e-3) / 1e9 / peak, 4), "traffic": None,
-                     "kernel": "k_sim_items (all layers)", "algorithmic_bytes_per_launch": bytes_,
-                     "peak_source": f"{src} HBM copy bandwidth", "sim_ms": round(sim_ms, 4)},
-        "plain": {"ms_per_step": round(ms_p, 4),
-                  "value": round(lookups / (ms_p * 1e-3) / 1e9, 3),
-                  "gpu_launches": launches_p,
-                  "how": "64 x (repack + are_simulate + are_risk_measures)"},
-        "speedup_vs_plain": round(ms_p / ms_b, 3),
-        "folded_variant": {"ms_per_step": round(ms_f, 4),
-                           "value": round(lookups / (ms_f * 1e-3) / 1e9, 3),
-                           "value_unit": "G event-ELT lookups/s equivalent",
-                           "gpu_launches": launches_f,
-                           "what": ("per layer: FP64 folded table (one lookup per occurrence) and "
-                                    "one exact trial pass; batched PML/TVaR")},
-        "tuned": tuned, "gpu_launches": launches, "clocks": clocks,
-        "pml_layer0": per_layer[0][0], "tvar_layer0": per_layer[0][1],
-        "parallelism": f"whole layers per GPU x{world} (greedy by ELT count)",
-    }
-    are.are_destroy(ctx)
+    line = portfolio_record(are, torch, prec, args.steps, args.warmup, tune=not args.no_tune,
+                            variants=not args.no_variants, rank=rank, world=world,
+                            local_rank=local_rank, n_trials=args.trials)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -622,91 +684,107 @@ def run_portfolio(args):
 # precision modes: 32 Pareto ELTs, long ragged trials, errors vs the oracle
 # ---------------------------------------------------------------------------
 
-def run_precision_stress(args):
-    import torch
+def precision_record(are, torch, steps, warmup, tune=True, compact=True, n_trials=1_000_000,
+                     n_sample=2000):
+    """Each precision mode on the precision-stress workload (1M ragged trials
+    of Poisson(1000) <= 3000 events over a 2M-event catalog, 32 Pareto(1.3)
+    ELTs, neutral terms: whole-trial sums reach the YLT): analysis time, and
+    the error against the FP64 oracle of the YLT on sampled trials and of
+    PML/TVaR through the tail trials."""
     import oracle
-    import paper_1308_2066_gb300 as are
-    torch.cuda.set_device(0)
-    wl = W.precision_stress(n_trials=min(args.trials, 1_000_000))
+    wl = W.precision_stress(n_trials=min(n_trials, 1_000_000))
     y = wl.yet
     ctx = are.are_create(0)
-    ids = torch.from_numpy(y.ids).cuda()
-    off = torch.from_numpy(y.offsets).cuda()
-    yet = are.are_load_yet(ctx, y.catalog, y.n_trials, off, 0, ids)
-    del ids, off
-    elts = [are.are_load_elt(ctx, e.ids, e.losses, e.fx, e.ded, e.lim, e.share) for e in wl.elts]
-    L = wl.layers[0]
-    layer = are.are_define_layer(ctx, elts, L.occ_r, L.occ_l, L.agg_r, L.agg_l)
-    n = y.n_trials
-    stream = torch.cuda.Stream()
-    out = torch.empty(n, dtype=torch.float64, device="cuda")
-    sample = np.sort(np.random.default_rng(7).choice(n, 2000, replace=False))
-    ref = oracle.simulate_layer(wl, trials=sample)
-    rows = {}
-    for p in (0, 2, 1):
-        tuned = are.are_autotune(ctx, [layer], yet, p, stream) if not args.no_tune else None
-        evs = []
-        for _ in range(args.warmup + args.steps):
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            are.are_simulate(ctx, layer, yet, 0, n, p, out, stream)
-            e1.record(stream)
-            evs.append((e0, e1))
-        torch.cuda.synchronize()
-        ms = float(np.mean([a.elapsed_time(b) for a, b in evs[args.warmup:]]))
-        got = out.cpu().numpy()
-        if p == 1:
-            kahan_ylt = got.copy()
-        d = np.abs(got[sample] - ref.ylt)
-        rel = d / np.maximum(np.abs(ref.ylt), 1e-300)
-        pml, tv = are.are_risk_measures(ctx, out, n, RPS, LEVELS, stream)
-        # PML/TVaR of the oracle over the GPU's tail trials (the top 1.25 m)
-        m_max = oracle.rank_for_level(n, LEVELS[0])
-        cand = np.argsort(-got)[: m_max + m_max // 4]
-        rc = oracle.simulate_layer(wl, trials=np.sort(cand))
-        full = np.zeros(n)
-        full[np.sort(cand)] = rc.ylt
-        rp, rt = oracle.risk_measures(full, RPS, LEVELS)
-        rows[PRECISION_NAMES[p]] = {
-            "sim_ms": round(ms, 4), "tuned": tuned,
-            "value": round(y.n_events * len(L.elts) / (ms * 1e-3) / 1e9, 3),
-            "ylt_rel_err_max": float(rel.max()), "ylt_rel_err_median": float(np.median(rel)),
-            "ylt_err_over_gross_max": float((d / ref.gross).max()),
-            "pml": [float(x) for x in pml], "pml_oracle": [float(x) for x in rp],
-            "pml_rel_err": [float(abs(a - b) / b) for a, b in zip(pml, rp)],
-            "tvar": [float(x) for x in tv], "tvar_oracle": [float(x) for x in rt],
-            "tvar_rel_err": [float(abs(a - b) / b) for a, b in zip(tv, rt)]}
-    # the compact table (row index + rows of the events in some ELT): a variant
-    # that does not read the rows of events absent from every ELT
-    are.are_set_table_layout(ctx, layer, are.ARE_LAYOUT_COMPACT)
-    are.are_prepare(ctx, layer, yet, 1, stream)
-    evs = []
-    for _ in range(args.warmup + args.steps):
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        are.are_simulate(ctx, layer, yet, 0, n, 1, out, stream)
-        e1.record(stream)
-        evs.append((e0, e1))
-    torch.cuda.synchronize()
-    ms_c = float(np.mean([a.elapsed_time(b) for a, b in evs[args.warmup:]]))
-    got = out.cpu().numpy()
-    rows["fp32_kahan_compact_variant"] = {
-        "sim_ms": round(ms_c, 4),
-        "value": round(y.n_events * len(L.elts) / (ms_c * 1e-3) / 1e9, 3),
-        "same_ylt_as_direct_fp32_kahan": bool(np.array_equal(got, kahan_ylt)),
-        "what": "compact table: row index over the 2M catalog + rows of the events present "
-                "in some ELT; rows of absent events are not read"}
-    are.are_set_table_layout(ctx, layer, are.ARE_LAYOUT_DIRECT)
-    head = rows[args.precision]
+    try:
+        ids = torch.from_numpy(y.ids).cuda()
+        off = torch.from_numpy(y.offsets).cuda()
+        yet = are.are_load_yet(ctx, y.catalog, y.n_trials, off, 0, ids)
+        del ids, off
+        elts = [are.are_load_elt(ctx, e.ids, e.losses, e.fx, e.ded, e.lim, e.share) for e in wl.elts]
+        L = wl.layers[0]
+        layer = are.are_define_layer(ctx, elts, L.occ_r, L.occ_l, L.agg_r, L.agg_l)
+        n = y.n_trials
+        stream = torch.cuda.Stream()
+        out = torch.empty(n, dtype=torch.float64, device="cuda")
+        sample = np.sort(np.random.default_rng(7).choice(n, min(n, n_sample), replace=False))
+        ref = oracle.simulate_layer(wl, trials=sample)
+        rows = {}
+        kahan_ylt = None
+
+        def timed(p):
+            evs = []
+            for _ in range(warmup + steps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                are.are_simulate(ctx, layer, yet, 0, n, p, out, stream)
+                e1.record(stream)
+                evs.append((e0, e1))
+            torch.cuda.synchronize()
+            return float(np.mean([a.elapsed_time(b) for a, b in evs[warmup:]]))
+
+        for p in (0, 2, 1):
+            tuned = are.are_autotune(ctx, [layer], yet, p, stream) if tune else None
+            ms = timed(p)
+            got = out.cpu().numpy()
+            if p == 1:
+                kahan_ylt = got.copy()
+            d = np.abs(got[sample] - ref.ylt)
+            rel = d / np.maximum(np.abs(ref.ylt), 1e-300)
+            pml, tv = are.are_risk_measures(ctx, out, n, RPS, LEVELS, stream)
+            # PML/TVaR of the oracle over the GPU's tail trials (the top 1.25 m)
+            m_max = oracle.rank_for_level(n, LEVELS[0])
+            cand = np.sort(np.argsort(-got)[: m_max + m_max // 4])
+            rc = oracle.simulate_layer(wl, trials=cand)
+            full = np.zeros(n)
+            full[cand] = rc.ylt
+            rp, rt = oracle.risk_measures(full, RPS, LEVELS)
+            rows[PRECISION_NAMES[p]] = {
+                "sim_ms": round(ms, 4), "tuned": tuned, "kernel": kernel_key(p, len(L.elts), tuned),
+                "value": round(y.n_events * len(L.elts) / (ms * 1e-3) / 1e9, 3),
+                "ylt_rel_err_max": float(rel.max()), "ylt_rel_err_median": float(np.median(rel)),
+                "pml": [float(x) for x in pml], "pml_oracle": [float(x) for x in rp],
+                "pml_rel_err": [float(abs(a - b) / b) for a, b in zip(pml, rp)],
+                "tvar": [float(x) for x in tv], "tvar_oracle": [float(x) for x in rt],
+                "tvar_rel_err": [float(abs(a - b) / b) for a, b in zip(tv, rt)]}
+        if compact:
+            # the compact table (row index + rows of the events in some ELT): a
+            # variant that does not read the rows of events absent from every ELT
+            are.are_set_table_layout(ctx, layer, are.ARE_LAYOUT_COMPACT)
+            are.are_prepare(ctx, layer, yet, 1, stream)
+            ms_c = timed(1)
+            got = out.cpu().numpy()
+            rows["fp32_kahan_compact_variant"] = {
+                "sim_ms": round(ms_c, 4),
+                "value": round(y.n_events * len(L.elts) / (ms_c * 1e-3) / 1e9, 3),
+                "ylt_rel_err_max_vs_direct": float(np.max(np.abs(got - kahan_ylt) /
+                                                          np.maximum(np.abs(kahan_ylt), 1e-300))),
+                "what": "compact table on the staged kernel: row index over the 2M catalog + rows "
+                        "of the events present in some ELT; rows of absent events are not read"}
+            are.are_set_table_layout(ctx, layer, are.ARE_LAYOUT_DIRECT)
+        return {"workload": wl.name, "trials": n, "events": y.n_events, "elts": len(L.elts),
+                "sample_trials": int(sample.size),
+                "errors_against": "FP64 oracle: sampled trials one by one; PML/TVaR over the "
+                                  "oracle's losses of the GPU's top 1.25 m trials",
+                "precisions": rows}
+    finally:
+        are.are_destroy(ctx)
+
+
+def run_precision_stress(args):
+    import torch
+    import paper_1308_2066_gb300 as are
+    torch.cuda.set_device(0)
+    rec = precision_record(are, torch, args.steps, args.warmup, tune=not args.no_tune,
+                           n_trials=args.trials)
+    head = rec["precisions"][args.precision]
     line = {"metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["sim_ms"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": DTYPES[{v: k for k, v in PRECISION_NAMES.items()}[args.precision]],
             "data": "synthetic: ragged Poisson(1000)<=3000 YET over 2M events, 32 Pareto(1.3) ELTs",
-            "config": {"workload": wl.name, "trials": n, "events": y.n_events, "elts": len(L.elts),
-                       "sample_trials": int(sample.size)},
-            "precisions": rows}
-    are.are_destroy(ctx)
+            "config": {"workload": rec["workload"], "trials": rec["trials"], "events": rec["events"],
+                       "elts": rec["elts"], "sample_trials": rec["sample_trials"]},
+            "precisions": rec["precisions"]}
     print(json.dumps(line), flush=True)
 
 
@@ -758,45 +836,84 @@ def serve_stream(are, ctx, hs, reqs, one_at_a_time, prec, k, folded=False):
             "g_lookups_s": round(lookups / wall / 1e9, 2)}, out
 
 
+def serving_record(are, torch, prec, rates, seconds_per_rate, min_requests=200,
+                   max_requests=2000, folded=True, n_trials=1_000_000):
+    """Poisson streams of pricing requests (1..16 random ELTs of a pool of
+    256, fresh layer terms, 1e4..1e6 trials) over a resident 1M x 1000 YET:
+    p50/p99 latency and throughput with continuous batching against one
+    request per launch, on the same request stream."""
+    wl = W.serving_pool(n_trials=min(n_trials, 1_000_000))
+    y = wl.yet
+    ctx = are.are_create(0)
+    try:
+        ids = torch.from_numpy(y.ids).cuda()
+        hs = {"yet": are.are_load_yet(ctx, y.catalog, y.n_trials, None, y.k, ids)}
+        del ids
+        hs["elts"] = [are.are_load_elt(ctx, e.ids, e.losses, e.fx, e.ded, e.lim, e.share)
+                      for e in wl.elts]
+        pooled = np.concatenate([e.losses for e in wl.elts[:16]])
+        rows = {}
+        for i, rate in enumerate(rates):
+            n_req = int(min(max_requests, max(min_requests, rate * seconds_per_rate)))
+            reqs = W.pricing_requests(n_req, rate, pool=len(wl.elts), max_trials=y.n_trials,
+                                      stream=10 + i, pooled_losses=pooled)
+            l0 = are.are_launch_count(ctx)
+            batched, _ = serve_stream(are, ctx, hs, reqs, False, prec, y.k)
+            batched["gpu_launches"] = are.are_launch_count(ctx) - l0
+            single, _ = serve_stream(are, ctx, hs, reqs, True, prec, y.k)
+            row = {"continuous_batching": batched, "one_request_per_launch": single,
+                   "p99_batched_over_single": round(batched["p99_ms"] / single["p99_ms"], 4)}
+            if folded:
+                f, _ = serve_stream(are, ctx, hs, reqs, False, prec, y.k, folded=True)
+                f["what"] = ("variant: continuous batching on folded tables (FP64 occurrence loss "
+                             "per catalog event, exact trial sums, one lookup per occurrence)")
+                row["folded_continuous_batching_variant"] = f
+            rows[str(int(rate))] = row
+        return {"workload": wl.name, "request_trials": "log-uniform 1e4..1e6 (YET prefix)",
+                "request_elts": "1..16 of the pool", "measures": "PML 100/250, TVaR 99",
+                "precision": PRECISION_NAMES[prec], "rates": rows}
+    finally:
+        are.are_destroy(ctx)
+
+
 def run_serving(args):
     import torch
     import paper_1308_2066_gb300 as are
     torch.cuda.set_device(0)
     prec = {v: k for k, v in PRECISION_NAMES.items()}[args.precision]
-    wl = W.serving_pool(n_trials=min(args.trials, 1_000_000))
-    y = wl.yet
-    ctx = are.are_create(0)
-    ids = torch.from_numpy(y.ids).cuda()
-    hs = {"yet": are.are_load_yet(ctx, y.catalog, y.n_trials, None, y.k, ids)}
-    del ids
-    hs["elts"] = [are.are_load_elt(ctx, e.ids, e.losses, e.fx, e.ded, e.lim, e.share)
-                  for e in wl.elts]
-    pooled = np.concatenate([e.losses for e in wl.elts[:16]])
-    rows = {}
-    for i, rate in enumerate(float(x) for x in args.rates.split(",")):
-        n_req = int(min(2000, max(200, rate * args.seconds_per_rate)))
-        reqs = W.pricing_requests(n_req, rate, pool=len(wl.elts), max_trials=y.n_trials,
-                                  stream=10 + i, pooled_losses=pooled)
-        l0 = are.are_launch_count(ctx)
-        batched, _ = serve_stream(are, ctx, hs, reqs, False, prec, y.k)
-        batched["gpu_launches"] = are.are_launch_count(ctx) - l0
-        single, _ = serve_stream(are, ctx, hs, reqs, True, prec, y.k)
-        folded, _ = serve_stream(are, ctx, hs, reqs, False, prec, y.k, folded=True)
-        folded["what"] = ("variant: continuous batching on folded tables (FP64 occurrence loss per "
-                          "catalog event, exact trial sums, one lookup per occurrence)")
-        rows[str(int(rate))] = {"continuous_batching": batched, "one_request_per_launch": single,
-                                "folded_continuous_batching_variant": folded}
+    rates = [float(x) for x in args.rates.split(",")]
+    rec = serving_record(are, torch, prec, rates, args.seconds_per_rate, n_trials=args.trials)
+    rows = rec["rates"]
     head = rows.get("200", next(iter(rows.values())))["continuous_batching"]
     line = {"metric": "p99 pricing latency", "value": head["p99_ms"], "unit": "ms",
             "n_gpus": 1, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
             "dtype": DTYPES[prec],
             "data": "synthetic: resident 1M x 1000 YET, 256 lognormal ELTs, Poisson arrivals",
-            "config": {"workload": wl.name, "request_trials": "log-uniform 1e4..1e6 (YET prefix)",
-                       "request_elts": "1..16 of the pool", "measures": "PML 100/250, TVaR 99",
-                       "precision": PRECISION_NAMES[prec], "headline_rate_req_s": 200},
+            "config": {k: v for k, v in rec.items() if k != "rates"} | {"headline_rate_req_s": 200},
             "rates": rows}
-    are.are_destroy(ctx)
     print(json.dumps(line), flush=True)
+
+
+def subrecords(are, torch, args):
+    """The portfolio, serving and precision-stress studies, each bounded to
+    a few tens of seconds, for the default run's line."""
+    out = {}
+    prec = {v: k for k, v in PRECISION_NAMES.items()}[args.precision]
+    for name, fn in (
+            ("portfolio", lambda: portfolio_record(are, torch, prec, 5, 2, variants=False)),
+            ("serving", lambda: serving_record(are, torch, prec, [200.0], 10.0,
+                                               min_requests=2000, max_requests=2000,
+                                               folded=False)),
+            ("precision_stress", lambda: precision_record(are, torch, 5, 2, compact=False))):
+        t0 = time.perf_counter()
+        try:
+            rec = fn()
+        except Exception as e:   # the headline line is still printed
+            rec = {"error": f"{type(e).__name__}: {e}"}
+        rec["wall_s"] = round(time.perf_counter() - t0, 1)
+        out[name] = rec
+        torch.cuda.empty_cache()
+    return out
 
 
 # ---------------------------------------------------------------------------
@@ -854,7 +971,8 @@ def main():
     for p in paths:
         rb = row_bytes(J, p, tuned.get(PRECISION_NAMES[p]))
         if rb not in ceilings:
-            ceilings[rb] = are.are_gather_ceiling(ctx, res.yet, rb, 0, y.n_trials, reps=3)
+            ceilings[rb] = are.are_gather_ceiling(ctx, res.yet, rb, 0, y.n_trials, reps=3,
+                                                  shapes=True)
 
     head = results[prec]
     lookups = world * y.n_events * J
@@ -920,6 +1038,10 @@ def main():
                                 "sample": f"first {n} of the {y.n_trials} trials ({dt:.1f} s wall, "
                                           f"FP64 oracle, all host threads)"}
     are.are_destroy(ctx)
+    del res
+    torch.cuda.empty_cache()
+    if world == 1 and not args.no_subrecords:
+        line.update(subrecords(are, torch, args))
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -86,14 +86,18 @@ typedef struct {
 } are_layer_terms;
 
 /* Arithmetic of the analysis stage.
- *   ARE_FP64          losses, terms and sums in FP64.
- *   ARE_FP32_KAHAN    losses and terms in FP32, per-event sums in FP32, the
- *                     trial's running sum in FP32 with Kahan compensation.
- *   ARE_FP32_FP64AGG  losses and terms in FP32, the trial's running sum in
- *                     FP64.
- * In every mode a loss enters the analysis as fx * loss - deductible, formed
- * in FP64 when the layer's table is built and rounded once to the mode's
- * type; the limit and share are applied in that type.
+ *   ARE_FP64          terms and sums in FP64; an event's terms are added in
+ *                     the layer's ELT order.
+ *   ARE_FP32_KAHAN    terms in FP32, per-event sums over ELTs in FP32, the
+ *                     trial's running sum in FP32 with Kahan compensation
+ *                     (the lanes' compensated pairs merged by exact two-sum
+ *                     steps).
+ *   ARE_FP32_FP64AGG  terms and per-event sums in FP32, the trial's running
+ *                     sum in FP64.
+ * In every mode an ELT's financial term of an event,
+ * share * min(max(fx * loss - deductible, 0), limit), is formed in FP64 (in
+ * that order of operations) when the layer's table is built and rounded once
+ * to the mode's type.  The order of the FP32 sums over ELTs is not fixed.
  * The paper does not state its precision; its losses are doubles
  * (Section III-B, data structure iii). */
 typedef enum {
@@ -231,10 +235,13 @@ ARE_API are_status are_simulate_portfolio(are_ctx *ctx, const int32_t *layers, i
 /* The launch configuration the autotuner picked for one kind of work. */
 typedef struct {
     int32_t kernel;          /* 0 persistent work items, 1 staged rows (one event per lane),
-                                2 register rows, 3 (FP64) staged rows of an FP32 screen with
-                                the marked entries read from the FP64 table */
-    int32_t rows_in_flight;  /* table rows each lane keeps in flight (persistent kernel: 4 or
-                                8; staged kernel: events per lane per batch, 1 or 2) */
+                                2 register rows (FP32: rows read straight into registers by
+                                jp/8 lanes each; FP64: one warp per trial), 3 (FP64) staged
+                                rows of an FP32 screen with the marked entries read from
+                                the FP64 table */
+    int32_t rows_in_flight;  /* FP32 register rows and persistent kernel: groups of 32 events
+                                per batch, 1 or 2; staged kernel: events per lane per
+                                batch, 1 or 2 */
     int32_t trials_per_item; /* trials per work item (persistent kernel) */
     int32_t blocks_per_sm;   /* 0 = as many as fit */
     double ms;               /* measured time of one pass */
@@ -316,18 +323,35 @@ ARE_API are_status are_simulate_streamed(are_ctx *ctx, int32_t layer, int32_t ca
                                          int64_t chunk_events, are_precision precision,
                                          double *ylt, void *stream);
 
+/* One launch shape of the gather ceiling and its measured rate. */
+typedef struct {
+    int32_t kind;            /* 0: 16-byte loads, row_bytes/16 lanes per row, each lane
+                                reading its row's id; 1: 32-byte loads, row_bytes/32 lanes
+                                per row, ids read once per 32 events and passed by shuffles
+                                (the FP32 register-rows kernel's shape); 2: whole rows
+                                copied into shared memory by 16-byte cp.async (the staged
+                                kernels' shape) */
+    int32_t rows_in_flight;  /* kind 0: rows per lane; kinds 1 and 2: groups of 32 events */
+    int32_t blocks_per_sm;   /* 256-thread blocks per SM */
+    double rows_per_s;
+} are_ceiling_shape;
+
 /* Gather ceiling -- a measurement helper, not a step of the method.  Reads,
  * for every event occurrence of trials trial_begin .. trial_begin +
  * n_trials - 1 of the YET, its id and one row of row_bytes bytes (32, 64 or
  * 128) of a zero table with one row per catalog event, as the analysis
  * kernels do, and nothing else; the table is allocated and freed inside the
- * call (against the memory budget).  *rows_per_s receives the best rate over
- * `reps` timed passes (1..100) and two launch shapes each: the bound that
- * the table-row reads put on any analysis kernel for this YET and row size.
- * Blocks the caller. */
+ * call (against the memory budget).  Every shape of are_ceiling_shape is
+ * timed with 2 to 16 rows per lane (or 1 to 4 groups of 32 events) in flight
+ * and 3, 4, 6 and 8 blocks per SM (as many as fit), the best of `reps` timed
+ * passes (1..100) each.  *rows_per_s receives the best rate of all: the bound
+ * that the table-row reads put on any analysis kernel for this YET and row
+ * size.  shapes (may be NULL) receives up to max_shapes of the shapes timed
+ * and *n_shapes (may be NULL) how many were timed.  Blocks the caller. */
 ARE_API are_status are_gather_ceiling(are_ctx *ctx, int32_t yet, int32_t row_bytes,
                                       int64_t trial_begin, int64_t n_trials, int32_t reps,
-                                      double *rows_per_s);
+                                      double *rows_per_s, are_ceiling_shape *shapes,
+                                      int32_t max_shapes, int32_t *n_shapes);
 
 /* ------------------------------------------------------------------------ */
 /* Filters on the YLT (Section II-C): PML and TVaR                           */

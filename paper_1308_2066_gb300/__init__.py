@@ -46,6 +46,11 @@ class TuneResult(C.Structure):
                 ("trials_per_item", C.c_int32), ("blocks_per_sm", C.c_int32), ("ms", C.c_double)]
 
 
+class CeilingShape(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("rows_in_flight", C.c_int32), ("blocks_per_sm", C.c_int32),
+                ("rows_per_s", C.c_double)]
+
+
 class LayerTerms(C.Structure):
     _fields_ = [("occ_ret", C.c_double), ("occ_lim", C.c_double), ("agg_ret", C.c_double),
                 ("agg_lim", C.c_double)]
@@ -110,7 +115,9 @@ _SIGS = {
     "are_simulate_streamed": (C.c_int32, [_P, C.c_int32, C.c_int32, C.c_int64, _P, C.c_int32, _P,
                                           C.c_int64, C.c_int, _P, _P]),
     "are_gather_ceiling": (C.c_int32, [_P, C.c_int32, C.c_int32, C.c_int64, C.c_int64,
-                                       C.c_int32, C.POINTER(C.c_double)]),
+                                       C.c_int32, C.POINTER(C.c_double),
+                                       C.POINTER(CeilingShape), C.c_int32,
+                                       C.POINTER(C.c_int32)]),
     "are_server_start": (C.c_int32, [_P, C.c_int32, C.POINTER(ServerCfg)]),
     "are_submit": (C.c_int32, [_P, C.POINTER(Request), C.POINTER(C.c_int64)]),
     "are_wait": (C.c_int32, [_P, C.c_int64, C.c_int64, C.POINTER(Result)]),
@@ -308,14 +315,22 @@ def are_simulate_streamed(ctx, layer: int, catalog_size: int, n_trials: int, off
 
 
 def are_gather_ceiling(ctx, yet: int, row_bytes: int, trial_begin: int = 0,
-                       n_trials: Optional[int] = None, reps: int = 3) -> float:
-    """Rows per second of a pure id-stream + table-row gather over the YET."""
+                       n_trials: Optional[int] = None, reps: int = 3, shapes: bool = False):
+    """Rows per second of a pure id-stream + table-row gather over the YET,
+    best over every launch shape; with shapes=True also the list of
+    (kind, rows_in_flight, blocks_per_sm, rows_per_s) of each shape timed."""
     if n_trials is None:
         raise ValueError("n_trials is required")
     out = C.c_double()
+    buf = (CeilingShape * 64)()
+    n = C.c_int32(0)
     _check(ctx, lib().are_gather_ceiling(ctx, int(yet), int(row_bytes), int(trial_begin),
-                                         int(n_trials), int(reps), C.byref(out)))
-    return out.value
+                                         int(n_trials), int(reps), C.byref(out), buf, 64,
+                                         C.byref(n)))
+    if not shapes:
+        return out.value
+    got = [(b.kind, b.rows_in_flight, b.blocks_per_sm, b.rows_per_s) for b in buf[: min(n.value, 64)]]
+    return out.value, got
 
 
 def are_risk_measures(ctx, ylt, n: Optional[int] = None,

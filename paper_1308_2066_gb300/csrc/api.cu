@@ -1174,7 +1174,8 @@ are_status are_simulate_streamed(are_ctx *ctx, int32_t layer, int32_t catalog_si
 }
 
 are_status are_gather_ceiling(are_ctx *ctx, int32_t yet, int32_t row_bytes, int64_t trial_begin,
-                              int64_t n_trials, int32_t reps, double *rows_per_s)
+                              int64_t n_trials, int32_t reps, double *rows_per_s,
+                              are_ceiling_shape *shapes, int32_t max_shapes, int32_t *n_shapes)
 {
     return guarded(ctx, [&] {
         NvtxRange nvtx("are_gather_ceiling");
@@ -1185,6 +1186,7 @@ are_status are_gather_ceiling(are_ctx *ctx, int32_t yet, int32_t row_bytes, int6
         ARE_CHECK(trial_begin >= 0 && n_trials >= 1 && trial_begin + n_trials <= y.n_trials,
                   ARE_EINVAL, "trial range outside the YET (or empty)");
         ARE_CHECK(rows_per_s, ARE_EINVAL, "rows_per_s is NULL");
+        ARE_CHECK(!shapes || max_shapes >= 0, ARE_EINVAL, "max_shapes must be >= 0");
         CallStream cs(ctx, nullptr);
         int64_t first, last;
         if (y.d_off) {
@@ -1203,9 +1205,18 @@ are_status are_gather_ceiling(are_ctx *ctx, int32_t yet, int32_t row_bytes, int6
         try {
             out = (float *)dalloc(ctx, out_bytes);
             ARE_CUDA_TRY(cudaMemsetAsync(tab, 0, tab_bytes, cs.s));
-            const float ms = gather_ceiling_ms(y.d_ids + first, last - first, row_bytes, reps,
-                                               ctx->num_sms, tab, out, cs.s, ctx->launches);
-            *rows_per_s = (double)(last - first) / ((double)ms * 1e-3);
+            const std::vector<CeilingShape> res = gather_ceiling(
+                y.d_ids + first, last - first, row_bytes, reps, ctx->num_sms, tab, out, cs.s,
+                ctx->launches);
+            double best = 0.0;
+            for (size_t i = 0; i < res.size(); ++i) {
+                best = std::max(best, res[i].rows_per_s);
+                if (shapes && (int64_t)i < max_shapes)
+                    shapes[i] = are_ceiling_shape{res[i].kind, res[i].rows_in_flight,
+                                                  res[i].blocks_per_sm, res[i].rows_per_s};
+            }
+            *rows_per_s = best;
+            if (n_shapes) *n_shapes = (int32_t)res.size();
             cs.finish();
         } catch (...) {
             if (out) dfree(ctx, out, out_bytes);

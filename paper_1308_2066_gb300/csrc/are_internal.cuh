@@ -274,8 +274,16 @@ bool folded_bits_in_smem(int32_t words);
 int launch_fold(const ScatterArgs &elts, double occ_r, double occ_l, int32_t catalog, ulonglong2 *F,
                 uint32_t *bits, unsigned long long *hmax, int num_sms, cudaStream_t s);
 int launch_folded(const FoldArgs &a, int num_sms, cudaStream_t s);
-float gather_ceiling_ms(const int32_t *ids, int64_t n, int row_bytes, int reps, int num_sms,
-                        const void *table, float *out, cudaStream_t s, uint64_t &launches);
+// One launch shape of the gather ceiling and its rate (ceiling.cu).
+struct CeilingShape {
+    int kind;              // 0 16-byte loads, 1 32-byte loads with shuffled ids, 2 cp.async staging
+    int rows_in_flight;    // rows per lane (0) or groups of 32 events (1, 2) in flight
+    int blocks_per_sm;     // 256-thread blocks per SM
+    double rows_per_s;
+};
+std::vector<CeilingShape> gather_ceiling(const int32_t *ids, int64_t n, int row_bytes, int reps,
+                                         int num_sms, const void *table, float *out, cudaStream_t s,
+                                         uint64_t &launches);
 int table_jp(int n_elts, bool fp32);
 
 // api.cu: how many blocks of `kern` (threads per block, bytes of dynamic

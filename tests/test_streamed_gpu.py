@@ -136,8 +136,12 @@ def test_gather_ceiling(are, ctx):
     h = are.are_load_yet(ctx, yet.catalog, yet.n_trials, None, yet.k, torch.from_numpy(yet.ids).cuda())
     try:
         for rb in (32, 64, 128):
-            rate = are.are_gather_ceiling(ctx, h, rb, 0, yet.n_trials, reps=1)
+            rate, shapes = are.are_gather_ceiling(ctx, h, rb, 0, yet.n_trials, reps=1, shapes=True)
             assert rate > 1e8
+            # every kind of shape was timed, and the best of them is the rate
+            assert {k for k, _, _, _ in shapes} == {0, 1, 2}
+            assert rate == max(r for _, _, _, r in shapes)
+            assert all(b >= 3 for _, _, b, _ in shapes)
         with pytest.raises(are.AreError):
             are.are_gather_ceiling(ctx, h, 48, 0, yet.n_trials)
         with pytest.raises(are.AreError):
