@@ -94,12 +94,13 @@ def hbm_peak():
 # when one of them changes).
 KERNEL_SOURCES = {
     "k_rows": ["simulate.cu", "rows.cuh", "are_internal.cuh"],
+    "k_rows64": ["rows64.cu", "rows.cuh", "fixed.cuh", "are_internal.cuh"],
     "k_simulate_staged": ["simulate.cu", "are_internal.cuh"],
     "k_staged": ["staged.cuh", "staged64.cu", "are_internal.cuh"],
     "k_screen64": ["screen64.cu", "staged.cuh", "are_internal.cuh"],
     "k_sim_items": ["sim_items.cu", "rows.cuh", "are_internal.cuh"],
     "k_simulate": ["simulate.cu", "are_internal.cuh"],
-    "k_folded": ["folded.cu", "are_internal.cuh"],
+    "k_folded": ["folded.cu", "fixed.cuh", "are_internal.cuh"],
 }
 
 
@@ -214,12 +215,12 @@ def kernel_key(prec: int, J: int, tuned=None) -> str:
     t = tuned or {}
     if prec == 0:
         jp = math.ceil(J / 4) * 4
-        kind = t.get("kernel", 1)
+        kind = t.get("kernel", 2)
         if kind == 3:
             return f"k_screen64<{8 if J <= 8 else 16 if J <= 16 else 32},fixed>"
         if kind == 1:
             return f"k_staged<double,{jp},fixed,ylt>"
-        return f"k_simulate<{jp},fixed>"
+        return f"k_rows64<{8 if J <= 16 else 16},{t.get('rows_in_flight', 2)},fixed>"
     jp = 8 if J <= 8 else 16 if J <= 16 else 32
     kind = t.get("kernel", 2)
     u = t.get("rows_in_flight", 2)
@@ -231,11 +232,18 @@ def kernel_key(prec: int, J: int, tuned=None) -> str:
 
 
 def row_bytes(J: int, prec, tuned=None) -> int:
-    """Bytes of one table row as the analysis kernels read it (the screened
-    FP64 kernel reads the FP32 screen's rows)."""
-    if prec == 0 and (tuned or {}).get("kernel", 1) != 3:
-        return math.ceil(J / 4) * 32
-    return 32 if J <= 8 else 64 if J <= 16 else 128
+    """Bytes of one table row as the analysis kernel reads it: the FP32
+    table's row; for FP64 the packed row (register-rows kernel, the FP32
+    table's size), the FP32 screen's row (screened kernel) or the dense FP64
+    row (staged kernel)."""
+    fp32_row = 32 if J <= 8 else 64 if J <= 16 else 128
+    if prec == 0:
+        kind = (tuned or {}).get("kernel", 2)
+        if kind == 1:
+            return math.ceil(J / 4) * 32
+        if kind == 2:
+            return 64 if J <= 16 else 128
+    return fp32_row
 
 
 class Resident:
@@ -363,16 +371,19 @@ def roofline(n_events, n_trials, J, prec, sim_ms, tuned=None, ceiling=None):
     """Roofline of the analysis kernel.  Its table rows are gathered from the
     L2-resident table, so the bound that applies is the gather ceiling: the
     same id stream and row reads with no arithmetic, measured live in this
-    run over every launch shape of are_gather_ceiling.  achieved and peak are
-    the algorithmic bytes (4 B id + the row in whole 32-B sectors per event,
-    8 B per trial) over the kernel's time and over the ceiling's time, so
-    frac = the kernel's rows/s over the ceiling's.  hbm_formula_frac puts the
-    same bytes over the measured HBM copy bandwidth (above 1: the rows are
-    not HBM traffic); dram_frac is the ncu-measured DRAM traffic of one
-    launch over the kernel's time, over that bandwidth."""
+    run over every launch shape of are_gather_ceiling for the kernel's row
+    size.  achieved and peak are the algorithmic bytes (4 B id + the row the
+    kernel reads per event, 8 B per trial) over the kernel's time and over
+    the ceiling's time, so frac = the kernel's rows/s over the ceiling's.
+    hbm_formula_frac puts the survey formula's bytes (the row of J entries of
+    the precision, in whole 32-B sectors) over the measured HBM copy
+    bandwidth (above 1: the rows are not HBM traffic); dram_frac is the
+    ncu-measured DRAM traffic of one launch over the kernel's time, over
+    that bandwidth."""
     hbm, src = hbm_peak()
-    elem = 8 if prec == 0 else 4
-    bytes_ = algorithmic_bytes(n_events, n_trials, J, elem)
+    rb = row_bytes(J, prec, tuned)
+    bytes_ = n_events * (4 + rb) + 8 * n_trials
+    survey_bytes = algorithmic_bytes(n_events, n_trials, J, 8 if prec == 0 else 4)
     secs = sim_ms * 1e-3
     achieved = bytes_ / secs / 1e9
     key = kernel_key(prec, J, tuned)
@@ -384,9 +395,10 @@ def roofline(n_events, n_trials, J, prec, sim_ms, tuned=None, ceiling=None):
             "peak": round(bytes_ / (n_events / best) / 1e9, 1), "unit": "GB/s",
             "frac": round(rate / best, 4), "traffic": traffic, "kernel": key,
             "algorithmic_bytes_per_launch": bytes_,
+            "survey_formula_bytes_per_launch": survey_bytes,
             "peak_source": ("measured live in this run: best of %d launch shapes of the gather "
                             "ceiling (ids + table rows, no arithmetic) on this YET" % len(shapes)),
-            "hbm_formula_frac": round(achieved / hbm, 4),
+            "hbm_formula_frac": round(survey_bytes / secs / 1e9 / hbm, 4),
             "dram_frac": (round(traffic / secs / 1e9 / hbm, 4) if traffic else None),
             "hbm_peak": hbm, "hbm_peak_source": f"{src} HBM copy bandwidth (MEASURED_PEAKS.json)",
             "l2_gather": {"row_bytes": row_bytes(J, prec, tuned),

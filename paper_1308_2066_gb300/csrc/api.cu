@@ -194,6 +194,12 @@ void free_table(are_ctx *ctx, Table &t)
     t = Table{};
 }
 
+void free_packed(are_ctx *ctx, Packed64 &p)
+{
+    dfree(ctx, p.d, p.bytes);
+    p = Packed64{};
+}
+
 void free_folded(are_ctx *ctx, Folded &f)
 {
     dfree(ctx, f.d, f.bytes);
@@ -301,6 +307,41 @@ Table &build_screen(are_ctx *ctx, Layer &L, int32_t catalog, cudaStream_t s)
     return u;
 }
 
+// The packed FP64 rows of the layer's FP64 table (which must be built for
+// `catalog`), read by the FP64 register-rows kernel.
+Packed64 &build_packed(are_ctx *ctx, Layer &L, int32_t catalog, cudaStream_t s)
+{
+    Packed64 &p = L.p64;
+    const int rw = packed_row_words((int)L.elts.size());
+    int64_t entries = 0;
+    for (int32_t h : L.elts) entries += ctx->elts.at(h).n;
+    ARE_CHECK(entries < (1LL << 32), ARE_EINVAL, "a layer's ELTs hold 2^32 or more entries");
+    const size_t rows_bytes = (size_t)catalog * rw * sizeof(unsigned long long);
+    const size_t need = rows_bytes + 256 + sizeof(double) * (size_t)std::max<int64_t>(entries, 1);
+    if (p.d && (p.catalog != catalog || p.rw != rw || p.bytes < need)) free_packed(ctx, p);
+    if (!p.d) {
+        ++L.generation;
+        p.d = dalloc(ctx, need);
+        p.bytes = need;
+        p.rows_bytes = rows_bytes;
+        p.catalog = catalog;
+        p.rw = rw;
+    }
+    const Table &t = L.t64;
+    ctx->launches += launch_pack64(static_cast<const double *>(t.d), t.jp, catalog, rw, p.rows(), p.ovf(),
+                                   p.used(), ctx->num_sms, s);
+    return p;
+}
+
+// The tables beside the FP64 table that an FP64 kernel choice reads: the
+// packed rows (register rows, kernel 2) or the FP32 screen (kernel 3).
+// `fresh`: the FP64 table was just rebuilt.
+void ensure_fp64_aux(are_ctx *ctx, Layer &L, int32_t catalog, int kernel, bool fresh, cudaStream_t s)
+{
+    if (kernel == 2 && (fresh || !L.p64.d || L.p64.catalog != catalog)) build_packed(ctx, L, catalog, s);
+    if (kernel == 3 && (fresh || !L.t32u.d || L.t32u.catalog != catalog)) build_screen(ctx, L, catalog, s);
+}
+
 void ensure_tables(are_ctx *ctx, Layer &L, const Yet &y, are_precision precision, cudaStream_t s,
                    bool rebuild)
 {
@@ -311,10 +352,9 @@ void ensure_tables(are_ctx *ctx, Layer &L, const Yet &y, are_precision precision
         return;
     }
     const Table &t = fp32 ? L.t32 : L.t64;
-    if (rebuild || !t.d || t.catalog != catalog) build_table(ctx, L, catalog, fp32, s);
-    if (!fp32 && tuned(ctx, precision, y, t.jp, false).kernel == 3 &&
-        (rebuild || !L.t32u.d || L.t32u.catalog != catalog))
-        build_screen(ctx, L, catalog, s);
+    const bool fresh = rebuild || !t.d || t.catalog != catalog;
+    if (fresh) build_table(ctx, L, catalog, fp32, s);
+    if (!fp32) ensure_fp64_aux(ctx, L, catalog, tuned(ctx, precision, y, t.jp, false).kernel, fresh, s);
 }
 
 Layer &layer_of(are_ctx *ctx, int32_t h)
@@ -397,6 +437,29 @@ ItemWork item_work(const Yet &y, int64_t trial_begin, int64_t n_trials, const It
     return w;
 }
 
+// The fixed-point scale of the FP64 register-rows kernel's exact running
+// sums: s = 125 - floor(log2(B)) for an upper bound B of every occurrence
+// loss of the layer -- min(OccL, the sum over its ELTs of the largest term),
+// the largest term being the term of the ELT's largest loss (a term is
+// non-decreasing in the loss), with a margin for the rounding of that sum.
+int fixed_scale(are_ctx *ctx, const Layer &L)
+{
+    double g = 0.0;
+    for (int32_t h : L.elts) {
+        const Elt &e = ctx->elts.at(h);
+        if (e.n == 0) continue;
+        double x = e.terms.fx * e.max_loss - e.terms.deductible;
+        x = x > 0.0 ? x : 0.0;
+        x = x > e.terms.limit ? e.terms.limit : x;
+        g += e.terms.share * x;
+    }
+    double b = std::min(g, L.terms.occ_lim) * (1.0 + 1e-9);
+    if (!(b > 0.0)) return 0;
+    int ex = 0;
+    std::frexp(b, &ex);          // b = f * 2^ex, 0.5 <= f < 1: floor(log2 b) = ex - 1
+    return 125 - (ex - 1);
+}
+
 // One layer's analysis stage with a given kernel choice.
 int run_single(are_ctx *ctx, const Layer &L, const Yet &y, int64_t trial_begin, int64_t n_trials,
                are_precision precision, double *d_out, const TuneEntry &te, cudaStream_t s)
@@ -436,13 +499,19 @@ int run_single(are_ctx *ctx, const Layer &L, const Yet &y, int64_t trial_begin, 
         a.kernel = 4;
         return launch_simulate(a, precision, L.comp.jp, &t32, &t64, ctx->num_sms, s);
     }
-    if (!fp32 && te.kernel == 3 && L.t32u.d && L.t32u.catalog == y.catalog) {
-        a.table2 = L.t32u.d;
-        a.jp64 = t.jp;
-        return launch_screen64(a, L.t32u.jp, t64, ctx->num_sms, s);
+    if (!fp32) {
+        if (te.kernel == 2 && L.p64.d && L.p64.catalog == y.catalog) {   // packed FP64 rows
+            a.table = L.p64.rows();
+            a.table2 = L.p64.ovf();
+            return launch_rows64(a, L.p64.rw, t64, fixed_scale(ctx, L), ctx->num_sms, s);
+        }
+        if (te.kernel == 3 && L.t32u.d && L.t32u.catalog == y.catalog) {   // the FP32 screen
+            a.table2 = L.t32u.d;
+            a.jp64 = t.jp;
+            return launch_screen64(a, L.t32u.jp, t64, ctx->num_sms, s);
+        }
+        return launch_staged64(a, t.jp, t64, false, ctx->num_sms, s);   // (or an aux table not built)
     }
-    if (!fp32 && (te.kernel == 1 || te.kernel == 3))   // 3 without its screen: the staged kernel
-        return launch_staged64(a, t.jp, t64, false, ctx->num_sms, s);
     return launch_simulate(a, precision, t.jp, &t32, &t64, ctx->num_sms, s);
 }
 
@@ -450,8 +519,8 @@ TuneEntry tuned(are_ctx *ctx, are_precision p, const Yet &y, int jp, bool multi)
 {
     auto it = ctx->tune.find(tune_key(p, y, jp, multi));
     if (it != ctx->tune.end()) return it->second;
-    TuneEntry d;   // untuned: FP32, the register-rows kernel (two groups of 32 events
-    d.kernel = p == ARE_FP64 ? 1 : 2;   // per batch); FP64, the staged kernel
+    TuneEntry d;   // untuned: the register-rows kernels, two groups of 32 events per batch
+    d.kernel = 2;
     d.cfg.rows_in_flight = 2;
     return d;
 }
@@ -584,14 +653,16 @@ void check_multi_args(are_ctx *ctx, const int32_t *layers, int32_t n_layers, con
     }
 }
 
+// Every layer's table; FP64 also the aux table of `fp64_kernel` (0: none).
 void ensure_tables(are_ctx *ctx, const int32_t *layers, int32_t n_layers, const Yet &y, bool fp32,
-                   cudaStream_t s, bool screens = false)
+                   cudaStream_t s, int fp64_kernel = 0)
 {
     for (int32_t i = 0; i < n_layers; ++i) {
         Layer &L = layer_of(ctx, layers[i]);
         const Table &t = fp32 ? L.t32 : L.t64;
-        if (!t.d || t.catalog != y.catalog) build_table(ctx, L, y.catalog, fp32, s);
-        if (!fp32 && screens && (!L.t32u.d || L.t32u.catalog != y.catalog)) build_screen(ctx, L, y.catalog, s);
+        const bool fresh = !t.d || t.catalog != y.catalog;
+        if (fresh) build_table(ctx, L, y.catalog, fp32, s);
+        if (!fp32) ensure_fp64_aux(ctx, L, y.catalog, fp64_kernel, fresh, s);
     }
 }
 
@@ -675,6 +746,7 @@ are_status are_destroy(are_ctx *ctx)
             free_table(ctx, kv.second.t32);
             free_table(ctx, kv.second.t64);
             free_table(ctx, kv.second.t32u);
+            free_packed(ctx, kv.second.p64);
             free_folded(ctx, kv.second.fold);
             free_compact(ctx, kv.second.comp);
         }
@@ -817,11 +889,13 @@ are_status are_load_elt(are_ctx *ctx, int32_t n_entries, const int32_t *event_id
         std::vector<int32_t> ids = to_host(event_ids, (size_t)n_entries, s);
         std::vector<double> loss = to_host(losses, (size_t)n_entries, s);
         int32_t max_id = -1;
+        double max_loss = 0.0;
         for (int32_t i = 0; i < n_entries; ++i) {
             ARE_CHECK(ids[i] >= 0, ARE_EINVAL, "negative event id in ELT");
             ARE_CHECK(nonneg_finite(loss[i]), ARE_EINVAL, "ELT losses must be finite and >= 0");
             ARE_CHECK(std::isfinite(f.fx * loss[i]), ARE_EINVAL, "fx * loss overflows");
             max_id = std::max(max_id, ids[i]);
+            max_loss = std::max(max_loss, loss[i]);
         }
         bool dup = false;
         if (n_entries == 0) {
@@ -842,6 +916,7 @@ are_status are_load_elt(are_ctx *ctx, int32_t n_entries, const int32_t *event_id
         Elt e;
         e.n = n_entries;
         e.max_id = max_id;
+        e.max_loss = max_loss;
         e.terms = f;
         try {
             e.d_ids = (int32_t *)dalloc(ctx, sizeof(int32_t) * n_entries);
@@ -922,6 +997,7 @@ are_status are_free_layer(are_ctx *ctx, int32_t h)
         free_table(ctx, L.t32);
         free_table(ctx, L.t64);
         free_table(ctx, L.t32u);
+        free_packed(ctx, L.p64);
         free_folded(ctx, L.fold);
         free_compact(ctx, L.comp);
         for (int32_t e : L.elts) ctx->elts[e].users--;
@@ -1334,9 +1410,8 @@ are_status are_simulate_portfolio(are_ctx *ctx, const int32_t *layers, int32_t n
         check_multi_args(ctx, layers, n_layers, y, trial_begin, n_trials, ylts);
         CallStream cs(ctx, stream);
         const bool fp32 = precision != ARE_FP64;
-        ensure_tables(ctx, layers, n_layers, y, fp32, cs.s,
-                      !fp32 && tuned(ctx, precision, y, max_width(ctx, layers, n_layers, fp32),
-                                     n_layers > 1).kernel == 3);
+        const int k = tuned(ctx, precision, y, max_width(ctx, layers, n_layers, fp32), n_layers > 1).kernel;
+        ensure_tables(ctx, layers, n_layers, y, fp32, cs.s, fp32 ? 0 : k);
         const std::vector<int32_t> lv(layers, layers + n_layers);
         const std::vector<double *> yv(ylts, ylts + n_layers);
         std::vector<uint64_t> gens;
@@ -1481,7 +1556,8 @@ are_status are_autotune(are_ctx *ctx, const int32_t *layers, int32_t n_layers, i
         check_multi_args(ctx, layers, n_layers, y, 0, y.n_trials, nullptr);
         CallStream cs(ctx, stream);
         const bool fp32 = precision != ARE_FP64;
-        ensure_tables(ctx, layers, n_layers, y, fp32, cs.s, !fp32);   // the screened kernel is a candidate
+        ensure_tables(ctx, layers, n_layers, y, fp32, cs.s, fp32 ? 0 : 2);   // FP64: packed rows
+        if (!fp32) ensure_tables(ctx, layers, n_layers, y, fp32, cs.s, 3);  // and the screen
         const bool multi = n_layers > 1;
         const int jp = max_width(ctx, layers, n_layers, fp32);
         const std::string key = tune_key(precision, y, jp, multi);
@@ -1508,8 +1584,14 @@ are_status are_autotune(are_ctx *ctx, const int32_t *layers, int32_t n_layers, i
                     cands.push_back(e);
                 }
         } else {
-            TuneEntry e;
-            for (int k : {1, 3, 2}) {   // staged, screened, register
+            for (int u : {1, 2}) {      // register rows over the FP32 screen
+                TuneEntry e;
+                e.kernel = 2;
+                e.cfg.rows_in_flight = u;
+                cands.push_back(e);
+            }
+            for (int k : {1, 3}) {      // staged FP64 rows, staged screen rows
+                TuneEntry e;
                 e.kernel = k;
                 cands.push_back(e);
             }

@@ -66,6 +66,7 @@ constexpr int64_t kIdPad = 64;     // zero ids after the last event (vector over
 struct Elt {
     int32_t n = 0;
     int32_t max_id = -1;
+    double max_loss = 0.0;         // largest loss of the ELT
     int32_t *d_ids = nullptr;
     double *d_loss = nullptr;
     are_fin_terms terms{};
@@ -117,11 +118,30 @@ struct Compact {
     float *rows() const { return reinterpret_cast<float *>(static_cast<char *>(d) + rows_off); }
 };
 
+// Packed FP64 table of one layer (built from t64 by launch_pack64): catalog
+// rows of rw 64-bit words -- the mask of the non-zero terms and an overflow
+// offset, then the non-zero terms in column order -- a counter and the
+// overflow terms, in one allocation laid out [rows | counter (256 B) | ovf].
+struct Packed64 {
+    int32_t catalog = -1;
+    int rw = 0;
+    void *d = nullptr;
+    size_t bytes = 0;
+    size_t rows_bytes = 0;
+    unsigned long long *rows() const { return static_cast<unsigned long long *>(d); }
+    unsigned long long *used() const
+    {
+        return reinterpret_cast<unsigned long long *>(static_cast<char *>(d) + rows_bytes);
+    }
+    double *ovf() const { return reinterpret_cast<double *>(static_cast<char *>(d) + rows_bytes + 256); }
+};
+
 struct Layer {
     std::vector<int32_t> elts;
     are_layer_terms terms{};
     Table t32, t64;
     Table t32u;              // FP32 screen of t64: its values rounded up
+    Packed64 p64;            // packed FP64 rows of t64
     Folded fold;
     int layout = 0;          // ARE_LAYOUT_DIRECT or ARE_LAYOUT_COMPACT (FP32 analysis)
     Compact comp;
@@ -153,7 +173,7 @@ struct SimArgs {
     int32_t n_elts;          // ELTs of the layer
     double agg_r, agg_l;
     double *ylt;             // n_trials (may be null when occurrences are written)
-    int kernel;              // 1 staged, 2 register rows
+    int kernel;              // 1 staged, 2 register rows, 3 (FP64) staged screen
     int epl;                 // staged FP32 kernel: events per lane per batch (1 or 2);
                              // register-rows kernel: groups of 32 events per batch (1 or 2)
     double *marg;            // per-occurrence marginals, or null
@@ -285,6 +305,9 @@ std::vector<CeilingShape> gather_ceiling(const int32_t *ids, int64_t n, int row_
                                          int num_sms, const void *table, float *out, cudaStream_t s,
                                          uint64_t &launches);
 int table_jp(int n_elts, bool fp32);
+int packed_row_words(int n_elts);
+int launch_pack64(const double *dense, int jp64, int32_t catalog, int rw, unsigned long long *rows,
+                  double *ovf, unsigned long long *ovf_used, int num_sms, cudaStream_t s);
 
 // api.cu: how many blocks of `kern` (threads per block, bytes of dynamic
 // shared memory) fit on one SM of the current device.  On the first call for
@@ -311,6 +334,13 @@ int launch_items(const ItemWork &w, int jp, const ItemConfig &cfg, are_precision
 int launch_staged64(const SimArgs &a, int jp, const TermsF64 &t, bool occ, int num_sms,
                     cudaStream_t s);
 int launch_staged32_occ(const SimArgs &a, int jp, const TermsF32 &t, int num_sms, cudaStream_t s);
+
+// rows64.cu: the FP64 register-rows kernel over the packed FP64 table
+// (a.table, row_words words per row; a.table2: its overflow terms); `scale`
+// is the fixed-point scale of its exact running sums (every occurrence loss
+// times 2^scale below 2^126).
+int launch_rows64(const SimArgs &a, int row_words, const TermsF64 &t, int scale, int num_sms,
+                  cudaStream_t s);
 
 // simulate.cu
 int launch_simulate(const SimArgs &a, are_precision prec, int jp, const TermsF32 *t32,

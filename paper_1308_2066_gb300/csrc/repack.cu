@@ -37,7 +37,58 @@ __global__ void k_scatter(T *__restrict__ tab, const ScatterArgs a)
     }
 }
 
+// Packed FP64 rows from the dense FP64 table: row e gets the mask of its
+// non-zero columns (low 32 bits of word 0) and those terms in column order
+// (words 1 .. rw - 1).  A row with more non-zero terms than that keeps the
+// first rw - 1 inline and all of them in a block of the overflow array,
+// whose offset goes to the high 32 bits of word 0 (blocks are handed out by
+// an atomic counter; each block holds its row's terms in column order).
+__global__ void k_pack64(const double *__restrict__ dense, int jp64, int32_t catalog, int rw,
+                         unsigned long long *__restrict__ rows, double *__restrict__ ovf,
+                         unsigned long long *__restrict__ ovf_used)
+{
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < catalog;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const double *d = dense + e * jp64;
+        unsigned long long *out = rows + e * rw;
+        uint32_t mask = 0;
+        for (int j = 0; j < jp64; ++j)
+            if (__double_as_longlong(d[j]) != 0) mask |= 1u << j;
+        const int cnt = __popc(mask);
+        uint32_t off = 0;
+        if (cnt > rw - 1) off = (uint32_t)atomicAdd(ovf_used, (unsigned long long)cnt);
+        out[0] = (unsigned long long)mask | ((unsigned long long)off << 32);
+        int k = 0;
+        for (uint32_t m = mask; m; m &= m - 1) {
+            const double x = d[__ffs(m) - 1];
+            if (k < rw - 1) out[1 + k] = (unsigned long long)__double_as_longlong(x);
+            if (cnt > rw - 1) ovf[off + k] = x;
+            ++k;
+        }
+        for (int i = 1 + (k < rw - 1 ? k : rw - 1); i < rw; ++i) out[i] = 0ull;
+    }
+}
+
 }  // namespace
+
+// Words per packed FP64 row: the FP32 table's row size (64 bytes up to 16
+// ELTs, 128 bytes up to 32).
+int packed_row_words(int n_elts) { return n_elts <= 16 ? 8 : 16; }
+
+// dense: the FP64 table (jp64 columns, catalog rows); rows: catalog x rw
+// words; ovf: room for every non-zero term of the layer; ovf_used: a device
+// counter, zeroed here.
+int launch_pack64(const double *dense, int jp64, int32_t catalog, int rw, unsigned long long *rows,
+                  double *ovf, unsigned long long *ovf_used, int num_sms, cudaStream_t s)
+{
+    ARE_CUDA_TRY(cudaMemsetAsync(ovf_used, 0, sizeof *ovf_used, s));
+    if (catalog <= 0) return 0;
+    int64_t blocks = ((int64_t)catalog + 255) / 256;
+    if (blocks > (int64_t)num_sms * 16) blocks = (int64_t)num_sms * 16;
+    k_pack64<<<(unsigned)blocks, 256, 0, s>>>(dense, jp64, catalog, rw, rows, ovf, ovf_used);
+    ARE_CUDA_TRY(cudaGetLastError());
+    return 1;
+}
 
 // Columns per row: J rounded up so a row fills whole 32-byte sectors; FP32
 // rows are 8, 16 or 32 floats (a power of two, so the lanes that share a row

@@ -1,23 +1,36 @@
-// rows.cuh -- the analysis stage (Basic Algorithm, Section II-B) over an FP32
-// layer table with every table row held in registers: the core of the
-// single-layer FP32 kernel (simulate.cu) and of the persistent multi-layer
-// kernel (sim_items.cu).
+// rows.cuh -- the analysis stage (Basic Algorithm, Section II-B) with every
+// table row held in registers: the core of the single-layer register-rows
+// kernels (simulate.cu for FP32 tables, rows64.cu for the FP64 path) and of
+// the persistent multi-layer kernel (sim_items.cu).
 //
-// The layer table holds, for each catalog event and each ELT of the layer,
-// the event's financial term f_j(x) = share * min(max(fx * x - D, 0), Lim)
-// (step 2 before its sum over ELTs), formed in FP64 when the table is built
-// and rounded once to FP32; a row is jp = 8, 16 or 32 floats.
+// A layer table holds, for each catalog event and each ELT of the layer, the
+// event's financial term f_j(x) = share * min(max(fx * x - D, 0), Lim) (step
+// 2 before its sum over ELTs), formed in FP64 when the table is built; an
+// FP32 table holds it rounded once to FP32 in rows of JP = 8, 16 or 32
+// floats, the packed FP64 table holds the non-zero FP64 terms of each event
+// in rows of the same size.
 //
 // Mapping (GB300).  A warp takes a contiguous range of trials and walks each
 // trial's events in batches of 32 * U events (a batch never spans two
 // trials).  Each group of 32 events is loaded with one coalesced read of
-// their ids; the rows are then read by R = jp / 8 lanes each, one 32-byte
+// their ids; the rows are then read by R = JP / 8 lanes each, one 32-byte
 // (256-bit) load per lane, so a warp load instruction fetches 32 / R whole
-// rows and every lane holds R * U row pieces in flight.  Each lane adds its
-// pieces' 8 terms (packed FP32x2 adds); a reduce-scatter across the R lanes
-// of a row (R - 1 shuffles) completes the sum over ELTs and leaves every lane
-// with one whole event per group, whose occurrence terms (step 3) and
-// running sum (step 4) it does alone.  Ids are read one batch ahead.
+// rows and every lane holds R * U row pieces in flight.  A reduce-scatter
+// across the R lanes of a row (R - 1 shuffles) leaves every lane with one
+// whole event per group, whose occurrence terms (step 3) and running sum
+// (step 4) it does alone.  Ids are read one batch ahead.  (A packed FP64 row
+// is read the same way, RW / 4 lanes per row.)
+//
+//   BodyF32  sums the FP32 terms (packed FP32x2 adds), clamps the event loss
+//            with the occurrence terms and keeps a Kahan-compensated or an
+//            FP64 running sum per lane.
+//   BodyP64  reads the packed FP64 table (a row: the mask of the non-zero
+//            terms, then those terms in column order), adds the terms in
+//            column order (the first taken as is, an FP64 add only where an
+//            event has two or more), so each event loss and occurrence loss
+//            is the oracle's bit for bit; the running sum is exact: 160-bit
+//            fixed-point integers, rounded to double once per trial
+//            (fixed.cuh).
 //
 // A trial's total is the warp's merge of its lanes' running sums.  The
 // totals of 32 consecutive trials are kept one per lane and finished
@@ -32,6 +45,7 @@
 #include <type_traits>
 
 #include "are_internal.cuh"
+#include "fixed.cuh"
 
 namespace are {
 namespace rows {
@@ -105,6 +119,23 @@ __device__ __forceinline__ double clamp_d(double v, double r, double l)
     return a < l ? a : l;
 }
 
+__device__ __forceinline__ uint64_t bits(double x) { return (uint64_t)__double_as_longlong(x); }
+__device__ __forceinline__ double dbl(uint64_t b) { return __longlong_as_double((long long)b); }
+
+// FP64 add/sub that the compiler may not hoist out of warp-uniform branches.
+__device__ __forceinline__ double vadd(double a, double b)
+{
+    double r;
+    asm volatile("add.rn.f64 %0, %1, %2;" : "=d"(r) : "d"(a), "d"(b));
+    return r;
+}
+__device__ __forceinline__ double vsub(double a, double b)
+{
+    double r;
+    asm volatile("sub.rn.f64 %0, %1, %2;" : "=d"(r) : "d"(a), "d"(b));
+    return r;
+}
+
 // Running sum of a lane's occurrence losses in FP32 with Kahan's
 // compensation; the value is s - c.  A trial's total merges the lanes' pairs
 // with exact two-sum steps, so the compensation survives the merge.
@@ -130,7 +161,6 @@ struct SumKahan {
             s = t;
         }
     }
-    __device__ __forceinline__ double value() const { return __dsub_rn((double)s, (double)c); }
 };
 
 // Running sum in FP64: an FP64 add is issued only when some lane of the warp
@@ -141,8 +171,7 @@ struct SumF64 {
     {
         const bool need = o != 0.f;
         if (__any_sync(kFull, need)) {
-            double r;
-            asm volatile("add.rn.f64 %0, %1, %2;" : "=d"(r) : "d"(s), "d"(widen(o)));
+            const double r = vadd(s, widen(o));
             if (need) s = r;
         }
     }
@@ -151,43 +180,221 @@ struct SumF64 {
 #pragma unroll
         for (int m = 16; m > 0; m >>= 1) s = __dadd_rn(s, __shfl_xor_sync(kFull, s, m));
     }
-    __device__ __forceinline__ double value() const { return s; }
 };
 
-template <int ACC>
-using SumOf = typename std::conditional<ACC == ARE_FP32_KAHAN, SumKahan, SumF64>::type;
+// The running sum of the FP64 path: exact, in fixed point.
+struct SumFixed {
+    fixed::Acc a;
+    __device__ __forceinline__ void warp_merge() { fixed::warp_sum(a); }
+};
 
-// What one range of trials reads and writes.
+// What one range of trials reads and writes, whatever the precision.
 struct Trials {
     const int32_t *ids;      // YET event ids
     const int64_t *off;      // ragged offsets (indexed by YET trial) or nullptr
     int32_t k;               // fixed events per trial
     int64_t trial_begin;     // YET trial of index 0
-    const float *table;      // [catalog][JP] terms
     double *ylt;             // trial losses, indexed like the trials
-    float occ_r, occ_l;
     double agg_r, agg_l;
 };
 
-// Analyses trials [t0, t1) (indices relative to trial_begin) and writes
-// their losses.  All 32 lanes of the warp call it with the same range.
-template <int JP, int U, int ACC, bool FIXED>
-__device__ __forceinline__ void run_trials(const Trials &a, int64_t t0, int64_t t1, int lane)
+// Reads U groups of 32 events' row pieces: lane (row, col) takes piece col
+// of the rows q * RPW + row of each group (R = JP / 8 lanes per row).
+template <int JP, int U>
+__device__ __forceinline__ void load_rows(const float *__restrict__ tab, const int32_t (&id)[U],
+                                          bool full, int lane, F8 (&v)[U][JP / 8])
 {
-    constexpr int R = JP / 8;       // lanes per row
-    constexpr int RPW = 32 / R;     // rows per warp load
-    constexpr int B = 32 * U;       // events per batch
-    static_assert(JP == 8 || JP == 16 || JP == 32, "table width");
+    constexpr int R = JP / 8, RPW = 32 / R;
     const int row = lane / R, col = lane % R;
-    if (t0 >= t1) return;
+    if (full) {
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+            for (int q = 0; q < R; ++q) {
+                const int32_t e = __shfl_sync(kFull, id[u], q * RPW + row);
+                v[u][q] = load8(tab + (size_t)(uint32_t)e * JP + col * 8);
+            }
+    } else {
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+            for (int q = 0; q < R; ++q) {
+                const int32_t e = __shfl_sync(kFull, id[u], q * RPW + row);
+                v[u][q] = e >= 0 ? load8(tab + (size_t)(uint32_t)e * JP + col * 8) : zero8();
+            }
+    }
+}
 
-    // Trial bounds.  Ragged YETs: lane i holds the offsets of trial w + i of
-    // a window of 32 trials, read once per window.
-    int64_t wt = t0 - 64, wb = 0, we = 0;
-    auto bounds = [&](int64_t t, int64_t &b, int64_t &e) {
+// FP32 table: the event losses are sums of FP32 terms.
+template <int JP, int U, int ACC>
+struct BodyF32 {
+    static_assert(JP == 8 || JP == 16 || JP == 32, "table width");
+    using Sum = typename std::conditional<ACC == ARE_FP32_KAHAN, SumKahan, SumF64>::type;
+    const float *table;      // [catalog][JP] terms
+    float occ_r, occ_l;
+
+    __device__ __forceinline__ void batch(const int32_t (&id)[U], bool full, int lane, Sum &acc) const
+    {
+        constexpr int R = JP / 8;
+        const int col = lane % R;
+        F8 v[U][R];
+        load_rows<JP, U>(table, id, full, lane, v);   // step 1: every ELT's entry, one row read
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            // step 2: the sum over ELTs -- this lane's pieces, then a
+            // reduce-scatter over the row's lanes (lane col keeps the event
+            // of load q = col; the others of a partial batch hold 0)
+            float p[R];
+#pragma unroll
+            for (int q = 0; q < R; ++q) p[q] = sum8(v[u][q]);
+#pragma unroll
+            for (int h = R / 2; h >= 1; h >>= 1) {
+                const bool hi = (col & h) != 0;
+#pragma unroll
+                for (int m = 0; m < h; ++m) {
+                    const float keep = hi ? p[m + h] : p[m];
+                    const float send = hi ? p[m] : p[m + h];
+                    p[m] = __fadd_rn(keep, __shfl_xor_sync(kFull, send, h));
+                }
+            }
+            // step 3 (occurrence terms), then the running sum of step 4
+            acc.add(fminf(fmaxf(__fsub_rn(p[0], occ_r), 0.f), occ_l));
+        }
+    }
+    __device__ __forceinline__ double total(const Sum &t) const
+    {
+        if constexpr (ACC == ARE_FP32_KAHAN) return __dsub_rn((double)t.s, (double)t.c);
+        else return t.s;
+    }
+};
+
+// 32 bytes of a packed FP64 row as four 64-bit words.
+struct W4 {
+    unsigned long long w[4];
+};
+__device__ __forceinline__ W4 load4w(const unsigned long long *p)
+{
+    W4 r;
+    asm volatile("ld.global.nc.v4.b64 {%0, %1, %2, %3}, [%4];"
+                 : "=l"(r.w[0]), "=l"(r.w[1]), "=l"(r.w[2]), "=l"(r.w[3])
+                 : "l"(p));
+    return r;
+}
+
+// FP64 path over the packed FP64 table (repack.cu, launch_pack64): row e is
+// RW = 8 or 16 words (64 or 128 bytes, the FP32 table's row size) -- word 0
+// holds the mask of the ELT columns whose term is not 0 (low 32 bits) and an
+// overflow offset (high 32 bits), words 1 .. RW - 1 the non-zero terms in
+// column order.  A row with more non-zero terms than that keeps the first
+// RW - 1 inline and all of them at the overflow offset.  The terms are
+// added in column order (the first taken as is, an FP64 add only where some
+// event has two or more), so every event loss and occurrence loss is the
+// oracle's bit for bit; the running sum is exact (fixed point, fixed.cuh).
+template <int RW, int U>
+struct BodyP64 {
+    using Sum = SumFixed;
+    static constexpr int R = RW / 4, RPW = 32 / R, CAP = RW - 1;
+    const unsigned long long *rows;   // [catalog][RW]
+    const double *ovf;                // overflow terms
+    int32_t scale;                    // fixed-point scale s: every occurrence loss * 2^s < 2^126
+    double occ_r, occ_l;
+
+    __device__ __forceinline__ void batch(const int32_t (&id)[U], bool full, int lane, Sum &acc) const
+    {
+        const int row = lane / R, col = lane % R;
+        // step 1: each event's whole row -- lane (row, col) reads piece col
+        // of the rows q * RPW + row
+        W4 v[U][R];
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+            for (int q = 0; q < R; ++q) {
+                const int32_t e = __shfl_sync(kFull, id[u], q * RPW + row);
+                if (full || e >= 0) {
+                    v[u][q] = load4w(rows + (size_t)(uint32_t)e * RW + col * 4);
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) v[u][q].w[i] = 0ull;
+                }
+            }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            // the lane's event is load q = col: its header and first two
+            // terms come from the row's lane col 0, one round per q
+            unsigned long long h = v[u][0].w[0], x0 = v[u][0].w[1], x1 = v[u][0].w[2];
+#pragma unroll
+            for (int q = 1; q < R; ++q) {
+                const unsigned long long a = __shfl_sync(kFull, v[u][q].w[0], row * R);
+                const unsigned long long b = __shfl_sync(kFull, v[u][q].w[1], row * R);
+                const unsigned long long c = __shfl_sync(kFull, v[u][q].w[2], row * R);
+                if (col == q) {
+                    h = a;
+                    x0 = b;
+                    x1 = c;
+                }
+            }
+            const int32_t ev = __shfl_sync(kFull, id[u], col * RPW + row);
+            const uint32_t mask = (uint32_t)h;
+            const int cnt = __popc(mask);
+            // step 2: the sum over ELTs in column order
+            double g = dbl(x0);                    // 0 when the row has no term
+            if (__any_sync(kFull, cnt >= 2)) {
+                if (cnt >= 2) g = vadd(g, dbl(x1));
+            }
+            if (__any_sync(kFull, cnt >= 3)) {     // rare: the rest from the row or its overflow
+                const unsigned long long *r = rows + (size_t)(uint32_t)ev * RW;
+                const double *o = ovf + (uint32_t)(h >> 32);
+                for (int i = 2; __any_sync(kFull, i < cnt); ++i) {
+                    if (i < cnt) {
+                        const double x = (cnt <= CAP || i < CAP) ? dbl(__ldg(r + 1 + i)) : __ldg(o + i);
+                        g = vadd(g, x);
+                    }
+                }
+            }
+            // step 3 on bit patterns: min(max(g - OccR, 0), OccL), the
+            // subtraction only where some lane has g > OccR
+            const bool need = bits(g) > bits(occ_r);
+            double o = 0.0;
+            if (__any_sync(kFull, need)) {
+                const double d = vsub(g, occ_r);
+                if (need) o = dbl(bits(d) < bits(occ_l) ? bits(d) : bits(occ_l));
+            }
+            // step 4's running sum, exact
+            if (bits(o) != 0) {
+                unsigned long long lo, hi;
+                fixed::to_fixed(o, scale, lo, hi);
+                acc.a.add(lo, hi, 0u);
+            }
+        }
+    }
+    __device__ __forceinline__ double total(const Sum &t) const { return fixed::to_double(t.a, scale); }
+};
+
+// The batches of a warp's trials [t0, t1): a cursor over the trials' events
+// in batches of 32 * U (a batch never spans two trials), with the ids of the
+// next batch read one batch ahead.  Ragged YETs: lane i holds the offsets of
+// trial w + i of a window of 32 trials, read once per window.
+template <int U, bool FIXED>
+struct Cursor {
+    static constexpr int B = 32 * U;
+    const Trials &a;
+    const int64_t t0, t1;
+    const int lane;
+    int64_t t, pos = 0, end = 0;
+    int64_t wt, wb = 0, we = 0;
+    int32_t nid[U];
+
+    __device__ __forceinline__ Cursor(const Trials &a_, int64_t t0_, int64_t t1_, int lane_)
+        : a(a_), t0(t0_), t1(t1_), lane(lane_), t(t0_), wt(t0_ - 64)
+    {
+        bounds();
+        load_ids();
+    }
+    __device__ __forceinline__ void bounds()
+    {
         if (FIXED) {
-            b = (a.trial_begin + t) * (int64_t)a.k;
-            e = b + a.k;
+            pos = (a.trial_begin + t) * (int64_t)a.k;
+            end = pos + a.k;
             return;
         }
         if (t - wt >= 32) {
@@ -197,92 +404,73 @@ __device__ __forceinline__ void run_trials(const Trials &a, int64_t t0, int64_t 
             we = in ? __ldg(a.off + a.trial_begin + t + lane + 1) : 0;
         }
         const int i = (int)(t - wt);
-        b = __shfl_sync(kFull, wb, i);
-        e = __shfl_sync(kFull, we, i);
-    };
-    // ids of a batch: group u's event u * 32 + lane (-1 past the trial)
-    auto load_ids = [&](int32_t(&d)[U], int64_t p, int64_t e) {
+        pos = __shfl_sync(kFull, wb, i);
+        end = __shfl_sync(kFull, we, i);
+    }
+    // ids of the next batch: group u's event u * 32 + lane (-1 past the trial)
+    __device__ __forceinline__ void load_ids()
+    {
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-            const int64_t ev = p + u * 32 + lane;
-            d[u] = ev < e ? __ldcs(a.ids + ev) : -1;
+            const int64_t ev = pos + u * 32 + lane;
+            nid[u] = ev < end ? __ldcs(a.ids + ev) : -1;
         }
-    };
-
-    SumOf<ACC> acc;
-    SumOf<ACC> kept;    // lane i: the total of trial (first of its 32) + i
-    int64_t t = t0, pos = 0, end = 0;
-    bounds(t, pos, end);
-    int32_t nid[U];
-    load_ids(nid, pos, end);
-    while (t < t1) {
-        const int64_t tc = t;
+    }
+    __device__ __forceinline__ bool more() const { return t < t1; }
+    // Hands out the next batch: its ids, event count (<= 0: a trial without
+    // events), trial and whether it ends the trial.
+    __device__ __forceinline__ void take(int32_t (&id)[U], int &cnt, int64_t &tc, bool &last)
+    {
+        tc = t;
         const int64_t left = end - pos;
-        const int cnt = left < B ? (int)left : B;   // <= 0: a trial without events
-        int32_t id[U];
+        cnt = left < B ? (int)left : B;
 #pragma unroll
         for (int u = 0; u < U; ++u) id[u] = nid[u];
         pos += B;
-        const bool last = pos >= end;
+        last = pos >= end;
         if (last) {
             ++t;
-            if (t < t1) bounds(t, pos, end);
+            if (t < t1) bounds();
         }
-        if (t < t1) load_ids(nid, pos, end);
+        if (t < t1) load_ids();
+    }
+};
 
-        if (cnt > 0) {
-            // step 1: every ELT's entry of each event, one row read per event
-            F8 v[U][R];
-            if (cnt == B) {
-#pragma unroll
-                for (int u = 0; u < U; ++u)
-#pragma unroll
-                    for (int q = 0; q < R; ++q) {
-                        const int32_t e = __shfl_sync(kFull, id[u], q * RPW + row);
-                        v[u][q] = load8(a.table + (size_t)(uint32_t)e * JP + col * 8);
-                    }
-            } else {
-#pragma unroll
-                for (int u = 0; u < U; ++u)
-#pragma unroll
-                    for (int q = 0; q < R; ++q) {
-                        const int32_t e = __shfl_sync(kFull, id[u], q * RPW + row);
-                        v[u][q] = e >= 0 ? load8(a.table + (size_t)(uint32_t)e * JP + col * 8) : zero8();
-                    }
-            }
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                // step 2: the sum over ELTs -- this lane's pieces, then a
-                // reduce-scatter over the row's lanes (lane col keeps the
-                // event of load q = col; the others of a partial batch hold 0)
-                float p[R];
-#pragma unroll
-                for (int q = 0; q < R; ++q) p[q] = sum8(v[u][q]);
-#pragma unroll
-                for (int h = R / 2; h >= 1; h >>= 1) {
-                    const bool hi = (col & h) != 0;
-#pragma unroll
-                    for (int m = 0; m < h; ++m) {
-                        const float keep = hi ? p[m + h] : p[m];
-                        const float send = hi ? p[m] : p[m + h];
-                        p[m] = __fadd_rn(keep, __shfl_xor_sync(kFull, send, h));
-                    }
-                }
-                // step 3 (occurrence terms), then the running sum of step 4
-                acc.add(fminf(fmaxf(__fsub_rn(p[0], a.occ_r), 0.f), a.occ_l));
-            }
-        }
-        if (last) {
-            acc.warp_merge();
-            const int slot = (int)((tc - t0) & 31);
-            if (lane == slot) kept = acc;
-            acc = SumOf<ACC>{};
-            if (slot == 31 || t >= t1) {
-                // step 4's aggregate terms for up to 32 trials at once: the
-                // trial loss is A_k = min(max(S_k - AggR, 0), AggL)
-                if (lane <= slot) a.ylt[tc - slot + lane] = clamp_d(kept.value(), a.agg_r, a.agg_l);
-            }
-        }
+// A trial's end: the warp merges its lanes' sums; the totals of 32
+// consecutive trials are kept one per lane and finished together with
+// step 4's aggregate terms, A_k = min(max(S_k - AggR, 0), AggL), and one
+// coalesced write.
+template <typename Body>
+__device__ __forceinline__ void end_trial(const Trials &a, const Body &body, typename Body::Sum &acc,
+                                          typename Body::Sum &kept, int64_t tc, int64_t t0, bool done,
+                                          int lane)
+{
+    acc.warp_merge();
+    const int slot = (int)((tc - t0) & 31);
+    if (lane == slot) kept = acc;
+    acc = typename Body::Sum{};
+    if (slot == 31 || done)
+        if (lane <= slot) a.ylt[tc - slot + lane] = clamp_d(body.total(kept), a.agg_r, a.agg_l);
+}
+
+// Analyses trials [t0, t1) (indices relative to trial_begin) and writes
+// their losses, one batch at a time.  All 32 lanes of the warp call it with
+// the same range.
+template <int U, bool FIXED, typename Body>
+__device__ __forceinline__ void run_trials(const Trials &a, const Body &body, int64_t t0, int64_t t1,
+                                           int lane)
+{
+    if (t0 >= t1) return;
+    typename Body::Sum acc, kept;
+    Cursor<U, FIXED> cur(a, t0, t1, lane);
+    while (cur.more()) {
+        int32_t id[U];
+        int cnt;
+        int64_t tc;
+        bool last;
+        cur.take(id, cnt, tc, last);
+        if (cnt > 0) body.batch(id, cnt == 32 * U, lane, acc);
+        if (last) end_trial(a, body, acc, kept, tc, t0, !cur.more(), lane);
     }
 }
 

@@ -60,13 +60,14 @@ __global__ void __launch_bounds__(256, items_min_blocks(JP, U)) k_sim_items(cons
         a.off = w.off;
         a.k = w.k;
         a.trial_begin = w.trial_begin;
-        a.table = L.table;
         a.ylt = L.ylt;
-        a.occ_r = L.occ_r;
-        a.occ_l = L.occ_l;
         a.agg_r = L.agg_r;
         a.agg_l = L.agg_l;
-        rows::run_trials<JP, U, ACC, FIXED>(a, t0, t1, lane);
+        rows::BodyF32<JP, U, ACC> body;
+        body.table = L.table;
+        body.occ_r = L.occ_r;
+        body.occ_l = L.occ_l;
+        rows::run_trials<U, FIXED>(a, body, t0, t1, lane);
     }
 }
 

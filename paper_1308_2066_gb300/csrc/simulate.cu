@@ -1,30 +1,14 @@
 // simulate.cu -- the analysis stage (Basic Algorithm, Section II-B) for one
-// layer over a range of trials, reading the layer's event-major
-// direct-access table built by repack.cu (each entry an event's financial
-// term in one ELT).  Three kernels:
+// layer over a range of trials with an FP32 layer table (each entry an
+// event's financial term in one ELT, built by repack.cu).  Two kernels:
 //
-//  * k_rows (FP32 tables, the default): rows held in registers, see rows.cuh.
-//  * k_simulate_staged (FP32 tables, a tuning candidate and the compact
-//    layout's kernel): one event per lane, rows staged in shared memory.
-//  * k_simulate (FP64 tables, a tuning candidate): one warp per trial; in a
-//    step each event's table row is read by R lanes with one 16-byte load
-//    each, the R lanes of a row add their parts by shuffles (the sum over
-//    ELTs of step 2), the row's first lane applies the occurrence terms
-//    (step 3) and adds the occurrence loss to its running sum; at the end of
-//    the trial the warp adds the lanes' sums and applies the aggregate terms
-//    (step 4).
+//  * k_rows (the default): rows held in registers, see rows.cuh.
+//  * k_simulate_staged (a tuning candidate, and the compact layout's
+//    kernel): one event per lane, rows staged in shared memory.
 //
 // The trial loss is the aggregate-clamped total: with non-negative
 // occurrence losses the de-cumulated marginals of step 4 telescope to it, so
 // the YLT needs no per-event scan.
-//
-// FP64 on GB300 runs at a small fraction of the FP32 rate, so the FP64 path
-// takes every decision it can on bit patterns: for non-negative doubles the
-// integer order of the bits is the numeric order, so "x > retention", the
-// limit clamp and the zero tests are integer compares.  A subtraction or an
-// addition is issued only when some lane of the warp needs one (adding an
-// exact zero or clamping a non-positive value changes nothing), which keeps
-// the FP64 pipe for the few occurrences that carry a loss.
 #include <cuda_runtime.h>
 
 #include <string>
@@ -51,84 +35,13 @@ __device__ __forceinline__ float2 add2(float2 a, float2 b)
     return d;
 }
 
-__device__ __forceinline__ uint64_t bits(double x) { return (uint64_t)__double_as_longlong(x); }
-__device__ __forceinline__ double dbl(uint64_t b) { return __longlong_as_double((long long)b); }
-
-// FP64 add/sub/mul that the compiler may not hoist out of the warp-uniform
-// branches below (it would otherwise compute them speculatively, and on this
-// chip every FP64 instruction is expensive).
+// FP64 add that the compiler may not hoist out of the warp-uniform branch
+// below (every FP64 instruction is expensive on this chip).
 __device__ __forceinline__ double vadd(double a, double b)
 {
     double r;
     asm volatile("add.rn.f64 %0, %1, %2;" : "=d"(r) : "d"(a), "d"(b));
     return r;
-}
-__device__ __forceinline__ double vsub(double a, double b)
-{
-    double r;
-    asm volatile("sub.rn.f64 %0, %1, %2;" : "=d"(r) : "d"(a), "d"(b));
-    return r;
-}
-__device__ __forceinline__ double vmul(double a, double b)
-{
-    double r;
-    asm volatile("mul.rn.f64 %0, %1, %2;" : "=d"(r) : "d"(a), "d"(b));
-    return r;
-}
-
-// a + b for non-negative doubles, issuing the FP64 add only when some lane of
-// the warp has two non-zero operands (x + 0 = x exactly).  All lanes call it.
-__device__ __forceinline__ double add_nn(double a, double b)
-{
-    const bool both = bits(a) != 0 && bits(b) != 0;
-    double r = bits(a) == 0 ? b : a;
-    if (__any_sync(kFull, both)) {
-        const double s = vadd(a, b);
-        if (both) r = s;
-    }
-    return r;
-}
-
-// min(max(x - r, 0), l) for x, r >= 0 and l >= 0 (+inf allowed).  The
-// subtraction is issued only when some lane has x > r.  All lanes call it.
-__device__ __forceinline__ double net_nn(double x, uint64_t r_bits, double r, uint64_t l_bits)
-{
-    const bool need = bits(x) > r_bits;
-    double out = 0.0;
-    if (__any_sync(kFull, need)) {
-        const double d = vsub(x, r);
-        const uint64_t db = bits(d);
-        if (need) out = dbl(db < l_bits ? db : l_bits);
-    }
-    return out;
-}
-
-// The occurrence terms as one lane of the FP64 register kernel uses them.
-struct LaneTermsF64 {
-    double occ_r;
-    uint64_t occ_r_b, occ_l_b;
-    __device__ void load(const TermsF64 &t)
-    {
-        occ_r = t.occ_r;
-        occ_r_b = bits(t.occ_r);
-        occ_l_b = bits(t.occ_l);
-    }
-    // sum over this lane's columns of the terms, in column order
-    __device__ __forceinline__ double part(const double2 &v) const { return add_nn(v.x, v.y); }
-};
-
-// Sum of the R lanes of a row into its first lane (col == 0), pairing
-// neighbours first.  Works for any R <= 32; every lane calls it.
-template <int R>
-__device__ __forceinline__ double row_sum(double v, int col)
-{
-#pragma unroll
-    for (int off = 1; off < R; off <<= 1) {
-        double o = __shfl_down_sync(kFull, v, off);
-        if (!((col & (2 * off - 1)) == 0 && col + off < R)) o = 0.0;
-        v = add_nn(v, o);
-    }
-    return v;
 }
 
 // Per-lane running sums of occurrence losses (step 4) for the staged FP32
@@ -170,70 +83,6 @@ __device__ __forceinline__ double net_d(double v, double r, double l)
     double a = v - r;
     a = a > 0.0 ? a : 0.0;
     return a < l ? a : l;
-}
-
-// The FP64 register kernel: R = JP / 2 lanes per row (two doubles each),
-// 32 / R rows per warp load, U rows per lane in flight.
-template <int JP, bool FIXED>
-__global__ void __launch_bounds__(256) k_simulate(const SimArgs a, const TermsF64 terms)
-{
-    constexpr int R = JP / 2;                  // lanes per row
-    constexpr int RPW = 32 / R;                // rows per warp load
-    constexpr int U = RPW >= 16 ? 4 : 8;       // rows per lane in flight
-    constexpr int B = RPW * U;                 // events per warp step
-    static_assert(JP % 2 == 0 && R >= 1 && R <= 32, "row layout");
-
-    const int lane = threadIdx.x & 31;
-    const int row = lane / R, col = lane % R;
-    const bool lane_on = row < RPW;
-    LaneTermsF64 lt;
-    lt.load(terms);
-    const double *tab = static_cast<const double *>(a.table);
-
-    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t n_warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-
-    for (int64_t t = warp; t < a.n_trials; t += n_warps) {
-        const int64_t tt = a.trial_begin + t;
-        const int64_t beg = FIXED ? tt * (int64_t)a.k : a.off[tt];
-        const int64_t end = FIXED ? beg + a.k : a.off[tt + 1];
-        double acc = 0.0;
-
-        int32_t nid[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int64_t e = beg + u * RPW + row;
-            nid[u] = (lane_on && e < end) ? __ldcs(a.ids + e) : -1;
-        }
-        for (int64_t s = beg; s < end; s += B) {
-            int32_t id[U];
-#pragma unroll
-            for (int u = 0; u < U; ++u) id[u] = nid[u];
-            if (s + B < end) {
-#pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    const int64_t e = s + B + u * RPW + row;
-                    nid[u] = (lane_on && e < end) ? __ldcs(a.ids + e) : -1;
-                }
-            }
-            double2 v[U];
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                if (id[u] >= 0)
-                    v[u] = __ldg(reinterpret_cast<const double2 *>(tab + (size_t)id[u] * JP) + col);
-                else
-                    v[u] = double2{};
-            }
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const double g = row_sum<R>(lt.part(v[u]), col);
-                const bool lead = col == 0 && id[u] >= 0;
-                acc = add_nn(acc, net_nn(lead ? g : 0.0, lt.occ_r_b, lt.occ_r, lt.occ_l_b));
-            }
-        }
-        const double S = warp_total(acc);
-        if (lane == 0) a.ylt[t] = net_d(S, a.agg_r, a.agg_l);
-    }
 }
 
 // ---------------------------------------------------------------------------
@@ -499,28 +348,6 @@ void launch_staged_fx(const SimArgs &a, const TermsF32 &terms, int num_sms, cuda
             : launch_staged<JP, ACC, true, 1>(a, terms, num_sms, s);
 }
 
-template <int JP, bool FIXED>
-void launch_register64(const SimArgs &a, const TermsF64 &terms, int num_sms, cudaStream_t s)
-{
-    auto kern = k_simulate<JP, FIXED>;
-    const int per_sm = fit_blocks(reinterpret_cast<const void *>(kern), 256, 0);
-    int64_t blocks = (a.n_trials + 7) / 8;
-    const int64_t cap = (int64_t)num_sms * per_sm;
-    if (blocks > cap) blocks = cap;
-    if (blocks < 1) blocks = 1;
-    kern<<<(unsigned)blocks, 256, 0, s>>>(a, terms);
-    ARE_CUDA_TRY(cudaGetLastError());
-}
-
-template <int JP>
-void launch_fx64(const SimArgs &a, const TermsF64 &terms, int num_sms, cudaStream_t s)
-{
-    if (a.off)
-        launch_register64<JP, false>(a, terms, num_sms, s);
-    else
-        launch_register64<JP, true>(a, terms, num_sms, s);
-}
-
 // ---------------------------------------------------------------------------
 // FP32 paths, rows in registers (rows.cuh): a warp takes a contiguous block
 // of the launch's trials.
@@ -535,12 +362,12 @@ __host__ __device__ constexpr int rows_min_blocks(int jp, int u)
 
 template <int JP, int U, int ACC, bool FIXED>
 __global__ void __launch_bounds__(256, rows_min_blocks(JP, U))
-    k_rows(const rows::Trials a, const int64_t n_trials)
+    k_rows(const rows::Trials a, const rows::BodyF32<JP, U, ACC> body, const int64_t n_trials)
 {
     const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    rows::run_trials<JP, U, ACC, FIXED>(a, warp * n_trials / nw, (warp + 1) * n_trials / nw, lane);
+    rows::run_trials<U, FIXED>(a, body, warp * n_trials / nw, (warp + 1) * n_trials / nw, lane);
 }
 
 template <int JP, int U, int ACC, bool FIXED>
@@ -557,13 +384,14 @@ void launch_rows_t(const SimArgs &a, const TermsF32 &tm, int num_sms, cudaStream
     t.off = a.off;
     t.k = a.k;
     t.trial_begin = a.trial_begin;
-    t.table = static_cast<const float *>(a.table);
     t.ylt = a.ylt;
-    t.occ_r = tm.occ_r;
-    t.occ_l = tm.occ_l;
     t.agg_r = a.agg_r;
     t.agg_l = a.agg_l;
-    kern<<<(unsigned)blocks, 256, 0, s>>>(t, a.n_trials);
+    rows::BodyF32<JP, U, ACC> body;
+    body.table = static_cast<const float *>(a.table);
+    body.occ_r = tm.occ_r;
+    body.occ_l = tm.occ_l;
+    kern<<<(unsigned)blocks, 256, 0, s>>>(t, body, a.n_trials);
     ARE_CUDA_TRY(cudaGetLastError());
 }
 
@@ -594,27 +422,15 @@ int launch_fp32(const SimArgs &a, int jp, const TermsF32 &tm, int num_sms, cudaS
 }  // namespace
 
 // FP32: the register-rows kernel unless a.kernel names the staged one (1,
-// or 4 for the compact layout); FP64: the register kernel.
+// or 4 for the compact layout).  (FP64 analyses run in staged64.cu,
+// screen64.cu and rows64.cu.)
 int launch_simulate(const SimArgs &a, are_precision prec, int jp, const TermsF32 *t32,
-                     const TermsF64 *t64, int num_sms, cudaStream_t s)
+                     const TermsF64 *, int num_sms, cudaStream_t s)
 {
     if (a.n_trials <= 0) return 0;
-    if (prec == ARE_FP64) {
-        switch (jp) {
-        case 4: return launch_fx64<4>(a, *t64, num_sms, s), 1;
-        case 8: return launch_fx64<8>(a, *t64, num_sms, s), 1;
-        case 12: return launch_fx64<12>(a, *t64, num_sms, s), 1;
-        case 16: return launch_fx64<16>(a, *t64, num_sms, s), 1;
-        case 20: return launch_fx64<20>(a, *t64, num_sms, s), 1;
-        case 24: return launch_fx64<24>(a, *t64, num_sms, s), 1;
-        case 28: return launch_fx64<28>(a, *t64, num_sms, s), 1;
-        case 32: return launch_fx64<32>(a, *t64, num_sms, s), 1;
-        }
-        throw Error{ARE_EINVAL, "no FP64 simulate kernel for table width " + std::to_string(jp)};
-    }
     if (prec == ARE_FP32_KAHAN) return launch_fp32<ARE_FP32_KAHAN>(a, jp, *t32, num_sms, s);
     if (prec == ARE_FP32_FP64AGG) return launch_fp32<ARE_FP32_FP64AGG>(a, jp, *t32, num_sms, s);
-    throw Error{ARE_EINVAL, "unknown precision"};
+    throw Error{ARE_EINVAL, "no FP32 simulate kernel for this precision"};
 }
 
 }  // namespace are

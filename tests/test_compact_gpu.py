@@ -38,17 +38,18 @@ def ctx(are):
 def pin_staged(are, ctx, L, layer, p):
     """Make the direct layout's analysis of this layer run on the staged
     kernel, with the compact layout's events per lane (2 with Kahan sums,
-    1 with FP64 sums)."""
+    1 with FP64 sums): every single-layer entry of this precision in the
+    tuning table is set to it."""
     are.are_autotune(ctx, [L.layers[layer]], L.yet, p)
     with tempfile.TemporaryDirectory() as d:
         path = os.path.join(d, "t.jsonl")
         are.are_tune_save(ctx, path)
         entries = [json.loads(x) for x in open(path) if x.strip()]
-        key = [e for e in entries if e["key"].startswith(f"p{p}_") and e["key"].endswith("_single")]
-        assert key
-        e = dict(key[0], kernel=1, rows_in_flight=2 if p == 1 else 1)
+        pinned = [dict(e, kernel=1, rows_in_flight=2 if p == 1 else 1) for e in entries
+                  if e["key"].startswith(f"p{p}_") and e["key"].endswith("_single")]
+        assert pinned
         with open(path, "w") as f:
-            f.write(json.dumps(e) + "\n")
+            f.write("".join(json.dumps(e) + "\n" for e in pinned))
         are.are_tune_load(ctx, path)
 
 

@@ -148,9 +148,9 @@ def test_every_kernel_choice(are, ctx, orc, tmp_path, p):
         assert key
         kinds = [1, 2] + ([0] if p != 0 else [3])
         for kind in kinds:
-            for u in ((8,) if (p == 0 and kind == 2) else (1, 2)):
-                e = dict(key[0], kernel=kind, rows_in_flight=u, trials_per_item=3)
-                path.write_text(json.dumps(e) + "\n")
+            for u in (1, 2):
+                path.write_text("".join(json.dumps(dict(e, kernel=kind, rows_in_flight=u,
+                                                        trials_per_item=3)) + "\n" for e in key))
                 are.are_tune_load(ctx, str(path))
                 ok, st = mixed_check(L.simulate(0, p), ref.ylt, trial_bound(wl, 0), RTOL[p])
                 assert ok, (kind, u, st)
@@ -186,7 +186,7 @@ def test_fp64_kernels_with_and_without_share_factors(are, ctx, orc, tmp_path, wi
         key = [e for e in entries if e["key"].startswith("p0_") and e["key"].endswith("_single")]
         assert key
         for kind in (1, 2, 3):
-            path.write_text(json.dumps(dict(key[0], kernel=kind)) + "\n")
+            path.write_text("".join(json.dumps(dict(e, kernel=kind)) + "\n" for e in key))
             are.are_tune_load(ctx, str(path))
             ok, st = mixed_check(L.simulate(0, 0), ref.ylt, trial_bound(wl, 0), RTOL[0])
             assert ok, (kind, st)
