@@ -343,7 +343,8 @@ typedef struct {
  * kernels do, and nothing else; the table is allocated and freed inside the
  * call (against the memory budget).  Every shape of are_ceiling_shape is
  * timed with 2 to 16 rows per lane (or 1 to 4 groups of 32 events) in flight
- * and 3, 4, 6 and 8 blocks per SM (as many as fit), the best of `reps` timed
+ * and 3, 4, 6 and 8 blocks per SM (those that fit, or as many as fit when that
+ * is fewer than 3), the best of `reps` timed
  * passes (1..100) each.  *rows_per_s receives the best rate of all: the bound
  * that the table-row reads put on any analysis kernel for this YET and row
  * size.  shapes (may be NULL) receives up to max_shapes of the shapes timed

@@ -186,8 +186,13 @@ void sweep(const int32_t *ids, int64_t n, const void *table, float *out, int rep
 {
     auto run = [&](int kind, int u, const void *kern, size_t smem, auto launch) {
         const int fit = fit_blocks(kern, kThreads, smem);
-        for (int bps : {3, 4, 6, 8}) {
-            if (bps > fit) break;
+        for (int bps : {3, 4, 6, 8, 0}) {
+            if (bps == 0) {   // a shape that fits fewer than 3 blocks: as many as fit
+                if (fit >= 3) break;
+                bps = fit;
+            } else if (bps > fit) {
+                continue;
+            }
             const int blocks = num_sms * bps;
             const float ms = best_ms([&] { launch(blocks); }, reps, s, a, b);
             launches += (uint64_t)reps + 1;

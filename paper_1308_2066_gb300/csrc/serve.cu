@@ -47,7 +47,7 @@ constexpr int kWidths3[3] = {8, 16, 32};
 constexpr size_t kAlign = 256;
 constexpr int64_t kWaitLimitUs = 120LL * 1000 * 1000;   // one iteration may not take longer
 constexpr double kStagedSlice = 32e6;         // events: a request this large runs on its own kernel
-constexpr double kEventsPerUs = 1.6e5;        // occurrences per microsecond (a table row each), for the aging
+constexpr double kEventsPerUs = 2.4e5;        // occurrences per microsecond (a table row each), for the aging
 
 size_t up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 

@@ -141,7 +141,7 @@ def test_gather_ceiling(are, ctx):
             # every kind of shape was timed, and the best of them is the rate
             assert {k for k, _, _, _ in shapes} == {0, 1, 2}
             assert rate == max(r for _, _, _, r in shapes)
-            assert all(b >= 3 for _, _, b, _ in shapes)
+            assert all(b >= 1 for _, _, b, _ in shapes)
         with pytest.raises(are.AreError):
             are.are_gather_ceiling(ctx, h, 48, 0, yet.n_trials)
         with pytest.raises(are.AreError):
