@@ -12,27 +12,31 @@
  * "Basic Algorithm for Aggregate Risk Analysis" box of Section II-B gives the
  * analysis stage, Table I the four layer terms, Section II-C the output.
  *
- * For one layer and each trial with events e_1..e_k in stored order it takes
- * the algorithm's steps in the paper's order:
- *   step 1  for every ELT j of the layer, x[d] = loss of e_d in ELT j (0 if
- *           absent) -- looked up by binary search in a sorted private copy of
- *           the ELT, not through a direct-access table;
- *   step 2  l[d] = share_j * min(max(fx_j * x[d] - D_j, 0), Lim_j), then
- *           lo[d] += l[d], ELTs taken in layer order;
- *   step 3  lo[d] = min(max(lo[d] - OccR, 0), OccL);
- *   step 4  lo[d] = lo[1] + ... + lo[d] (running sum S_d),
- *           lo[d] = min(max(lo[d] - AggR, 0), AggL)  (A_d),
- *           lo[d] = A_d - A_{d-1} (marginal m_d, A_0 = 0),
- *           lr = m_1 + ... + m_k.
+ * What it computes, for one layer and each trial with events e_1..e_k in
+ * stored order (written from the definitions of Sections II-A to II-C):
+ *   - an event's loss in ELT j is its entry there (0 if the ELT has none),
+ *     looked up by binary search in a sorted private copy of the ELT, not
+ *     through a direct-access table;
+ *   - its loss net of ELT j's financial terms is
+ *     f_j(x) = share_j * min(max(fx_j * x - D_j, 0), Lim_j);
+ *   - the event loss g_d is the sum of f_j over the layer's ELTs, added in
+ *     layer order;
+ *   - the occurrence loss is o_d = min(max(g_d - OccR, 0), OccL) (Table I);
+ *   - the running total S_d = o_1 + ... + o_d, its aggregate-clamped value
+ *     A_d = min(max(S_d - AggR, 0), AggL) (Table I), and the marginal
+ *     m_d = A_d - A_{d-1} with A_0 = 0;
+ *   - the trial loss A_k, beside S_k and the literal sum of the marginals.
+ * Each trial is one pass over its occurrences in stored order.
  *
  * Readings where the paper is silent (each also listed in the design notes):
- *   - the financial terms I of an ELT are (fx, D, Lim, share) applied as in
- *     step 2 above;
- *   - the de-cumulation uses the clamped cumulative values of the step
- *     before it (a backward loop), with A_0 = 0;
- *   - the trial loss written to the YLT is A_k; because every lo[d] >= 0 the
- *     marginals telescope and lr equals A_k up to rounding, and lr is
- *     returned beside it as a self-check;
+ *   - the financial terms I of an ELT are (fx, D, Lim, share) applied as
+ *     f_j above;
+ *   - the marginal of an occurrence is taken between the clamped running
+ *     totals A_d and A_{d-1} (the de-cumulation of the paper's step 4 read
+ *     with the clamped cumulative values), with A_0 = 0;
+ *   - the trial loss written to the YLT is A_k; because every o_d >= 0 the
+ *     marginals telescope and their literal sum equals A_k up to rounding;
+ *     it is returned beside A_k as a self-check;
  *   - a trial with no events has loss 0;
  *   - PML at return period RP is the m-th largest trial loss with
  *     m = ceil(N / RP); TVaR at level a is the mean of the m largest trial
@@ -122,7 +126,7 @@ static double net_of(double v, double r, double l)
 }
 
 /* ------------------------------------------------------------------------ */
-/* Analysis stage for one trial.                                             */
+/* Analysis stage for one trial (Section II-B).                              */
 /* ------------------------------------------------------------------------ */
 
 typedef struct {
@@ -135,59 +139,44 @@ typedef struct {
 typedef struct {
     double ylt;    /* A_k: trial loss net of all terms */
     double s;      /* S_k: cumulative occurrence loss before aggregate terms */
-    double gross;  /* sum over d and j of fx_j * x[d][j] */
+    double gross;  /* sum over the occurrences and ELTs of fx_j * x (event by event) */
     double lr;     /* literal sum of the marginals m_d */
-    double occ_max;/* max over d of the occurrence loss lo[d] after step 3 */
+    double occ_max;/* largest occurrence loss o_d */
 } or_trial_out;
 
-/* lo, x, l: scratch of at least k doubles.  marg: NULL or k doubles. */
-static void simulate_trial(const or_layer *L, const int32_t *ev, int64_t k,
-                           double *lo, double *x, double *l, double *marg,
+/* One trial's occurrences in stored order.  marg: NULL or k doubles. */
+static void simulate_trial(const or_layer *L, const int32_t *ev, int64_t k, double *marg,
                            or_trial_out *out)
 {
-    double gross = 0.0;
-    for (int64_t d = 0; d < k; ++d)
-        lo[d] = 0.0;
-
-    /* step 1 and step 2, ELT by ELT in layer order */
-    for (int32_t j = 0; j < L->n_elts; ++j) {
-        for (int64_t d = 0; d < k; ++d)
-            x[d] = L->elt[j].n ? dict_lookup(&L->elt[j], ev[d]) : 0.0;
-        for (int64_t d = 0; d < k; ++d) {
-            double conv = L->fx[j] * x[d];
-            gross += conv;
-            l[d] = L->share[j] * net_of(conv, L->ded[j], L->lim[j]);
-        }
-        for (int64_t d = 0; d < k; ++d)
-            lo[d] += l[d];
-    }
-
-    /* step 3: occurrence terms, each occurrence on its own */
-    double occ_max = 0.0;
+    double gross = 0.0, occ_max = 0.0, lr = 0.0;
+    double S = 0.0;     /* running total of the occurrence losses */
+    double A = 0.0;     /* its aggregate-clamped value */
+    double prev = 0.0;  /* the aggregate-clamped total before this occurrence */
     for (int64_t d = 0; d < k; ++d) {
-        lo[d] = net_of(lo[d], L->occ_r, L->occ_l);
-        if (lo[d] > occ_max)
-            occ_max = lo[d];
+        /* the event loss: each ELT's entry net of its financial terms,
+           added over the ELTs in layer order */
+        double g = 0.0;
+        for (int32_t j = 0; j < L->n_elts; ++j) {
+            const double x = L->elt[j].n ? dict_lookup(&L->elt[j], ev[d]) : 0.0;
+            const double conv = L->fx[j] * x;
+            gross += conv;
+            g += L->share[j] * net_of(conv, L->ded[j], L->lim[j]);
+        }
+        /* the occurrence loss (occurrence terms of Table I) */
+        const double o = net_of(g, L->occ_r, L->occ_l);
+        if (o > occ_max)
+            occ_max = o;
+        /* the running total, its aggregate terms, the marginal */
+        S += o;
+        A = net_of(S, L->agg_r, L->agg_l);
+        const double m = A - prev;
+        prev = A;
+        if (marg)
+            marg[d] = m;
+        lr += m;
     }
-
-    /* step 4: running sum, aggregate terms, de-cumulation, trial total */
-    for (int64_t d = 1; d < k; ++d)
-        lo[d] = lo[d - 1] + lo[d];
-    double s = k ? lo[k - 1] : 0.0;
-    for (int64_t d = 0; d < k; ++d)
-        lo[d] = net_of(lo[d], L->agg_r, L->agg_l);
-    double ylt = k ? lo[k - 1] : 0.0;
-    for (int64_t d = k - 1; d >= 1; --d)
-        lo[d] = lo[d] - lo[d - 1];
-    double lr = 0.0;
-    for (int64_t d = 0; d < k; ++d)
-        lr += lo[d];
-    if (marg)
-        for (int64_t d = 0; d < k; ++d)
-            marg[d] = lo[d];
-
-    out->ylt = ylt;
-    out->s = s;
+    out->ylt = A;
+    out->s = S;
     out->gross = gross;
     out->lr = lr;
     out->occ_max = occ_max;
@@ -229,16 +218,10 @@ int or_simulate(int64_t n_trials, const int64_t *offsets, int32_t k_fixed,
     for (int32_t j = 0; j < n_elts && rc == OR_OK; ++j)
         rc = dict_build(&dicts[j], elt_off[j + 1] - elt_off[j], elt_ids + elt_off[j],
                         elt_loss + elt_off[j]);
-    int64_t kmax = 0;
     for (int64_t s = 0; s < n_sel && rc == OR_OK; ++s) {
         int64_t t = sel ? sel[s] : s;
-        if (t < 0 || t >= n_trials) {
+        if (t < 0 || t >= n_trials)
             rc = OR_EINVAL;
-            break;
-        }
-        int64_t k = offsets ? offsets[t + 1] - offsets[t] : k_fixed;
-        if (k > kmax)
-            kmax = k;
     }
     if (rc == OR_OK) {
         or_layer L = {n_elts, dicts, fx, ded, lim, share, occ_r, occ_l, agg_r, agg_l};
@@ -248,35 +231,20 @@ int or_simulate(int64_t n_trials, const int64_t *offsets, int32_t k_fixed,
 #else
         n_threads = 1;
 #endif
-        int fail = 0;
-#pragma omp parallel num_threads(n_threads)
-        {
-            double *buf = (double *)malloc(sizeof(double) * 3 * (size_t)(kmax > 0 ? kmax : 1));
-            if (!buf) {
-#pragma omp atomic write
-                fail = 1;
-            }
-#pragma omp for schedule(dynamic, 16)
-            for (int64_t s = 0; s < n_sel; ++s) {
-                if (!buf)
-                    continue;
-                int64_t t = sel ? sel[s] : s;
-                int64_t b = offsets ? offsets[t] : t * (int64_t)k_fixed;
-                int64_t k = offsets ? offsets[t + 1] - b : k_fixed;
-                or_trial_out o;
-                simulate_trial(&L, ids + b, k, buf, buf + kmax, buf + 2 * kmax,
-                               marg ? marg + marg_off[s] : NULL, &o);
-                if (ylt) ylt[s] = o.ylt;
-                if (s_total) s_total[s] = o.s;
-                if (gross) gross[s] = o.gross;
-                if (lr_literal) lr_literal[s] = o.lr;
-                if (occ_max) occ_max[s] = o.occ_max;
-                if (n_events) n_events[s] = k;
-            }
-            free(buf);
+#pragma omp parallel for num_threads(n_threads) schedule(dynamic, 16)
+        for (int64_t s = 0; s < n_sel; ++s) {
+            int64_t t = sel ? sel[s] : s;
+            int64_t b = offsets ? offsets[t] : t * (int64_t)k_fixed;
+            int64_t k = offsets ? offsets[t + 1] - b : k_fixed;
+            or_trial_out o;
+            simulate_trial(&L, ids + b, k, marg ? marg + marg_off[s] : NULL, &o);
+            if (ylt) ylt[s] = o.ylt;
+            if (s_total) s_total[s] = o.s;
+            if (gross) gross[s] = o.gross;
+            if (lr_literal) lr_literal[s] = o.lr;
+            if (occ_max) occ_max[s] = o.occ_max;
+            if (n_events) n_events[s] = k;
         }
-        if (fail)
-            rc = OR_ENOMEM;
     }
     for (int32_t j = 0; j < n_elts; ++j)
         free(dicts[j].p);

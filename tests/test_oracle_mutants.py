@@ -16,19 +16,19 @@ SRC = os.path.join(ROOT, "oracle", "oracle.c")
 MUTANTS = {
     "deductible_dropped": ("net_of(conv, L->ded[j], L->lim[j])", "net_of(conv, 0.0, L->lim[j])"),
     "elt_limit_dropped": ("net_of(conv, L->ded[j], L->lim[j])", "net_of(conv, L->ded[j], 1e300)"),
-    "share_dropped": ("l[d] = L->share[j] * net_of(", "l[d] = net_of("),
-    "fx_dropped": ("double conv = L->fx[j] * x[d];", "double conv = x[d];"),
+    "share_dropped": ("g += L->share[j] * net_of(", "g += net_of("),
+    "fx_dropped": ("const double conv = L->fx[j] * x;", "const double conv = x;"),
     "retention_sign": ("double a = v - r;", "double a = v + r;"),
-    "occ_terms_swapped": ("net_of(lo[d], L->occ_r, L->occ_l)", "net_of(lo[d], L->occ_l, L->occ_r)"),
-    "occ_step_skipped": ("lo[d] = net_of(lo[d], L->occ_r, L->occ_l);", "(void)0;"),
-    "cumulative_sum_dropped": ("lo[d] = lo[d - 1] + lo[d];", "lo[d] = lo[d];"),
-    "agg_limit_from_occ": ("net_of(lo[d], L->agg_r, L->agg_l)", "net_of(lo[d], L->agg_r, L->occ_l)"),
-    "ylt_before_agg_terms": ("double ylt = k ? lo[k - 1] : 0.0;", "double ylt = s;"),
-    "decumulate_forward_in_place": ("for (int64_t d = k - 1; d >= 1; --d)", "for (int64_t d = 1; d < k; ++d)"),
+    "occ_terms_swapped": ("net_of(g, L->occ_r, L->occ_l)", "net_of(g, L->occ_l, L->occ_r)"),
+    "occ_step_skipped": ("const double o = net_of(g, L->occ_r, L->occ_l);", "const double o = g;"),
+    "cumulative_sum_dropped": ("S += o;", "S = o;"),
+    "agg_limit_from_occ": ("net_of(S, L->agg_r, L->agg_l)", "net_of(S, L->agg_r, L->occ_l)"),
+    "ylt_before_agg_terms": ("out->ylt = A;", "out->ylt = S;"),
+    "decumulate_forward_in_place": ("prev = A;", "prev = m;"),
     "lookup_wrong_slot": ("return t->p[mid].loss;", "return t->p[lo].loss;"),
     "lookup_wrong_elt": ("dict_lookup(&L->elt[j], ev[d])", "dict_lookup(&L->elt[0], ev[d])"),
     "last_elt_skipped": ("for (int32_t j = 0; j < L->n_elts; ++j) {", "for (int32_t j = 0; j + 1 < L->n_elts; ++j) {"),
-    "gross_before_fx": ("gross += conv;", "gross += x[d];"),
+    "gross_before_fx": ("gross += conv;", "gross += x;"),
     "pml_rank_off_by_one": ("pml[r] = v[m - 1];", "pml[r] = v[m < n ? m : m - 1];"),
     "tvar_divisor": ("tvar[r] = acc / (double)m;", "tvar[r] = acc / (double)(m + 1);"),
     "level_rank_complement": ("int64_t q = 1000000000 - a_nano;", "int64_t q = a_nano;"),
