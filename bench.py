@@ -94,6 +94,7 @@ def hbm_peak():
 # when one of them changes).
 KERNEL_SOURCES = {
     "k_rows": ["simulate.cu", "rows.cuh", "are_internal.cuh"],
+    "k_rows_packed": ["simulate.cu", "rows.cuh", "are_internal.cuh"],
     "k_rows64": ["rows64.cu", "rows.cuh", "fixed.cuh", "are_internal.cuh"],
     "k_simulate_staged": ["simulate.cu", "are_internal.cuh"],
     "k_staged": ["staged.cuh", "staged64.cu", "are_internal.cuh"],
@@ -145,7 +146,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "100", "-i", str(self.device)],
+                 "-lms", "25", "-i", str(self.device)],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
@@ -220,29 +221,34 @@ def kernel_key(prec: int, J: int, tuned=None) -> str:
             return f"k_screen64<{8 if J <= 8 else 16 if J <= 16 else 32},fixed>"
         if kind == 1:
             return f"k_staged<double,{jp},fixed,ylt>"
-        return f"k_rows64<{8 if J <= 16 else 16},{t.get('rows_in_flight', 2)},fixed>"
+        return f"k_rows64<8,{t.get('rows_in_flight', 2)},fixed>"
     jp = 8 if J <= 8 else 16 if J <= 16 else 32
     kind = t.get("kernel", 2)
     u = t.get("rows_in_flight", 2)
     if kind == 0:
         return f"k_sim_items<{jp},{u},{prec},fixed>"
     if kind == 2:
+        if jp == 32:
+            return f"k_rows_packed<{u},{prec},fixed>"
         return f"k_rows<{jp},{u},{prec},fixed>"
     return f"k_simulate_staged<{jp},{prec},fixed,epl{2 if u == 2 else 1}>"
 
 
 def row_bytes(J: int, prec, tuned=None) -> int:
-    """Bytes of one table row as the analysis kernel reads it: the FP32
-    table's row; for FP64 the packed row (register-rows kernel, the FP32
-    table's size), the FP32 screen's row (screened kernel) or the dense FP64
-    row (staged kernel)."""
+    """Bytes of one table row as the analysis kernel reads it: the dense
+    FP32 row, or for more than 16 ELTs the packed FP32 row (register-rows
+    kernel); for FP64 the packed row (register-rows kernel), the FP32
+    screen's row (screened kernel) or the dense FP64 row (staged kernel)."""
     fp32_row = 32 if J <= 8 else 64 if J <= 16 else 128
+    kind = (tuned or {}).get("kernel", 2)
     if prec == 0:
-        kind = (tuned or {}).get("kernel", 2)
         if kind == 1:
             return math.ceil(J / 4) * 32
         if kind == 2:
-            return 64 if J <= 16 else 128
+            return 64
+        return fp32_row
+    if kind == 2 and J > 16:
+        return 64
     return fp32_row
 
 
@@ -536,7 +542,8 @@ def portfolio_kernel_name(tuned, prec) -> str:
         return (f"k_sim_items<jp,{u},{prec},ragged>: one persistent launch per table width, "
                 f"{(tuned or {}).get('trials_per_item')} trials per work item")
     if kind == 2:
-        return f"k_rows<jp,{u},{prec},ragged>: one launch per layer, back to back in the graph"
+        return (f"k_rows<jp,{u},{prec},ragged> (k_rows_packed<{u},{prec},ragged> for layers of more than "
+                f"16 ELTs): one launch per layer, back to back in the graph")
     return f"k_simulate_staged<jp,{prec},ragged,epl{u}>: one launch per layer, back to back in the graph"
 
 
@@ -804,7 +811,7 @@ def run_precision_stress(args):
 # serving: Poisson stream of pricing requests over a resident YET and ELT pool
 # ---------------------------------------------------------------------------
 
-def serve_stream(are, ctx, hs, reqs, one_at_a_time, prec, k, folded=False):
+def serve_stream(are, ctx, hs, reqs, one_at_a_time, prec, k, folded=False, least_work_first=False):
     """Submit each request at its arrival time, collect every result; returns
     per-request latencies (ms) and the wall time from first submit to last result."""
     import queue
@@ -812,7 +819,7 @@ def serve_stream(are, ctx, hs, reqs, one_at_a_time, prec, k, folded=False):
     out = []
     are.are_server_start(ctx, hs["yet"], max_inflight=32, max_pending=100000,
                          arena_bytes=6 << 30, one_at_a_time=one_at_a_time, precision=prec,
-                         folded=folded)
+                         folded=folded, least_work_first=least_work_first)
 
     def collect():
         while True:
@@ -873,8 +880,11 @@ def serving_record(are, torch, prec, rates, seconds_per_rate, min_requests=200,
             batched, _ = serve_stream(are, ctx, hs, reqs, False, prec, y.k)
             batched["gpu_launches"] = are.are_launch_count(ctx) - l0
             single, _ = serve_stream(are, ctx, hs, reqs, True, prec, y.k)
+            lwf, _ = serve_stream(are, ctx, hs, reqs, False, prec, y.k, least_work_first=True)
+            lwf["what"] = "continuous batching, the budget to the least remaining work first"
             row = {"continuous_batching": batched, "one_request_per_launch": single,
-                   "p99_batched_over_single": round(batched["p99_ms"] / single["p99_ms"], 4)}
+                   "p99_batched_over_single": round(batched["p99_ms"] / single["p99_ms"], 4),
+                   "least_work_first": lwf}
             if folded:
                 f, _ = serve_stream(are, ctx, hs, reqs, False, prec, y.k, folded=True)
                 f["what"] = ("variant: continuous batching on folded tables (FP64 occurrence loss "

@@ -235,11 +235,14 @@ ARE_API are_status are_simulate_portfolio(are_ctx *ctx, const int32_t *layers, i
 /* The launch configuration the autotuner picked for one kind of work. */
 typedef struct {
     int32_t kernel;          /* 0 persistent work items, 1 staged rows (one event per lane),
-                                2 register rows (FP32: rows read straight into registers by
-                                jp/8 lanes each; FP64: one warp per trial), 3 (FP64) staged
-                                rows of an FP32 screen with the marked entries read from
-                                the FP64 table */
-    int32_t rows_in_flight;  /* FP32 register rows and persistent kernel: groups of 32 events
+                                2 register rows (rows read straight into registers by a
+                                warp per block of trials; FP32: the dense row of up to 16
+                                ELTs, jp/8 lanes each, or for more ELTs a packed 64-byte row
+                                of the non-zero terms; FP64: a packed 64-byte row of the
+                                non-zero terms, exact trial sums), 3 (FP64) staged rows of
+                                an FP32 screen with the marked entries read from the FP64
+                                table */
+    int32_t rows_in_flight;  /* register rows and persistent kernel: groups of 32 events
                                 per batch, 1 or 2; staged kernel: events per lane per
                                 batch, 1 or 2 */
     int32_t trials_per_item; /* trials per work item (persistent kernel) */
@@ -389,11 +392,14 @@ ARE_API are_status are_risk_measures_batch(are_ctx *ctx, const double *const *yl
  * resident YET and the context's resident ELTs.  A scheduler thread inside
  * the library admits queued requests while request slots and arena memory
  * are free, hands each iteration's budget of events_per_launch to the
- * admitted requests in order of least remaining work (so few tables are
- * live per launch and short requests overtake long ones), and runs all
- * slices of an iteration in one persistent launch; a request arriving while
- * others run joins at the next iteration.  When a request's last slice is done its PML/TVaR are
- * selected and its result posted.  All device waits are bounded. */
+ * admitted requests in arrival order (or, with least_work_first, in order
+ * of least remaining work less the time waited, so short requests overtake
+ * long ones), and runs the slices of small requests in one persistent
+ * launch and those of large ones on the single-layer kernel; a request
+ * arriving while others run joins at the next iteration, and the next
+ * iteration is always queued behind the running one.  When a request's last
+ * slice is done its PML/TVaR are selected and its result posted.  All
+ * device waits are bounded. */
 typedef struct {
     int32_t max_inflight;      /* requests admitted at once, 1..256 */
     int32_t max_pending;       /* queued requests; a submit beyond is ARE_EBUSY */
@@ -407,6 +413,10 @@ typedef struct {
                                   occurrence loss per catalog event, exact trial sums, one
                                   lookup per occurrence -- the variant of are_simulate_folded);
                                   precision is then not used */
+    int32_t least_work_first;  /* 0: the budget goes to the admitted requests in arrival order
+                                  (the lowest tail latency when request sizes are bounded);
+                                  1: in order of least remaining work less the time waited
+                                  (short requests overtake long ones) */
 } are_server_cfg;
 
 /* One pricing request: a layer of the context's ELTs with its own layer terms,

@@ -60,7 +60,8 @@ class ServerCfg(C.Structure):
     _fields_ = [("max_inflight", C.c_int32), ("max_pending", C.c_int32),
                 ("arena_bytes", C.c_size_t), ("events_per_launch", C.c_int64),
                 ("trials_per_item", C.c_int32), ("one_at_a_time", C.c_int32),
-                ("precision", C.c_int), ("stall_us", C.c_int64), ("folded", C.c_int32)]
+                ("precision", C.c_int), ("stall_us", C.c_int64), ("folded", C.c_int32),
+                ("least_work_first", C.c_int32)]
 
 
 class Request(C.Structure):
@@ -416,9 +417,10 @@ def are_server_start(ctx, yet: int, max_inflight: int = 32, max_pending: int = 4
                      arena_bytes: int = 4 << 30, events_per_launch: int = 0,
                      trials_per_item: int = 0, one_at_a_time: bool = False,
                      precision: int = ARE_FP32_KAHAN, stall_us: int = 0,
-                     folded: bool = False) -> None:
+                     folded: bool = False, least_work_first: bool = False) -> None:
     cfg = ServerCfg(max_inflight, max_pending, arena_bytes, events_per_launch, trials_per_item,
-                    int(bool(one_at_a_time)), precision, stall_us, int(bool(folded)))
+                    int(bool(one_at_a_time)), precision, stall_us, int(bool(folded)),
+                    int(bool(least_work_first)))
     _check(ctx, lib().are_server_start(ctx, int(yet), C.byref(cfg)))
 
 

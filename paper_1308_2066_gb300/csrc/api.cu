@@ -194,10 +194,10 @@ void free_table(are_ctx *ctx, Table &t)
     t = Table{};
 }
 
-void free_packed(are_ctx *ctx, Packed64 &p)
+void free_packed(are_ctx *ctx, Packed &p)
 {
     dfree(ctx, p.d, p.bytes);
-    p = Packed64{};
+    p = Packed{};
 }
 
 void free_folded(are_ctx *ctx, Folded &f)
@@ -307,17 +307,13 @@ Table &build_screen(are_ctx *ctx, Layer &L, int32_t catalog, cudaStream_t s)
     return u;
 }
 
-// The packed FP64 rows of the layer's FP64 table (which must be built for
-// `catalog`), read by the FP64 register-rows kernel.
-Packed64 &build_packed(are_ctx *ctx, Layer &L, int32_t catalog, cudaStream_t s)
+// (Re)allocates packed table p for `catalog` rows of `row_bytes` and an
+// overflow of `ovf_bytes`.
+void size_packed(are_ctx *ctx, Layer &L, Packed &p, int32_t catalog, int rw, size_t row_bytes,
+                 size_t ovf_bytes)
 {
-    Packed64 &p = L.p64;
-    const int rw = packed_row_words((int)L.elts.size());
-    int64_t entries = 0;
-    for (int32_t h : L.elts) entries += ctx->elts.at(h).n;
-    ARE_CHECK(entries < (1LL << 32), ARE_EINVAL, "a layer's ELTs hold 2^32 or more entries");
-    const size_t rows_bytes = (size_t)catalog * rw * sizeof(unsigned long long);
-    const size_t need = rows_bytes + 256 + sizeof(double) * (size_t)std::max<int64_t>(entries, 1);
+    const size_t rows_bytes = (size_t)catalog * row_bytes;
+    const size_t need = rows_bytes + 256 + std::max<size_t>(ovf_bytes, 8);
     if (p.d && (p.catalog != catalog || p.rw != rw || p.bytes < need)) free_packed(ctx, p);
     if (!p.d) {
         ++L.generation;
@@ -327,18 +323,56 @@ Packed64 &build_packed(are_ctx *ctx, Layer &L, int32_t catalog, cudaStream_t s)
         p.catalog = catalog;
         p.rw = rw;
     }
+}
+
+int64_t layer_entries(are_ctx *ctx, const Layer &L)
+{
+    int64_t entries = 0;
+    for (int32_t h : L.elts) entries += ctx->elts.at(h).n;
+    ARE_CHECK(entries < (1LL << 32), ARE_EINVAL, "a layer's ELTs hold 2^32 or more entries");
+    return entries;
+}
+
+// The packed FP64 rows of the layer's FP64 table (which must be built for
+// `catalog`), read by the FP64 register-rows kernel.
+Packed &build_packed64(are_ctx *ctx, Layer &L, int32_t catalog, cudaStream_t s)
+{
+    Packed &p = L.p64;
+    const int rw = packed_row_words((int)L.elts.size());
+    size_packed(ctx, L, p, catalog, rw, rw * sizeof(unsigned long long),
+                sizeof(double) * (size_t)layer_entries(ctx, L));
     const Table &t = L.t64;
-    ctx->launches += launch_pack64(static_cast<const double *>(t.d), t.jp, catalog, rw, p.rows(), p.ovf(),
+    ctx->launches += launch_pack64(static_cast<const double *>(t.d), t.jp, catalog, rw,
+                                   static_cast<unsigned long long *>(p.rows()),
+                                   static_cast<double *>(p.ovf()), p.used(), ctx->num_sms, s);
+    return p;
+}
+
+// The packed FP32 rows of a layer of more than 16 ELTs (its FP32 table must
+// be built for `catalog`), read by the FP32 register-rows kernel.
+Packed &build_packed32(are_ctx *ctx, Layer &L, int32_t catalog, cudaStream_t s)
+{
+    Packed &p = L.p32;
+    size_packed(ctx, L, p, catalog, 16, 16 * sizeof(float), sizeof(float) * (size_t)layer_entries(ctx, L));
+    const Table &t = L.t32;
+    ctx->launches += launch_pack32(static_cast<const float *>(t.d), t.jp, catalog,
+                                   static_cast<uint32_t *>(p.rows()), static_cast<float *>(p.ovf()),
                                    p.used(), ctx->num_sms, s);
     return p;
 }
 
-// The tables beside the FP64 table that an FP64 kernel choice reads: the
-// packed rows (register rows, kernel 2) or the FP32 screen (kernel 3).
-// `fresh`: the FP64 table was just rebuilt.
-void ensure_fp64_aux(are_ctx *ctx, Layer &L, int32_t catalog, int kernel, bool fresh, cudaStream_t s)
+// The tables beside a layer's table that a kernel choice reads.  FP64: the
+// packed rows (register rows, kernel 2) or the FP32 screen (kernel 3); FP32:
+// the packed rows of a layer of more than 16 ELTs (register rows, kernel 2).
+// `fresh`: the layer's table was just rebuilt.
+void ensure_aux(are_ctx *ctx, Layer &L, int32_t catalog, bool fp32, int kernel, bool fresh, cudaStream_t s)
 {
-    if (kernel == 2 && (fresh || !L.p64.d || L.p64.catalog != catalog)) build_packed(ctx, L, catalog, s);
+    if (fp32) {
+        if (kernel == 2 && L.t32.jp == 32 && (fresh || !L.p32.d || L.p32.catalog != catalog))
+            build_packed32(ctx, L, catalog, s);
+        return;
+    }
+    if (kernel == 2 && (fresh || !L.p64.d || L.p64.catalog != catalog)) build_packed64(ctx, L, catalog, s);
     if (kernel == 3 && (fresh || !L.t32u.d || L.t32u.catalog != catalog)) build_screen(ctx, L, catalog, s);
 }
 
@@ -354,7 +388,7 @@ void ensure_tables(are_ctx *ctx, Layer &L, const Yet &y, are_precision precision
     const Table &t = fp32 ? L.t32 : L.t64;
     const bool fresh = rebuild || !t.d || t.catalog != catalog;
     if (fresh) build_table(ctx, L, catalog, fp32, s);
-    if (!fp32) ensure_fp64_aux(ctx, L, catalog, tuned(ctx, precision, y, t.jp, false).kernel, fresh, s);
+    ensure_aux(ctx, L, catalog, fp32, tuned(ctx, precision, y, t.jp, false).kernel, fresh, s);
 }
 
 Layer &layer_of(are_ctx *ctx, int32_t h)
@@ -493,6 +527,12 @@ int run_single(are_ctx *ctx, const Layer &L, const Yet &y, int64_t trial_begin, 
     TermsF64 t64;
     fill_terms(L, t32, t64);
     a.n_elts = (int32_t)L.elts.size();
+    if (fp32 && !compact && te.kernel == 2 && t.jp == 32 && L.p32.d && L.p32.catalog == y.catalog) {
+        a.table = L.p32.rows();   // register rows over the packed FP32 rows
+        a.table2 = L.p32.ovf();
+        a.kernel = 5;
+        return launch_simulate(a, precision, t.jp, &t32, &t64, ctx->num_sms, s);
+    }
     if (compact) {   // the staged kernel, through the row index
         a.table = L.comp.rows();
         a.table2 = L.comp.row_of();
@@ -653,16 +693,16 @@ void check_multi_args(are_ctx *ctx, const int32_t *layers, int32_t n_layers, con
     }
 }
 
-// Every layer's table; FP64 also the aux table of `fp64_kernel` (0: none).
+// Every layer's table and the tables beside it that `kernel` reads (0: none).
 void ensure_tables(are_ctx *ctx, const int32_t *layers, int32_t n_layers, const Yet &y, bool fp32,
-                   cudaStream_t s, int fp64_kernel = 0)
+                   cudaStream_t s, int kernel = 0)
 {
     for (int32_t i = 0; i < n_layers; ++i) {
         Layer &L = layer_of(ctx, layers[i]);
         const Table &t = fp32 ? L.t32 : L.t64;
         const bool fresh = !t.d || t.catalog != y.catalog;
         if (fresh) build_table(ctx, L, y.catalog, fp32, s);
-        if (!fp32) ensure_fp64_aux(ctx, L, y.catalog, fp64_kernel, fresh, s);
+        ensure_aux(ctx, L, y.catalog, fp32, kernel, fresh, s);
     }
 }
 
@@ -747,6 +787,7 @@ are_status are_destroy(are_ctx *ctx)
             free_table(ctx, kv.second.t64);
             free_table(ctx, kv.second.t32u);
             free_packed(ctx, kv.second.p64);
+            free_packed(ctx, kv.second.p32);
             free_folded(ctx, kv.second.fold);
             free_compact(ctx, kv.second.comp);
         }
@@ -998,6 +1039,7 @@ are_status are_free_layer(are_ctx *ctx, int32_t h)
         free_table(ctx, L.t64);
         free_table(ctx, L.t32u);
         free_packed(ctx, L.p64);
+        free_packed(ctx, L.p32);
         free_folded(ctx, L.fold);
         free_compact(ctx, L.comp);
         for (int32_t e : L.elts) ctx->elts[e].users--;
@@ -1411,7 +1453,7 @@ are_status are_simulate_portfolio(are_ctx *ctx, const int32_t *layers, int32_t n
         CallStream cs(ctx, stream);
         const bool fp32 = precision != ARE_FP64;
         const int k = tuned(ctx, precision, y, max_width(ctx, layers, n_layers, fp32), n_layers > 1).kernel;
-        ensure_tables(ctx, layers, n_layers, y, fp32, cs.s, fp32 ? 0 : k);
+        ensure_tables(ctx, layers, n_layers, y, fp32, cs.s, k);
         const std::vector<int32_t> lv(layers, layers + n_layers);
         const std::vector<double *> yv(ylts, ylts + n_layers);
         std::vector<uint64_t> gens;
@@ -1556,8 +1598,8 @@ are_status are_autotune(are_ctx *ctx, const int32_t *layers, int32_t n_layers, i
         check_multi_args(ctx, layers, n_layers, y, 0, y.n_trials, nullptr);
         CallStream cs(ctx, stream);
         const bool fp32 = precision != ARE_FP64;
-        ensure_tables(ctx, layers, n_layers, y, fp32, cs.s, fp32 ? 0 : 2);   // FP64: packed rows
-        if (!fp32) ensure_tables(ctx, layers, n_layers, y, fp32, cs.s, 3);  // and the screen
+        ensure_tables(ctx, layers, n_layers, y, fp32, cs.s, 2);              // packed rows
+        if (!fp32) ensure_tables(ctx, layers, n_layers, y, fp32, cs.s, 3);  // FP64: the screen
         const bool multi = n_layers > 1;
         const int jp = max_width(ctx, layers, n_layers, fp32);
         const std::string key = tune_key(precision, y, jp, multi);

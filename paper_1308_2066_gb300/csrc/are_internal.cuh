@@ -118,22 +118,27 @@ struct Compact {
     float *rows() const { return reinterpret_cast<float *>(static_cast<char *>(d) + rows_off); }
 };
 
-// Packed FP64 table of one layer (built from t64 by launch_pack64): catalog
-// rows of rw 64-bit words -- the mask of the non-zero terms and an overflow
-// offset, then the non-zero terms in column order -- a counter and the
-// overflow terms, in one allocation laid out [rows | counter (256 B) | ovf].
-struct Packed64 {
+// Packed table of one layer: catalog rows of 64 or 128 bytes holding each
+// event's non-zero terms in column order behind a header (the column mask
+// and an overflow offset), a counter and the overflow terms, in one
+// allocation laid out [rows | counter (256 B) | overflow].  FP64 (built from
+// t64 by launch_pack64): rw = 8 64-bit words per row, the header in word 0,
+// up to 7 terms inline and every term of a longer row in the overflow.
+// FP32 (built from t32 by launch_pack32, for layers of more than 16 ELTs):
+// 16 32-bit words, the mask in word 0 and the offset in word 1, up to 14
+// terms inline and the rest of a longer row in the overflow.
+struct Packed {
     int32_t catalog = -1;
     int rw = 0;
     void *d = nullptr;
     size_t bytes = 0;
     size_t rows_bytes = 0;
-    unsigned long long *rows() const { return static_cast<unsigned long long *>(d); }
+    void *rows() const { return d; }
     unsigned long long *used() const
     {
         return reinterpret_cast<unsigned long long *>(static_cast<char *>(d) + rows_bytes);
     }
-    double *ovf() const { return reinterpret_cast<double *>(static_cast<char *>(d) + rows_bytes + 256); }
+    void *ovf() const { return static_cast<char *>(d) + rows_bytes + 256; }
 };
 
 struct Layer {
@@ -141,7 +146,8 @@ struct Layer {
     are_layer_terms terms{};
     Table t32, t64;
     Table t32u;              // FP32 screen of t64: its values rounded up
-    Packed64 p64;            // packed FP64 rows of t64
+    Packed p64;              // packed FP64 rows of t64
+    Packed p32;              // packed FP32 rows of t32 (layers of more than 16 ELTs)
     Folded fold;
     int layout = 0;          // ARE_LAYOUT_DIRECT or ARE_LAYOUT_COMPACT (FP32 analysis)
     Compact comp;
@@ -308,6 +314,8 @@ int table_jp(int n_elts, bool fp32);
 int packed_row_words(int n_elts);
 int launch_pack64(const double *dense, int jp64, int32_t catalog, int rw, unsigned long long *rows,
                   double *ovf, unsigned long long *ovf_used, int num_sms, cudaStream_t s);
+int launch_pack32(const float *dense, int jp, int32_t catalog, uint32_t *rows, float *ovf,
+                  unsigned long long *ovf_used, int num_sms, cudaStream_t s);
 
 // api.cu: how many blocks of `kern` (threads per block, bytes of dynamic
 // shared memory) fit on one SM of the current device.  On the first call for

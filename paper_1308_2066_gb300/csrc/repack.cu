@@ -69,11 +69,59 @@ __global__ void k_pack64(const double *__restrict__ dense, int jp64, int32_t cat
     }
 }
 
+// Packed FP32 rows (16 words, 64 bytes) from a dense FP32 table of up to 32
+// columns: word 0 holds the mask of the non-zero columns, word 1 an overflow
+// offset, words 2 .. 15 the first 14 non-zero terms in column order (the
+// rest 0).  The terms of a row past the 14th go, in column order, to a block
+// of the overflow array handed out by an atomic counter.
+__global__ void k_pack32(const float *__restrict__ dense, int jp, int32_t catalog,
+                         uint32_t *__restrict__ rows, float *__restrict__ ovf,
+                         unsigned long long *__restrict__ ovf_used)
+{
+    constexpr int kInline = 14;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < catalog;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const float *d = dense + e * jp;
+        uint32_t *out = rows + e * 16;
+        uint32_t mask = 0;
+        for (int j = 0; j < jp; ++j)
+            if (__float_as_uint(d[j]) != 0) mask |= 1u << j;
+        const int cnt = __popc(mask);
+        uint32_t off = 0;
+        if (cnt > kInline) off = (uint32_t)atomicAdd(ovf_used, (unsigned long long)(cnt - kInline));
+        out[0] = mask;
+        out[1] = off;
+        int k = 0;
+        for (uint32_t m = mask; m; m &= m - 1) {
+            const float x = d[__ffs(m) - 1];
+            if (k < kInline) out[2 + k] = __float_as_uint(x);
+            else ovf[off + k - kInline] = x;
+            ++k;
+        }
+        for (int i = 2 + (k < kInline ? k : kInline); i < 16; ++i) out[i] = 0u;
+    }
+}
+
 }  // namespace
 
-// Words per packed FP64 row: the FP32 table's row size (64 bytes up to 16
-// ELTs, 128 bytes up to 32).
-int packed_row_words(int n_elts) { return n_elts <= 16 ? 8 : 16; }
+// dense: an FP32 table of jp <= 32 columns; rows: catalog x 16 words; ovf:
+// room for every non-zero term past the 14th of any row; ovf_used: a device
+// counter, zeroed here.
+int launch_pack32(const float *dense, int jp, int32_t catalog, uint32_t *rows, float *ovf,
+                  unsigned long long *ovf_used, int num_sms, cudaStream_t s)
+{
+    ARE_CUDA_TRY(cudaMemsetAsync(ovf_used, 0, sizeof *ovf_used, s));
+    if (catalog <= 0) return 0;
+    int64_t blocks = ((int64_t)catalog + 255) / 256;
+    if (blocks > (int64_t)num_sms * 16) blocks = (int64_t)num_sms * 16;
+    k_pack32<<<(unsigned)blocks, 256, 0, s>>>(dense, jp, catalog, rows, ovf, ovf_used);
+    ARE_CUDA_TRY(cudaGetLastError());
+    return 1;
+}
+
+// Words per packed FP64 row: 64 bytes (the header and 7 terms) for every
+// layer; a row of more non-zero terms takes the rest from the overflow.
+int packed_row_words(int) { return 8; }
 
 // dense: the FP64 table (jp64 columns, catalog rows); rows: catalog x rw
 // words; ovf: room for every non-zero term of the layer; ovf_used: a device

@@ -24,6 +24,8 @@
 //   BodyF32  sums the FP32 terms (packed FP32x2 adds), clamps the event loss
 //            with the occurrence terms and keeps a Kahan-compensated or an
 //            FP64 running sum per lane.
+//   BodyPackedF32  the same over packed FP32 rows (layers of more than 16
+//            ELTs: 64-byte rows of the non-zero terms behind a header).
 //   BodyP64  reads the packed FP64 table (a row: the mask of the non-zero
 //            terms, then those terms in column order), adds the terms in
 //            column order (the first taken as is, an FP64 add only where an
@@ -268,6 +270,74 @@ struct BodyF32 {
     }
 };
 
+// FP32 table of more than 16 ELTs, packed (repack.cu, launch_pack32): row e
+// is 16 words (64 bytes) -- the mask of the ELTs whose term is not 0 (word
+// 0), an overflow offset (word 1), the first 14 of those terms (words 2 ..
+// 15); the terms of a row past the 14th are in the overflow array.  The
+// rows are read and summed as BodyF32's (the header words taken out of the
+// sums); a row with more than 14 terms adds the rest from the overflow.
+template <int U, int ACC>
+struct BodyPackedF32 {
+    using Sum = typename std::conditional<ACC == ARE_FP32_KAHAN, SumKahan, SumF64>::type;
+    static constexpr int R = 2, RPW = 16, INLINE = 14;
+    const float *rows;       // [catalog][16]
+    const float *ovf;        // the terms past the 14th of the longer rows
+    float occ_r, occ_l;
+
+    __device__ __forceinline__ void batch(const int32_t (&id)[U], bool full, int lane, Sum &acc) const
+    {
+        const int row = lane / R, col = lane % R;
+        F8 v[U][R];
+        load_rows<16, U>(rows, id, full, lane, v);   // step 1: each event's whole row
+        // the headers are in the pieces of the rows' first lanes
+        bool over = false;
+        if (col == 0) {
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+#pragma unroll
+                for (int q = 0; q < R; ++q) {
+                    over |= __popc(__float_as_uint(v[u][q].v[0])) > INLINE;
+                    v[u][q].v[0] = 0.f;
+                    v[u][q].v[1] = 0.f;
+                }
+        }
+        float g[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            // step 2: the sum over ELTs -- this lane's pieces, then a
+            // reduce-scatter over the row's two lanes
+            float p[R];
+#pragma unroll
+            for (int q = 0; q < R; ++q) p[q] = sum8(v[u][q]);
+            const bool hi = (col & 1) != 0;
+            const float keep = hi ? p[1] : p[0];
+            const float send = hi ? p[0] : p[1];
+            g[u] = __fadd_rn(keep, __shfl_xor_sync(kFull, send, 1));
+        }
+        if (__any_sync(kFull, over)) {   // rare: a row with more than 14 terms
+            const uint32_t *w = reinterpret_cast<const uint32_t *>(rows);
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int32_t ev = __shfl_sync(kFull, id[u], col * RPW + row);   // the lane's event
+                const uint32_t mask = ev >= 0 ? __ldg(w + (size_t)(uint32_t)ev * 16) : 0u;
+                const int extra = __popc(mask) - INLINE;
+                if (extra > 0) {
+                    const float *o = ovf + __ldg(w + (size_t)(uint32_t)ev * 16 + 1);
+                    for (int i = 0; i < extra; ++i) g[u] = __fadd_rn(g[u], __ldg(o + i));
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u)   // step 3 (occurrence terms), then the running sum of step 4
+            acc.add(fminf(fmaxf(__fsub_rn(g[u], occ_r), 0.f), occ_l));
+    }
+    __device__ __forceinline__ double total(const Sum &t) const
+    {
+        if constexpr (ACC == ARE_FP32_KAHAN) return __dsub_rn((double)t.s, (double)t.c);
+        else return t.s;
+    }
+};
+
 // 32 bytes of a packed FP64 row as four 64-bit words.
 struct W4 {
     unsigned long long w[4];
@@ -282,10 +352,9 @@ __device__ __forceinline__ W4 load4w(const unsigned long long *p)
 }
 
 // FP64 path over the packed FP64 table (repack.cu, launch_pack64): row e is
-// RW = 8 or 16 words (64 or 128 bytes, the FP32 table's row size) -- word 0
-// holds the mask of the ELT columns whose term is not 0 (low 32 bits) and an
-// overflow offset (high 32 bits), words 1 .. RW - 1 the non-zero terms in
-// column order.  A row with more non-zero terms than that keeps the first
+// RW words (8: 64 bytes, at every layer width) -- word 0 holds the mask of
+// the ELT columns whose term is not 0 (low 32 bits) and an overflow offset
+// (high 32 bits), words 1 .. RW - 1 the non-zero terms in column order.  A row with more non-zero terms than that keeps the first
 // RW - 1 inline and all of them at the overflow offset.  The terms are
 // added in column order (the first taken as is, an FP64 add only where some
 // event has two or more), so every event loss and occurrence loss is the

@@ -6,15 +6,16 @@
 //   1. admits queued requests in arrival order while a request slot and
 //      arena memory for the request's table and YLT are free (admission by
 //      memory), building each admitted request's direct-access table;
-//   2. hands out events_per_launch to the running requests in order of
-//      least remaining work, less the time each has already waited
-//      (so a long request is not overtaken for ever by short ones that keep
-//      arriving); each takes what it needs, the last one a partial slice.
-//      The slices of small requests run in one persistent launch of the
-//      multi-layer kernel (one launch per table width); a request of at
-//      least kStagedSlice events runs its slices on the single-layer staged
-//      kernel, which is faster per event.  The kernel is chosen per request,
-//      so a request's result does not depend on the requests around it;
+//   2. hands out events_per_launch to the running requests in arrival
+//      order, or (least_work_first) in order of least remaining work less
+//      the time each has already waited (so a long request is not
+//      overtaken for ever by short ones that keep arriving); each takes
+//      what it needs, the last one a partial slice.  The slices of small
+//      requests run in one persistent launch of the multi-layer kernel (one
+//      launch per table width); a request of at least kLargeSlice events
+//      runs its slices on the single-layer register-rows kernel, which is
+//      faster per event.  The kernel is chosen per request, so a request's
+//      result does not depend on the requests around it;
 //   3. selects PML/TVaR for the requests whose last slice was in the launch;
 //   4. waits (bounded) for the previous iteration and posts its results.
 // One iteration is always queued ahead of the one being waited for, so the
@@ -46,7 +47,7 @@ constexpr int kMaxSlots = 256;
 constexpr int kWidths3[3] = {8, 16, 32};
 constexpr size_t kAlign = 256;
 constexpr int64_t kWaitLimitUs = 120LL * 1000 * 1000;   // one iteration may not take longer
-constexpr double kStagedSlice = 32e6;         // events: a request this large runs on its own kernel
+constexpr double kLargeSlice = 32e6;         // events: a request this large runs on its own kernel
 constexpr double kEventsPerUs = 2.4e5;        // occurrences per microsecond (a table row each), for the aging
 
 size_t up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
@@ -117,7 +118,7 @@ struct Slot {
     size_t tab_off = 0, tab_bytes = 0, ylt_off = 0, ylt_bytes = 0;
     LayerF32 rec{};
     int64_t launched = 0;           // trials handed to launches so far
-    bool staged = false;            // large request: its slices run on the staged kernel
+    bool large = false;             // its slices run on the single-layer register-rows kernel
     uint64_t finish_iter = 0;       // iteration whose completion posts the result
     SelectScratch sel;
     double *h_res = nullptr;        // pinned, 2 * kMaxTargets
@@ -342,7 +343,7 @@ void scheduler(Server *SP)
                     sl.busy = true;
                     sl.cancelled = sl.finishing = false;
                     sl.launched = 0;
-                    sl.staged = (double)sl.req.n_trials * S.mean_events >= kStagedSlice;
+                    sl.large = (double)sl.req.n_trials * S.mean_events >= kLargeSlice;
                     sl.t_admit = Clock::now();
                     S.running[sl.req.ticket] = free_slot;
                     admitted.push_back(free_slot);
@@ -354,10 +355,13 @@ void scheduler(Server *SP)
                 fill_record(S, S.slots[i]);
             }
 
-            // Slices of this iteration: running requests in order of least
-            // remaining work, each taking what is left of the event budget.
-            // Short requests overtake long ones, and a launch touches only a
-            // few requests' tables, which keeps them resident in L2.
+            // Slices of this iteration: running requests in arrival order
+            // (or least remaining work first), each taking what is left of
+            // the event budget.  Arrival order keeps a request from being
+            // stretched by later ones -- with request sizes bounded that
+            // gives the lowest tail latency; least work first lets short
+            // requests overtake long ones.  Either way a launch touches only
+            // a few requests' tables, which keeps them resident in L2.
             const int buf = (int)(S.iter & 1);
             std::vector<int> part[3], big, fold;
             std::vector<int64_t> slice;
@@ -368,10 +372,12 @@ void scheduler(Server *SP)
                 for (int i = 0; i < (int)S.slots.size(); ++i) {
                     const Slot &sl = S.slots[i];
                     if (!sl.busy || sl.cancelled || sl.launched >= sl.req.n_trials) continue;
-                    // remaining GPU time (estimated: a row gather per occurrence) less
-                    // the time since the request was submitted
+                    // arrival order: the time since submission, longest first;
+                    // least work first: remaining GPU time (estimated: a row
+                    // gather per occurrence) less the time since submission
+                    const double waited = us_between(sl.req.t_submit, now);
                     const double work_us = (double)(sl.req.n_trials - sl.launched) * S.mean_events / kEventsPerUs;
-                    order.emplace_back(work_us - us_between(sl.req.t_submit, now), i);
+                    order.emplace_back(S.cfg.least_work_first ? work_us - waited : -waited, i);
                 }
                 std::sort(order.begin(), order.end());
                 slice.assign(S.slots.size(), 0);
@@ -389,7 +395,7 @@ void scheduler(Server *SP)
                     left_budget -= (double)take;
                     if (S.cfg.folded)
                         fold.push_back(o.second);
-                    else if (sl.staged)
+                    else if (sl.large)
                         big.push_back(o.second);
                     else
                         part[sl.jp == 8 ? 0 : sl.jp == 16 ? 1 : 2].push_back(o.second);
@@ -462,7 +468,7 @@ void scheduler(Server *SP)
                 fa.ylt = reinterpret_cast<double *>(S.d_arena + sl.ylt_off) + sl.launched;
                 launches += launch_folded(fa, S.ctx->num_sms, S.stream);
             }
-            // large slices, one staged single-layer launch each
+            // large slices, one single-layer register-rows launch each
             for (int i : big) {
                 const Slot &sl = S.slots[i];
                 SimArgs sa;

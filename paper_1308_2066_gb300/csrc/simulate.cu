@@ -2,7 +2,8 @@
 // layer over a range of trials with an FP32 layer table (each entry an
 // event's financial term in one ELT, built by repack.cu).  Two kernels:
 //
-//  * k_rows (the default): rows held in registers, see rows.cuh.
+//  * k_rows (the default): rows held in registers, see rows.cuh; over packed
+//    rows (k_rows_packed) for layers of more than 16 ELTs.
 //  * k_simulate_staged (a tuning candidate, and the compact layout's
 //    kernel): one event per lane, rows staged in shared memory.
 //
@@ -395,6 +396,54 @@ void launch_rows_t(const SimArgs &a, const TermsF32 &tm, int num_sms, cudaStream
     ARE_CUDA_TRY(cudaGetLastError());
 }
 
+// Packed FP32 rows (layers of more than 16 ELTs): a.table the rows, a.table2
+// the overflow terms.
+template <int U, int ACC, bool FIXED>
+__global__ void __launch_bounds__(256, rows_min_blocks(16, U))
+    k_rows_packed(const rows::Trials a, const rows::BodyPackedF32<U, ACC> body, const int64_t n_trials)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    rows::run_trials<U, FIXED>(a, body, warp * n_trials / nw, (warp + 1) * n_trials / nw, lane);
+}
+
+template <int U, int ACC, bool FIXED>
+void launch_packed_t(const SimArgs &a, const TermsF32 &tm, int num_sms, cudaStream_t s)
+{
+    auto kern = k_rows_packed<U, ACC, FIXED>;
+    const int per_sm = fit_blocks(reinterpret_cast<const void *>(kern), 256, 0);
+    int64_t blocks = (a.n_trials + 7) / 8;
+    const int64_t cap = (int64_t)num_sms * per_sm;
+    if (blocks > cap) blocks = cap;
+    if (blocks < 1) blocks = 1;
+    rows::Trials t;
+    t.ids = a.ids;
+    t.off = a.off;
+    t.k = a.k;
+    t.trial_begin = a.trial_begin;
+    t.ylt = a.ylt;
+    t.agg_r = a.agg_r;
+    t.agg_l = a.agg_l;
+    rows::BodyPackedF32<U, ACC> body;
+    body.rows = static_cast<const float *>(a.table);
+    body.ovf = static_cast<const float *>(a.table2);
+    body.occ_r = tm.occ_r;
+    body.occ_l = tm.occ_l;
+    kern<<<(unsigned)blocks, 256, 0, s>>>(t, body, a.n_trials);
+    ARE_CUDA_TRY(cudaGetLastError());
+}
+
+template <int ACC>
+void launch_packed(const SimArgs &a, const TermsF32 &tm, int num_sms, cudaStream_t s)
+{
+    const bool two = a.epl != 1;
+    if (a.off)
+        two ? launch_packed_t<2, ACC, false>(a, tm, num_sms, s) : launch_packed_t<1, ACC, false>(a, tm, num_sms, s);
+    else
+        two ? launch_packed_t<2, ACC, true>(a, tm, num_sms, s) : launch_packed_t<1, ACC, true>(a, tm, num_sms, s);
+}
+
 template <int JP, int ACC>
 void launch_rows(const SimArgs &a, const TermsF32 &tm, int num_sms, cudaStream_t s)
 {
@@ -410,6 +459,10 @@ void launch_rows(const SimArgs &a, const TermsF32 &tm, int num_sms, cudaStream_t
 template <int ACC>
 int launch_fp32(const SimArgs &a, int jp, const TermsF32 &tm, int num_sms, cudaStream_t s)
 {
+    if (a.kernel == 5) {   // register rows over packed FP32 rows
+        launch_packed<ACC>(a, tm, num_sms, s);
+        return 1;
+    }
     const bool staged = a.kernel == 1 || a.kernel == 4;   // 4: the compact table's rows
     switch (jp) {
     case 8: staged ? launch_staged_fx<8, ACC>(a, tm, num_sms, s) : launch_rows<8, ACC>(a, tm, num_sms, s); return 1;
@@ -422,8 +475,8 @@ int launch_fp32(const SimArgs &a, int jp, const TermsF32 &tm, int num_sms, cudaS
 }  // namespace
 
 // FP32: the register-rows kernel unless a.kernel names the staged one (1,
-// or 4 for the compact layout).  (FP64 analyses run in staged64.cu,
-// screen64.cu and rows64.cu.)
+// or 4 for the compact layout) or the packed rows (5).  (FP64 analyses run
+// in staged64.cu, screen64.cu and rows64.cu.)
 int launch_simulate(const SimArgs &a, are_precision prec, int jp, const TermsF32 *t32,
                      const TermsF64 *, int num_sms, cudaStream_t s)
 {

@@ -184,6 +184,35 @@ def test_fixed_trial_lengths_at_batch_edges(are, ctx, orc, k):
         L.release()
 
 
+@pytest.mark.parametrize("J", [17, 20, 32])
+def test_packed_rows_past_the_inline_terms(are, orc, J):
+    """Layers of more than 16 ELTs run the register-rows kernels over packed
+    rows: the mask of the non-zero terms and up to 14 FP32 terms inline (the
+    rest in an overflow array), or up to 7 FP64 terms inline (a longer row's
+    terms all in the overflow).  Events that every ELT holds have J non-zero
+    terms, past the inline ones; the others have a few.  Every precision
+    matches the oracle; a fresh context keeps the untuned default."""
+    g = np.random.Generator(np.random.PCG64(900 + J))
+    C = 3000
+    yet = W.yet_poisson(g, 2000, 40, C)
+    shared = g.permutation(C)[:600]
+    elts = []
+    for _ in range(J):
+        ids = np.unique(np.concatenate([shared, g.permutation(C)[:400]])).astype(np.int32)
+        elts.append(W.ELT(ids, np.exp(g.normal(9.0, 1.5, ids.size))))
+    wl = W.Workload("packed", yet, elts, [W.Layer(list(range(J)), 1e3, INF, 1e4, INF)])
+    c = are.are_create(0)
+    try:
+        L = Loaded(are, c, wl)
+        ref = orc.simulate_layer(wl)
+        for p in (0, 1, 2):
+            ok, st = mixed_check(L.simulate(0, p), ref.ylt, trial_bound(wl, 0), RTOL[p])
+            assert ok, (p, st)
+        L.release()
+    finally:
+        are.are_destroy(c)
+
+
 def test_empty_trials_and_short_tails(are, ctx, orc):
     g = np.random.Generator(np.random.PCG64(77))
     yet = W.yet_poisson(g, 4000, 3, 300)         # many empty and 1-2 event trials

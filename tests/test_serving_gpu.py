@@ -112,6 +112,46 @@ def test_same_result_alone_and_in_the_mix(are, served):
     assert seq["pml"] == alone["pml"] and seq["tvar"] == alone["tvar"]
 
 
+@pytest.fixture(scope="module")
+def long_yet(are, pool):
+    """A 1M x 200 YET over the pool's catalog, for requests of 2e8 events."""
+    g = np.random.Generator(np.random.PCG64(46))
+    return W.yet_fixed(g, 1_000_000, 200, CATALOG, timestamps=False)
+
+
+@pytest.mark.parametrize("least_work_first", [False, True])
+def test_budget_order(are, pool, long_yet, least_work_first):
+    """Each launch's event budget goes to the admitted requests in arrival
+    order, or with least_work_first to the least remaining work first (less
+    the time waited).  A large request (2e8 events, ten launches' budget)
+    submitted just before small ones: in arrival order the small ones wait
+    for its last slice; least work first they finish long before it."""
+    import torch
+    _, elts = pool
+    ctx = are.are_create(0)
+    try:
+        y = are.are_load_yet(ctx, CATALOG, long_yet.n_trials, None, long_yet.k,
+                             torch.from_numpy(long_yet.ids).cuda())
+        hs = [are.are_load_elt(ctx, e.ids, e.losses, e.fx, e.ded, e.lim, e.share) for e in elts[:8]]
+        are.are_server_start(ctx, y, max_inflight=8, events_per_launch=20_000_000,
+                             least_work_first=least_work_first)
+        big = dict(members=[0, 1, 2], occ_r=1e4, occ_l=1e6, agg_r=0.0, agg_l=math.inf,
+                   n_trials=long_yet.n_trials)
+        small = [dict(big, members=[3 + i], n_trials=200) for i in range(4)]
+        tb = submit(are, ctx, hs, big)
+        ts = [submit(are, ctx, hs, r) for r in small]
+        rb = are.are_wait(ctx, tb, 60_000_000)
+        rs = [are.are_wait(ctx, t, 60_000_000) for t in ts]
+        are.are_server_stop(ctx)
+        assert rb["status"] == are.ARE_OK and all(r["status"] == are.ARE_OK for r in rs)
+        if least_work_first:
+            assert max(r["total_us"] for r in rs) < 0.5 * rb["total_us"], (rb, rs)
+        else:
+            assert min(r["total_us"] for r in rs) > 0.5 * rb["total_us"], (rb, rs)
+    finally:
+        are.are_destroy(ctx)
+
+
 def test_admission_by_memory(are, served):
     ctx, y, hs = served
     table16 = CATALOG * 16 * 4
@@ -187,11 +227,12 @@ def test_stop_drops_queued_requests(are, served):
     are.are_server_stop(ctx)
 
 
-def test_large_request_on_the_staged_kernel(are):
+def test_large_request_on_the_single_layer_kernel(are):
     """A request of at least 32M events runs its slices on the single-layer
-    staged kernel: its result equals are_simulate + are_risk_measures on the
-    same layer (the same kernel and arithmetic per trial), alone and in a
-    mix of small requests, sliced into many launches."""
+    register-rows kernel: its result equals are_simulate + are_risk_measures
+    on the same layer (the same kernel and arithmetic per trial), alone and
+    in a mix of small requests, sliced into many launches, in either budget
+    order."""
     import torch
     g = np.random.Generator(np.random.PCG64(45))
     n, k, C = 80_000, 500, 20_000
@@ -212,8 +253,9 @@ def test_large_request_on_the_staged_kernel(are):
 
         small = [dict(members=[int(x) for x in g.choice(12, int(g.integers(1, 9)), replace=False)],
                       n=int(g.integers(1000, 20_000))) for _ in range(12)]
-        for mix in (False, True):
-            are.are_server_start(ctx, y, max_inflight=16, events_per_launch=10_000_000)
+        for mix, lwf in ((False, False), (True, False), (True, True)):
+            are.are_server_start(ctx, y, max_inflight=16, events_per_launch=10_000_000,
+                                 least_work_first=lwf)
             tickets = []
             if mix:
                 tickets += [are.are_submit(ctx, [hs[m] for m in r["members"]], 1e4, 1e6, 0, math.inf,
