@@ -207,13 +207,16 @@ def items_bytes(wl) -> int:
     return sum(algorithmic_bytes(y.n_events, y.n_trials, len(L.elts), 4) for L in wl.layers)
 
 
-def kernel_key(prec: int, J: int, tuned=None) -> str:
+def kernel_key(prec: int, J: int, tuned=None, rows=None) -> str:
     """Name of the kernel that runs the analysis stage for this precision
-    under the tuned choice (untuned: the register-rows kernel with two groups
-    of 32 events per batch for FP32, the staged kernel for FP64)."""
+    under the tuned choice (untuned: the register-rows kernels with two
+    groups of 32 events per batch).  rows: (row_bytes, packed) from
+    are_layer_rows, which names the packed-row instances."""
     if prec == "folded":
         return "k_folded<fixed,smem_bits>"
     t = tuned or {}
+    rb, packed = rows if rows else (None, False)
+    u = t.get("rows_in_flight", 2)
     if prec == 0:
         jp = math.ceil(J / 4) * 4
         kind = t.get("kernel", 2)
@@ -221,35 +224,22 @@ def kernel_key(prec: int, J: int, tuned=None) -> str:
             return f"k_screen64<{8 if J <= 8 else 16 if J <= 16 else 32},fixed>"
         if kind == 1:
             return f"k_staged<double,{jp},fixed,ylt>"
-        return f"k_rows64<8,{t.get('rows_in_flight', 2)},fixed>"
+        return f"k_rows64<{(rb or 64) // 8},{u},fixed>"
     jp = 8 if J <= 8 else 16 if J <= 16 else 32
     kind = t.get("kernel", 2)
-    u = t.get("rows_in_flight", 2)
     if kind == 0:
         return f"k_sim_items<{jp},{u},{prec},fixed>"
     if kind == 2:
-        if jp == 32:
-            return f"k_rows_packed<{u},{prec},fixed>"
+        if packed:
+            return f"k_rows_packed<{rb // 4},{u},{prec},fixed>"
         return f"k_rows<{jp},{u},{prec},fixed>"
     return f"k_simulate_staged<{jp},{prec},fixed,epl{2 if u == 2 else 1}>"
 
 
-def row_bytes(J: int, prec, tuned=None) -> int:
-    """Bytes of one table row as the analysis kernel reads it: the dense
-    FP32 row, or for more than 16 ELTs the packed FP32 row (register-rows
-    kernel); for FP64 the packed row (register-rows kernel), the FP32
-    screen's row (screened kernel) or the dense FP64 row (staged kernel)."""
-    fp32_row = 32 if J <= 8 else 64 if J <= 16 else 128
-    kind = (tuned or {}).get("kernel", 2)
-    if prec == 0:
-        if kind == 1:
-            return math.ceil(J / 4) * 32
-        if kind == 2:
-            return 64
-        return fp32_row
-    if kind == 2 and J > 16:
-        return 64
-    return fp32_row
+def layer_rows(are, ctx, layer, yet, prec, tuned=None):
+    """(row_bytes, packed) of the rows the analysis of this layer reads per
+    occurrence under the tuned kernel choice (the library's answer)."""
+    return are.are_layer_rows(ctx, layer, yet, prec, (tuned or {}).get("kernel", -1))
 
 
 class Resident:
@@ -373,7 +363,7 @@ SHAPE_NAMES = {0: "16-byte loads, lane reads its row's id",
                2: "cp.async rows staged in shared memory"}
 
 
-def roofline(n_events, n_trials, J, prec, sim_ms, tuned=None, ceiling=None):
+def roofline(n_events, n_trials, J, prec, sim_ms, tuned=None, ceiling=None, rows=None):
     """Roofline of the analysis kernel.  Its table rows are gathered from the
     L2-resident table, so the bound that applies is the gather ceiling: the
     same id stream and row reads with no arithmetic, measured live in this
@@ -387,12 +377,12 @@ def roofline(n_events, n_trials, J, prec, sim_ms, tuned=None, ceiling=None):
     ncu-measured DRAM traffic of one launch over the kernel's time, over
     that bandwidth."""
     hbm, src = hbm_peak()
-    rb = row_bytes(J, prec, tuned)
+    rb = rows[0]
     bytes_ = n_events * (4 + rb) + 8 * n_trials
     survey_bytes = algorithmic_bytes(n_events, n_trials, J, 8 if prec == 0 else 4)
     secs = sim_ms * 1e-3
     achieved = bytes_ / secs / 1e9
-    key = kernel_key(prec, J, tuned)
+    key = kernel_key(prec, J, tuned, rows)
     traffic = ncu_traffic(key)
     best, shapes = ceiling
     rate = n_events / secs
@@ -407,7 +397,7 @@ def roofline(n_events, n_trials, J, prec, sim_ms, tuned=None, ceiling=None):
             "hbm_formula_frac": round(survey_bytes / secs / 1e9 / hbm, 4),
             "dram_frac": (round(traffic / secs / 1e9 / hbm, 4) if traffic else None),
             "hbm_peak": hbm, "hbm_peak_source": f"{src} HBM copy bandwidth (MEASURED_PEAKS.json)",
-            "l2_gather": {"row_bytes": row_bytes(J, prec, tuned),
+            "l2_gather": {"row_bytes": rb, "packed_rows": rows[1],
                           "achieved_rows_per_s": round(rate, 1),
                           "ceiling_rows_per_s": round(best, 1),
                           "ceiling_shape": {"kind": SHAPE_NAMES[top[0]], "in_flight": top[1],
@@ -542,8 +532,8 @@ def portfolio_kernel_name(tuned, prec) -> str:
         return (f"k_sim_items<jp,{u},{prec},ragged>: one persistent launch per table width, "
                 f"{(tuned or {}).get('trials_per_item')} trials per work item")
     if kind == 2:
-        return (f"k_rows<jp,{u},{prec},ragged> (k_rows_packed<{u},{prec},ragged> for layers of more than "
-                f"16 ELTs): one launch per layer, back to back in the graph")
+        return (f"k_rows<jp,{u},{prec},ragged> (k_rows_packed<pw,{u},{prec},ragged> over the packed rows "
+                f"of the layers of more than 8 ELTs): one launch per layer, back to back in the graph")
     return f"k_simulate_staged<jp,{prec},ragged,epl{u}>: one launch per layer, back to back in the graph"
 
 
@@ -640,8 +630,8 @@ def portfolio_record(are, torch, prec, steps, warmup, tune=True, variants=True, 
         # take for every layer's rows, against the analysis' time
         ceil = {}
         t_ceil = 0.0
-        for L in wl.layers:
-            rb = row_bytes(len(L.elts), prec, tuned)
+        for h in layers:
+            rb, _ = layer_rows(are, ctx, h, yet, prec, tuned)
             if rb not in ceil:
                 ceil[rb] = are.are_gather_ceiling(ctx, yet, rb, 0, n, reps=2)
             t_ceil += y.n_events / ceil[rb]
@@ -758,7 +748,8 @@ def precision_record(are, torch, steps, warmup, tune=True, compact=True, n_trial
             full[cand] = rc.ylt
             rp, rt = oracle.risk_measures(full, RPS, LEVELS)
             rows[PRECISION_NAMES[p]] = {
-                "sim_ms": round(ms, 4), "tuned": tuned, "kernel": kernel_key(p, len(L.elts), tuned),
+                "sim_ms": round(ms, 4), "tuned": tuned,
+                "kernel": kernel_key(p, len(L.elts), tuned, layer_rows(are, ctx, layer, yet, p, tuned)),
                 "value": round(y.n_events * len(L.elts) / (ms * 1e-3) / 1e9, 3),
                 "ylt_rel_err_max": float(rel.max()), "ylt_rel_err_median": float(np.median(rel)),
                 "pml": [float(x) for x in pml], "pml_oracle": [float(x) for x in rp],
@@ -923,8 +914,8 @@ def subrecords(are, torch, args):
     prec = {v: k for k, v in PRECISION_NAMES.items()}[args.precision]
     for name, fn in (
             ("portfolio", lambda: portfolio_record(are, torch, prec, 5, 2, variants=False)),
-            ("serving", lambda: serving_record(are, torch, prec, [200.0], 10.0,
-                                               min_requests=2000, max_requests=2000,
+            ("serving", lambda: serving_record(are, torch, prec, [50.0, 200.0], 20.0,
+                                               min_requests=1000, max_requests=2000,
                                                folded=False)),
             ("precision_stress", lambda: precision_record(are, torch, 5, 2, compact=False))):
         t0 = time.perf_counter()
@@ -989,9 +980,10 @@ def main():
         folded["ms"] = max_over_ranks(folded["ms"], world, torch)
         folded["sim_ms"] = max_over_ranks(folded["sim_ms"], world, torch)
     # the gather ceiling for each row size timed (same YET, no arithmetic)
-    ceilings = {}
+    ceilings, rows = {}, {}
     for p in paths:
-        rb = row_bytes(J, p, tuned.get(PRECISION_NAMES[p]))
+        rows[p] = layer_rows(are, ctx, res.layer, res.yet, p, tuned.get(PRECISION_NAMES[p]))
+        rb = rows[p][0]
         if rb not in ceilings:
             ceilings[rb] = are.are_gather_ceiling(ctx, res.yet, rb, 0, y.n_trials, reps=3,
                                                   shapes=True)
@@ -1020,8 +1012,7 @@ def main():
                    "parallelism": f"trial blocks per GPU x{world}",
                    "gpu": torch.cuda.get_device_name()},
         "roofline": roofline(y.n_events, y.n_trials, J, prec, head["sim_ms"],
-                             tuned.get(PRECISION_NAMES[prec]),
-                             ceilings[row_bytes(J, prec, tuned.get(PRECISION_NAMES[prec]))]),
+                             tuned.get(PRECISION_NAMES[prec]), ceilings[rows[prec][0]], rows[prec]),
         "tuned": tuned,
         "gpu_launches": head["launches"],
         "clocks": head["clocks"],
@@ -1032,8 +1023,8 @@ def main():
                              "sim_ms": round(r["sim_ms"], 4),
                              "value": round(lookups / (r["ms"] / args.steps * 1e-3) / 1e9, 3),
                              "roofline": roofline(y.n_events, y.n_trials, J, p, r["sim_ms"],
-                                                  tuned.get(PRECISION_NAMES[p]),
-                                                  ceilings[row_bytes(J, p, tuned.get(PRECISION_NAMES[p]))]),
+                                                  tuned.get(PRECISION_NAMES[p]), ceilings[rows[p][0]],
+                                                  rows[p]),
                              "pml": r["pml"], "tvar": r["tvar"], "clocks": r["clocks"]}
         for p, r in results.items() if p != prec}
     if folded is not None:

@@ -194,6 +194,18 @@ ARE_API are_status are_free_layer(are_ctx *ctx, int32_t layer_handle);
 #define ARE_LAYOUT_COMPACT 1
 ARE_API are_status are_set_table_layout(are_ctx *ctx, int32_t layer, int32_t layout);
 
+/* The table rows an analysis of `layer` over `yet` reads (Section III-B's
+ * direct access, one row per event occurrence), for reporting: *row_bytes
+ * receives the bytes of one row and *packed 1 where the rows are packed (the
+ * column mask and the non-zero terms of each event, built when the layer's
+ * entries per catalog event are few), else 0.  kernel: a kernel choice as in
+ * are_tune_result (0 .. 3), or -1 for the one a single-layer are_simulate of
+ * this kind of work uses now (tuned, or the default).  Nothing is built or
+ * launched.  ARE_ENOTFOUND for an unknown handle, ARE_EINVAL for a bad
+ * kernel or a NULL output. */
+ARE_API are_status are_layer_rows(are_ctx *ctx, int32_t layer, int32_t yet, are_precision precision,
+                                  int32_t kernel, int32_t *row_bytes, int32_t *packed);
+
 /* Preprocessing (Section II-B, stage 1; Section III-B's direct access
  * tables): (re)build the layer's event-major direct-access table for the
  * YET's catalog in the given precision, on `stream`.  are_simulate builds
@@ -392,9 +404,10 @@ ARE_API are_status are_risk_measures_batch(are_ctx *ctx, const double *const *yl
  * resident YET and the context's resident ELTs.  A scheduler thread inside
  * the library admits queued requests while request slots and arena memory
  * are free, hands each iteration's budget of events_per_launch to the
- * admitted requests in arrival order (or, with least_work_first, in order
- * of least remaining work less the time waited, so short requests overtake
- * long ones), and runs the slices of small requests in one persistent
+ * admitted requests in arrival order, the oldest whole (or, with
+ * least_work_first, in order of least remaining work less the time waited,
+ * so short requests overtake long ones), and runs the slices of small
+ * requests in one persistent
  * launch and those of large ones on the single-layer kernel; a request
  * arriving while others run joins at the next iteration, and the next
  * iteration is always queued behind the running one.  When a request's last
@@ -413,10 +426,12 @@ typedef struct {
                                   occurrence loss per catalog event, exact trial sums, one
                                   lookup per occurrence -- the variant of are_simulate_folded);
                                   precision is then not used */
-    int32_t least_work_first;  /* 0: the budget goes to the admitted requests in arrival order
-                                  (the lowest tail latency when request sizes are bounded);
-                                  1: in order of least remaining work less the time waited
-                                  (short requests overtake long ones) */
+    int32_t least_work_first;  /* 0: arrival order -- the oldest admitted request runs whole
+                                  and the ones behind it share the budget (nothing overtakes,
+                                  which gives the lowest tail latency when request sizes are
+                                  bounded); 1: the budget goes in order of least remaining
+                                  work less the time waited (short requests overtake long
+                                  ones, which are cut into slices) */
 } are_server_cfg;
 
 /* One pricing request: a layer of the context's ELTs with its own layer terms,

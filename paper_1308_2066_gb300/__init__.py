@@ -111,6 +111,8 @@ _SIGS = {
     "are_simulate_occurrences": (C.c_int32, [_P, C.c_int32, C.c_int32, C.c_int64, C.c_int64,
                                              C.c_int, _P, _P, _P, _P]),
     "are_set_table_layout": (C.c_int32, [_P, C.c_int32, C.c_int32]),
+    "are_layer_rows": (C.c_int32, [_P, C.c_int32, C.c_int32, C.c_int, C.c_int32,
+                                   C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
     "are_prepare_folded": (C.c_int32, [_P, C.c_int32, C.c_int32, _P]),
     "are_simulate_folded": (C.c_int32, [_P, C.c_int32, C.c_int32, C.c_int64, C.c_int64, _P, _P]),
     "are_simulate_streamed": (C.c_int32, [_P, C.c_int32, C.c_int32, C.c_int64, _P, C.c_int32, _P,
@@ -288,6 +290,15 @@ def are_simulate_occurrences(ctx, layer: int, yet: int, trial_begin: int, n_tria
 def are_set_table_layout(ctx, layer: int, layout: int) -> None:
     """ARE_LAYOUT_DIRECT (one row per catalog event) or ARE_LAYOUT_COMPACT."""
     _check(ctx, lib().are_set_table_layout(ctx, int(layer), int(layout)))
+
+
+def are_layer_rows(ctx, layer: int, yet: int, precision: int, kernel: int = -1):
+    """(row_bytes, packed): the table row an analysis of the layer over the
+    YET reads per occurrence, under a kernel choice (-1: the current one)."""
+    rb, pk = C.c_int32(0), C.c_int32(0)
+    _check(ctx, lib().are_layer_rows(ctx, int(layer), int(yet), int(precision), int(kernel),
+                                     C.byref(rb), C.byref(pk)))
+    return rb.value, bool(pk.value)
 
 
 def are_prepare_folded(ctx, layer: int, yet: int, stream=None) -> None:

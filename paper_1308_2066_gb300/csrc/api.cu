@@ -333,12 +333,20 @@ int64_t layer_entries(are_ctx *ctx, const Layer &L)
     return entries;
 }
 
+// Words per packed row of the layer over a catalog of `catalog` events (0:
+// the dense FP32 row), from its ELT entries per catalog event.
+int row_words(are_ctx *ctx, const Layer &L, int32_t catalog, bool fp32)
+{
+    const double tpe = catalog > 0 ? (double)layer_entries(ctx, L) / (double)catalog : 0.0;
+    return packed_row_words((int)L.elts.size(), tpe, fp32);
+}
+
 // The packed FP64 rows of the layer's FP64 table (which must be built for
 // `catalog`), read by the FP64 register-rows kernel.
 Packed &build_packed64(are_ctx *ctx, Layer &L, int32_t catalog, cudaStream_t s)
 {
     Packed &p = L.p64;
-    const int rw = packed_row_words((int)L.elts.size());
+    const int rw = row_words(ctx, L, catalog, false);
     size_packed(ctx, L, p, catalog, rw, rw * sizeof(unsigned long long),
                 sizeof(double) * (size_t)layer_entries(ctx, L));
     const Table &t = L.t64;
@@ -348,14 +356,14 @@ Packed &build_packed64(are_ctx *ctx, Layer &L, int32_t catalog, cudaStream_t s)
     return p;
 }
 
-// The packed FP32 rows of a layer of more than 16 ELTs (its FP32 table must
+// The packed FP32 rows (pw words each) of the layer's FP32 table (which must
 // be built for `catalog`), read by the FP32 register-rows kernel.
-Packed &build_packed32(are_ctx *ctx, Layer &L, int32_t catalog, cudaStream_t s)
+Packed &build_packed32(are_ctx *ctx, Layer &L, int32_t catalog, int pw, cudaStream_t s)
 {
     Packed &p = L.p32;
-    size_packed(ctx, L, p, catalog, 16, 16 * sizeof(float), sizeof(float) * (size_t)layer_entries(ctx, L));
+    size_packed(ctx, L, p, catalog, pw, pw * sizeof(float), sizeof(float) * (size_t)layer_entries(ctx, L));
     const Table &t = L.t32;
-    ctx->launches += launch_pack32(static_cast<const float *>(t.d), t.jp, catalog,
+    ctx->launches += launch_pack32(static_cast<const float *>(t.d), t.jp, catalog, pw,
                                    static_cast<uint32_t *>(p.rows()), static_cast<float *>(p.ovf()),
                                    p.used(), ctx->num_sms, s);
     return p;
@@ -363,16 +371,19 @@ Packed &build_packed32(are_ctx *ctx, Layer &L, int32_t catalog, cudaStream_t s)
 
 // The tables beside a layer's table that a kernel choice reads.  FP64: the
 // packed rows (register rows, kernel 2) or the FP32 screen (kernel 3); FP32:
-// the packed rows of a layer of more than 16 ELTs (register rows, kernel 2).
-// `fresh`: the layer's table was just rebuilt.
+// the packed rows where the layer's row size calls for them (register rows,
+// kernel 2).  `fresh`: the layer's table was just rebuilt.
 void ensure_aux(are_ctx *ctx, Layer &L, int32_t catalog, bool fp32, int kernel, bool fresh, cudaStream_t s)
 {
     if (fp32) {
-        if (kernel == 2 && L.t32.jp == 32 && (fresh || !L.p32.d || L.p32.catalog != catalog))
-            build_packed32(ctx, L, catalog, s);
+        const int pw = kernel == 2 ? row_words(ctx, L, catalog, true) : 0;
+        if (pw && (fresh || !L.p32.d || L.p32.catalog != catalog || L.p32.rw != pw))
+            build_packed32(ctx, L, catalog, pw, s);
         return;
     }
-    if (kernel == 2 && (fresh || !L.p64.d || L.p64.catalog != catalog)) build_packed64(ctx, L, catalog, s);
+    if (kernel == 2 && (fresh || !L.p64.d || L.p64.catalog != catalog ||
+                        L.p64.rw != row_words(ctx, L, catalog, false)))
+        build_packed64(ctx, L, catalog, s);
     if (kernel == 3 && (fresh || !L.t32u.d || L.t32u.catalog != catalog)) build_screen(ctx, L, catalog, s);
 }
 
@@ -527,11 +538,12 @@ int run_single(are_ctx *ctx, const Layer &L, const Yet &y, int64_t trial_begin, 
     TermsF64 t64;
     fill_terms(L, t32, t64);
     a.n_elts = (int32_t)L.elts.size();
-    if (fp32 && !compact && te.kernel == 2 && t.jp == 32 && L.p32.d && L.p32.catalog == y.catalog) {
+    if (fp32 && !compact && te.kernel == 2 && L.p32.d && L.p32.catalog == y.catalog &&
+        L.p32.rw == row_words(ctx, L, y.catalog, true)) {
         a.table = L.p32.rows();   // register rows over the packed FP32 rows
         a.table2 = L.p32.ovf();
         a.kernel = 5;
-        return launch_simulate(a, precision, t.jp, &t32, &t64, ctx->num_sms, s);
+        return launch_simulate(a, precision, L.p32.rw, &t32, &t64, ctx->num_sms, s);
     }
     if (compact) {   // the staged kernel, through the row index
         a.table = L.comp.rows();
@@ -1105,6 +1117,36 @@ are_status are_set_table_layout(are_ctx *ctx, int32_t layer, int32_t layout)
                   "layout must be ARE_LAYOUT_DIRECT or ARE_LAYOUT_COMPACT");
         if (L.layout != layout) ++L.generation;
         L.layout = layout;
+    });
+}
+
+are_status are_layer_rows(are_ctx *ctx, int32_t layer, int32_t yet, are_precision precision,
+                          int32_t kernel, int32_t *row_bytes, int32_t *packed)
+{
+    return guarded(ctx, [&] {
+        ARE_CHECK(row_bytes && packed, ARE_EINVAL, "row_bytes and packed must not be NULL");
+        ARE_CHECK(kernel >= -1 && kernel <= 3, ARE_EINVAL, "kernel must lie in -1 .. 3");
+        check_precision(precision);
+        const Layer &L = layer_of(ctx, layer);
+        const Yet &y = yet_of(ctx, yet);
+        const bool fp32 = precision != ARE_FP64;
+        const int J = (int)L.elts.size();
+        const int k = kernel >= 0 ? kernel : tuned(ctx, precision, y, table_jp(J, fp32), false).kernel;
+        int rb = table_jp(J, fp32) * (fp32 ? 4 : 8), pk = 0;
+        if (fp32 && L.layout != ARE_LAYOUT_COMPACT && k == 2) {
+            const int pw = row_words(ctx, L, y.catalog, true);
+            if (pw) {
+                rb = pw * 4;
+                pk = 1;
+            }
+        } else if (!fp32 && k == 2) {
+            rb = row_words(ctx, L, y.catalog, false) * 8;
+            pk = 1;
+        } else if (!fp32 && k == 3) {
+            rb = table_jp(J, true) * 4;   // the screen's rows (and the marked FP64 entries)
+        }
+        *row_bytes = rb;
+        *packed = pk;
     });
 }
 

@@ -118,15 +118,16 @@ struct Compact {
     float *rows() const { return reinterpret_cast<float *>(static_cast<char *>(d) + rows_off); }
 };
 
-// Packed table of one layer: catalog rows of 64 or 128 bytes holding each
-// event's non-zero terms in column order behind a header (the column mask
-// and an overflow offset), a counter and the overflow terms, in one
-// allocation laid out [rows | counter (256 B) | overflow].  FP64 (built from
-// t64 by launch_pack64): rw = 8 64-bit words per row, the header in word 0,
-// up to 7 terms inline and every term of a longer row in the overflow.
-// FP32 (built from t32 by launch_pack32, for layers of more than 16 ELTs):
-// 16 32-bit words, the mask in word 0 and the offset in word 1, up to 14
-// terms inline and the rest of a longer row in the overflow.
+// Packed table of one layer: catalog rows of 32 or 64 bytes holding each
+// event's non-zero terms in column order behind the mask of their columns,
+// a counter and the overflow terms, in one allocation laid out [rows |
+// counter (256 B) | overflow].  FP64 (built from t64 by launch_pack64):
+// rw = 4 or 8 64-bit words per row, the mask and the overflow offset in word
+// 0, up to rw - 1 terms inline and every term of a longer row in the
+// overflow.  FP32 (built from t32 by launch_pack32): rw = 8 or 16 32-bit
+// words, the mask in word 0, up to rw - 1 terms inline; a longer row keeps
+// rw - 2 inline and the offset of the rest in its last word.  The row size
+// follows the layer's entries per catalog event (packed_row_words).
 struct Packed {
     int32_t catalog = -1;
     int rw = 0;
@@ -147,7 +148,7 @@ struct Layer {
     Table t32, t64;
     Table t32u;              // FP32 screen of t64: its values rounded up
     Packed p64;              // packed FP64 rows of t64
-    Packed p32;              // packed FP32 rows of t32 (layers of more than 16 ELTs)
+    Packed p32;              // packed FP32 rows of t32 (layers of more than 8 ELTs)
     Folded fold;
     int layout = 0;          // ARE_LAYOUT_DIRECT or ARE_LAYOUT_COMPACT (FP32 analysis)
     Compact comp;
@@ -311,10 +312,10 @@ std::vector<CeilingShape> gather_ceiling(const int32_t *ids, int64_t n, int row_
                                          int num_sms, const void *table, float *out, cudaStream_t s,
                                          uint64_t &launches);
 int table_jp(int n_elts, bool fp32);
-int packed_row_words(int n_elts);
+int packed_row_words(int n_elts, double terms_per_event, bool fp32);
 int launch_pack64(const double *dense, int jp64, int32_t catalog, int rw, unsigned long long *rows,
                   double *ovf, unsigned long long *ovf_used, int num_sms, cudaStream_t s);
-int launch_pack32(const float *dense, int jp, int32_t catalog, uint32_t *rows, float *ovf,
+int launch_pack32(const float *dense, int jp, int32_t catalog, int pw, uint32_t *rows, float *ovf,
                   unsigned long long *ovf_used, int num_sms, cudaStream_t s);
 
 // api.cu: how many blocks of `kern` (threads per block, bytes of dynamic

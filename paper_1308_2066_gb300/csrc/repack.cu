@@ -37,9 +37,9 @@ __global__ void k_scatter(T *__restrict__ tab, const ScatterArgs a)
     }
 }
 
-// Packed FP64 rows from the dense FP64 table: row e gets the mask of its
-// non-zero columns (low 32 bits of word 0) and those terms in column order
-// (words 1 .. rw - 1).  A row with more non-zero terms than that keeps the
+// Packed FP64 rows (rw = 4 or 8 words: 32 or 64 bytes) from the dense FP64
+// table: row e gets the mask of its non-zero columns (low 32 bits of word 0)
+// and those terms in column order (words 1 .. rw - 1).  A row with more non-zero terms than that keeps the
 // first rw - 1 inline and all of them in a block of the overflow array,
 // whose offset goes to the high 32 bits of word 0 (blocks are handed out by
 // an atomic counter; each block holds its row's terms in column order).
@@ -69,59 +69,77 @@ __global__ void k_pack64(const double *__restrict__ dense, int jp64, int32_t cat
     }
 }
 
-// Packed FP32 rows (16 words, 64 bytes) from a dense FP32 table of up to 32
-// columns: word 0 holds the mask of the non-zero columns, word 1 an overflow
-// offset, words 2 .. 15 the first 14 non-zero terms in column order (the
-// rest 0).  The terms of a row past the 14th go, in column order, to a block
-// of the overflow array handed out by an atomic counter.
-__global__ void k_pack32(const float *__restrict__ dense, int jp, int32_t catalog,
+// Packed FP32 rows (pw = 8 or 16 words: 32 or 64 bytes) from a dense FP32
+// table of up to 32 columns: word 0 holds the mask of the non-zero columns,
+// words 1 .. pw - 1 those terms in column order (the rest 0).  A row of more
+// than pw - 1 non-zero terms keeps the first pw - 2 inline and in word
+// pw - 1 the offset of a block of the overflow array (handed out by an
+// atomic counter) that holds the rest in column order.
+__global__ void k_pack32(const float *__restrict__ dense, int jp, int32_t catalog, int pw,
                          uint32_t *__restrict__ rows, float *__restrict__ ovf,
                          unsigned long long *__restrict__ ovf_used)
 {
-    constexpr int kInline = 14;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < catalog;
          e += (int64_t)gridDim.x * blockDim.x) {
         const float *d = dense + e * jp;
-        uint32_t *out = rows + e * 16;
+        uint32_t *out = rows + e * pw;
         uint32_t mask = 0;
         for (int j = 0; j < jp; ++j)
             if (__float_as_uint(d[j]) != 0) mask |= 1u << j;
         const int cnt = __popc(mask);
+        const bool over = cnt > pw - 1;
+        const int inl = over ? pw - 2 : cnt;
         uint32_t off = 0;
-        if (cnt > kInline) off = (uint32_t)atomicAdd(ovf_used, (unsigned long long)(cnt - kInline));
+        if (over) off = (uint32_t)atomicAdd(ovf_used, (unsigned long long)(cnt - inl));
         out[0] = mask;
-        out[1] = off;
         int k = 0;
         for (uint32_t m = mask; m; m &= m - 1) {
             const float x = d[__ffs(m) - 1];
-            if (k < kInline) out[2 + k] = __float_as_uint(x);
-            else ovf[off + k - kInline] = x;
+            if (k < inl) out[1 + k] = __float_as_uint(x);
+            else ovf[off + k - inl] = x;
             ++k;
         }
-        for (int i = 2 + (k < kInline ? k : kInline); i < 16; ++i) out[i] = 0u;
+        for (int i = 1 + inl; i < pw; ++i) out[i] = 0u;
+        if (over) out[pw - 1] = off;
     }
 }
 
 }  // namespace
 
-// dense: an FP32 table of jp <= 32 columns; rows: catalog x 16 words; ovf:
-// room for every non-zero term past the 14th of any row; ovf_used: a device
+// dense: an FP32 table of jp <= 32 columns; rows: catalog x pw words (8 or
+// 16); ovf: room for every non-zero term of the layer; ovf_used: a device
 // counter, zeroed here.
-int launch_pack32(const float *dense, int jp, int32_t catalog, uint32_t *rows, float *ovf,
+int launch_pack32(const float *dense, int jp, int32_t catalog, int pw, uint32_t *rows, float *ovf,
                   unsigned long long *ovf_used, int num_sms, cudaStream_t s)
 {
+    if (pw != 8 && pw != 16) throw Error{ARE_EINVAL, "packed FP32 rows are 8 or 16 words"};
     ARE_CUDA_TRY(cudaMemsetAsync(ovf_used, 0, sizeof *ovf_used, s));
     if (catalog <= 0) return 0;
     int64_t blocks = ((int64_t)catalog + 255) / 256;
     if (blocks > (int64_t)num_sms * 16) blocks = (int64_t)num_sms * 16;
-    k_pack32<<<(unsigned)blocks, 256, 0, s>>>(dense, jp, catalog, rows, ovf, ovf_used);
+    k_pack32<<<(unsigned)blocks, 256, 0, s>>>(dense, jp, catalog, pw, rows, ovf, ovf_used);
     ARE_CUDA_TRY(cudaGetLastError());
     return 1;
 }
 
-// Words per packed FP64 row: 64 bytes (the header and 7 terms) for every
-// layer; a row of more non-zero terms takes the rest from the overflow.
-int packed_row_words(int) { return 8; }
+// Words per packed row for a layer whose ELTs hold `terms_per_event`
+// entries per catalog event on average (an upper bound of the mean count of
+// non-zero terms in a row), or 0 for the dense FP32 row.  32-byte rows (one
+// sector, one lane per row) where the rows that overflow them are rare: FP32
+// (7 terms inline) up to 2 entries per event for tables of more than 8 ELTs
+// (8 or fewer already have 32-byte dense rows); FP64 (3 terms inline) up to
+// 0.5.  Otherwise FP32 keeps the dense 64-byte row up to 16 ELTs and packs
+// wider tables into 64-byte rows (15 terms inline), and FP64 packs into
+// 64-byte rows (7 terms inline).
+int packed_row_words(int n_elts, double terms_per_event, bool fp32)
+{
+    if (fp32) {
+        if (n_elts <= 8) return 0;
+        if (terms_per_event <= 2.0) return 8;
+        return n_elts > 16 ? 16 : 0;
+    }
+    return terms_per_event <= 0.5 ? 4 : 8;
+}
 
 // dense: the FP64 table (jp64 columns, catalog rows); rows: catalog x rw
 // words; ovf: room for every non-zero term of the layer; ovf_used: a device

@@ -7,8 +7,8 @@
 // event's financial term f_j(x) = share * min(max(fx * x - D, 0), Lim) (step
 // 2 before its sum over ELTs), formed in FP64 when the table is built; an
 // FP32 table holds it rounded once to FP32 in rows of JP = 8, 16 or 32
-// floats, the packed FP64 table holds the non-zero FP64 terms of each event
-// in rows of the same size.
+// floats; a packed table holds each event's non-zero terms (FP32 or FP64)
+// behind the mask of their columns, in rows of 32 or 64 bytes.
 //
 // Mapping (GB300).  A warp takes a contiguous range of trials and walks each
 // trial's events in batches of 32 * U events (a batch never spans two
@@ -18,14 +18,14 @@
 // rows and every lane holds R * U row pieces in flight.  A reduce-scatter
 // across the R lanes of a row (R - 1 shuffles) leaves every lane with one
 // whole event per group, whose occurrence terms (step 3) and running sum
-// (step 4) it does alone.  Ids are read one batch ahead.  (A packed FP64 row
-// is read the same way, RW / 4 lanes per row.)
+// (step 4) it does alone.  Ids are read one batch ahead.  (Packed rows are
+// read the same way: 32-byte rows by one lane each, 64-byte rows by two.)
 //
 //   BodyF32  sums the FP32 terms (packed FP32x2 adds), clamps the event loss
 //            with the occurrence terms and keeps a Kahan-compensated or an
 //            FP64 running sum per lane.
-//   BodyPackedF32  the same over packed FP32 rows (layers of more than 16
-//            ELTs: 64-byte rows of the non-zero terms behind a header).
+//   BodyPackedF32  the same over packed FP32 rows (32- or 64-byte rows of
+//            the non-zero terms behind their column mask).
 //   BodyP64  reads the packed FP64 table (a row: the mask of the non-zero
 //            terms, then those terms in column order), adds the terms in
 //            column order (the first taken as is, an FP64 add only where an
@@ -270,60 +270,68 @@ struct BodyF32 {
     }
 };
 
-// FP32 table of more than 16 ELTs, packed (repack.cu, launch_pack32): row e
-// is 16 words (64 bytes) -- the mask of the ELTs whose term is not 0 (word
-// 0), an overflow offset (word 1), the first 14 of those terms (words 2 ..
-// 15); the terms of a row past the 14th are in the overflow array.  The
-// rows are read and summed as BodyF32's (the header words taken out of the
-// sums); a row with more than 14 terms adds the rest from the overflow.
-template <int U, int ACC>
+// Packed FP32 table (repack.cu, launch_pack32): row e is PW = 8 or 16 words
+// (32 or 64 bytes) -- word 0 the mask of the ELT columns whose term is not
+// 0, then up to PW - 1 of those terms in column order.  A row of more terms
+// keeps the first PW - 2 inline and in word PW - 1 the offset of the rest
+// (in column order) in the overflow array.  The rows are read and summed as
+// BodyF32's, the mask word taken out of the sum; the events with an
+// overflow (rare: where some lane has one) redo their sum from the row's
+// inline terms and the overflow.
+template <int PW, int U, int ACC>
 struct BodyPackedF32 {
     using Sum = typename std::conditional<ACC == ARE_FP32_KAHAN, SumKahan, SumF64>::type;
-    static constexpr int R = 2, RPW = 16, INLINE = 14;
-    const float *rows;       // [catalog][16]
-    const float *ovf;        // the terms past the 14th of the longer rows
+    static constexpr int R = PW / 8, RPW = 32 / R, SLOTS = PW - 1;
+    const float *rows;       // [catalog][PW]
+    const float *ovf;        // the terms past the inline ones of the longer rows
     float occ_r, occ_l;
 
     __device__ __forceinline__ void batch(const int32_t (&id)[U], bool full, int lane, Sum &acc) const
     {
         const int row = lane / R, col = lane % R;
         F8 v[U][R];
-        load_rows<16, U>(rows, id, full, lane, v);   // step 1: each event's whole row
-        // the headers are in the pieces of the rows' first lanes
+        load_rows<PW, U>(rows, id, full, lane, v);   // step 1: each event's whole row
+        // the masks are in the pieces of the rows' first lanes
         bool over = false;
         if (col == 0) {
 #pragma unroll
             for (int u = 0; u < U; ++u)
 #pragma unroll
                 for (int q = 0; q < R; ++q) {
-                    over |= __popc(__float_as_uint(v[u][q].v[0])) > INLINE;
+                    over |= __popc(__float_as_uint(v[u][q].v[0])) > SLOTS;
                     v[u][q].v[0] = 0.f;
-                    v[u][q].v[1] = 0.f;
                 }
         }
         float g[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-            // step 2: the sum over ELTs -- this lane's pieces, then a
-            // reduce-scatter over the row's two lanes
-            float p[R];
+            // step 2: the sum over ELTs -- this lane's pieces, then (two
+            // lanes per row) a reduce-scatter over the row's lanes
+            if constexpr (R == 1) {
+                g[u] = sum8(v[u][0]);
+            } else {
+                float p[R];
 #pragma unroll
-            for (int q = 0; q < R; ++q) p[q] = sum8(v[u][q]);
-            const bool hi = (col & 1) != 0;
-            const float keep = hi ? p[1] : p[0];
-            const float send = hi ? p[0] : p[1];
-            g[u] = __fadd_rn(keep, __shfl_xor_sync(kFull, send, 1));
+                for (int q = 0; q < R; ++q) p[q] = sum8(v[u][q]);
+                const bool hi = (col & 1) != 0;
+                const float keep = hi ? p[1] : p[0];
+                const float send = hi ? p[0] : p[1];
+                g[u] = __fadd_rn(keep, __shfl_xor_sync(kFull, send, 1));
+            }
         }
-        if (__any_sync(kFull, over)) {   // rare: a row with more than 14 terms
+        if (__any_sync(kFull, over)) {   // rare: a row with an overflow
             const uint32_t *w = reinterpret_cast<const uint32_t *>(rows);
 #pragma unroll
             for (int u = 0; u < U; ++u) {
                 const int32_t ev = __shfl_sync(kFull, id[u], col * RPW + row);   // the lane's event
-                const uint32_t mask = ev >= 0 ? __ldg(w + (size_t)(uint32_t)ev * 16) : 0u;
-                const int extra = __popc(mask) - INLINE;
-                if (extra > 0) {
-                    const float *o = ovf + __ldg(w + (size_t)(uint32_t)ev * 16 + 1);
-                    for (int i = 0; i < extra; ++i) g[u] = __fadd_rn(g[u], __ldg(o + i));
+                const uint32_t *r = w + (size_t)(uint32_t)(ev >= 0 ? ev : 0) * PW;
+                const int cnt = ev >= 0 ? __popc(__ldg(r)) : 0;
+                if (cnt > SLOTS) {
+                    float t = 0.f;
+                    for (int i = 1; i < SLOTS; ++i) t = __fadd_rn(t, __uint_as_float(__ldg(r + i)));
+                    const float *o = ovf + __ldg(r + SLOTS);
+                    for (int i = 0; i < cnt - (SLOTS - 1); ++i) t = __fadd_rn(t, __ldg(o + i));
+                    g[u] = t;
                 }
             }
         }
@@ -352,7 +360,7 @@ __device__ __forceinline__ W4 load4w(const unsigned long long *p)
 }
 
 // FP64 path over the packed FP64 table (repack.cu, launch_pack64): row e is
-// RW words (8: 64 bytes, at every layer width) -- word 0 holds the mask of
+// RW = 4 or 8 words (32 or 64 bytes) -- word 0 holds the mask of
 // the ELT columns whose term is not 0 (low 32 bits) and an overflow offset
 // (high 32 bits), words 1 .. RW - 1 the non-zero terms in column order.  A row with more non-zero terms than that keeps the first
 // RW - 1 inline and all of them at the overflow offset.  The terms are

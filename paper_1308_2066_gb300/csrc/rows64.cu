@@ -1,10 +1,10 @@
 // rows64.cu -- the FP64 analysis stage (Basic Algorithm, Section II-B) for
 // one layer, with the table rows held in registers (rows.cuh, BodyP64).
 //
-// The FP64 terms are read from the layer's packed FP64 table: one 64-byte
-// row per catalog event holding the mask of the ELTs whose term is not 0 and
-// up to 7 of those terms in column order (a longer row's terms are all in an
-// overflow array).  At the paper's sizes a dense FP64 row (8 bytes per
+// The FP64 terms are read from the layer's packed FP64 table: one 32- or
+// 64-byte row per catalog event holding the mask of the ELTs whose term is
+// not 0 and up to 3 or 7 of those terms in column order (a longer row's
+// terms are all in an overflow array).  At the paper's sizes a dense FP64 row (8 bytes per
 // ELT: 128 MB at 1M events x 16 ELTs, the size of L2) would come half from
 // HBM, and a non-zero term is a few per cent of the entries.  Every
 // occurrence reads its event's whole row; the terms are added in column
@@ -81,6 +81,10 @@ void go(const SimArgs &a, const TermsF64 &tm, int scale, int num_sms, cudaStream
 int launch_rows64(const SimArgs &a, int row_words, const TermsF64 &t, int scale, int num_sms, cudaStream_t s)
 {
     if (a.n_trials <= 0) return 0;
+    if (row_words == 4) {
+        go<4>(a, t, scale, num_sms, s);
+        return 1;
+    }
     if (row_words == 8) {
         go<8>(a, t, scale, num_sms, s);
         return 1;

@@ -7,10 +7,11 @@
 //      arena memory for the request's table and YLT are free (admission by
 //      memory), building each admitted request's direct-access table;
 //   2. hands out events_per_launch to the running requests in arrival
-//      order, or (least_work_first) in order of least remaining work less
-//      the time each has already waited (so a long request is not
-//      overtaken for ever by short ones that keep arriving); each takes
-//      what it needs, the last one a partial slice.  The slices of small
+//      order (the oldest runs whole, the others share the budget), or
+//      (least_work_first) in order of least remaining work less the time
+//      each has already waited (so a long request is not overtaken for
+//      ever by short ones that keep arriving); each takes what it needs,
+//      the last one a partial slice.  The slices of small
 //      requests run in one persistent launch of the multi-layer kernel (one
 //      launch per table width); a request of at least kLargeSlice events
 //      runs its slices on the single-layer register-rows kernel, which is
@@ -386,7 +387,11 @@ void scheduler(Server *SP)
                     Slot &sl = S.slots[o.second];
                     const int64_t left = sl.req.n_trials - sl.launched;
                     int64_t take = left;
-                    if (!S.cfg.one_at_a_time) {
+                    // in arrival order the oldest request runs whole: nothing
+                    // may overtake it, so cutting it into slices would only
+                    // add launches; the requests behind it share the budget
+                    const bool head = !S.cfg.least_work_first && &o == &order.front();
+                    if (!S.cfg.one_at_a_time && !head) {
                         if (left_budget < tpi) break;
                         take = std::min<int64_t>(left, (int64_t)left_budget / tpi * tpi);
                         if (take < left && take < tpi) take = std::min<int64_t>(left, tpi);

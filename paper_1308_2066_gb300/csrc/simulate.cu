@@ -396,11 +396,11 @@ void launch_rows_t(const SimArgs &a, const TermsF32 &tm, int num_sms, cudaStream
     ARE_CUDA_TRY(cudaGetLastError());
 }
 
-// Packed FP32 rows (layers of more than 16 ELTs): a.table the rows, a.table2
-// the overflow terms.
-template <int U, int ACC, bool FIXED>
-__global__ void __launch_bounds__(256, rows_min_blocks(16, U))
-    k_rows_packed(const rows::Trials a, const rows::BodyPackedF32<U, ACC> body, const int64_t n_trials)
+// Packed FP32 rows of PW words (8 or 16): a.table the rows, a.table2 the
+// overflow terms.
+template <int PW, int U, int ACC, bool FIXED>
+__global__ void __launch_bounds__(256, rows_min_blocks(PW, U))
+    k_rows_packed(const rows::Trials a, const rows::BodyPackedF32<PW, U, ACC> body, const int64_t n_trials)
 {
     const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -408,10 +408,10 @@ __global__ void __launch_bounds__(256, rows_min_blocks(16, U))
     rows::run_trials<U, FIXED>(a, body, warp * n_trials / nw, (warp + 1) * n_trials / nw, lane);
 }
 
-template <int U, int ACC, bool FIXED>
+template <int PW, int U, int ACC, bool FIXED>
 void launch_packed_t(const SimArgs &a, const TermsF32 &tm, int num_sms, cudaStream_t s)
 {
-    auto kern = k_rows_packed<U, ACC, FIXED>;
+    auto kern = k_rows_packed<PW, U, ACC, FIXED>;
     const int per_sm = fit_blocks(reinterpret_cast<const void *>(kern), 256, 0);
     int64_t blocks = (a.n_trials + 7) / 8;
     const int64_t cap = (int64_t)num_sms * per_sm;
@@ -425,7 +425,7 @@ void launch_packed_t(const SimArgs &a, const TermsF32 &tm, int num_sms, cudaStre
     t.ylt = a.ylt;
     t.agg_r = a.agg_r;
     t.agg_l = a.agg_l;
-    rows::BodyPackedF32<U, ACC> body;
+    rows::BodyPackedF32<PW, U, ACC> body;
     body.rows = static_cast<const float *>(a.table);
     body.ovf = static_cast<const float *>(a.table2);
     body.occ_r = tm.occ_r;
@@ -434,14 +434,16 @@ void launch_packed_t(const SimArgs &a, const TermsF32 &tm, int num_sms, cudaStre
     ARE_CUDA_TRY(cudaGetLastError());
 }
 
-template <int ACC>
+template <int PW, int ACC>
 void launch_packed(const SimArgs &a, const TermsF32 &tm, int num_sms, cudaStream_t s)
 {
     const bool two = a.epl != 1;
     if (a.off)
-        two ? launch_packed_t<2, ACC, false>(a, tm, num_sms, s) : launch_packed_t<1, ACC, false>(a, tm, num_sms, s);
+        two ? launch_packed_t<PW, 2, ACC, false>(a, tm, num_sms, s)
+            : launch_packed_t<PW, 1, ACC, false>(a, tm, num_sms, s);
     else
-        two ? launch_packed_t<2, ACC, true>(a, tm, num_sms, s) : launch_packed_t<1, ACC, true>(a, tm, num_sms, s);
+        two ? launch_packed_t<PW, 2, ACC, true>(a, tm, num_sms, s)
+            : launch_packed_t<PW, 1, ACC, true>(a, tm, num_sms, s);
 }
 
 template <int JP, int ACC>
@@ -459,8 +461,10 @@ void launch_rows(const SimArgs &a, const TermsF32 &tm, int num_sms, cudaStream_t
 template <int ACC>
 int launch_fp32(const SimArgs &a, int jp, const TermsF32 &tm, int num_sms, cudaStream_t s)
 {
-    if (a.kernel == 5) {   // register rows over packed FP32 rows
-        launch_packed<ACC>(a, tm, num_sms, s);
+    if (a.kernel == 5) {   // register rows over packed FP32 rows of jp words
+        if (jp == 8) launch_packed<8, ACC>(a, tm, num_sms, s);
+        else if (jp == 16) launch_packed<16, ACC>(a, tm, num_sms, s);
+        else throw Error{ARE_EINVAL, "packed FP32 rows are 8 or 16 words"};
         return 1;
     }
     const bool staged = a.kernel == 1 || a.kernel == 4;   // 4: the compact table's rows

@@ -184,27 +184,46 @@ def test_fixed_trial_lengths_at_batch_edges(are, ctx, orc, k):
         L.release()
 
 
-@pytest.mark.parametrize("J", [17, 20, 32])
-def test_packed_rows_past_the_inline_terms(are, orc, J):
-    """Layers of more than 16 ELTs run the register-rows kernels over packed
-    rows: the mask of the non-zero terms and up to 14 FP32 terms inline (the
-    rest in an overflow array), or up to 7 FP64 terms inline (a longer row's
-    terms all in the overflow).  Events that every ELT holds have J non-zero
-    terms, past the inline ones; the others have a few.  Every precision
-    matches the oracle; a fresh context keeps the untuned default."""
-    g = np.random.Generator(np.random.PCG64(900 + J))
-    C = 3000
+# (J, catalog, events every ELT holds, other entries per ELT,
+#  FP32 rows, FP64 rows) -- rows as (bytes, packed) from are_layer_rows
+PACKED_CASES = [
+    (8, 40_000, 200, 300, (32, False), (32, True)),
+    (9, 40_000, 200, 300, (32, True), (32, True)),
+    (12, 40_000, 200, 300, (32, True), (32, True)),
+    (20, 40_000, 200, 300, (32, True), (32, True)),
+    (32, 40_000, 200, 300, (32, True), (32, True)),
+    (32, 20_000, 100, 1500, (64, True), (64, True)),
+    (12, 3000, 600, 400, (64, False), (64, True)),
+    (17, 3000, 600, 400, (64, True), (64, True)),
+]
+
+
+@pytest.mark.parametrize("case", PACKED_CASES, ids=lambda c: f"j{c[0]}_c{c[1]}")
+def test_packed_rows_past_the_inline_terms(are, orc, case):
+    """The register-rows kernels read packed rows -- the mask of an event's
+    non-zero terms, then up to 7 or 15 FP32 terms (3 or 7 FP64) inline, the
+    rest of a longer row in an overflow array -- of 32 bytes where the
+    layer's entries per catalog event are few, else 64 bytes (or, for up to
+    16 ELTs in FP32, the dense row).  The events that every ELT holds have J
+    non-zero terms, past the inline ones; the others have a few.  Every
+    precision matches the oracle, with the row size the layer calls for, on
+    a fresh context (the untuned default)."""
+    J, C, n_shared, n_other, rows32, rows64 = case
+    g = np.random.Generator(np.random.PCG64(900 + J + C))
     yet = W.yet_poisson(g, 2000, 40, C)
-    shared = g.permutation(C)[:600]
+    shared = g.permutation(C)[:n_shared]
     elts = []
     for _ in range(J):
-        ids = np.unique(np.concatenate([shared, g.permutation(C)[:400]])).astype(np.int32)
+        ids = np.unique(np.concatenate([shared, g.permutation(C)[:n_other]])).astype(np.int32)
         elts.append(W.ELT(ids, np.exp(g.normal(9.0, 1.5, ids.size))))
     wl = W.Workload("packed", yet, elts, [W.Layer(list(range(J)), 1e3, INF, 1e4, INF)])
     c = are.are_create(0)
     try:
         L = Loaded(are, c, wl)
+        assert are.are_layer_rows(c, L.layers[0], L.yet, 1) == rows32
+        assert are.are_layer_rows(c, L.layers[0], L.yet, 0) == rows64
         ref = orc.simulate_layer(wl)
+        assert np.isin(yet.ids, shared).sum() > 50     # rows past the inline terms are read
         for p in (0, 1, 2):
             ok, st = mixed_check(L.simulate(0, p), ref.ylt, trial_bound(wl, 0), RTOL[p])
             assert ok, (p, st)

@@ -231,8 +231,8 @@ def test_large_request_on_the_single_layer_kernel(are):
     """A request of at least 32M events runs its slices on the single-layer
     register-rows kernel: its result equals are_simulate + are_risk_measures
     on the same layer (the same kernel and arithmetic per trial), alone and
-    in a mix of small requests, sliced into many launches, in either budget
-    order."""
+    in a mix of small requests, whole (arrival order) or sliced into many
+    launches (least work first)."""
     import torch
     g = np.random.Generator(np.random.PCG64(45))
     n, k, C = 80_000, 500, 20_000
