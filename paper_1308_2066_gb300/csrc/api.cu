@@ -1668,7 +1668,7 @@ are_status are_autotune(are_ctx *ctx, const int32_t *layers, int32_t n_layers, i
                     cands.push_back(e);
                 }
         } else {
-            for (int u : {1, 2}) {      // register rows over the FP32 screen
+            for (int u : {1, 2}) {      // register rows over the packed FP64 rows
                 TuneEntry e;
                 e.kernel = 2;
                 e.cfg.rows_in_flight = u;
