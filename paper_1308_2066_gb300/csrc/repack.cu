@@ -75,32 +75,51 @@ __global__ void k_pack64(const double *__restrict__ dense, int jp64, int32_t cat
 // than pw - 1 non-zero terms keeps the first pw - 2 inline and in word
 // pw - 1 the offset of a block of the overflow array (handed out by an
 // atomic counter) that holds the rest in column order.
-__global__ void k_pack32(const float *__restrict__ dense, int jp, int32_t catalog, int pw,
-                         uint32_t *__restrict__ rows, float *__restrict__ ovf,
-                         unsigned long long *__restrict__ ovf_used)
+template <int JP, int PW>
+__global__ void k_pack32(const float *__restrict__ dense, int32_t catalog, uint32_t *__restrict__ rows,
+                         float *__restrict__ ovf, unsigned long long *__restrict__ ovf_used)
 {
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < catalog;
          e += (int64_t)gridDim.x * blockDim.x) {
-        const float *d = dense + e * jp;
-        uint32_t *out = rows + e * pw;
-        uint32_t mask = 0;
-        for (int j = 0; j < jp; ++j)
-            if (__float_as_uint(d[j]) != 0) mask |= 1u << j;
-        const int cnt = __popc(mask);
-        const bool over = cnt > pw - 1;
-        const int inl = over ? pw - 2 : cnt;
-        uint32_t off = 0;
-        if (over) off = (uint32_t)atomicAdd(ovf_used, (unsigned long long)(cnt - inl));
-        out[0] = mask;
-        int k = 0;
-        for (uint32_t m = mask; m; m &= m - 1) {
-            const float x = d[__ffs(m) - 1];
-            if (k < inl) out[1 + k] = __float_as_uint(x);
-            else ovf[off + k - inl] = x;
-            ++k;
+        // the dense row in 16-byte loads
+        uint32_t v[JP];
+        const uint4 *d = reinterpret_cast<const uint4 *>(dense + e * JP);
+#pragma unroll
+        for (int q = 0; q < JP / 4; ++q) {
+            const uint4 x = __ldcs(d + q);
+            v[4 * q] = x.x;
+            v[4 * q + 1] = x.y;
+            v[4 * q + 2] = x.z;
+            v[4 * q + 3] = x.w;
         }
-        for (int i = 1 + inl; i < pw; ++i) out[i] = 0u;
-        if (over) out[pw - 1] = off;
+        uint32_t mask = 0;
+#pragma unroll
+        for (int j = 0; j < JP; ++j) mask |= (v[j] != 0u ? 1u : 0u) << j;
+        const int cnt = __popc(mask);
+        const bool over = cnt > PW - 1;
+        const int inl = over ? PW - 2 : cnt;
+        // word 1 + r holds the non-zero term of rank r (column order), r < inl
+        uint32_t w[PW];
+        w[0] = mask;
+#pragma unroll
+        for (int i = 1; i < PW; ++i) w[i] = 0u;
+#pragma unroll
+        for (int j = 0; j < JP; ++j) {
+            const int r = __popc(mask & ((1u << j) - 1u));
+#pragma unroll
+            for (int i = 1; i < PW; ++i)
+                if (((mask >> j) & 1u) && r == i - 1 && r < inl) w[i] = v[j];
+        }
+        if (over) {   // rare: the terms past the inline ones go to an overflow block
+            const uint32_t off = (uint32_t)atomicAdd(ovf_used, (unsigned long long)(cnt - inl));
+            int k = 0;
+            for (uint32_t m = mask; m; m &= m - 1, ++k)
+                if (k >= inl) ovf[off + k - inl] = __uint_as_float(v[__ffs(m) - 1]);
+            w[PW - 1] = off;
+        }
+        uint4 *out = reinterpret_cast<uint4 *>(rows + e * PW);
+#pragma unroll
+        for (int q = 0; q < PW / 4; ++q) out[q] = make_uint4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
     }
 }
 
@@ -117,7 +136,15 @@ int launch_pack32(const float *dense, int jp, int32_t catalog, int pw, uint32_t 
     if (catalog <= 0) return 0;
     int64_t blocks = ((int64_t)catalog + 255) / 256;
     if (blocks > (int64_t)num_sms * 16) blocks = (int64_t)num_sms * 16;
-    k_pack32<<<(unsigned)blocks, 256, 0, s>>>(dense, jp, catalog, pw, rows, ovf, ovf_used);
+    if (jp == 16 && pw == 8)
+        k_pack32<16, 8><<<(unsigned)blocks, 256, 0, s>>>(dense, catalog, rows, ovf, ovf_used);
+    else if (jp == 32 && pw == 8)
+        k_pack32<32, 8><<<(unsigned)blocks, 256, 0, s>>>(dense, catalog, rows, ovf, ovf_used);
+    else if (jp == 32 && pw == 16)
+        k_pack32<32, 16><<<(unsigned)blocks, 256, 0, s>>>(dense, catalog, rows, ovf, ovf_used);
+    else
+        throw Error{ARE_EINVAL, "no packed FP32 rows of " + std::to_string(pw) + " words for a table of " +
+                                    std::to_string(jp) + " columns"};
     ARE_CUDA_TRY(cudaGetLastError());
     return 1;
 }

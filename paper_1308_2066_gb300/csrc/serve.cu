@@ -107,6 +107,7 @@ struct Request {
     std::vector<int32_t> elts;
     are_layer_terms terms{};
     int64_t n_trials = 0;
+    int64_t entries = 0;            // ELT entries of the request's layer
     int n_rp = 0, n_tv = 0;
     int64_t ranks[kMaxTargets] = {};
     Clock::time_point t_submit;
@@ -120,6 +121,8 @@ struct Slot {
     LayerF32 rec{};
     int64_t launched = 0;           // trials handed to launches so far
     bool large = false;             // its slices run on the single-layer register-rows kernel
+    int pw = 0;                     // large: words per packed row (0: the dense rows)
+    size_t dense_bytes = 0;         // the dense table at the start of the block; packed rows after it
     uint64_t finish_iter = 0;       // iteration whose completion posts the result
     SelectScratch sel;
     double *h_res = nullptr;        // pinned, 2 * kMaxTargets
@@ -201,6 +204,22 @@ ulonglong2 *folded_F(char *b, int32_t catalog)
     return reinterpret_cast<ulonglong2 *>(b + 256 + up((size_t)folded_words(catalog) * 4));
 }
 
+// A large request's packed rows in its arena block, after the dense table:
+// [dense | rows | counter (256 B) | overflow].
+uint32_t *packed_rows(Server &S, const Slot &sl)
+{
+    return reinterpret_cast<uint32_t *>(S.d_arena + sl.tab_off + up(sl.dense_bytes));
+}
+unsigned long long *packed_used(Server &S, const Slot &sl)
+{
+    return reinterpret_cast<unsigned long long *>(
+        reinterpret_cast<char *>(packed_rows(S, sl)) + up((size_t)S.y->catalog * sl.pw * sizeof(float)));
+}
+float *packed_ovf(Server &S, const Slot &sl)
+{
+    return reinterpret_cast<float *>(reinterpret_cast<char *>(packed_used(S, sl)) + 256);
+}
+
 // Table of an admitted request, built on the server stream in its arena block.
 void build_request_table(Server &S, Slot &sl)
 {
@@ -227,8 +246,13 @@ void build_request_table(Server &S, Slot &sl)
                                     S.ctx->num_sms, S.stream));
         return;
     }
-    ARE_CUDA_TRY(cudaMemsetAsync(S.d_arena + sl.tab_off, 0, sl.tab_bytes, S.stream));
-    add_launches(S, launch_scatter_table(S.d_arena + sl.tab_off, true, a, S.stream));
+    char *b = S.d_arena + sl.tab_off;
+    ARE_CUDA_TRY(cudaMemsetAsync(b, 0, sl.dense_bytes, S.stream));
+    add_launches(S, launch_scatter_table(b, true, a, S.stream));
+    if (sl.pw)
+        add_launches(S, launch_pack32(reinterpret_cast<const float *>(b), sl.jp, S.y->catalog, sl.pw,
+                                      packed_rows(S, sl), packed_ovf(S, sl), packed_used(S, sl),
+                                      S.ctx->num_sms, S.stream));
 }
 
 void fill_record(Server &S, Slot &sl)
@@ -328,8 +352,18 @@ void scheduler(Server *SP)
                     Request &r = S.pending.front();
                     Slot &sl = S.slots[free_slot];
                     sl.jp = table_jp((int)r.elts.size(), true);
+                    sl.large = (double)r.n_trials * S.mean_events >= kLargeSlice;
+                    // a large request's single-layer kernel reads packed rows
+                    // where the layer's entries per catalog event are few
+                    sl.pw = sl.large && !S.cfg.folded
+                                ? packed_row_words((int)r.elts.size(),
+                                                   (double)r.entries / (double)S.y->catalog, true)
+                                : 0;
+                    sl.dense_bytes = (size_t)S.y->catalog * sl.jp * sizeof(float);
                     sl.tab_bytes = S.cfg.folded ? folded_block_bytes(S.y->catalog)
-                                                : (size_t)S.y->catalog * sl.jp * sizeof(float);
+                                   : sl.pw ? up(sl.dense_bytes) + up((size_t)S.y->catalog * sl.pw * sizeof(float)) +
+                                                 256 + up(sizeof(float) * (size_t)r.entries + 8)
+                                           : sl.dense_bytes;
                     sl.ylt_bytes = sizeof(double) * (size_t)r.n_trials;
                     size_t a = 0, b = 0;
                     if (!S.arena.take(sl.tab_bytes, a)) break;
@@ -344,7 +378,6 @@ void scheduler(Server *SP)
                     sl.busy = true;
                     sl.cancelled = sl.finishing = false;
                     sl.launched = 0;
-                    sl.large = (double)sl.req.n_trials * S.mean_events >= kLargeSlice;
                     sl.t_admit = Clock::now();
                     S.running[sl.req.ticket] = free_slot;
                     admitted.push_back(free_slot);
@@ -489,10 +522,16 @@ void scheduler(Server *SP)
                 sa.ylt = sl.rec.ylt + sl.launched;
                 sa.kernel = 2;
                 sa.epl = 2;
+                if (sl.pw) {   // over the packed rows
+                    sa.table = packed_rows(S, sl);
+                    sa.table2 = packed_ovf(S, sl);
+                    sa.kernel = 5;
+                }
                 TermsF32 tm;
                 tm.occ_r = sl.rec.occ_r;
                 tm.occ_l = sl.rec.occ_l;
-                launches += launch_simulate(sa, S.cfg.precision, sl.jp, &tm, nullptr, S.ctx->num_sms, S.stream);
+                launches += launch_simulate(sa, S.cfg.precision, sl.pw ? sl.pw : sl.jp, &tm, nullptr,
+                                            S.ctx->num_sms, S.stream);
             }
             // requests whose last slice is in this launch: select their risk measures
             {
@@ -685,6 +724,7 @@ are_status are_submit(are_ctx *ctx, const are_request *req, int64_t *ticket)
                 ARE_CHECK(std::find(r.elts.begin(), r.elts.end(), req->elt_handles[j]) == r.elts.end(),
                           ARE_EINVAL, "ELT appears twice in the request");
                 r.elts.push_back(req->elt_handles[j]);
+                r.entries += e->second.n;
             }
             for (int32_t i = 0; i < req->n_rp; ++i) {
                 r.ranks[i] = rank_for_return_period(req->n_trials, req->return_periods[i]);

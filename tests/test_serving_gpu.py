@@ -227,12 +227,15 @@ def test_stop_drops_queued_requests(are, served):
     are.are_server_stop(ctx)
 
 
-def test_large_request_on_the_single_layer_kernel(are):
+@pytest.mark.parametrize("members", [[3, 1, 4, 0, 5, 9, 2, 6], [7, 3, 11, 1, 4, 0, 10, 5, 9, 2, 8, 6]],
+                         ids=["j8_dense_rows", "j12_packed_rows"])
+def test_large_request_on_the_single_layer_kernel(are, members):
     """A request of at least 32M events runs its slices on the single-layer
-    register-rows kernel: its result equals are_simulate + are_risk_measures
-    on the same layer (the same kernel and arithmetic per trial), alone and
-    in a mix of small requests, whole (arrival order) or sliced into many
-    launches (least work first)."""
+    register-rows kernel (over packed rows for the 12-ELT layer, whose ELTs
+    hold few entries per catalog event): its result equals are_simulate +
+    are_risk_measures on the same layer (the same kernel, rows and
+    arithmetic per trial), alone and in a mix of small requests, whole
+    (arrival order) or sliced into many launches (least work first)."""
     import torch
     g = np.random.Generator(np.random.PCG64(45))
     n, k, C = 80_000, 500, 20_000
@@ -242,8 +245,9 @@ def test_large_request_on_the_single_layer_kernel(are):
     try:
         y = are.are_load_yet(ctx, C, n, None, k, torch.from_numpy(yet.ids).cuda())
         hs = [are.are_load_elt(ctx, e.ids, e.losses, e.fx, e.ded, e.lim, e.share) for e in elts]
-        members, terms = [3, 1, 4, 0, 5, 9, 2, 6], (2e4, 1e6, 5e4, 5e7)
+        terms = (2e4, 1e6, 5e4, 5e7)
         layer = are.are_define_layer(ctx, [hs[m] for m in members], *terms)
+        assert are.are_layer_rows(ctx, layer, y, are.ARE_FP32_KAHAN)[1] == (len(members) > 8)
         out = torch.empty(n, dtype=torch.float64, device="cuda")
         are.are_simulate(ctx, layer, y, 0, n, are.ARE_FP32_KAHAN, out)
         pml, tv = are.are_risk_measures(ctx, out, n, RPS, LEVELS)
