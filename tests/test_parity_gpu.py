@@ -114,6 +114,23 @@ def test_risk_measures_negative_and_tied_values(are, ctx, orc):
     assert rel_close(tv, rtv, 1e-13)
 
 
+def test_layer_rows_arguments(are, ctx, tiny):
+    """are_layer_rows reports, launches nothing and rejects bad arguments."""
+    h, y = tiny.layers[0], tiny.yet
+    l0 = are.are_launch_count(ctx)
+    for p in PRECISIONS:
+        for k in (-1, 0, 1, 2, 3):
+            rb, packed = are.are_layer_rows(ctx, h, y, p, k)
+            assert rb in (32, 64, 128) and (not packed or k in (-1, 2))
+    assert are.are_launch_count(ctx) == l0
+    with pytest.raises(are.AreError) as e:
+        are.are_layer_rows(ctx, h, y, 1, 4)
+    assert e.value.status == are.ARE_EINVAL
+    with pytest.raises(are.AreError) as e:
+        are.are_layer_rows(ctx, 987654, y, 1)
+    assert e.value.status == are.ARE_ENOTFOUND
+
+
 def test_risk_measure_arguments_rejected(are, ctx):
     y = np.ones(10)
     for rps, lv in (([0.5], []), ([], [1.0]), ([], [0.0]), ([float("nan")], [])):
