@@ -257,13 +257,34 @@ class Resident:
         self.layer = are.are_define_layer(ctx, self.elts, L.occ_r, L.occ_l, L.agg_r, L.agg_l)
 
 
+class StepMeasures:
+    """A step's PML/TVaR: selected into device arrays (the call only
+    enqueues) and copied to pinned host memory on the step's stream, so
+    consecutive steps queue back to back; read after the stream is done."""
+
+    def __init__(self, torch):
+        self.d_pml = torch.empty(len(RPS), dtype=torch.float64, device="cuda")
+        self.d_tv = torch.empty(len(LEVELS), dtype=torch.float64, device="cuda")
+        self.h_pml = torch.empty(len(RPS), dtype=torch.float64, pin_memory=True)
+        self.h_tv = torch.empty(len(LEVELS), dtype=torch.float64, pin_memory=True)
+
+    def select(self, are, torch, ctx, ylt, n, stream):
+        are.are_risk_measures(ctx, ylt, n, RPS, LEVELS, stream, out=(self.d_pml, self.d_tv))
+        with torch.cuda.stream(stream):
+            self.h_pml.copy_(self.d_pml, non_blocking=True)
+            self.h_tv.copy_(self.d_tv, non_blocking=True)
+
+    def values(self):
+        return [float(x) for x in self.h_pml], [float(x) for x in self.h_tv]
+
+
 def time_path(are, torch, res, prec, steps, warmup, stream, ylt, gather=None, world=1):
     """Run warmup + timed steps of one precision; returns timing dict."""
     ctx, wl = res.ctx, res.wl
     n = wl.yet.n_trials
     sim_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
               for _ in range(steps)]
-    out = {}
+    meas = StepMeasures(torch)
 
     def step(i=None):
         are.are_prepare(ctx, res.layer, res.yet, prec, stream)
@@ -275,9 +296,9 @@ def time_path(are, torch, res, prec, steps, warmup, stream, ylt, gather=None, wo
         if gather is not None:
             with torch.cuda.stream(stream):
                 full = gather(ylt)
-            out["pml"], out["tvar"] = are.are_risk_measures(ctx, full, None, RPS, LEVELS, stream)
+            meas.select(are, torch, ctx, full, full.numel(), stream)
         else:
-            out["pml"], out["tvar"] = are.are_risk_measures(ctx, ylt, n, RPS, LEVELS, stream)
+            meas.select(are, torch, ctx, ylt, n, stream)
 
     for _ in range(warmup):
         step()
@@ -296,8 +317,9 @@ def time_path(are, torch, res, prec, steps, warmup, stream, ylt, gather=None, wo
     launches = are.are_launch_count(ctx) - l0
     ms = start.elapsed_time(end)
     sim_ms = float(np.mean([a.elapsed_time(b) for a, b in sim_ev]))
+    pml, tvar = meas.values()
     return {"ms": ms, "sim_ms": sim_ms, "launches": launches, "clocks": clk.summary(),
-            "pml": [float(x) for x in out["pml"]], "tvar": [float(x) for x in out["tvar"]]}
+            "pml": pml, "tvar": tvar}
 
 
 def time_folded(are, torch, res, steps, warmup, stream, ylt, gather=None, world=1):
@@ -307,7 +329,7 @@ def time_folded(are, torch, res, steps, warmup, stream, ylt, gather=None, world=
     n = wl.yet.n_trials
     sim_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
               for _ in range(steps)]
-    out = {}
+    meas = StepMeasures(torch)
 
     def step(i=None):
         are.are_prepare_folded(ctx, res.layer, res.yet, stream)
@@ -319,9 +341,9 @@ def time_folded(are, torch, res, steps, warmup, stream, ylt, gather=None, world=
         if gather is not None:
             with torch.cuda.stream(stream):
                 full = gather(ylt)
-            out["pml"], out["tvar"] = are.are_risk_measures(ctx, full, None, RPS, LEVELS, stream)
+            meas.select(are, torch, ctx, full, full.numel(), stream)
         else:
-            out["pml"], out["tvar"] = are.are_risk_measures(ctx, ylt, n, RPS, LEVELS, stream)
+            meas.select(are, torch, ctx, ylt, n, stream)
 
     for _ in range(warmup):
         step()
@@ -340,7 +362,7 @@ def time_folded(are, torch, res, steps, warmup, stream, ylt, gather=None, world=
     return {"ms": start.elapsed_time(end),
             "sim_ms": float(np.mean([a.elapsed_time(b) for a, b in sim_ev])),
             "launches": are.are_launch_count(ctx) - l0, "clocks": clk.summary(),
-            "pml": [float(x) for x in out["pml"]], "tvar": [float(x) for x in out["tvar"]]}
+            "pml": meas.values()[0], "tvar": meas.values()[1]}
 
 
 def barrier(world):
@@ -485,39 +507,55 @@ def run_e2e(are, torch, ctx, wl, prec, steps, warmup, world):
     """Per step, from pinned host memory through the public API: load the
     ELTs, define the layer, build its table, analyse the host-resident YET
     (its copy to the device overlapped with the analysis, chunk by chunk),
-    select PML/TVaR and read them back."""
+    select PML/TVaR and read them back.  The YET is held in host memory with
+    its ids packed in the bits the catalog needs (are_pack_ids, once, before
+    the timed steps); the same steps over int32 ids are reported beside."""
     y = wl.yet
-    ids_pinned = torch.from_numpy(y.ids).pin_memory()
     L = wl.layers[0]
-    h2d = y.ids.nbytes + sum(e.ids.nbytes + e.losses.nbytes for e in wl.elts)
+    bits = max(1, int(y.catalog - 1).bit_length())
+    words = are.packed_words(y.n_events, bits)
+    packed = torch.empty(words, dtype=torch.int32, pin_memory=True)
+    are.are_pack_ids(ctx, y.ids, bits, packed.data_ptr())
+    ids_pinned = torch.from_numpy(y.ids).pin_memory()
+    elt_bytes = sum(e.ids.nbytes + e.losses.nbytes for e in wl.elts)
     ylt = torch.empty(y.n_trials, dtype=torch.float64, device="cuda")
     d2h = 8 * (len(RPS) + len(LEVELS))
 
-    def step():
-        elts = [are.are_load_elt(ctx, e.ids, e.losses, e.fx, e.ded, e.lim, e.share)
-                for e in wl.elts]
-        layer = are.are_define_layer(ctx, elts, L.occ_r, L.occ_l, L.agg_r, L.agg_l)
-        are.are_simulate_streamed(ctx, layer, y.catalog, y.n_trials, None, y.k, ids_pinned, prec, ylt)
-        are.are_risk_measures(ctx, ylt, y.n_trials, RPS, LEVELS)
-        are.are_free_layer(ctx, layer)
-        for h in elts:
-            are.are_free_elt(ctx, h)
+    def timed(analyse):
+        def step():
+            elts = [are.are_load_elt(ctx, e.ids, e.losses, e.fx, e.ded, e.lim, e.share)
+                    for e in wl.elts]
+            layer = are.are_define_layer(ctx, elts, L.occ_r, L.occ_l, L.agg_r, L.agg_l)
+            analyse(layer)
+            are.are_risk_measures(ctx, ylt, y.n_trials, RPS, LEVELS)
+            are.are_free_layer(ctx, layer)
+            for h in elts:
+                are.are_free_elt(ctx, h)
 
-    for _ in range(warmup):
-        step()
-    barrier(world)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(steps):
-        step()
-    torch.cuda.synchronize()
-    dt = max_over_ranks(time.perf_counter() - t0, world, torch)
+        for _ in range(warmup):
+            step()
+        barrier(world)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            step()
+        torch.cuda.synchronize()
+        return max_over_ranks(time.perf_counter() - t0, world, torch)
+
+    dt = timed(lambda layer: are.are_simulate_streamed_packed(
+        ctx, layer, y.catalog, y.n_trials, None, y.k, packed.data_ptr(), bits, prec, ylt))
+    dt32 = timed(lambda layer: are.are_simulate_streamed(
+        ctx, layer, y.catalog, y.n_trials, None, y.k, ids_pinned, prec, ylt))
     J = len(L.elts)
     value = world * steps * y.n_events * J / dt / 1e9
-    return {"value": round(value, 3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+    return {"value": round(value, 3), "unit": UNIT, "h2d_bytes_per_step": int(4 * words + elt_bytes),
             "d2h_bytes_per_step": int(d2h), "ms_per_step": round(dt / steps * 1e3, 3),
-            "how": "are_load_elt x J, are_define_layer, are_simulate_streamed (host YET, "
-                   "copy overlapped with the analysis), are_risk_measures, frees"}
+            "how": (f"are_load_elt x J, are_define_layer, are_simulate_streamed_packed (host YET with "
+                    f"{bits}-bit ids, copy overlapped with the analysis), are_risk_measures, frees"),
+            "int32_ids": {"value": round(world * steps * y.n_events * J / dt32 / 1e9, 3),
+                          "ms_per_step": round(dt32 / steps * 1e3, 3),
+                          "h2d_bytes_per_step": int(y.ids.nbytes + elt_bytes),
+                          "how": "the same steps with are_simulate_streamed over int32 ids"}}
 
 
 # ---------------------------------------------------------------------------
@@ -1007,7 +1045,8 @@ def main():
         "data": "synthetic: seeded uniform YET ids, lognormal(11,1.5) ELT losses (paper's data is proprietary)",
         "config": {"workload": wl.name, "trials_per_gpu": y.n_trials, "events_per_trial": y.k,
                    "elts": J, "catalog": y.catalog, "precision": PRECISION_NAMES[prec],
-                   "step": "repack table + simulate all trials + PML 100/250 + TVaR 99 readback",
+                   "step": ("repack table + simulate all trials + PML 100/250 + TVaR 99 into device "
+                            "arrays + their copy to pinned host memory; steps queued back to back"),
                    "l2": "inputs larger than L2 (4 GB YET streamed every step)",
                    "parallelism": f"trial blocks per GPU x{world}",
                    "gpu": torch.cuda.get_device_name()},

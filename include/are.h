@@ -338,6 +338,28 @@ ARE_API are_status are_simulate_streamed(are_ctx *ctx, int32_t layer, int32_t ca
                                          int64_t chunk_events, are_precision precision,
                                          double *ylt, void *stream);
 
+/* are_simulate_streamed over a host YET whose event ids are packed id_bits
+ * bits each (1 .. 32; ceil(log2(catalog_size)) is enough): id i occupies
+ * bits i * id_bits .. (i + 1) * id_bits - 1 of the stream of 32-bit words
+ * packed_ids (bit b of the stream is bit b % 32 of word b / 32), as
+ * are_pack_ids writes it: ceil(n_events * id_bits / 32) words of host
+ * memory.  Only those words cross the host-to-device link (2.5 bytes per id
+ * for a catalog of up to 2^20 events, against 4); the ids are unpacked and
+ * checked on the device as each chunk arrives.  Same results, arguments,
+ * stream and error behaviour as are_simulate_streamed otherwise. */
+ARE_API are_status are_simulate_streamed_packed(are_ctx *ctx, int32_t layer, int32_t catalog_size,
+                                                int64_t n_trials, const int64_t *offsets,
+                                                int32_t events_per_trial, const uint32_t *packed_ids,
+                                                int32_t id_bits, int64_t chunk_events,
+                                                are_precision precision, double *ylt, void *stream);
+
+/* Packs n event ids (host memory, each in [0, 2^id_bits)) id_bits bits each
+ * into ceil(n * id_bits / 32) 32-bit words of host memory, the layout
+ * are_simulate_streamed_packed reads.  Host work only; ARE_EINVAL for an id
+ * that does not fit. */
+ARE_API are_status are_pack_ids(are_ctx *ctx, const int32_t *ids, int64_t n, int32_t id_bits,
+                                uint32_t *out);
+
 /* One launch shape of the gather ceiling and its measured rate. */
 typedef struct {
     int32_t kind;            /* 0: 16-byte loads, row_bytes/16 lanes per row, each lane
@@ -379,9 +401,15 @@ ARE_API are_status are_gather_ceiling(are_ctx *ctx, int32_t yet, int32_t row_byt
  *   tvar_out[r] = the mean of the m largest losses,
  *                 m = ceil(n * (1 - tvar_levels[r])), level read to the
  *                 nearest 1e-9 and strictly between 0 and 1.
- * pml_out and tvar_out are host arrays.  The paper names these measures
- * without defining them (Section I, Section II-C); this is the reading the
- * library takes.  Synchronises `stream`. */
+ * The paper names these measures without defining them (Section I,
+ * Section II-C); this is the reading the library takes.
+ * pml_out and tvar_out are both host arrays (the call synchronises
+ * `stream`) or both device arrays (ylt must then be device memory: the call
+ * only enqueues the selection and the copies into them, and returns; the
+ * values are there when `stream` reaches that point).  The selection's
+ * scratch belongs to the context, so selections of one context on
+ * different streams must not overlap.  Mixed host and device outputs, or
+ * device outputs with a host YLT, are ARE_EINVAL. */
 ARE_API are_status are_risk_measures(are_ctx *ctx, const double *ylt, int64_t n,
                              const double *return_periods, int32_t n_rp, double *pml_out,
                              const double *tvar_levels, int32_t n_tv, double *tvar_out,

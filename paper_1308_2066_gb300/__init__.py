@@ -117,6 +117,9 @@ _SIGS = {
     "are_simulate_folded": (C.c_int32, [_P, C.c_int32, C.c_int32, C.c_int64, C.c_int64, _P, _P]),
     "are_simulate_streamed": (C.c_int32, [_P, C.c_int32, C.c_int32, C.c_int64, _P, C.c_int32, _P,
                                           C.c_int64, C.c_int, _P, _P]),
+    "are_simulate_streamed_packed": (C.c_int32, [_P, C.c_int32, C.c_int32, C.c_int64, _P, C.c_int32, _P,
+                                                 C.c_int32, C.c_int64, C.c_int, _P, _P]),
+    "are_pack_ids": (C.c_int32, [_P, _P, C.c_int64, C.c_int32, _P]),
     "are_gather_ceiling": (C.c_int32, [_P, C.c_int32, C.c_int32, C.c_int64, C.c_int64,
                                        C.c_int32, C.POINTER(C.c_double),
                                        C.POINTER(CeilingShape), C.c_int32,
@@ -326,6 +329,34 @@ def are_simulate_streamed(ctx, layer: int, catalog_size: int, n_trials: int, off
                                             _stream(stream)))
 
 
+def are_simulate_streamed_packed(ctx, layer: int, catalog_size: int, n_trials: int, offsets,
+                                 events_per_trial: int, packed_ids, id_bits: int, precision: int, ylt,
+                                 chunk_events: int = 0, stream=None) -> None:
+    """are_simulate_streamed over ids packed id_bits bits each (see
+    are_pack_ids)."""
+    _check(ctx, lib().are_simulate_streamed_packed(ctx, int(layer), int(catalog_size), int(n_trials),
+                                                   _addr(offsets, np.int64), int(events_per_trial),
+                                                   _addr(packed_ids, np.uint32), int(id_bits),
+                                                   int(chunk_events), int(precision),
+                                                   _addr(ylt, np.float64), _stream(stream)))
+
+
+def packed_words(n: int, id_bits: int) -> int:
+    """32-bit words that n ids of id_bits bits take."""
+    return (int(n) * int(id_bits) + 31) // 32
+
+
+def are_pack_ids(ctx, ids, id_bits: int, out=None):
+    """Packs host int32 ids id_bits bits each into uint32 words (a new numpy
+    array, or `out`: a host numpy array or pinned tensor of packed_words
+    words); returns the words."""
+    n = _len(ids)
+    if out is None:
+        out = np.empty(packed_words(n, id_bits), np.uint32)
+    _check(ctx, lib().are_pack_ids(ctx, _addr(ids, np.int32), n, int(id_bits), _addr(out, np.uint32)))
+    return out
+
+
 def are_gather_ceiling(ctx, yet: int, row_bytes: int, trial_begin: int = 0,
                        n_trials: Optional[int] = None, reps: int = 3, shapes: bool = False):
     """Rows per second of a pure id-stream + table-row gather over the YET,
@@ -347,11 +378,19 @@ def are_gather_ceiling(ctx, yet: int, row_bytes: int, trial_begin: int = 0,
 
 def are_risk_measures(ctx, ylt, n: Optional[int] = None,
                       return_periods: Sequence[float] = (100.0, 250.0),
-                      tvar_levels: Sequence[float] = (0.99,), stream=None):
-    """Returns (pml, tvar) as numpy float64 arrays."""
+                      tvar_levels: Sequence[float] = (0.99,), stream=None, out=None):
+    """Returns (pml, tvar) as numpy float64 arrays; with out=(pml, tvar)
+    (device float64 arrays, a device YLT) the call only enqueues the
+    selection into them and returns None."""
     n = _len(ylt) if n is None else int(n)
     rp = np.ascontiguousarray(return_periods, dtype=np.float64)
     lv = np.ascontiguousarray(tvar_levels, dtype=np.float64)
+    if out is not None:
+        pml, tv = out
+        _check(ctx, lib().are_risk_measures(ctx, _addr(ylt, np.float64), n, rp.ctypes.data,
+                                            rp.shape[0], _addr(pml, np.float64), lv.ctypes.data,
+                                            lv.shape[0], _addr(tv, np.float64), _stream(stream)))
+        return None
     pml = np.empty(rp.shape[0], np.float64)
     tv = np.empty(lv.shape[0], np.float64)
     _check(ctx, lib().are_risk_measures(ctx, _addr(ylt, np.float64), n, rp.ctypes.data,

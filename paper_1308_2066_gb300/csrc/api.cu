@@ -1209,13 +1209,14 @@ are_status are_simulate_folded(are_ctx *ctx, int32_t layer, int32_t yet, int64_t
     });
 }
 
-are_status are_simulate_streamed(are_ctx *ctx, int32_t layer, int32_t catalog_size, int64_t n_trials,
-                                 const int64_t *offsets, int32_t events_per_trial,
-                                 const int32_t *event_ids, int64_t chunk_events,
-                                 are_precision precision, double *ylt, void *stream)
+// The analysis over a host-resident YET, chunk by chunk (are_simulate_streamed
+// and are_simulate_streamed_packed).  id_bits 0: event_ids is int32[n_events];
+// 1 .. 32: a stream of 32-bit words holding the ids packed id_bits bits each.
+static void simulate_streamed(are_ctx *ctx, int32_t layer, int32_t catalog_size, int64_t n_trials,
+                       const int64_t *offsets, int32_t events_per_trial, const void *event_ids, int id_bits,
+                       int64_t chunk_events, are_precision precision, double *ylt, void *stream)
 {
-    return guarded(ctx, [&] {
-        NvtxRange nvtx("are_simulate_streamed");
+    {
         check_precision(precision);
         Layer &L = layer_of(ctx, layer);
         ARE_CHECK(catalog_size > 0, ARE_EINVAL, "catalog_size must be > 0");
@@ -1267,12 +1268,16 @@ are_status are_simulate_streamed(are_ctx *ctx, int32_t layer, int32_t catalog_si
             t = u;
         }
         const size_t buf_bytes = sizeof(int32_t) * (size_t)(longest + 4 + kIdPad);
+        // packed ids: the words of the longest chunk, a partial word on each
+        // side and one more the unpacking may read
+        const size_t wbuf_bytes = id_bits ? sizeof(uint32_t) * (size_t)((longest * id_bits + 31) / 32 + 3) : 0;
 
         const bool fp32 = precision != ARE_FP64;
         ensure_tables(ctx, L, v, precision, s, false);
         const int jp = table_jp((int)L.elts.size(), fp32);
         int64_t *d_off = nullptr;
         int32_t *buf[2] = {nullptr, nullptr};
+        uint32_t *wbuf[2] = {nullptr, nullptr};
         const bool dev_out = is_device_ptr(ylt);
         double *d_out = nullptr;
         cudaEvent_t start = nullptr, ready[2] = {nullptr, nullptr}, done[2] = {nullptr, nullptr};
@@ -1281,6 +1286,7 @@ are_status are_simulate_streamed(are_ctx *ctx, int32_t layer, int32_t catalog_si
                 if (e) cudaEventDestroy(e);
             if (!dev_out) dfree(ctx, d_out, sizeof(double) * n_trials);
             for (int i = 0; i < 2; ++i) dfree(ctx, buf[i], buf_bytes);
+            for (int i = 0; i < 2; ++i) dfree(ctx, wbuf[i], wbuf_bytes);
             dfree(ctx, d_off, d_off ? sizeof(int64_t) * (n_trials + 1) : 0);
         };
         try {
@@ -1290,6 +1296,11 @@ are_status are_simulate_streamed(are_ctx *ctx, int32_t layer, int32_t catalog_si
             }
             v.d_off = d_off;
             for (int i = 0; i < 2; ++i) buf[i] = (int32_t *)dalloc(ctx, buf_bytes);
+            if (id_bits)
+                for (int i = 0; i < 2; ++i) {
+                    wbuf[i] = (uint32_t *)dalloc(ctx, wbuf_bytes);
+                    ARE_CUDA_TRY(cudaMemsetAsync(wbuf[i], 0, wbuf_bytes, s));
+                }
             d_out = dev_out ? ylt : (double *)dalloc(ctx, sizeof(double) * n_trials);
             for (cudaEvent_t *e : {&start, &ready[0], &ready[1], &done[0], &done[1]})
                 ARE_CUDA_TRY(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
@@ -1306,13 +1317,24 @@ are_status are_simulate_streamed(are_ctx *ctx, int32_t layer, int32_t catalog_si
                 // chunk's preparation runs on the analysis stream
                 if (c >= 2) ARE_CUDA_TRY(cudaStreamWaitEvent(cp, done[slot], 0));
                 int32_t *b = buf[slot];
-                if (n) ARE_CUDA_TRY(cudaMemcpyAsync(b + lead, event_ids + first, sizeof(int32_t) * n,
-                                                    cudaMemcpyHostToDevice, cp));
+                if (!id_bits) {
+                    if (n)
+                        ARE_CUDA_TRY(cudaMemcpyAsync(b + lead, static_cast<const int32_t *>(event_ids) + first,
+                                                     sizeof(int32_t) * n, cudaMemcpyHostToDevice, cp));
+                } else if (n) {   // the words that hold the chunk's ids
+                    const int64_t w0 = first * id_bits / 32, w1 = ((first + n) * id_bits + 31) / 32;
+                    ARE_CUDA_TRY(cudaMemcpyAsync(wbuf[slot], static_cast<const uint32_t *>(event_ids) + w0,
+                                                 sizeof(uint32_t) * (w1 - w0), cudaMemcpyHostToDevice, cp));
+                }
                 ARE_CUDA_TRY(cudaEventRecord(ready[slot], cp));
                 ARE_CUDA_TRY(cudaStreamWaitEvent(s, ready[slot], 0));
                 if (lead) ARE_CUDA_TRY(cudaMemsetAsync(b, 0, sizeof(int32_t) * lead, s));
                 ARE_CUDA_TRY(cudaMemsetAsync(b + lead + n, 0, sizeof(int32_t) * kIdPad, s));
-                ctx->launches += launch_sanitize_ids(b + lead, n, catalog_size, ctx->d_flag, s);
+                if (!id_bits)
+                    ctx->launches += launch_sanitize_ids(b + lead, n, catalog_size, ctx->d_flag, s);
+                else
+                    ctx->launches += launch_unpack_ids(wbuf[slot], first * id_bits - first * id_bits / 32 * 32,
+                                                       id_bits, n, catalog_size, b + lead, ctx->d_flag, s);
                 Yet cv = v;
                 cv.d_ids = b + lead - first;   // indexed by the YET's own event numbers
                 ctx->launches += run_single(ctx, L, cv, t0, t1 - t0, precision, d_out + t0, te, s);
@@ -1330,6 +1352,59 @@ are_status are_simulate_streamed(are_ctx *ctx, int32_t layer, int32_t catalog_si
             throw;
         }
         cleanup();
+    }
+}
+
+are_status are_simulate_streamed(are_ctx *ctx, int32_t layer, int32_t catalog_size, int64_t n_trials,
+                                 const int64_t *offsets, int32_t events_per_trial,
+                                 const int32_t *event_ids, int64_t chunk_events,
+                                 are_precision precision, double *ylt, void *stream)
+{
+    return guarded(ctx, [&] {
+        NvtxRange nvtx("are_simulate_streamed");
+        simulate_streamed(ctx, layer, catalog_size, n_trials, offsets, events_per_trial, event_ids, 0,
+                          chunk_events, precision, ylt, stream);
+    });
+}
+
+are_status are_simulate_streamed_packed(are_ctx *ctx, int32_t layer, int32_t catalog_size, int64_t n_trials,
+                                        const int64_t *offsets, int32_t events_per_trial,
+                                        const uint32_t *packed_ids, int32_t id_bits, int64_t chunk_events,
+                                        are_precision precision, double *ylt, void *stream)
+{
+    return guarded(ctx, [&] {
+        NvtxRange nvtx("are_simulate_streamed_packed");
+        ARE_CHECK(id_bits >= 1 && id_bits <= 32, ARE_EINVAL, "id_bits must lie in 1 .. 32");
+        simulate_streamed(ctx, layer, catalog_size, n_trials, offsets, events_per_trial, packed_ids, id_bits,
+                          chunk_events, precision, ylt, stream);
+    });
+}
+
+are_status are_pack_ids(are_ctx *ctx, const int32_t *ids, int64_t n, int32_t id_bits, uint32_t *out)
+{
+    return guarded(ctx, [&] {
+        ARE_CHECK(id_bits >= 1 && id_bits <= 32, ARE_EINVAL, "id_bits must lie in 1 .. 32");
+        ARE_CHECK(n >= 0 && (n == 0 || (ids && out)), ARE_EINVAL, "NULL array");
+        ARE_CHECK(!is_device_ptr(ids) && !is_device_ptr(out), ARE_EINVAL, "ids and out must be host memory");
+        const uint64_t lim = id_bits == 32 ? (1ull << 32) : (1ull << id_bits);
+        const int64_t words = (n * id_bits + 31) / 32;
+        uint64_t acc = 0;   // bits not yet written, the lowest first
+        int have = 0;
+        int64_t w = 0;
+        for (int64_t i = 0; i < n; ++i) {
+            const int32_t v = ids[i];
+            ARE_CHECK(v >= 0 && (uint64_t)v < lim, ARE_EINVAL,
+                      "id " + std::to_string(v) + " does not fit in " + std::to_string(id_bits) + " bits");
+            acc |= (uint64_t)(uint32_t)v << have;
+            have += id_bits;
+            if (have >= 32) {
+                out[w++] = (uint32_t)acc;
+                acc >>= 32;
+                have -= 32;
+            }
+        }
+        if (have > 0) out[w++] = (uint32_t)acc;
+        ARE_CHECK(w == words, ARE_EINVAL, "internal: packed word count");
     });
 }
 
@@ -1452,6 +1527,33 @@ are_status are_risk_measures(are_ctx *ctx, const double *ylt, int64_t n,
         for (int32_t r = 0; r < n_rp; ++r) ranks.push_back(rank_rp(n, return_periods[r]));
         for (int32_t r = 0; r < n_tv; ++r) ranks.push_back(rank_level(n, tvar_levels[r]));
         if (ranks.empty()) return;
+        // device outputs: the call only enqueues (see the header)
+        const bool dev_pml = n_rp > 0 && is_device_ptr(pml_out), dev_tv = n_tv > 0 && is_device_ptr(tvar_out);
+        const bool dev_out = dev_pml || dev_tv;
+        if (dev_out) {
+            ARE_CHECK((n_rp == 0 || dev_pml) && (n_tv == 0 || dev_tv), ARE_EINVAL,
+                      "pml_out and tvar_out must both be host or both be device arrays");
+            ARE_CHECK(is_device_ptr(ylt), ARE_EINVAL, "device outputs need a device YLT");
+            CallStream cs(ctx, stream);
+            cudaStream_t s = cs.s;
+            const int32_t nr = (int32_t)ranks.size();
+            for (int32_t b = 0; b < nr; b += kMaxTargets) {
+                const int nt = std::min<int32_t>(kMaxTargets, nr - b);
+                ctx->launches += launch_select(ylt, n, ranks.data() + b, nt, ctx->sel, ctx->num_sms, s);
+                // result: (m-th largest, mean of the m largest) per target
+                const int p_end = std::min(b + nt, n_rp);
+                if (p_end > b)
+                    ARE_CUDA_TRY(cudaMemcpy2DAsync(pml_out + b, sizeof(double), ctx->sel.result, 2 * sizeof(double),
+                                                   sizeof(double), p_end - b, cudaMemcpyDeviceToDevice, s));
+                const int t_begin = std::max(b, n_rp);
+                if (b + nt > t_begin)
+                    ARE_CUDA_TRY(cudaMemcpy2DAsync(tvar_out + (t_begin - n_rp), sizeof(double),
+                                                   ctx->sel.result + 2 * (t_begin - b) + 1, 2 * sizeof(double),
+                                                   sizeof(double), b + nt - t_begin, cudaMemcpyDeviceToDevice, s));
+            }
+            cs.finish();
+            return;
+        }
         CallStream cs(ctx, stream);
         cudaStream_t s = cs.s;
         const bool dev_in = is_device_ptr(ylt);

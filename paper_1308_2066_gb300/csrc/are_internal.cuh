@@ -328,6 +328,11 @@ int fit_blocks(const void *kern, int threads, size_t smem);
 // validate.cu: each sets *flag (device int, zeroed by the caller) non-zero on a violation
 int launch_check_ids(const int32_t *ids, int64_t n, int32_t catalog, int *flag, cudaStream_t s);
 int launch_sanitize_ids(int32_t *ids, int64_t n, int32_t catalog, int *flag, cudaStream_t s);
+// ids of `bits` bits each packed into 32-bit words (id j at bit bit0 + j *
+// bits; one word past the last id readable) -> int32, checked against the
+// catalog like launch_sanitize_ids.
+int launch_unpack_ids(const uint32_t *words, int64_t bit0, int bits, int64_t n, int32_t catalog, int32_t *out,
+                      int *flag, cudaStream_t s);
 int launch_check_offsets(const int64_t *off, int64_t n_trials, int64_t n_events, int *flag,
                           cudaStream_t s);
 int launch_check_timestamps(const float *ts, const int64_t *off, int64_t n_trials, int32_t k,

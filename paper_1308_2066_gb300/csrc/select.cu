@@ -34,6 +34,7 @@ constexpr int kThreads = 256;
 constexpr int kLimbs = 3;                      // 32-bit limbs of one scaled value (< 2^96)
 constexpr int kAccWords = 2 * kLimbs + 1;      // per target: positive limbs, negative limbs, count
 constexpr int kCtrlWords = 4;                  // blocks arrived, top word of the largest |value|
+constexpr int kPre = 8;                        // values a lane loads before it processes them
 
 __device__ __forceinline__ uint64_t key_of(double x)
 {
@@ -258,24 +259,33 @@ __global__ void __launch_bounds__(kThreads) k_hist(Sel s, int64_t n, int nt, int
     const int lane = threadIdx.x & 31;
     unsigned int mag = 0;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    // warp-uniform loop: every lane takes part in the warp's histogram adds
+    // warp-uniform loop: every lane takes part in the warp's histogram adds;
+    // kPre values per lane are loaded before the first is counted
     for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n;
-         base += stride) {
-        const int64_t i = base + lane;
-        const bool ok = i < n;
-        const double x = ok ? v[i] : 0.0;
-        const uint64_t k = key_of(x);
-        const uint32_t d = (uint32_t)(k >> shift) & 0xffu;
-        if (pass == 0) {
-            hist_add(h, ok, d, lane);
-            const unsigned int m32 =
-                (unsigned int)(((unsigned long long)__double_as_longlong(x) >> 32) & 0x7fffffffu);
-            mag = m32 > mag ? m32 : mag;
-        } else {
+         base += stride * kPre) {
+        double xs[kPre];
 #pragma unroll
-            for (int t = 0; t < kMaxTargets; ++t) {
-                if (t >= nt) break;
-                hist_add(h + t * kBins, ok && (k >> (shift + 8)) == pre[t], d, lane);
+        for (int u = 0; u < kPre; ++u) {
+            const int64_t i = base + u * stride + lane;
+            xs[u] = i < n ? v[i] : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < kPre; ++u) {
+            const bool ok = base + u * stride + lane < n;
+            const double x = xs[u];
+            const uint64_t k = key_of(x);
+            const uint32_t d = (uint32_t)(k >> shift) & 0xffu;
+            if (pass == 0) {
+                hist_add(h, ok, d, lane);
+                const unsigned int m32 =
+                    (unsigned int)(((unsigned long long)__double_as_longlong(x) >> 32) & 0x7fffffffu);
+                mag = m32 > mag ? m32 : mag;
+            } else {
+#pragma unroll
+                for (int t = 0; t < kMaxTargets; ++t) {
+                    if (t >= nt) break;
+                    hist_add(h + t * kBins, ok && (k >> (shift + 8)) == pre[t], d, lane);
+                }
             }
         }
     }
@@ -329,22 +339,29 @@ __global__ void __launch_bounds__(kThreads) k_tail(Sel s, int64_t n, int nt, Ran
     const int sc = tail_scale(ctrl[1]);
     __syncthreads();
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        const double x = v[i];
-        const uint64_t k = key_of(x);
-        if (k > kmin) {
-            unsigned long long lo, hi;
-            scaled(x, sc, lo, hi);
-            const int sign = x < 0.0 ? kLimbs : 0;
-            const unsigned long long l0 = lo & 0xffffffffull, l1 = lo >> 32, l2 = hi;
+    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < n; i0 += stride * kPre) {
+        double xs[kPre];   // kPre values loaded before the first is added
 #pragma unroll
-            for (int t = 0; t < kMaxTargets; ++t) {
-                if (t < nt && k > kt[t]) {
-                    unsigned long long *p = a + t * kAccWords;
-                    atomicAdd(p + sign, l0);
-                    atomicAdd(p + sign + 1, l1);
-                    atomicAdd(p + sign + 2, l2);
-                    atomicAdd(p + 2 * kLimbs, 1ull);
+        for (int u = 0; u < kPre; ++u) xs[u] = i0 + u * stride < n ? v[i0 + u * stride] : 0.0;
+#pragma unroll
+        for (int u = 0; u < kPre; ++u) {
+            if (i0 + u * stride >= n) break;
+            const double x = xs[u];
+            const uint64_t k = key_of(x);
+            if (k > kmin) {
+                unsigned long long lo, hi;
+                scaled(x, sc, lo, hi);
+                const int sign = x < 0.0 ? kLimbs : 0;
+                const unsigned long long l0 = lo & 0xffffffffull, l1 = lo >> 32, l2 = hi;
+#pragma unroll
+                for (int t = 0; t < kMaxTargets; ++t) {
+                    if (t < nt && k > kt[t]) {
+                        unsigned long long *p = a + t * kAccWords;
+                        atomicAdd(p + sign, l0);
+                        atomicAdd(p + sign + 1, l1);
+                        atomicAdd(p + sign + 2, l2);
+                        atomicAdd(p + 2 * kLimbs, 1ull);
+                    }
                 }
             }
         }

@@ -41,6 +41,28 @@ __global__ void k_sanitize_ids(int32_t *__restrict__ ids, int64_t n, int32_t cat
     if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(flag, 1);
 }
 
+// Ids of `bits` bits each (1 .. 32), packed little-endian into 32-bit
+// words: id j starts at bit bit0 + j * bits of `words`, which must be
+// readable one word past the last id.  Writes them as int32 to out; an id
+// outside [0, catalog) is written as 0 and sets bit 0 of *flag.
+__global__ void k_unpack_ids(const uint32_t *__restrict__ words, int64_t bit0, int bits, int64_t n,
+                             int32_t catalog, int32_t *__restrict__ out, int *flag)
+{
+    int bad = 0;
+    const uint64_t mask = bits >= 32 ? 0xffffffffull : ((1ull << bits) - 1ull);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const int64_t b = bit0 + i * bits;
+        const int64_t w = b >> 5;
+        const uint64_t x = (((uint64_t)__ldg(words + w + 1) << 32) | __ldg(words + w)) >> (b & 31);
+        const uint32_t v = (uint32_t)(x & mask);
+        const bool ok = v < (uint32_t)catalog;
+        __stcs(out + i, ok ? (int32_t)v : 0);
+        bad |= !ok;
+    }
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(flag, 1);
+}
+
 __global__ void k_check_offsets(const int64_t *__restrict__ off, int64_t n_trials,
                                 int64_t n_events, int *flag)
 {
@@ -95,6 +117,15 @@ int launch_check_timestamps(const float *ts, const int64_t *off, int64_t n_trial
 {
     if (n_trials <= 0) return 0;
     k_check_ts<<<blocks_for(n_trials), 256, 0, s>>>(ts, off, n_trials, k, flag);
+    ARE_CUDA_TRY(cudaGetLastError());
+    return 1;
+}
+
+int launch_unpack_ids(const uint32_t *words, int64_t bit0, int bits, int64_t n, int32_t catalog, int32_t *out,
+                      int *flag, cudaStream_t s)
+{
+    if (n <= 0) return 0;
+    k_unpack_ids<<<blocks_for(n), 256, 0, s>>>(words, bit0, bits, n, catalog, out, flag);
     ARE_CUDA_TRY(cudaGetLastError());
     return 1;
 }

@@ -105,6 +105,33 @@ def test_risk_measures_on_oracle_ylt(are, ctx, orc, n):
         assert rel_close(tv, rtv, 1e-13), (tv, rtv)
 
 
+def test_risk_measures_into_device_arrays(are, ctx, orc):
+    """With device output arrays the selection is only enqueued: the same
+    values as the host-output call, for more targets than one selection
+    batch takes (the PML and TVaR runs split across batches)."""
+    import torch
+    g = np.random.default_rng(5)
+    y = np.round(g.lognormal(12, 2.0, 300_001), 2)
+    rps = [1.0, 2.0, 5.0, 10.0, 50.0, 100.0, 250.0]
+    lv = [0.5, 0.9, 0.99, 0.995, 0.999]
+    yd = torch.from_numpy(y).cuda()
+    want_pml, want_tv = are.are_risk_measures(ctx, yd, None, rps, lv)
+    s = torch.cuda.Stream()
+    pml = torch.full((len(rps),), -1.0, dtype=torch.float64, device="cuda")
+    tv = torch.full((len(lv),), -1.0, dtype=torch.float64, device="cuda")
+    assert are.are_risk_measures(ctx, yd, None, rps, lv, stream=s, out=(pml, tv)) is None
+    s.synchronize()
+    np.testing.assert_array_equal(pml.cpu().numpy(), want_pml)
+    np.testing.assert_array_equal(tv.cpu().numpy(), want_tv)
+    rpml, rtv = orc.risk_measures(y, rps, lv)
+    np.testing.assert_array_equal(want_pml, rpml)
+    # host and device outputs mixed, or a host YLT with device outputs
+    for ylt, out in ((yd, (pml, np.empty(len(lv)))), (y, (pml, tv))):
+        with pytest.raises(are.AreError) as e:
+            are.are_risk_measures(ctx, ylt, None, rps, lv, out=out)
+        assert e.value.status == are.ARE_EINVAL
+
+
 def test_risk_measures_negative_and_tied_values(are, ctx, orc):
     y = np.array([-5.0, 3.0, 3.0, 3.0, -0.0, 0.0, 2.5, -1e300, 1e300, 7.0])
     rps, lv = [1.0, 2.0, 3.0, 10.0], [0.5, 0.7, 0.95]

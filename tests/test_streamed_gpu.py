@@ -1,5 +1,6 @@
 """are_simulate_streamed: the analysis over a host-resident YET, copied to
-the device chunk by chunk while earlier chunks are analysed.  Each trial is
+the device chunk by chunk while earlier chunks are analysed (ids as int32,
+or packed a few bits each by are_pack_ids).  Each trial is
 computed by the same kernel as are_simulate, so the YLTs must be equal bit
 for bit, whatever the chunking; the FP64 result is also checked against the
 oracle."""
@@ -102,6 +103,84 @@ def test_invalid_ids_and_arguments(are, ctx):
             are.are_simulate_streamed(ctx, L.layers[0], wl.yet.catalog, 500, None, 0, wl.yet.ids, 1, out)
     finally:
         L.release()
+
+
+def pack_bits(ids, bits):
+    """The packed layout written out independently: id i in bits
+    i*bits .. (i+1)*bits-1 of a little-endian stream of 32-bit words."""
+    n = len(ids)
+    words = np.zeros((n * bits + 31) // 32 + 1, np.uint64)
+    for i, v in enumerate(ids.astype(np.uint64)):
+        b = i * bits
+        w, sh = b // 32, b % 32
+        x = int(v) << sh
+        words[w] |= np.uint64(x & 0xFFFFFFFF)
+        words[w + 1] |= np.uint64(x >> 32)
+    return words[: (n * bits + 31) // 32].astype(np.uint32)
+
+
+def test_pack_ids_layout(are, ctx):
+    g = np.random.default_rng(21)
+    for bits in (1, 7, 13, 20, 31, 32):
+        n = 1000 + bits
+        hi = min(1 << bits, 2**31 - 1)
+        ids = g.integers(0, hi, size=n, dtype=np.int64).astype(np.int32)
+        np.testing.assert_array_equal(are.are_pack_ids(ctx, ids, bits), pack_bits(ids, bits))
+    with pytest.raises(are.AreError) as e:
+        are.are_pack_ids(ctx, np.array([0, 8], np.int32), 3)      # 8 needs 4 bits
+    assert e.value.status == are.ARE_EINVAL
+    assert are.are_pack_ids(ctx, np.zeros(0, np.int32), 20).size == 0
+
+
+@pytest.mark.parametrize("bits", [None, 32, 20])
+def test_packed_ids_equal_plain_streaming(are, ctx, bits):
+    """Ids packed in the fewest bits the catalog needs (or 20, or 32): the
+    same YLT as the resident analysis, fixed and ragged YETs, every chunking;
+    ids past the catalog that the bits can hold are reported."""
+    import torch
+    g = np.random.Generator(np.random.PCG64(15))
+    counts = g.choice([0, 1, 5, 33, 300, 2000], size=700)
+    off = np.zeros(701, np.int64)
+    np.cumsum(counts, out=off[1:])
+    C = 6000
+    need = int(np.ceil(np.log2(C)))
+    b = need if bits is None else bits
+    ids = g.integers(0, C, size=int(off[-1]), dtype=np.int32)
+    elts = [W.percentile_terms(W.elt_lognormal(g, C, 900)) for _ in range(11)]
+    for offsets, k in ((off, 0), (None, None)):
+        if offsets is None:   # a fixed YET over the same ids
+            k = 97
+            n_trials = len(ids) // k
+            yet = W.YET(catalog=C, n_trials=n_trials, ids=ids[: n_trials * k].copy(), k=k)
+        else:
+            yet = W.YET(catalog=C, n_trials=700, ids=ids, offsets=offsets)
+        wl = W.Workload("p", yet, elts, [W.Layer(list(range(11)), 1e4, 1e6, 5e4, 5e8)])
+        L = Loaded(are, ctx, wl, timestamps=False)
+        try:
+            words = are.are_pack_ids(ctx, yet.ids, b)
+            pinned = torch.from_numpy(words.view(np.int32)).pin_memory()
+            for p in (0, 1):
+                ref = L.simulate(0, p)
+                for chunk in (0, 1000, 4099):
+                    out = torch.full((yet.n_trials,), -1.0, dtype=torch.float64, device="cuda")
+                    are.are_simulate_streamed_packed(ctx, L.layers[0], C, yet.n_trials, yet.offsets,
+                                                     k or 0, pinned.data_ptr(), b, p, out,
+                                                     chunk_events=chunk)
+                    np.testing.assert_array_equal(out.cpu().numpy(), ref)
+            if b > need:   # an id the bits can hold but the catalog does not
+                bad = yet.ids.copy()
+                bad[len(bad) // 2] = C
+                out = torch.zeros(yet.n_trials, dtype=torch.float64, device="cuda")
+                with pytest.raises(are.AreError) as e:
+                    are.are_simulate_streamed_packed(ctx, L.layers[0], C, yet.n_trials, yet.offsets,
+                                                     k or 0, are.are_pack_ids(ctx, bad, b), b, 1, out)
+                assert e.value.status == are.ARE_EINVAL
+        finally:
+            L.release()
+    with pytest.raises(are.AreError) as e:
+        are.are_simulate_streamed_packed(ctx, 0, C, 1, None, 5, np.zeros(4, np.uint32), 0, 1,
+                                         np.zeros(1))
+    assert e.value.status == are.ARE_EINVAL
 
 
 def test_device_offsets_and_caller_stream(are, ctx):
