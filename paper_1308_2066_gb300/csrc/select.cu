@@ -9,9 +9,18 @@
 // exactly (8 passes of 8 bits, every target rank in the same pass), then one
 // more pass adds the values above it.
 //
+// Two forms.  The single-YLT selection (launch_select: are_risk_measures,
+// the pricing server) takes five launches: the radix form's first two
+// passes (each target's bucket of the top 16 key bits), a pass that keeps
+// the keys of each target's bucket and sums the values above it, and one
+// block per target that finishes the selection among the kept keys
+// (details above k_collect).  The multi-YLT selection (a
+// portfolio's YLTs together) and the allocation-free one use the 8-pass
+// radix form below.
+//
 // GB300 choices.  Each histogram pass ends with the pick of the next digit,
 // done by whichever block of the pass finishes last (a counter and memory
-// fences, no waiting), so a selection is 10 launches.  Histogram counts are
+// fences, no waiting), so a radix selection is 10 launches.  Histogram counts are
 // aggregated per warp (lanes with the digit of the warp's first active lane
 // add once), since early passes send most values to one or two bins.  The tail sum avoids FP64
 // arithmetic, which GB300 issues at a small fraction of its integer rate:
@@ -412,6 +421,251 @@ __global__ void __launch_bounds__(kThreads) k_tail(Sel s, int64_t n, int nt, Ran
     if (threadIdx.x == 0) ctrl[0] = 0;
 }
 
+// ---------------------------------------------------------------------------
+// Single-YLT selection in five launches
+// ---------------------------------------------------------------------------
+//
+// k_init and the first two radix passes (k_hist, passes 0 and 1) find each
+// target's bucket of the keys' top 16 bits (sign, exponent and four mantissa
+// bits: 1/16 of an octave), its rank inside the bucket and the largest
+// magnitude, as in the radix form.  Then:
+// * k_collect: every key in a target's bucket is appended to the target's
+//   candidate list (up to kCand); every value in a higher bucket is added,
+//   scaled, to the target's exact integer tail sum and counted;
+// * k_finish, one block per target: the exact rank among the candidates by
+//   the remaining 48 bits (six 8-bit digits) in shared memory, then the
+//   bucket's values above the selected one added to the tail sum, and the
+//   result.  A bucket of more than kCand keys (a long run of ties) is
+//   selected by the same block from the whole YLT instead.
+
+constexpr int kCand = 16384;            // candidate keys kept per target
+constexpr int kFinThreads = 1024;
+
+struct Sel2 {
+    Sel sel;                     // the radix form's scratch (state, acc, ctrl, result)
+    unsigned long long *app;     // per target: keys appended to its list (zero between calls)
+    unsigned long long *cand;    // per target: kCand keys of its bucket
+};
+
+// Adds x (scaled by 2^sc) to the accumulator words a (positive and negative
+// limbs apart, then a count) in shared memory for the lanes with `on` set,
+// summed over the warp first (one set of atomics per warp and sign).  Every
+// lane must call it.
+__device__ __forceinline__ void acc_add_warp(unsigned long long *a, bool on, double x, int sc, int lane)
+{
+    if (!__any_sync(kFull, on)) return;
+    unsigned long long lo = 0, hi = 0;
+    if (on) scaled(x, sc, lo, hi);
+    for (int g = 0; g < 2; ++g) {   // positive, then negative values
+        const bool mine = on && ((x < 0.0) == (g == 1));
+        if (!__any_sync(kFull, mine)) continue;
+        unsigned long long w0 = mine ? (lo & 0xffffffffull) : 0, w1 = mine ? lo >> 32 : 0, w2 = mine ? hi : 0;
+        unsigned long long c = mine ? 1ull : 0ull;
+#pragma unroll
+        for (int off = 16; off; off >>= 1) {
+            w0 += __shfl_xor_sync(kFull, w0, off);
+            w1 += __shfl_xor_sync(kFull, w1, off);
+            w2 += __shfl_xor_sync(kFull, w2, off);
+            c += __shfl_xor_sync(kFull, c, off);
+        }
+        if (lane == 0) {
+            atomicAdd(a + g * kLimbs, w0);
+            atomicAdd(a + g * kLimbs + 1, w1);
+            atomicAdd(a + g * kLimbs + 2, w2);
+            atomicAdd(a + 2 * kLimbs, c);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) k_collect(Sel2 s2, int64_t n, int nt)
+{
+    const Sel &s = s2.sel;
+    const double *__restrict__ v = s.single;
+    __shared__ unsigned long long a[kMaxTargets * kAccWords];
+    for (int i = threadIdx.x; i < nt * kAccWords; i += blockDim.x) a[i] = 0;
+    uint32_t P[kMaxTargets];
+#pragma unroll
+    for (int t = 0; t < kMaxTargets; ++t) P[t] = t < nt ? (uint32_t)(s.state[2 * t] >> 48) : 0xffffffffu;
+    const int sc = tail_scale(s.ctrl[1]);
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    // warp-uniform loop: the lanes of a warp append their candidates together
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n;
+         base += stride * kPre) {
+        double xs[kPre];
+#pragma unroll
+        for (int u = 0; u < kPre; ++u) {
+            const int64_t i = base + u * stride + lane;
+            xs[u] = i < n ? v[i] : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < kPre; ++u) {
+            const bool ok = base + u * stride + lane < n;
+            const uint64_t k = key_of(xs[u]);
+            const uint32_t p = (uint32_t)(k >> 48);
+#pragma unroll
+            for (int t = 0; t < kMaxTargets; ++t) {
+                if (t >= nt) break;
+                const bool in = ok && p == P[t];
+                const unsigned b = __ballot_sync(kFull, in);
+                if (b) {
+                    const int leader = __ffs(b) - 1;
+                    unsigned long long at = 0;
+                    if (lane == leader) at = atomicAdd(s2.app + t, (unsigned long long)__popc(b));
+                    at = __shfl_sync(kFull, at, leader);
+                    const unsigned long long slot = at + (unsigned long long)__popc(b & ((1u << lane) - 1u));
+                    if (in && slot < (unsigned long long)kCand) s2.cand[(size_t)t * kCand + slot] = k;
+                }
+                acc_add_warp(a + t * kAccWords, ok && p > P[t], xs[u], sc, lane);
+            }
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < nt * kAccWords; i += blockDim.x)
+        if (a[i]) atomicAdd(&s.acc[i], a[i]);
+}
+
+// (value of key kt, mean of the m largest) from the accumulator words A of
+// the values above kt (sum and count, scaled by 2^sc).
+__device__ void tail_result(const unsigned long long (&A)[kAccWords], uint64_t kt, long long m, int sc,
+                            double *res)
+{
+    U192 pos, neg;
+    for (int g = 0; g < 2; ++g) {
+        U192 &z = g ? neg : pos;
+        const unsigned long long A0 = A[g * kLimbs], A1 = A[g * kLimbs + 1], A2 = A[g * kLimbs + 2];
+        add192(z, A0, 0, 0);
+        add192(z, A1 << 32, A1 >> 32, 0);
+        add192(z, 0, A2, 0);
+    }
+    const unsigned long long c = A[2 * kLimbs];
+    const double vt = value_of(kt);
+    const unsigned long long q = (unsigned long long)m - c;   // >= 1: ties at the m-th value
+    unsigned long long lo, hi;
+    scaled(vt, sc, lo, hi);
+    U192 &z = vt < 0.0 ? neg : pos;
+    add192(z, lo * q, __umul64hi(lo, q), 0);
+    add192(z, 0, hi * q, __umul64hi(hi, q));
+    double sum;
+    if (less192(pos, neg)) {
+        sub192(neg, pos);
+        sum = -to_double(neg, sc);
+    } else {
+        sub192(pos, neg);
+        sum = to_double(pos, sc);
+    }
+    res[0] = vt;
+    res[1] = __ddiv_rn(sum, (double)m);
+}
+
+// One warp: the bucket of h (256 counts in shared memory) that holds rank
+// rem, counting down from the top bucket; extends the prefix pre.
+__device__ __forceinline__ void pick_shared(const uint32_t *h, unsigned long long &pre, unsigned long long &rem,
+                                            int shift, int lane)
+{
+    uint32_t c[8];
+    unsigned long long lane_sum = 0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        c[i] = h[kBins - 1 - (lane * 8 + i)];   // lane 0 holds the top buckets
+        lane_sum += c[i];
+    }
+    unsigned long long incl = lane_sum;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const unsigned long long o = __shfl_up_sync(kFull, incl, off);
+        if (lane >= off) incl += o;
+    }
+    const unsigned long long excl = incl - lane_sum;
+    const unsigned long long r = rem;
+    __syncwarp();
+    if (excl < r && r <= incl) {
+        unsigned long long above = excl;
+        int b = 0;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            if (above + c[i] >= r) {
+                b = kBins - 1 - (lane * 8 + i);
+                break;
+            }
+            above += c[i];
+        }
+        pre |= (unsigned long long)b << shift;
+        rem = r - above;
+    }
+}
+
+// One block per target, kFinThreads threads, kCand keys of dynamic shared memory.
+__global__ void __launch_bounds__(kFinThreads) k_finish(Sel2 s2, int64_t n, Ranks r)
+{
+    const Sel &s = s2.sel;
+    const double *__restrict__ v = s.single;
+    extern __shared__ unsigned long long keys[];
+    __shared__ uint32_t hist[kBins];
+    __shared__ unsigned long long a[kAccWords];
+    __shared__ unsigned long long s_pre, s_rem;
+    const int t = blockIdx.x, lane = threadIdx.x & 31;
+    const uint64_t P = s.state[2 * t] >> 48;
+    const unsigned long long app = s2.app[t];
+    const bool fits = app <= (unsigned long long)kCand;
+    const int64_t cnt = fits ? (int64_t)app : n;   // keys to scan: the candidates, or the whole YLT
+    const int sc = tail_scale(s.ctrl[1]);
+    if (fits)
+        for (int64_t i = threadIdx.x; i < cnt; i += blockDim.x) keys[i] = __ldcg(s2.cand + (size_t)t * kCand + i);
+    if (threadIdx.x < kAccWords) a[threadIdx.x] = 0;
+    if (threadIdx.x == 0) {
+        s_pre = P << 48;
+        s_rem = s.state[2 * t + 1];
+    }
+    __syncthreads();
+    // the remaining 48 bits, 8 at a time, among the keys of the bucket
+    for (int shift = 40; shift >= 0; shift -= 8) {
+        for (int i = threadIdx.x; i < kBins; i += blockDim.x) hist[i] = 0;
+        __syncthreads();
+        const uint64_t pre = s_pre >> (shift + 8);
+        // warp-uniform: the keys share most leading bits, so the warp adds per bin
+        for (int64_t base = threadIdx.x & ~31; base < cnt; base += blockDim.x) {
+            const int64_t i = base + lane;
+            const bool ok = i < cnt;
+            const uint64_t k = ok ? (fits ? keys[i] : key_of(v[i])) : 0ull;
+            hist_add(hist, ok && (k >> (shift + 8)) == pre, (uint32_t)(k >> shift) & 0xffu, lane);
+        }
+        __syncthreads();
+        if (threadIdx.x < 32) pick_shared(hist, s_pre, s_rem, shift, threadIdx.x);
+        __syncthreads();
+    }
+    const uint64_t kt = s_pre;
+    // the bucket's values above the selected one
+    for (int64_t base = threadIdx.x & ~31; base < cnt; base += blockDim.x) {
+        const int64_t i = base + lane;
+        const bool ok = i < cnt;
+        const uint64_t k = ok ? (fits ? keys[i] : key_of(v[i])) : 0ull;
+        acc_add_warp(a, ok && (k >> 48) == P && k > kt, value_of(k), sc, lane);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long A[kAccWords];
+        for (int i = 0; i < kAccWords; ++i) A[i] = a[i] + __ldcg(s.acc + t * kAccWords + i);
+        tail_result(A, kt, r.m[t], sc, s.result + 2 * t);
+        s2.app[t] = 0;
+    }
+}
+
+cudaError_t enqueue2(const Sel2 &s, int64_t n, const int64_t *ranks, int nt, cudaStream_t st)
+{
+    Ranks r{};
+    for (int t = 0; t < nt; ++t) r.m[t] = ranks[t];
+    const dim3 grid((unsigned)s.sel.blocks, 1u);
+    k_init<<<1, kThreads, 0, st>>>(s.sel, r, nt);
+    for (int pass = 0; pass < 2; ++pass) k_hist<<<grid, kThreads, 0, st>>>(s.sel, n, nt, pass);
+    k_collect<<<s.sel.blocks, kThreads, 0, st>>>(s, n, nt);
+    const size_t smem = sizeof(unsigned long long) * kCand;
+    fit_blocks(reinterpret_cast<const void *>(k_finish), kFinThreads, smem);   // raises the shared-memory limit
+    k_finish<<<nt, kFinThreads, smem, st>>>(s, n, r);
+    return cudaGetLastError();
+}
+
 cudaError_t enqueue(const Sel &s, int n_ylt, int64_t n, const int64_t *ranks, int nt,
                     cudaStream_t st)
 {
@@ -441,6 +695,9 @@ void select_alloc(SelectScratch &s, int num_sms)
     ARE_CUDA_TRY(cudaMalloc(&s.ctrl, sizeof(unsigned int) * kCtrlWords));
     ARE_CUDA_TRY(cudaMalloc(&s.acc, sizeof(unsigned long long) * kMaxTargets * kAccWords));
     ARE_CUDA_TRY(cudaMalloc(&s.result, sizeof(double) * 2 * kMaxTargets));
+    ARE_CUDA_TRY(cudaMalloc(&s.app, sizeof(unsigned long long) * kMaxTargets));
+    ARE_CUDA_TRY(cudaMalloc(&s.cand, sizeof(unsigned long long) * kCand * kMaxTargets));
+    ARE_CUDA_TRY(cudaMemset(s.app, 0, sizeof(unsigned long long) * kMaxTargets));   // zero between calls
 }
 
 void select_free(SelectScratch &s)
@@ -450,6 +707,8 @@ void select_free(SelectScratch &s)
     cudaFree(s.ctrl);
     cudaFree(s.acc);
     cudaFree(s.result);
+    cudaFree(s.app);
+    cudaFree(s.cand);
     s = SelectScratch{};
 }
 
@@ -465,8 +724,10 @@ int launch_select(const double *ylt, int64_t n, const int64_t *ranks, int nt, Se
                   int num_sms, cudaStream_t st)
 {
     (void)num_sms;
-    ARE_CUDA_TRY(select_enqueue(ylt, n, ranks, nt, s, st));
-    return kSelectLaunches;
+    Sel2 sel{Sel{ylt, nullptr, s.hist, s.state, s.ctrl, s.acc, s.result, blocks_for(n, s.max_blocks)}, s.app,
+             s.cand};
+    ARE_CUDA_TRY(enqueue2(sel, n, ranks, nt, st));
+    return kSelectLaunches1;
 }
 
 namespace {

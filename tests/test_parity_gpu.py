@@ -105,6 +105,31 @@ def test_risk_measures_on_oracle_ylt(are, ctx, orc, n):
         assert rel_close(tv, rtv, 1e-13), (tv, rtv)
 
 
+def test_risk_measures_long_ties_and_successive_calls(are, ctx, orc):
+    """The single-YLT selection keeps up to 16384 keys of a target's bucket
+    (1/16 of an octave) for its last step; a longer run of equal values
+    there is selected from the whole YLT instead.  Successive calls on
+    YLTs of falling magnitude and of other lengths leave no state behind."""
+    import torch
+    g = np.random.default_rng(9)
+    n = 200_000
+    y = np.concatenate([10.0 + g.lognormal(3, 1, 80_000), np.full(120_000, 5.0)])
+    y = y[g.permutation(n)]
+    rps, lv = [1.0, 2.0, 3.0, 100.0], [0.3, 0.5, 0.99]
+    for arr in (y, -y, y * 1e-200, y[:4097], np.full(50_000, 7.25), y * 1e200, y):
+        rpml, rtv = orc.risk_measures(arr, rps, lv)
+        pml, tv = are.are_risk_measures(ctx, torch.from_numpy(arr).cuda(), None, rps, lv)
+        np.testing.assert_array_equal(pml, rpml)
+        # the tail sum is exact and rounded once, then divided: math.fsum's
+        # correctly rounded sum over m gives the same double; the oracle's
+        # sequential sum is within its own rounding of it
+        top = np.sort(arr)[::-1]
+        want = [math.fsum(top[: orc.rank_for_level(arr.size, a)]) / orc.rank_for_level(arr.size, a)
+                for a in lv]
+        np.testing.assert_array_equal(tv, want)
+        assert rel_close(tv, rtv, 1e-11), (tv, rtv)
+
+
 def test_risk_measures_into_device_arrays(are, ctx, orc):
     """With device output arrays the selection is only enqueued: the same
     values as the host-output call, for more targets than one selection
