@@ -39,33 +39,46 @@ __global__ void k_scatter(T *__restrict__ tab, const ScatterArgs a)
 
 // Packed FP64 rows (rw = 4 or 8 words: 32 or 64 bytes) from the dense FP64
 // table: row e gets the mask of its non-zero columns (low 32 bits of word 0)
-// and those terms in column order (words 1 .. rw - 1).  A row with more non-zero terms than that keeps the
-// first rw - 1 inline and all of them in a block of the overflow array,
-// whose offset goes to the high 32 bits of word 0 (blocks are handed out by
-// an atomic counter; each block holds its row's terms in column order).
-__global__ void k_pack64(const double *__restrict__ dense, int jp64, int32_t catalog, int rw,
+// and those terms in column order (words 1 .. rw - 1).  A row with more
+// non-zero terms than that keeps the first rw - 1 inline and all of them in
+// a block of the overflow array, whose offset goes to the high 32 bits of
+// word 0 (blocks are handed out by an atomic counter; each block holds its
+// row's terms in column order).
+template <int RW>
+__global__ void k_pack64(const double *__restrict__ dense, int jp64, int32_t catalog,
                          unsigned long long *__restrict__ rows, double *__restrict__ ovf,
                          unsigned long long *__restrict__ ovf_used)
 {
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < catalog;
          e += (int64_t)gridDim.x * blockDim.x) {
         const double *d = dense + e * jp64;
-        unsigned long long *out = rows + e * rw;
+        // the mask in 16-byte loads (rows are whole multiples of 32 bytes)
+        const ulonglong2 *d2 = reinterpret_cast<const ulonglong2 *>(d);
         uint32_t mask = 0;
-        for (int j = 0; j < jp64; ++j)
-            if (__double_as_longlong(d[j]) != 0) mask |= 1u << j;
-        const int cnt = __popc(mask);
-        uint32_t off = 0;
-        if (cnt > rw - 1) off = (uint32_t)atomicAdd(ovf_used, (unsigned long long)cnt);
-        out[0] = (unsigned long long)mask | ((unsigned long long)off << 32);
-        int k = 0;
-        for (uint32_t m = mask; m; m &= m - 1) {
-            const double x = d[__ffs(m) - 1];
-            if (k < rw - 1) out[1 + k] = (unsigned long long)__double_as_longlong(x);
-            if (cnt > rw - 1) ovf[off + k] = x;
-            ++k;
+        for (int q = 0; q < jp64 / 2; ++q) {
+            const ulonglong2 x = __ldg(d2 + q);
+            mask |= (x.x != 0ull ? 1u : 0u) << (2 * q);
+            mask |= (x.y != 0ull ? 1u : 0u) << (2 * q + 1);
         }
-        for (int i = 1 + (k < rw - 1 ? k : rw - 1); i < rw; ++i) out[i] = 0ull;
+        const int cnt = __popc(mask);
+        const bool over = cnt > RW - 1;
+        uint32_t off = 0;
+        if (over) off = (uint32_t)atomicAdd(ovf_used, (unsigned long long)cnt);
+        unsigned long long w[RW];
+        w[0] = (unsigned long long)mask | ((unsigned long long)off << 32);
+#pragma unroll
+        for (int i = 1; i < RW; ++i) w[i] = 0ull;
+        int k = 0;
+        for (uint32_t m = mask; m; m &= m - 1, ++k) {
+            const double x = __ldg(d + __ffs(m) - 1);
+#pragma unroll
+            for (int i = 1; i < RW; ++i)
+                if (k == i - 1) w[i] = (unsigned long long)__double_as_longlong(x);
+            if (over) ovf[off + k] = x;
+        }
+        ulonglong2 *out = reinterpret_cast<ulonglong2 *>(rows + e * RW);
+#pragma unroll
+        for (int q = 0; q < RW / 2; ++q) out[q] = make_ulonglong2(w[2 * q], w[2 * q + 1]);
     }
 }
 
@@ -178,7 +191,12 @@ int launch_pack64(const double *dense, int jp64, int32_t catalog, int rw, unsign
     if (catalog <= 0) return 0;
     int64_t blocks = ((int64_t)catalog + 255) / 256;
     if (blocks > (int64_t)num_sms * 16) blocks = (int64_t)num_sms * 16;
-    k_pack64<<<(unsigned)blocks, 256, 0, s>>>(dense, jp64, catalog, rw, rows, ovf, ovf_used);
+    if (rw == 4)
+        k_pack64<4><<<(unsigned)blocks, 256, 0, s>>>(dense, jp64, catalog, rows, ovf, ovf_used);
+    else if (rw == 8)
+        k_pack64<8><<<(unsigned)blocks, 256, 0, s>>>(dense, jp64, catalog, rows, ovf, ovf_used);
+    else
+        throw Error{ARE_EINVAL, "packed FP64 rows are 4 or 8 words"};
     ARE_CUDA_TRY(cudaGetLastError());
     return 1;
 }

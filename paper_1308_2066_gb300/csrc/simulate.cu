@@ -3,7 +3,8 @@
 // event's financial term in one ELT, built by repack.cu).  Two kernels:
 //
 //  * k_rows (the default): rows held in registers, see rows.cuh; over packed
-//    rows (k_rows_packed) for layers of more than 16 ELTs.
+//    rows (k_rows_packed) where a layer of more than 8 ELTs holds few entries
+//    per catalog event.
 //  * k_simulate_staged (a tuning candidate, and the compact layout's
 //    kernel): one event per lane, rows staged in shared memory.
 //
