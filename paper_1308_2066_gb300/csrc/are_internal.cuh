@@ -362,12 +362,12 @@ int launch_simulate(const SimArgs &a, are_precision prec, int jp, const TermsF32
 
 // select.cu
 struct SelectScratch {
-    uint32_t *hist = nullptr;       // kMaxTargets * 256
+    uint32_t *hist = nullptr;       // 3 * kMaxTargets * 256
     unsigned long long *state = nullptr;  // per target: prefix, remaining rank
     unsigned int *ctrl = nullptr;   // 4 words: blocks arrived, top word of the largest |value|
     unsigned long long *acc = nullptr;    // per target: integer tail sums and count (7 words)
     double *result = nullptr;       // per target: value, tail mean
-    unsigned long long *app = nullptr;    // single-YLT selection, per target: keys kept (zero between calls)
+    unsigned long long *app = nullptr;    // single-YLT selection, per target: keys kept
     unsigned long long *cand = nullptr;   // per target: the kept keys of its bucket
     int max_blocks = 0;
 };
@@ -380,7 +380,6 @@ int64_t rank_for_level(int64_t n, double a);
 const char *static_last_error();
 void select_free(SelectScratch &s);
 constexpr int kSelectLaunches = 1 + 8 + 1;    // the multi-YLT and allocation-free selections
-constexpr int kSelectLaunches1 = 5;            // the single-YLT selection (launch_select)
 inline int select_max_blocks(int num_sms) { return num_sms * 4; }
 // ranks[t] (1-based, descending order) for n_targets <= kMaxTargets; writes
 // result[2*t] = m-th largest value, result[2*t+1] = mean of the m largest.

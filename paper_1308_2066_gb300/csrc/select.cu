@@ -10,13 +10,10 @@
 // more pass adds the values above it.
 //
 // Two forms.  The single-YLT selection (launch_select: are_risk_measures,
-// the pricing server) takes five launches: the radix form's first two
-// passes (each target's bucket of the top 16 key bits), a pass that keeps
-// the keys of each target's bucket and sums the values above it, and one
-// block per target that finishes the selection among the kept keys
-// (details above k_collect).  The multi-YLT selection (a
-// portfolio's YLTs together) and the allocation-free one use the 8-pass
-// radix form below.
+// the pricing server) runs the passes below in one cooperative launch, with
+// a grid-wide barrier between them (details above k_select_coop).  The
+// multi-YLT selection (a portfolio's YLTs together) and the allocation-free
+// one launch one kernel per pass.
 //
 // GB300 choices.  Each histogram pass ends with the pick of the next digit,
 // done by whichever block of the pass finishes last (a counter and memory
@@ -27,6 +24,7 @@
 // each value above the selected one is scaled by a power of two taken from
 // the largest magnitude of the YLT and added as 32-bit limbs to integer
 // accumulators, so the sum is exact, and it is rounded to double once.
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include <cstdio>
@@ -37,6 +35,7 @@
 namespace are {
 namespace {
 
+namespace cg = cooperative_groups;
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kBins = 256;
 constexpr int kThreads = 256;
@@ -422,29 +421,38 @@ __global__ void __launch_bounds__(kThreads) k_tail(Sel s, int64_t n, int nt, Ran
 }
 
 // ---------------------------------------------------------------------------
-// Single-YLT selection in five launches
+// Single-YLT selection in one cooperative launch
 // ---------------------------------------------------------------------------
 //
-// k_init and the first two radix passes (k_hist, passes 0 and 1) find each
-// target's bucket of the keys' top 16 bits (sign, exponent and four mantissa
-// bits: 1/16 of an octave), its rank inside the bucket and the largest
-// magnitude, as in the radix form.  Then:
-// * k_collect: every key in a target's bucket is appended to the target's
-//   candidate list (up to kCand); every value in a higher bucket is added,
-//   scaled, to the target's exact integer tail sum and counted;
-// * k_finish, one block per target: the exact rank among the candidates by
-//   the remaining 48 bits (six 8-bit digits) in shared memory, then the
-//   bucket's values above the selected one added to the tail sum, and the
-//   result.  A bucket of more than kCand keys (a long run of ties) is
-//   selected by the same block from the whole YLT instead.
+// One kernel whose blocks are all resident (a cooperative launch), with a
+// grid-wide barrier where the radix form has a launch boundary:
+// 1. two radix passes find each target's bucket of the top 16 key bits
+//    (sign, exponent and four mantissa bits: 1/16 of an octave) and its rank
+//    in it;
+// 2. one pass keeps the keys of each target's bucket (up to kCand) and adds
+//    the values of higher buckets to the target's exact tail sum;
+// 3. block t selects among target t's kept keys by their last 48 bits in
+//    shared memory and adds the bucket's values above the selected one; if
+//    a bucket holds more than kCand keys (a long run of ties), every block
+//    runs the remaining six radix passes over the whole YLT instead.
+// In a radix pass every block picks every target's next digit itself from
+// the pass's global histogram (the same counts give the same digit), so one
+// barrier per pass is enough.  The histograms rotate through three buffers:
+// the buffer of pass p is cleared by block 0 during pass p + 2, after every
+// block has read it (before the barrier of pass p + 1) and before it is
+// written again (pass p + 3).
 
 constexpr int kCand = 16384;            // candidate keys kept per target
-constexpr int kFinThreads = 1024;
+constexpr int kCoopThreads = 512;
 
-struct Sel2 {
-    Sel sel;                     // the radix form's scratch (state, acc, ctrl, result)
-    unsigned long long *app;     // per target: keys appended to its list (zero between calls)
+struct SelC {
+    const double *v;
+    uint32_t *hist;              // 3 x kMaxTargets x kBins counts, zero between calls
+    unsigned long long *acc;     // kMaxTargets x kAccWords
+    unsigned int *ctrl;          // [1] top word of the largest |value|, zero between calls
+    unsigned long long *app;     // per target: keys kept
     unsigned long long *cand;    // per target: kCand keys of its bucket
+    double *result;              // per target: value, mean of the m largest
 };
 
 // Adds x (scaled by 2^sc) to the accumulator words a (positive and negative
@@ -475,55 +483,6 @@ __device__ __forceinline__ void acc_add_warp(unsigned long long *a, bool on, dou
             atomicAdd(a + 2 * kLimbs, c);
         }
     }
-}
-
-__global__ void __launch_bounds__(kThreads) k_collect(Sel2 s2, int64_t n, int nt)
-{
-    const Sel &s = s2.sel;
-    const double *__restrict__ v = s.single;
-    __shared__ unsigned long long a[kMaxTargets * kAccWords];
-    for (int i = threadIdx.x; i < nt * kAccWords; i += blockDim.x) a[i] = 0;
-    uint32_t P[kMaxTargets];
-#pragma unroll
-    for (int t = 0; t < kMaxTargets; ++t) P[t] = t < nt ? (uint32_t)(s.state[2 * t] >> 48) : 0xffffffffu;
-    const int sc = tail_scale(s.ctrl[1]);
-    __syncthreads();
-    const int lane = threadIdx.x & 31;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    // warp-uniform loop: the lanes of a warp append their candidates together
-    for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n;
-         base += stride * kPre) {
-        double xs[kPre];
-#pragma unroll
-        for (int u = 0; u < kPre; ++u) {
-            const int64_t i = base + u * stride + lane;
-            xs[u] = i < n ? v[i] : 0.0;
-        }
-#pragma unroll
-        for (int u = 0; u < kPre; ++u) {
-            const bool ok = base + u * stride + lane < n;
-            const uint64_t k = key_of(xs[u]);
-            const uint32_t p = (uint32_t)(k >> 48);
-#pragma unroll
-            for (int t = 0; t < kMaxTargets; ++t) {
-                if (t >= nt) break;
-                const bool in = ok && p == P[t];
-                const unsigned b = __ballot_sync(kFull, in);
-                if (b) {
-                    const int leader = __ffs(b) - 1;
-                    unsigned long long at = 0;
-                    if (lane == leader) at = atomicAdd(s2.app + t, (unsigned long long)__popc(b));
-                    at = __shfl_sync(kFull, at, leader);
-                    const unsigned long long slot = at + (unsigned long long)__popc(b & ((1u << lane) - 1u));
-                    if (in && slot < (unsigned long long)kCand) s2.cand[(size_t)t * kCand + slot] = k;
-                }
-                acc_add_warp(a + t * kAccWords, ok && p > P[t], xs[u], sc, lane);
-            }
-        }
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < nt * kAccWords; i += blockDim.x)
-        if (a[i]) atomicAdd(&s.acc[i], a[i]);
 }
 
 // (value of key kt, mean of the m largest) from the accumulator words A of
@@ -596,74 +555,258 @@ __device__ __forceinline__ void pick_shared(const uint32_t *h, unsigned long lon
     }
 }
 
-// One block per target, kFinThreads threads, kCand keys of dynamic shared memory.
-__global__ void __launch_bounds__(kFinThreads) k_finish(Sel2 s2, int64_t n, Ranks r)
+// One radix pass of the cooperative selection (digit bits shift .. shift + 7)
+// over the keys that share each target's prefix st[2t] (pass 0: every key,
+// one histogram for all targets), ending with the grid barrier and every
+// block's pick of every target's digit.  pass 0 also gathers the largest
+// magnitude into ctrl[1].
+__device__ void coop_pass(const SelC &s, int64_t n, int nt, int pass, unsigned long long *st, uint32_t *h,
+                          unsigned int *s_mag, cg::grid_group &grid)
 {
-    const Sel &s = s2.sel;
-    const double *__restrict__ v = s.single;
-    extern __shared__ unsigned long long keys[];
-    __shared__ uint32_t hist[kBins];
-    __shared__ unsigned long long a[kAccWords];
-    __shared__ unsigned long long s_pre, s_rem;
-    const int t = blockIdx.x, lane = threadIdx.x & 31;
-    const uint64_t P = s.state[2 * t] >> 48;
-    const unsigned long long app = s2.app[t];
-    const bool fits = app <= (unsigned long long)kCand;
-    const int64_t cnt = fits ? (int64_t)app : n;   // keys to scan: the candidates, or the whole YLT
-    const int sc = tail_scale(s.ctrl[1]);
-    if (fits)
-        for (int64_t i = threadIdx.x; i < cnt; i += blockDim.x) keys[i] = __ldcg(s2.cand + (size_t)t * kCand + i);
-    if (threadIdx.x < kAccWords) a[threadIdx.x] = 0;
-    if (threadIdx.x == 0) {
-        s_pre = P << 48;
-        s_rem = s.state[2 * t + 1];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int shift = 56 - 8 * pass;
+    const int rows = pass == 0 ? 1 : nt;
+    uint32_t *gh = s.hist + (size_t)(pass % 3) * kMaxTargets * kBins;
+    for (int i = threadIdx.x; i < rows * kBins; i += blockDim.x) h[i] = 0;
+    if (blockIdx.x == 0 && pass >= 2) {   // the buffer of pass - 2, read by every block already
+        uint32_t *old = s.hist + (size_t)((pass - 2) % 3) * kMaxTargets * kBins;
+        for (int i = threadIdx.x; i < kMaxTargets * kBins; i += blockDim.x) old[i] = 0;
     }
+    if (pass == 0 && threadIdx.x == 0) *s_mag = 0;
     __syncthreads();
-    // the remaining 48 bits, 8 at a time, among the keys of the bucket
-    for (int shift = 40; shift >= 0; shift -= 8) {
-        for (int i = threadIdx.x; i < kBins; i += blockDim.x) hist[i] = 0;
-        __syncthreads();
-        const uint64_t pre = s_pre >> (shift + 8);
-        // warp-uniform: the keys share most leading bits, so the warp adds per bin
-        for (int64_t base = threadIdx.x & ~31; base < cnt; base += blockDim.x) {
-            const int64_t i = base + lane;
-            const bool ok = i < cnt;
-            const uint64_t k = ok ? (fits ? keys[i] : key_of(v[i])) : 0ull;
-            hist_add(hist, ok && (k >> (shift + 8)) == pre, (uint32_t)(k >> shift) & 0xffu, lane);
+    uint64_t pre[kMaxTargets];
+#pragma unroll
+    for (int t = 0; t < kMaxTargets; ++t) pre[t] = t < nt ? st[2 * t] >> (shift + 8) : 0ull;
+    unsigned int mag = 0;
+    // warp-uniform loop: every lane takes part in the warp's histogram adds
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n;
+         base += stride * kPre) {
+        double xs[kPre];
+#pragma unroll
+        for (int u = 0; u < kPre; ++u) {
+            const int64_t i = base + u * stride + lane;
+            xs[u] = i < n ? s.v[i] : 0.0;
         }
-        __syncthreads();
-        if (threadIdx.x < 32) pick_shared(hist, s_pre, s_rem, shift, threadIdx.x);
-        __syncthreads();
+#pragma unroll
+        for (int u = 0; u < kPre; ++u) {
+            const bool ok = base + u * stride + lane < n;
+            const uint64_t k = key_of(xs[u]);
+            const uint32_t d = (uint32_t)(k >> shift) & 0xffu;
+            if (pass == 0) {
+                hist_add(h, ok, d, lane);
+                const unsigned int m32 =
+                    (unsigned int)(((unsigned long long)__double_as_longlong(xs[u]) >> 32) & 0x7fffffffu);
+                if (ok) mag = m32 > mag ? m32 : mag;
+            } else {
+#pragma unroll
+                for (int t = 0; t < kMaxTargets; ++t) {
+                    if (t >= nt) break;
+                    hist_add(h + t * kBins, ok && (k >> (shift + 8)) == pre[t], d, lane);
+                }
+            }
+        }
     }
-    const uint64_t kt = s_pre;
-    // the bucket's values above the selected one
-    for (int64_t base = threadIdx.x & ~31; base < cnt; base += blockDim.x) {
-        const int64_t i = base + lane;
-        const bool ok = i < cnt;
-        const uint64_t k = ok ? (fits ? keys[i] : key_of(v[i])) : 0ull;
-        acc_add_warp(a, ok && (k >> 48) == P && k > kt, value_of(k), sc, lane);
+    if (pass == 0) {
+#pragma unroll
+        for (int off = 16; off; off >>= 1) {
+            const unsigned int o = __shfl_xor_sync(kFull, mag, off);
+            mag = o > mag ? o : mag;
+        }
+        if (lane == 0 && mag) atomicMax(s_mag, mag);
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        unsigned long long A[kAccWords];
-        for (int i = 0; i < kAccWords; ++i) A[i] = a[i] + __ldcg(s.acc + t * kAccWords + i);
-        tail_result(A, kt, r.m[t], sc, s.result + 2 * t);
-        s2.app[t] = 0;
-    }
+    for (int i = threadIdx.x; i < rows * kBins; i += blockDim.x)
+        if (h[i]) atomicAdd(&gh[i], h[i]);
+    if (pass == 0 && threadIdx.x == 0 && *s_mag) atomicMax(&s.ctrl[1], *s_mag);
+    grid.sync();
+    // every block picks every target's digit from the pass's histogram
+    if (warp < nt) pick(gh + (pass == 0 ? 0 : warp) * kBins, st + 2 * warp, shift, lane);
+    __syncthreads();
 }
 
-cudaError_t enqueue2(const Sel2 &s, int64_t n, const int64_t *ranks, int nt, cudaStream_t st)
+// Block t's exact selection among the n_keys candidate keys of target t's
+// bucket (in shared memory): the remaining 48 bits, 8 at a time; returns the
+// key and adds the bucket's values above it to a.
+__device__ uint64_t finish_in_block(const unsigned long long *keys, int n_keys, unsigned long long *st_t,
+                                    uint32_t *h, unsigned long long *a, int sc)
+{
+    const int lane = threadIdx.x & 31;
+    for (int shift = 40; shift >= 0; shift -= 8) {
+        for (int i = threadIdx.x; i < kBins; i += blockDim.x) h[i] = 0;
+        __syncthreads();
+        const uint64_t pre = st_t[0] >> (shift + 8);
+        // warp-uniform: the keys share most leading bits, so the warp adds per bin
+        for (int base = threadIdx.x & ~31; base < n_keys; base += blockDim.x) {
+            const int i = base + lane;
+            const bool ok = i < n_keys;
+            const uint64_t k = ok ? keys[i] : 0ull;
+            hist_add(h, ok && (k >> (shift + 8)) == pre, (uint32_t)(k >> shift) & 0xffu, lane);
+        }
+        __syncthreads();
+        if (threadIdx.x < 32) pick_shared(h, st_t[0], st_t[1], shift, lane);
+        __syncthreads();
+    }
+    const uint64_t kt = st_t[0];
+    for (int base = threadIdx.x & ~31; base < n_keys; base += blockDim.x) {
+        const int i = base + lane;
+        const bool ok = i < n_keys;
+        const uint64_t k = ok ? keys[i] : 0ull;
+        acc_add_warp(a, ok && k > kt, value_of(k), sc, lane);
+    }
+    __syncthreads();
+    return kt;
+}
+
+__global__ void __launch_bounds__(kCoopThreads) k_select_coop(SelC s, int64_t n, int nt, Ranks r)
+{
+    cg::grid_group grid = cg::this_grid();
+    extern __shared__ unsigned long long keys[];   // kCand: the candidates of a block's target
+    __shared__ uint32_t h[kMaxTargets * kBins];
+    __shared__ unsigned long long st[2 * kMaxTargets];   // per target: key prefix, rank left (the same in every block)
+    __shared__ unsigned long long a[kMaxTargets * kAccWords];
+    __shared__ unsigned int s_mag;
+    const int lane = threadIdx.x & 31;
+    if (threadIdx.x < nt) {
+        st[2 * threadIdx.x] = 0ull;
+        st[2 * threadIdx.x + 1] = (unsigned long long)r.m[threadIdx.x];
+    }
+    if (blockIdx.x == 0) {   // the counters and sums of step 2, used after the next two barriers
+        for (int i = threadIdx.x; i < kMaxTargets * kAccWords; i += blockDim.x) s.acc[i] = 0;
+        for (int i = threadIdx.x; i < kMaxTargets; i += blockDim.x) s.app[i] = 0;
+    }
+    __syncthreads();
+    // 1. two radix passes: each target's bucket of the top 16 key bits and its rank in it
+    coop_pass(s, n, nt, 0, st, h, &s_mag, grid);
+    coop_pass(s, n, nt, 1, st, h, &s_mag, grid);
+    const int sc = tail_scale(__ldcg(&s.ctrl[1]));
+    uint32_t P[kMaxTargets];
+#pragma unroll
+    for (int t = 0; t < kMaxTargets; ++t) P[t] = t < nt ? (uint32_t)(st[2 * t] >> 48) : 0xffffffffu;
+    // 2. the keys of each target's bucket kept (up to kCand); the values of
+    //    higher buckets added to the target's exact tail sum
+    for (int i = threadIdx.x; i < nt * kAccWords; i += blockDim.x) a[i] = 0;
+    __syncthreads();
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n;
+         base += stride * kPre) {
+        double xs[kPre];
+#pragma unroll
+        for (int u = 0; u < kPre; ++u) {
+            const int64_t i = base + u * stride + lane;
+            xs[u] = i < n ? s.v[i] : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < kPre; ++u) {
+            const bool ok = base + u * stride + lane < n;
+            const uint64_t k = key_of(xs[u]);
+            const uint32_t p = (uint32_t)(k >> 48);
+#pragma unroll
+            for (int t = 0; t < kMaxTargets; ++t) {
+                if (t >= nt) break;
+                const bool in = ok && p == P[t];
+                const unsigned b = __ballot_sync(kFull, in);
+                if (b) {
+                    const int leader = __ffs(b) - 1;
+                    unsigned long long at = 0;
+                    if (lane == leader) at = atomicAdd(s.app + t, (unsigned long long)__popc(b));
+                    at = __shfl_sync(kFull, at, leader);
+                    const unsigned long long slot = at + (unsigned long long)__popc(b & ((1u << lane) - 1u));
+                    if (in && slot < (unsigned long long)kCand) s.cand[(size_t)t * kCand + slot] = k;
+                }
+                acc_add_warp(a + t * kAccWords, ok && p > P[t], xs[u], sc, lane);
+            }
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < nt * kAccWords; i += blockDim.x)
+        if (a[i]) atomicAdd(&s.acc[i], a[i]);
+    grid.sync();
+    bool fits = true;
+    for (int t = 0; t < nt; ++t) fits &= __ldcg(s.app + t) <= (unsigned long long)kCand;
+    uint64_t kt[kMaxTargets];
+    if (fits) {
+        // 3a. block t selects among target t's kept keys in shared memory
+        const int t = blockIdx.x;
+        if (t < nt) {
+            const int n_keys = (int)__ldcg(s.app + t);
+            for (int i = threadIdx.x; i < n_keys; i += blockDim.x) keys[i] = __ldcg(s.cand + (size_t)t * kCand + i);
+            if (threadIdx.x < kAccWords) a[threadIdx.x] = 0;
+            __syncthreads();
+            const uint64_t k = finish_in_block(keys, n_keys, st + 2 * t, h, a, sc);
+            if (threadIdx.x == 0) {
+                unsigned long long A[kAccWords];
+                for (int i = 0; i < kAccWords; ++i) A[i] = a[i] + __ldcg(s.acc + t * kAccWords + i);
+                tail_result(A, k, r.m[t], sc, s.result + 2 * t);
+            }
+        }
+        if (blockIdx.x == 0) {   // leave the histograms and the magnitude zero for the next call
+            __syncthreads();
+            for (int i = threadIdx.x; i < 2 * kMaxTargets * kBins; i += blockDim.x) s.hist[i] = 0;   // passes 0, 1
+            if (threadIdx.x == 0) s.ctrl[1] = 0;
+        }
+        return;
+    }
+    // 3b. a bucket of more than kCand keys: the remaining six radix passes
+    //     over the whole YLT, then the buckets' values above the keys
+    for (int pass = 2; pass < 8; ++pass) coop_pass(s, n, nt, pass, st, h, &s_mag, grid);
+#pragma unroll
+    for (int t = 0; t < kMaxTargets; ++t) kt[t] = t < nt ? st[2 * t] : ~0ull;
+    for (int i = threadIdx.x; i < nt * kAccWords; i += blockDim.x) a[i] = 0;
+    __syncthreads();
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n;
+         base += stride * kPre) {
+        double xs[kPre];
+#pragma unroll
+        for (int u = 0; u < kPre; ++u) {
+            const int64_t i = base + u * stride + lane;
+            xs[u] = i < n ? s.v[i] : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < kPre; ++u) {
+            const bool ok = base + u * stride + lane < n;
+            const uint64_t k = key_of(xs[u]);
+            const uint32_t p = (uint32_t)(k >> 48);
+#pragma unroll
+            for (int t = 0; t < kMaxTargets; ++t) {
+                if (t >= nt) break;
+                acc_add_warp(a + t * kAccWords, ok && p == P[t] && k > kt[t], xs[u], sc, lane);
+            }
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < nt * kAccWords; i += blockDim.x)
+        if (a[i]) atomicAdd(&s.acc[i], a[i]);
+    grid.sync();
+    if (blockIdx.x != 0) return;
+    if (threadIdx.x < nt) {
+        const int t = threadIdx.x;
+        unsigned long long A[kAccWords];
+        for (int i = 0; i < kAccWords; ++i) A[i] = __ldcg(s.acc + t * kAccWords + i);
+        tail_result(A, kt[t], r.m[t], sc, s.result + 2 * t);
+    }
+    __syncthreads();
+    // leave the histograms and the magnitude zero for the next call
+    for (int i = threadIdx.x; i < 3 * kMaxTargets * kBins; i += blockDim.x) s.hist[i] = 0;
+    if (threadIdx.x == 0) s.ctrl[1] = 0;
+}
+
+cudaError_t enqueue_coop(const SelC &s, int64_t n, const int64_t *ranks, int nt, int num_sms, cudaStream_t st)
 {
     Ranks r{};
     for (int t = 0; t < nt; ++t) r.m[t] = ranks[t];
-    const dim3 grid((unsigned)s.sel.blocks, 1u);
-    k_init<<<1, kThreads, 0, st>>>(s.sel, r, nt);
-    for (int pass = 0; pass < 2; ++pass) k_hist<<<grid, kThreads, 0, st>>>(s.sel, n, nt, pass);
-    k_collect<<<s.sel.blocks, kThreads, 0, st>>>(s, n, nt);
     const size_t smem = sizeof(unsigned long long) * kCand;
-    fit_blocks(reinterpret_cast<const void *>(k_finish), kFinThreads, smem);   // raises the shared-memory limit
-    k_finish<<<nt, kFinThreads, smem, st>>>(s, n, r);
-    return cudaGetLastError();
+    const int per_sm = fit_blocks(reinterpret_cast<const void *>(k_select_coop), kCoopThreads, smem);
+    int64_t blocks = (n + (int64_t)kCoopThreads * kPre - 1) / ((int64_t)kCoopThreads * kPre);
+    const int64_t cap = (int64_t)num_sms * per_sm;   // every block resident
+    if (blocks > cap) blocks = cap;
+    if (blocks < nt) blocks = nt;                    // a block per target for the last step
+    SelC sc = s;
+    int64_t nn = n;
+    int ntt = nt;
+    void *args[] = {&sc, &nn, &ntt, &r};
+    return cudaLaunchCooperativeKernel(reinterpret_cast<const void *>(k_select_coop), dim3((unsigned)blocks),
+                                       dim3(kCoopThreads), args, smem, st);
 }
 
 cudaError_t enqueue(const Sel &s, int n_ylt, int64_t n, const int64_t *ranks, int nt,
@@ -690,14 +833,18 @@ int blocks_for(int64_t n, int cap)
 void select_alloc(SelectScratch &s, int num_sms)
 {
     s.max_blocks = select_max_blocks(num_sms);
-    ARE_CUDA_TRY(cudaMalloc(&s.hist, sizeof(uint32_t) * kMaxTargets * kBins));
+    // three histogram buffers for the cooperative selection
+    ARE_CUDA_TRY(cudaMalloc(&s.hist, sizeof(uint32_t) * 3 * kMaxTargets * kBins));
     ARE_CUDA_TRY(cudaMalloc(&s.state, sizeof(unsigned long long) * 2 * kMaxTargets));
     ARE_CUDA_TRY(cudaMalloc(&s.ctrl, sizeof(unsigned int) * kCtrlWords));
     ARE_CUDA_TRY(cudaMalloc(&s.acc, sizeof(unsigned long long) * kMaxTargets * kAccWords));
     ARE_CUDA_TRY(cudaMalloc(&s.result, sizeof(double) * 2 * kMaxTargets));
     ARE_CUDA_TRY(cudaMalloc(&s.app, sizeof(unsigned long long) * kMaxTargets));
     ARE_CUDA_TRY(cudaMalloc(&s.cand, sizeof(unsigned long long) * kCand * kMaxTargets));
-    ARE_CUDA_TRY(cudaMemset(s.app, 0, sizeof(unsigned long long) * kMaxTargets));   // zero between calls
+    // the cooperative selection leaves these zero at its end
+    ARE_CUDA_TRY(cudaMemset(s.hist, 0, sizeof(uint32_t) * 3 * kMaxTargets * kBins));
+    ARE_CUDA_TRY(cudaMemset(s.ctrl, 0, sizeof(unsigned int) * kCtrlWords));
+    ARE_CUDA_TRY(cudaMemset(s.acc, 0, sizeof(unsigned long long) * kMaxTargets * kAccWords));
 }
 
 void select_free(SelectScratch &s)
@@ -723,11 +870,9 @@ cudaError_t select_enqueue(const double *ylt, int64_t n, const int64_t *ranks, i
 int launch_select(const double *ylt, int64_t n, const int64_t *ranks, int nt, SelectScratch &s,
                   int num_sms, cudaStream_t st)
 {
-    (void)num_sms;
-    Sel2 sel{Sel{ylt, nullptr, s.hist, s.state, s.ctrl, s.acc, s.result, blocks_for(n, s.max_blocks)}, s.app,
-             s.cand};
-    ARE_CUDA_TRY(enqueue2(sel, n, ranks, nt, st));
-    return kSelectLaunches1;
+    const SelC sel{ylt, s.hist, s.acc, s.ctrl, s.app, s.cand, s.result};
+    ARE_CUDA_TRY(enqueue_coop(sel, n, ranks, nt, num_sms, st));
+    return 1;
 }
 
 namespace {
