@@ -248,11 +248,12 @@ ARE_API are_status are_simulate_portfolio(are_ctx *ctx, const int32_t *layers, i
 typedef struct {
     int32_t kernel;          /* 0 persistent work items, 1 staged rows (one event per lane),
                                 2 register rows (rows read straight into registers by a
-                                warp per block of trials; FP32: the dense row of up to 16
-                                ELTs, jp/8 lanes each, or for more ELTs a packed 64-byte row
-                                of the non-zero terms; FP64: a packed 64-byte row of the
-                                non-zero terms, exact trial sums), 3 (FP64) staged rows of
-                                an FP32 screen with the marked entries read from the FP64
+                                warp per block of trials: a packed row of the non-zero
+                                terms behind their column mask, 32 bytes where the layer
+                                holds few entries per catalog event, else 64, or in FP32
+                                the dense row of up to 16 ELTs; are_layer_rows tells which;
+                                FP64 with exact trial sums), 3 (FP64) staged rows of an
+                                FP32 screen with the marked entries read from the FP64
                                 table */
     int32_t rows_in_flight;  /* register rows and persistent kernel: groups of 32 events
                                 per batch, 1 or 2; staged kernel: events per lane per
