@@ -356,31 +356,25 @@ Packed &build_packed64(are_ctx *ctx, Layer &L, int32_t catalog, cudaStream_t s)
     return p;
 }
 
-// The packed FP32 rows (pw words each) of the layer's FP32 table (which must
-// be built for `catalog`), read by the FP32 register-rows kernel.
-Packed &build_packed32(are_ctx *ctx, Layer &L, int32_t catalog, int pw, cudaStream_t s)
+// The packed FP32 rows (pw words each) built straight from the layer's ELT
+// entries, with no dense table: what the FP32 register-rows kernel reads.
+Packed &build_packed32_direct(are_ctx *ctx, Layer &L, int32_t catalog, int pw, cudaStream_t s)
 {
     Packed &p = L.p32;
+    const ScatterArgs a = scatter_args(ctx, L, catalog, table_jp((int)L.elts.size(), true));
     size_packed(ctx, L, p, catalog, pw, pw * sizeof(float), sizeof(float) * (size_t)layer_entries(ctx, L));
-    const Table &t = L.t32;
-    ctx->launches += launch_pack32(static_cast<const float *>(t.d), t.jp, catalog, pw,
-                                   static_cast<uint32_t *>(p.rows()), static_cast<float *>(p.ovf()),
-                                   p.used(), ctx->num_sms, s);
+    ctx->launches += launch_pack32_direct(a, catalog, pw, static_cast<uint32_t *>(p.rows()),
+                                          static_cast<float *>(p.ovf()), p.used(), s);
     return p;
 }
 
-// The tables beside a layer's table that a kernel choice reads.  FP64: the
-// packed rows (register rows, kernel 2) or the FP32 screen (kernel 3); FP32:
-// the packed rows where the layer's row size calls for them (register rows,
-// kernel 2).  `fresh`: the layer's table was just rebuilt.
+// The tables beside a layer's FP64 table that a kernel choice reads: the
+// packed rows (register rows, kernel 2) or the FP32 screen (kernel 3).
+// `fresh`: the layer's table was just rebuilt.  (The FP32 packed rows are
+// built from the ELT entries, build_packed32_direct.)
 void ensure_aux(are_ctx *ctx, Layer &L, int32_t catalog, bool fp32, int kernel, bool fresh, cudaStream_t s)
 {
-    if (fp32) {
-        const int pw = kernel == 2 ? row_words(ctx, L, catalog, true) : 0;
-        if (pw && (fresh || !L.p32.d || L.p32.catalog != catalog || L.p32.rw != pw))
-            build_packed32(ctx, L, catalog, pw, s);
-        return;
-    }
+    if (fp32) return;
     if (kernel == 2 && (fresh || !L.p64.d || L.p64.catalog != catalog ||
                         L.p64.rw != row_words(ctx, L, catalog, false)))
         build_packed64(ctx, L, catalog, s);
@@ -396,10 +390,18 @@ void ensure_tables(are_ctx *ctx, Layer &L, const Yet &y, are_precision precision
         if (rebuild || !L.comp.d || L.comp.catalog != catalog) build_compact(ctx, L, catalog, s);
         return;
     }
+    const int jp = table_jp((int)L.elts.size(), fp32);
+    const int kernel = tuned(ctx, precision, y, jp, false).kernel;
+    const int pw = fp32 && kernel == 2 ? row_words(ctx, L, catalog, true) : 0;
+    if (pw) {   // packed rows straight from the ELT entries; a dense table only when a kernel needs one
+        if (rebuild || !L.p32.d || L.p32.catalog != catalog || L.p32.rw != pw)
+            build_packed32_direct(ctx, L, catalog, pw, s);
+        return;
+    }
     const Table &t = fp32 ? L.t32 : L.t64;
     const bool fresh = rebuild || !t.d || t.catalog != catalog;
     if (fresh) build_table(ctx, L, catalog, fp32, s);
-    ensure_aux(ctx, L, catalog, fp32, tuned(ctx, precision, y, t.jp, false).kernel, fresh, s);
+    ensure_aux(ctx, L, catalog, fp32, kernel, fresh, s);
 }
 
 Layer &layer_of(are_ctx *ctx, int32_t h)
@@ -711,6 +713,12 @@ void ensure_tables(are_ctx *ctx, const int32_t *layers, int32_t n_layers, const 
 {
     for (int32_t i = 0; i < n_layers; ++i) {
         Layer &L = layer_of(ctx, layers[i]);
+        const int pw = fp32 && kernel == 2 ? row_words(ctx, L, y.catalog, true) : 0;
+        if (pw) {   // packed rows straight from the ELT entries
+            if (!L.p32.d || L.p32.catalog != y.catalog || L.p32.rw != pw)
+                build_packed32_direct(ctx, L, y.catalog, pw, s);
+            continue;
+        }
         const Table &t = fp32 ? L.t32 : L.t64;
         const bool fresh = !t.d || t.catalog != y.catalog;
         if (fresh) build_table(ctx, L, y.catalog, fp32, s);
@@ -1743,6 +1751,7 @@ are_status are_autotune(are_ctx *ctx, const int32_t *layers, int32_t n_layers, i
         CallStream cs(ctx, stream);
         const bool fp32 = precision != ARE_FP64;
         ensure_tables(ctx, layers, n_layers, y, fp32, cs.s, 2);              // packed rows
+        ensure_tables(ctx, layers, n_layers, y, fp32, cs.s, 1);              // dense rows
         if (!fp32) ensure_tables(ctx, layers, n_layers, y, fp32, cs.s, 3);  // FP64: the screen
         const bool multi = n_layers > 1;
         const int jp = max_width(ctx, layers, n_layers, fp32);

@@ -124,10 +124,11 @@ struct Compact {
 // counter (256 B) | overflow].  FP64 (built from t64 by launch_pack64):
 // rw = 4 or 8 64-bit words per row, the mask and the overflow offset in word
 // 0, up to rw - 1 terms inline and every term of a longer row in the
-// overflow.  FP32 (built from t32 by launch_pack32): rw = 8 or 16 32-bit
-// words, the mask in word 0, up to rw - 1 terms inline; a longer row keeps
-// rw - 2 inline and the offset of the rest in its last word.  The row size
-// follows the layer's entries per catalog event (packed_row_words).
+// overflow.  FP32 (built from the ELT entries by launch_pack32_direct):
+// rw = 8 or 16 32-bit words, the mask in word 0, up to rw - 1 terms inline;
+// a longer row keeps rw - 2 inline and the offset of the rest in its last
+// word.  The row size follows the layer's entries per catalog event
+// (packed_row_words).
 struct Packed {
     int32_t catalog = -1;
     int rw = 0;
@@ -315,8 +316,8 @@ int table_jp(int n_elts, bool fp32);
 int packed_row_words(int n_elts, double terms_per_event, bool fp32);
 int launch_pack64(const double *dense, int jp64, int32_t catalog, int rw, unsigned long long *rows,
                   double *ovf, unsigned long long *ovf_used, int num_sms, cudaStream_t s);
-int launch_pack32(const float *dense, int jp, int32_t catalog, int pw, uint32_t *rows, float *ovf,
-                  unsigned long long *ovf_used, int num_sms, cudaStream_t s);
+int launch_pack32_direct(const ScatterArgs &a, int32_t catalog, int pw, uint32_t *rows, float *ovf,
+                         unsigned long long *ovf_used, cudaStream_t s);
 
 // api.cu: how many blocks of `kern` (threads per block, bytes of dynamic
 // shared memory) fit on one SM of the current device.  On the first call for

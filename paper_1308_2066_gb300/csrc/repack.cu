@@ -82,84 +82,90 @@ __global__ void k_pack64(const double *__restrict__ dense, int jp64, int32_t cat
     }
 }
 
-// Packed FP32 rows (pw = 8 or 16 words: 32 or 64 bytes) from a dense FP32
-// table of up to 32 columns: word 0 holds the mask of the non-zero columns,
-// words 1 .. pw - 1 those terms in column order (the rest 0).  A row of more
-// than pw - 1 non-zero terms keeps the first pw - 2 inline and in word
-// pw - 1 the offset of a block of the overflow array (handed out by an
-// atomic counter) that holds the rest in column order.
-template <int JP, int PW>
-__global__ void k_pack32(const float *__restrict__ dense, int32_t catalog, uint32_t *__restrict__ rows,
-                         float *__restrict__ ovf, unsigned long long *__restrict__ ovf_used)
+// Packed FP32 rows (pw = 8 or 16 words: 32 or 64 bytes): word 0 holds the
+// mask of the ELT columns whose term is not 0, words 1 .. pw - 1 those terms
+// in column order (the rest 0).  A row of more than pw - 1 non-zero terms
+// keeps the first pw - 2 inline and in word pw - 1 the offset of a block of
+// the overflow array (handed out by an atomic counter) that holds the rest
+// in column order.
+// They are built straight from the ELT entries (no dense table): three
+// passes over the entries of every ELT (grid.y = ELT j), each entry's term
+// formed and rounded as k_scatter forms it.  ELT ids are
+// unique, so each (row, column) is one entry's alone.
+// 1. the mask: bit j of word 0 of the entry's row where its term is not 0;
+__global__ void k_pack32_mask(const ScatterArgs a, uint32_t *__restrict__ rows, int pw)
 {
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < catalog;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        // the dense row in 16-byte loads
-        uint32_t v[JP];
-        const uint4 *d = reinterpret_cast<const uint4 *>(dense + e * JP);
-#pragma unroll
-        for (int q = 0; q < JP / 4; ++q) {
-            const uint4 x = __ldcs(d + q);
-            v[4 * q] = x.x;
-            v[4 * q + 1] = x.y;
-            v[4 * q + 2] = x.z;
-            v[4 * q + 3] = x.w;
-        }
-        uint32_t mask = 0;
-#pragma unroll
-        for (int j = 0; j < JP; ++j) mask |= (v[j] != 0u ? 1u : 0u) << j;
-        const int cnt = __popc(mask);
-        const bool over = cnt > PW - 1;
-        const int inl = over ? PW - 2 : cnt;
-        // word 1 + r holds the non-zero term of rank r (column order), r < inl
-        uint32_t w[PW];
-        w[0] = mask;
-#pragma unroll
-        for (int i = 1; i < PW; ++i) w[i] = 0u;
-#pragma unroll
-        for (int j = 0; j < JP; ++j) {
-            const int r = __popc(mask & ((1u << j) - 1u));
-#pragma unroll
-            for (int i = 1; i < PW; ++i)
-                if (((mask >> j) & 1u) && r == i - 1 && r < inl) w[i] = v[j];
-        }
-        if (over) {   // rare: the terms past the inline ones go to an overflow block
+    const int j = blockIdx.y;
+    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < a.n[j]; i += gridDim.x * blockDim.x) {
+        const float f = (float)fin_term(a.loss[j][i], a.fx[j], a.ded[j], a.lim[j], a.share[j]);
+        if (__float_as_uint(f) != 0u) atomicOr(rows + (size_t)a.ids[j][i] * pw, 1u << j);
+    }
+}
+
+// 2. the inline terms: rank r (the set mask bits below j) goes to word 1 + r;
+//    in a row that overflows, the entry of the first rank past the inline
+//    ones takes the row's overflow block and writes its offset to the last
+//    word;
+__global__ void k_pack32_place(const ScatterArgs a, uint32_t *__restrict__ rows, int pw, float *__restrict__ ovf,
+                               unsigned long long *__restrict__ ovf_used)
+{
+    const int j = blockIdx.y;
+    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < a.n[j]; i += gridDim.x * blockDim.x) {
+        const float f = (float)fin_term(a.loss[j][i], a.fx[j], a.ded[j], a.lim[j], a.share[j]);
+        if (__float_as_uint(f) == 0u) continue;
+        uint32_t *row = rows + (size_t)a.ids[j][i] * pw;
+        const uint32_t mask = row[0];
+        const int cnt = __popc(mask), r = __popc(mask & ((1u << j) - 1u));
+        const bool over = cnt > pw - 1;
+        const int inl = over ? pw - 2 : cnt;
+        if (r < inl) {
+            row[1 + r] = __float_as_uint(f);
+        } else if (r == inl) {
             const uint32_t off = (uint32_t)atomicAdd(ovf_used, (unsigned long long)(cnt - inl));
-            int k = 0;
-            for (uint32_t m = mask; m; m &= m - 1, ++k)
-                if (k >= inl) ovf[off + k - inl] = __uint_as_float(v[__ffs(m) - 1]);
-            w[PW - 1] = off;
+            row[pw - 1] = off;
+            ovf[off] = f;
         }
-        uint4 *out = reinterpret_cast<uint4 *>(rows + e * PW);
-#pragma unroll
-        for (int q = 0; q < PW / 4; ++q) out[q] = make_uint4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
+    }
+}
+
+// 3. the other terms past the inline ones, at their rank in the row's block.
+__global__ void k_pack32_over(const ScatterArgs a, const uint32_t *__restrict__ rows, int pw,
+                              float *__restrict__ ovf)
+{
+    const int j = blockIdx.y;
+    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < a.n[j]; i += gridDim.x * blockDim.x) {
+        const uint32_t *row = rows + (size_t)a.ids[j][i] * pw;
+        const uint32_t mask = row[0];
+        const int cnt = __popc(mask), inl = pw - 2;
+        if (cnt <= pw - 1) continue;   // no overflow in this row
+        const int r = __popc(mask & ((1u << j) - 1u));
+        if (!((mask >> j) & 1u) || r <= inl) continue;
+        ovf[row[pw - 1] + (r - inl)] = (float)fin_term(a.loss[j][i], a.fx[j], a.ded[j], a.lim[j], a.share[j]);
     }
 }
 
 }  // namespace
 
-// dense: an FP32 table of jp <= 32 columns; rows: catalog x pw words (8 or
-// 16); ovf: room for every non-zero term of the layer; ovf_used: a device
-// counter, zeroed here.
-int launch_pack32(const float *dense, int jp, int32_t catalog, int pw, uint32_t *rows, float *ovf,
-                  unsigned long long *ovf_used, int num_sms, cudaStream_t s)
+// Packed FP32 rows (pw words) straight from the layer's ELT entries: rows
+// catalog x pw words, ovf room for every entry, ovf_used a device counter.
+// Three launches, no dense table.
+int launch_pack32_direct(const ScatterArgs &a, int32_t catalog, int pw, uint32_t *rows, float *ovf,
+                         unsigned long long *ovf_used, cudaStream_t s)
 {
     if (pw != 8 && pw != 16) throw Error{ARE_EINVAL, "packed FP32 rows are 8 or 16 words"};
     ARE_CUDA_TRY(cudaMemsetAsync(ovf_used, 0, sizeof *ovf_used, s));
     if (catalog <= 0) return 0;
-    int64_t blocks = ((int64_t)catalog + 255) / 256;
-    if (blocks > (int64_t)num_sms * 16) blocks = (int64_t)num_sms * 16;
-    if (jp == 16 && pw == 8)
-        k_pack32<16, 8><<<(unsigned)blocks, 256, 0, s>>>(dense, catalog, rows, ovf, ovf_used);
-    else if (jp == 32 && pw == 8)
-        k_pack32<32, 8><<<(unsigned)blocks, 256, 0, s>>>(dense, catalog, rows, ovf, ovf_used);
-    else if (jp == 32 && pw == 16)
-        k_pack32<32, 16><<<(unsigned)blocks, 256, 0, s>>>(dense, catalog, rows, ovf, ovf_used);
-    else
-        throw Error{ARE_EINVAL, "no packed FP32 rows of " + std::to_string(pw) + " words for a table of " +
-                                    std::to_string(jp) + " columns"};
+    ARE_CUDA_TRY(cudaMemsetAsync(rows, 0, sizeof(uint32_t) * (size_t)catalog * pw, s));
+    int32_t nmax = 0;
+    for (int j = 0; j < a.n_elts; ++j) nmax = a.n[j] > nmax ? a.n[j] : nmax;
+    if (nmax == 0 || a.n_elts == 0) return 0;
+    dim3 grid((unsigned)((nmax + 255) / 256), (unsigned)a.n_elts);
+    if (grid.x > 4096) grid.x = 4096;
+    k_pack32_mask<<<grid, 256, 0, s>>>(a, rows, pw);
+    k_pack32_place<<<grid, 256, 0, s>>>(a, rows, pw, ovf, ovf_used);
+    k_pack32_over<<<grid, 256, 0, s>>>(a, rows, pw, ovf);
     ARE_CUDA_TRY(cudaGetLastError());
-    return 1;
+    return 3;
 }
 
 // Words per packed row for a layer whose ELTs hold `terms_per_event`

@@ -270,9 +270,9 @@ struct BodyF32 {
     }
 };
 
-// Packed FP32 table (repack.cu, launch_pack32): row e is PW = 8 or 16 words
-// (32 or 64 bytes) -- word 0 the mask of the ELT columns whose term is not
-// 0, then up to PW - 1 of those terms in column order.  A row of more terms
+// Packed FP32 table (repack.cu, launch_pack32_direct): row e is PW = 8 or
+// 16 words (32 or 64 bytes) -- word 0 the mask of the ELT columns whose term
+// is not 0, then up to PW - 1 of those terms in column order.  A row of more terms
 // keeps the first PW - 2 inline and in word PW - 1 the offset of the rest
 // (in column order) in the overflow array.  The rows are read and summed as
 // BodyF32's, the mask word taken out of the sum; the events with an

@@ -122,7 +122,7 @@ struct Slot {
     int64_t launched = 0;           // trials handed to launches so far
     bool large = false;             // its slices run on the single-layer register-rows kernel
     int pw = 0;                     // large: words per packed row (0: the dense rows)
-    size_t dense_bytes = 0;         // the dense table at the start of the block; packed rows after it
+    size_t dense_bytes = 0;         // the dense table (0 for packed rows, which fill the block)
     uint64_t finish_iter = 0;       // iteration whose completion posts the result
     SelectScratch sel;
     double *h_res = nullptr;        // pinned, 2 * kMaxTargets
@@ -204,8 +204,8 @@ ulonglong2 *folded_F(char *b, int32_t catalog)
     return reinterpret_cast<ulonglong2 *>(b + 256 + up((size_t)folded_words(catalog) * 4));
 }
 
-// A large request's packed rows in its arena block, after the dense table:
-// [dense | rows | counter (256 B) | overflow].
+// A large request's packed rows in its arena block: [rows | counter (256 B) |
+// overflow].
 uint32_t *packed_rows(Server &S, const Slot &sl)
 {
     return reinterpret_cast<uint32_t *>(S.d_arena + sl.tab_off + up(sl.dense_bytes));
@@ -246,13 +246,14 @@ void build_request_table(Server &S, Slot &sl)
                                     S.ctx->num_sms, S.stream));
         return;
     }
+    if (sl.pw) {   // packed rows straight from the ELT entries
+        add_launches(S, launch_pack32_direct(a, S.y->catalog, sl.pw, packed_rows(S, sl), packed_ovf(S, sl),
+                                             packed_used(S, sl), S.stream));
+        return;
+    }
     char *b = S.d_arena + sl.tab_off;
     ARE_CUDA_TRY(cudaMemsetAsync(b, 0, sl.dense_bytes, S.stream));
     add_launches(S, launch_scatter_table(b, true, a, S.stream));
-    if (sl.pw)
-        add_launches(S, launch_pack32(reinterpret_cast<const float *>(b), sl.jp, S.y->catalog, sl.pw,
-                                      packed_rows(S, sl), packed_ovf(S, sl), packed_used(S, sl),
-                                      S.ctx->num_sms, S.stream));
 }
 
 void fill_record(Server &S, Slot &sl)
@@ -359,10 +360,10 @@ void scheduler(Server *SP)
                                 ? packed_row_words((int)r.elts.size(),
                                                    (double)r.entries / (double)S.y->catalog, true)
                                 : 0;
-                    sl.dense_bytes = (size_t)S.y->catalog * sl.jp * sizeof(float);
+                    sl.dense_bytes = sl.pw ? 0 : (size_t)S.y->catalog * sl.jp * sizeof(float);
                     sl.tab_bytes = S.cfg.folded ? folded_block_bytes(S.y->catalog)
-                                   : sl.pw ? up(sl.dense_bytes) + up((size_t)S.y->catalog * sl.pw * sizeof(float)) +
-                                                 256 + up(sizeof(float) * (size_t)r.entries + 8)
+                                   : sl.pw ? up((size_t)S.y->catalog * sl.pw * sizeof(float)) + 256 +
+                                                 up(sizeof(float) * (size_t)r.entries + 8)
                                            : sl.dense_bytes;
                     sl.ylt_bytes = sizeof(double) * (size_t)r.n_trials;
                     size_t a = 0, b = 0;
