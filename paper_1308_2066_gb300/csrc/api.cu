@@ -341,18 +341,17 @@ int row_words(are_ctx *ctx, const Layer &L, int32_t catalog, bool fp32)
     return packed_row_words((int)L.elts.size(), tpe, fp32);
 }
 
-// The packed FP64 rows of the layer's FP64 table (which must be built for
-// `catalog`), read by the FP64 register-rows kernel.
+// The packed FP64 rows of the layer, built straight from its ELT entries (no
+// dense table), read by the FP64 register-rows kernel.
 Packed &build_packed64(are_ctx *ctx, Layer &L, int32_t catalog, cudaStream_t s)
 {
     Packed &p = L.p64;
     const int rw = row_words(ctx, L, catalog, false);
     size_packed(ctx, L, p, catalog, rw, rw * sizeof(unsigned long long),
                 sizeof(double) * (size_t)layer_entries(ctx, L));
-    const Table &t = L.t64;
-    ctx->launches += launch_pack64(static_cast<const double *>(t.d), t.jp, catalog, rw,
-                                   static_cast<unsigned long long *>(p.rows()),
-                                   static_cast<double *>(p.ovf()), p.used(), ctx->num_sms, s);
+    const ScatterArgs a = scatter_args(ctx, L, catalog, table_jp((int)L.elts.size(), false));
+    ctx->launches += launch_pack64_direct(a, catalog, rw, static_cast<unsigned long long *>(p.rows()),
+                                          static_cast<double *>(p.ovf()), p.used(), s);
     return p;
 }
 
@@ -368,17 +367,30 @@ Packed &build_packed32_direct(are_ctx *ctx, Layer &L, int32_t catalog, int pw, c
     return p;
 }
 
-// The tables beside a layer's FP64 table that a kernel choice reads: the
-// packed rows (register rows, kernel 2) or the FP32 screen (kernel 3).
-// `fresh`: the layer's table was just rebuilt.  (The FP32 packed rows are
-// built from the ELT entries, build_packed32_direct.)
+// The table beside a layer's dense FP64 table that a kernel choice reads:
+// the FP32 screen (kernel 3).  `fresh`: the layer's table was just rebuilt.
+// (The packed rows of the register-rows kernels are built from the ELT
+// entries: build_packed32_direct, build_packed64.)
 void ensure_aux(are_ctx *ctx, Layer &L, int32_t catalog, bool fp32, int kernel, bool fresh, cudaStream_t s)
 {
-    if (fp32) return;
-    if (kernel == 2 && (fresh || !L.p64.d || L.p64.catalog != catalog ||
-                        L.p64.rw != row_words(ctx, L, catalog, false)))
-        build_packed64(ctx, L, catalog, s);
-    if (kernel == 3 && (fresh || !L.t32u.d || L.t32u.catalog != catalog)) build_screen(ctx, L, catalog, s);
+    if (!fp32 && kernel == 3 && (fresh || !L.t32u.d || L.t32u.catalog != catalog)) build_screen(ctx, L, catalog, s);
+}
+
+// The packed rows a register-rows analysis (kernel 2) of the layer reads,
+// built if missing (or always, with rebuild); false where it reads the
+// dense FP32 table instead.
+bool ensure_packed(are_ctx *ctx, Layer &L, int32_t catalog, bool fp32, cudaStream_t s, bool rebuild)
+{
+    const int w = row_words(ctx, L, catalog, fp32);
+    if (!w) return false;
+    Packed &p = fp32 ? L.p32 : L.p64;
+    if (rebuild || !p.d || p.catalog != catalog || p.rw != w) {
+        if (fp32)
+            build_packed32_direct(ctx, L, catalog, w, s);
+        else
+            build_packed64(ctx, L, catalog, s);
+    }
+    return true;
 }
 
 void ensure_tables(are_ctx *ctx, Layer &L, const Yet &y, are_precision precision, cudaStream_t s,
@@ -392,12 +404,8 @@ void ensure_tables(are_ctx *ctx, Layer &L, const Yet &y, are_precision precision
     }
     const int jp = table_jp((int)L.elts.size(), fp32);
     const int kernel = tuned(ctx, precision, y, jp, false).kernel;
-    const int pw = fp32 && kernel == 2 ? row_words(ctx, L, catalog, true) : 0;
-    if (pw) {   // packed rows straight from the ELT entries; a dense table only when a kernel needs one
-        if (rebuild || !L.p32.d || L.p32.catalog != catalog || L.p32.rw != pw)
-            build_packed32_direct(ctx, L, catalog, pw, s);
-        return;
-    }
+    // packed rows straight from the ELT entries; a dense table only when a kernel needs one
+    if (kernel == 2 && ensure_packed(ctx, L, catalog, fp32, s, rebuild)) return;
     const Table &t = fp32 ? L.t32 : L.t64;
     const bool fresh = rebuild || !t.d || t.catalog != catalog;
     if (fresh) build_table(ctx, L, catalog, fp32, s);
@@ -713,12 +721,7 @@ void ensure_tables(are_ctx *ctx, const int32_t *layers, int32_t n_layers, const 
 {
     for (int32_t i = 0; i < n_layers; ++i) {
         Layer &L = layer_of(ctx, layers[i]);
-        const int pw = fp32 && kernel == 2 ? row_words(ctx, L, y.catalog, true) : 0;
-        if (pw) {   // packed rows straight from the ELT entries
-            if (!L.p32.d || L.p32.catalog != y.catalog || L.p32.rw != pw)
-                build_packed32_direct(ctx, L, y.catalog, pw, s);
-            continue;
-        }
+        if (kernel == 2 && ensure_packed(ctx, L, y.catalog, fp32, s, false)) continue;   // packed rows
         const Table &t = fp32 ? L.t32 : L.t64;
         const bool fresh = !t.d || t.catalog != y.catalog;
         if (fresh) build_table(ctx, L, y.catalog, fp32, s);

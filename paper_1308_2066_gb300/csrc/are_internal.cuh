@@ -121,7 +121,8 @@ struct Compact {
 // Packed table of one layer: catalog rows of 32 or 64 bytes holding each
 // event's non-zero terms in column order behind the mask of their columns,
 // a counter and the overflow terms, in one allocation laid out [rows |
-// counter (256 B) | overflow].  FP64 (built from t64 by launch_pack64):
+// counter (256 B) | overflow].  FP64 (built from the ELT entries by
+// launch_pack64_direct):
 // rw = 4 or 8 64-bit words per row, the mask and the overflow offset in word
 // 0, up to rw - 1 terms inline and every term of a longer row in the
 // overflow.  FP32 (built from the ELT entries by launch_pack32_direct):
@@ -314,8 +315,8 @@ std::vector<CeilingShape> gather_ceiling(const int32_t *ids, int64_t n, int row_
                                          uint64_t &launches);
 int table_jp(int n_elts, bool fp32);
 int packed_row_words(int n_elts, double terms_per_event, bool fp32);
-int launch_pack64(const double *dense, int jp64, int32_t catalog, int rw, unsigned long long *rows,
-                  double *ovf, unsigned long long *ovf_used, int num_sms, cudaStream_t s);
+int launch_pack64_direct(const ScatterArgs &a, int32_t catalog, int rw, unsigned long long *rows, double *ovf,
+                         unsigned long long *ovf_used, cudaStream_t s);
 int launch_pack32_direct(const ScatterArgs &a, int32_t catalog, int pw, uint32_t *rows, float *ovf,
                          unsigned long long *ovf_used, cudaStream_t s);
 

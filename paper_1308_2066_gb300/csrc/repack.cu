@@ -37,48 +37,56 @@ __global__ void k_scatter(T *__restrict__ tab, const ScatterArgs a)
     }
 }
 
-// Packed FP64 rows (rw = 4 or 8 words: 32 or 64 bytes) from the dense FP64
-// table: row e gets the mask of its non-zero columns (low 32 bits of word 0)
-// and those terms in column order (words 1 .. rw - 1).  A row with more
-// non-zero terms than that keeps the first rw - 1 inline and all of them in
-// a block of the overflow array, whose offset goes to the high 32 bits of
-// word 0 (blocks are handed out by an atomic counter; each block holds its
-// row's terms in column order).
-template <int RW>
-__global__ void k_pack64(const double *__restrict__ dense, int jp64, int32_t catalog,
-                         unsigned long long *__restrict__ rows, double *__restrict__ ovf,
-                         unsigned long long *__restrict__ ovf_used)
+// Packed FP64 rows (rw = 4 or 8 words: 32 or 64 bytes): row e holds the
+// mask of its non-zero columns (low 32 bits of word 0) and those terms in
+// column order (words 1 .. rw - 1).  A row with more non-zero terms than
+// that keeps the first rw - 1 inline and all of them in a block of the
+// overflow array, whose offset goes to the high 32 bits of word 0 (blocks
+// are handed out by an atomic counter; each block holds its row's terms in
+// column order).  Built straight from the ELT entries in three passes (grid.y
+// = ELT j), each entry's term formed as k_scatter forms it; ELT ids are
+// unique, so each (row, column) is one entry's alone.
+// 1. the mask;
+__global__ void k_pack64_mask(const ScatterArgs a, unsigned long long *__restrict__ rows, int rw)
 {
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < catalog;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        const double *d = dense + e * jp64;
-        // the mask in 16-byte loads (rows are whole multiples of 32 bytes)
-        const ulonglong2 *d2 = reinterpret_cast<const ulonglong2 *>(d);
-        uint32_t mask = 0;
-        for (int q = 0; q < jp64 / 2; ++q) {
-            const ulonglong2 x = __ldg(d2 + q);
-            mask |= (x.x != 0ull ? 1u : 0u) << (2 * q);
-            mask |= (x.y != 0ull ? 1u : 0u) << (2 * q + 1);
+    const int j = blockIdx.y;
+    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < a.n[j]; i += gridDim.x * blockDim.x) {
+        const double x = fin_term(a.loss[j][i], a.fx[j], a.ded[j], a.lim[j], a.share[j]);
+        if (__double_as_longlong(x) != 0) atomicOr(rows + (size_t)a.ids[j][i] * rw, 1ull << j);
+    }
+}
+
+// 2. the inline terms at their rank; in a row that overflows, the entry of
+//    rank 0 takes the row's overflow block and writes its offset;
+__global__ void k_pack64_place(const ScatterArgs a, unsigned long long *__restrict__ rows, int rw,
+                               unsigned long long *__restrict__ ovf_used)
+{
+    const int j = blockIdx.y;
+    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < a.n[j]; i += gridDim.x * blockDim.x) {
+        const double x = fin_term(a.loss[j][i], a.fx[j], a.ded[j], a.lim[j], a.share[j]);
+        if (__double_as_longlong(x) == 0) continue;
+        unsigned long long *row = rows + (size_t)a.ids[j][i] * rw;
+        const uint32_t mask = (uint32_t)row[0];
+        const int cnt = __popc(mask), r = __popc(mask & ((1u << j) - 1u));
+        if (r < rw - 1) row[1 + r] = (unsigned long long)__double_as_longlong(x);
+        if (cnt > rw - 1 && r == 0) {
+            const unsigned long long off = atomicAdd(ovf_used, (unsigned long long)cnt);
+            atomicOr(row, off << 32);
         }
-        const int cnt = __popc(mask);
-        const bool over = cnt > RW - 1;
-        uint32_t off = 0;
-        if (over) off = (uint32_t)atomicAdd(ovf_used, (unsigned long long)cnt);
-        unsigned long long w[RW];
-        w[0] = (unsigned long long)mask | ((unsigned long long)off << 32);
-#pragma unroll
-        for (int i = 1; i < RW; ++i) w[i] = 0ull;
-        int k = 0;
-        for (uint32_t m = mask; m; m &= m - 1, ++k) {
-            const double x = __ldg(d + __ffs(m) - 1);
-#pragma unroll
-            for (int i = 1; i < RW; ++i)
-                if (k == i - 1) w[i] = (unsigned long long)__double_as_longlong(x);
-            if (over) ovf[off + k] = x;
-        }
-        ulonglong2 *out = reinterpret_cast<ulonglong2 *>(rows + e * RW);
-#pragma unroll
-        for (int q = 0; q < RW / 2; ++q) out[q] = make_ulonglong2(w[2 * q], w[2 * q + 1]);
+    }
+}
+
+// 3. every term of an overflowing row into its block.
+__global__ void k_pack64_over(const ScatterArgs a, const unsigned long long *__restrict__ rows, int rw,
+                              double *__restrict__ ovf)
+{
+    const int j = blockIdx.y;
+    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < a.n[j]; i += gridDim.x * blockDim.x) {
+        const unsigned long long h = rows[(size_t)a.ids[j][i] * rw];
+        const uint32_t mask = (uint32_t)h;
+        if (__popc(mask) <= rw - 1 || !((mask >> j) & 1u)) continue;
+        const int r = __popc(mask & ((1u << j) - 1u));
+        ovf[(uint32_t)(h >> 32) + r] = fin_term(a.loss[j][i], a.fx[j], a.ded[j], a.lim[j], a.share[j]);
     }
 }
 
@@ -187,24 +195,26 @@ int packed_row_words(int n_elts, double terms_per_event, bool fp32)
     return terms_per_event <= 0.5 ? 4 : 8;
 }
 
-// dense: the FP64 table (jp64 columns, catalog rows); rows: catalog x rw
-// words; ovf: room for every non-zero term of the layer; ovf_used: a device
-// counter, zeroed here.
-int launch_pack64(const double *dense, int jp64, int32_t catalog, int rw, unsigned long long *rows,
-                  double *ovf, unsigned long long *ovf_used, int num_sms, cudaStream_t s)
+// Packed FP64 rows (rw words) straight from the layer's ELT entries: rows
+// catalog x rw words, ovf room for every entry, ovf_used a device counter.
+// Three launches, no dense table.
+int launch_pack64_direct(const ScatterArgs &a, int32_t catalog, int rw, unsigned long long *rows, double *ovf,
+                         unsigned long long *ovf_used, cudaStream_t s)
 {
+    if (rw != 4 && rw != 8) throw Error{ARE_EINVAL, "packed FP64 rows are 4 or 8 words"};
     ARE_CUDA_TRY(cudaMemsetAsync(ovf_used, 0, sizeof *ovf_used, s));
     if (catalog <= 0) return 0;
-    int64_t blocks = ((int64_t)catalog + 255) / 256;
-    if (blocks > (int64_t)num_sms * 16) blocks = (int64_t)num_sms * 16;
-    if (rw == 4)
-        k_pack64<4><<<(unsigned)blocks, 256, 0, s>>>(dense, jp64, catalog, rows, ovf, ovf_used);
-    else if (rw == 8)
-        k_pack64<8><<<(unsigned)blocks, 256, 0, s>>>(dense, jp64, catalog, rows, ovf, ovf_used);
-    else
-        throw Error{ARE_EINVAL, "packed FP64 rows are 4 or 8 words"};
+    ARE_CUDA_TRY(cudaMemsetAsync(rows, 0, sizeof(unsigned long long) * (size_t)catalog * rw, s));
+    int32_t nmax = 0;
+    for (int j = 0; j < a.n_elts; ++j) nmax = a.n[j] > nmax ? a.n[j] : nmax;
+    if (nmax == 0 || a.n_elts == 0) return 0;
+    dim3 grid((unsigned)((nmax + 255) / 256), (unsigned)a.n_elts);
+    if (grid.x > 4096) grid.x = 4096;
+    k_pack64_mask<<<grid, 256, 0, s>>>(a, rows, rw);
+    k_pack64_place<<<grid, 256, 0, s>>>(a, rows, rw, ovf_used);
+    k_pack64_over<<<grid, 256, 0, s>>>(a, rows, rw, ovf);
     ARE_CUDA_TRY(cudaGetLastError());
-    return 1;
+    return 3;
 }
 
 // Columns per row: J rounded up so a row fills whole 32-byte sectors; FP32

@@ -359,14 +359,15 @@ __device__ __forceinline__ W4 load4w(const unsigned long long *p)
     return r;
 }
 
-// FP64 path over the packed FP64 table (repack.cu, launch_pack64): row e is
-// RW = 4 or 8 words (32 or 64 bytes) -- word 0 holds the mask of
+// FP64 path over the packed FP64 table (repack.cu, launch_pack64_direct):
+// row e is RW = 4 or 8 words (32 or 64 bytes) -- word 0 holds the mask of
 // the ELT columns whose term is not 0 (low 32 bits) and an overflow offset
-// (high 32 bits), words 1 .. RW - 1 the non-zero terms in column order.  A row with more non-zero terms than that keeps the first
-// RW - 1 inline and all of them at the overflow offset.  The terms are
-// added in column order (the first taken as is, an FP64 add only where some
-// event has two or more), so every event loss and occurrence loss is the
-// oracle's bit for bit; the running sum is exact (fixed point, fixed.cuh).
+// (high 32 bits), words 1 .. RW - 1 the non-zero terms in column order.  A
+// row with more non-zero terms than that keeps the first RW - 1 inline and
+// all of them at the overflow offset.  The terms are added in column order
+// (the first taken as is, an FP64 add only where some event has two or
+// more), so every event loss and occurrence loss is the oracle's bit for
+// bit; the running sum is exact (fixed point, fixed.cuh).
 template <int RW, int U>
 struct BodyP64 {
     using Sum = SumFixed;
