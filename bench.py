@@ -393,7 +393,7 @@ def roofline(n_events, n_trials, J, prec, sim_ms, tuned=None, ceiling=None, rows
     size.  achieved and peak are the algorithmic bytes (4 B id + the row the
     kernel reads per event, 8 B per trial) over the kernel's time and over
     the ceiling's time, so frac = the kernel's rows/s over the ceiling's.
-    hbm_formula_frac puts the survey formula's bytes (the row of J entries of
+    hbm_formula_frac puts the dense-row formula's bytes (the row of J entries of
     the precision, in whole 32-B sectors) over the measured HBM copy
     bandwidth (above 1: the rows are not HBM traffic); dram_frac is the
     ncu-measured DRAM traffic of one launch over the kernel's time, over
@@ -401,7 +401,7 @@ def roofline(n_events, n_trials, J, prec, sim_ms, tuned=None, ceiling=None, rows
     hbm, src = hbm_peak()
     rb = rows[0]
     bytes_ = n_events * (4 + rb) + 8 * n_trials
-    survey_bytes = algorithmic_bytes(n_events, n_trials, J, 8 if prec == 0 else 4)
+    dense_bytes = algorithmic_bytes(n_events, n_trials, J, 8 if prec == 0 else 4)
     secs = sim_ms * 1e-3
     achieved = bytes_ / secs / 1e9
     key = kernel_key(prec, J, tuned, rows)
@@ -413,10 +413,10 @@ def roofline(n_events, n_trials, J, prec, sim_ms, tuned=None, ceiling=None, rows
             "peak": round(bytes_ / (n_events / best) / 1e9, 1), "unit": "GB/s",
             "frac": round(rate / best, 4), "traffic": traffic, "kernel": key,
             "algorithmic_bytes_per_launch": bytes_,
-            "survey_formula_bytes_per_launch": survey_bytes,
+            "dense_formula_bytes_per_launch": dense_bytes,
             "peak_source": ("measured live in this run: best of %d launch shapes of the gather "
                             "ceiling (ids + table rows, no arithmetic) on this YET" % len(shapes)),
-            "hbm_formula_frac": round(survey_bytes / secs / 1e9 / hbm, 4),
+            "hbm_formula_frac": round(dense_bytes / secs / 1e9 / hbm, 4),
             "dram_frac": (round(traffic / secs / 1e9 / hbm, 4) if traffic else None),
             "hbm_peak": hbm, "hbm_peak_source": f"{src} HBM copy bandwidth (MEASURED_PEAKS.json)",
             "l2_gather": {"row_bytes": rb, "packed_rows": rows[1],
