@@ -559,6 +559,75 @@ def run_e2e(are, torch, ctx, wl, prec, steps, warmup, world):
 
 
 # ---------------------------------------------------------------------------
+# the per-occurrence outputs and the compact table on the paper-scale layer
+# ---------------------------------------------------------------------------
+
+def next_record(are, torch, res, steps, warmup):
+    """Per-occurrence outputs (the marginal of every occurrence, each trial's
+    largest occurrence loss and the YLT) in FP64 and FP32 + Kahan, and the
+    FP32 + Kahan analysis over the compact table (a row index and rows only
+    for the events some ELT holds), timed with CUDA events on the resident
+    paper-scale workload and checked against the direct analysis's YLT."""
+    ctx, wl = res.ctx, res.wl
+    y = wl.yet
+    n, J = y.n_trials, len(wl.layers[0].elts)
+    stream = torch.cuda.Stream()
+    hbm, _ = hbm_peak()
+    out = {}
+
+    def timed(fn):
+        for _ in range(warmup):
+            fn()
+        evs = []
+        for _ in range(steps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            evs.append((a, b))
+        torch.cuda.synchronize()
+        return float(np.median([a.elapsed_time(b) for a, b in evs]))
+
+    ref = torch.empty(n, dtype=torch.float64, device="cuda")
+    ylt = torch.empty(n, dtype=torch.float64, device="cuda")
+    marg = torch.empty(y.n_events, dtype=torch.float64, device="cuda")
+    occ_max = torch.empty(n, dtype=torch.float64, device="cuda")
+    for p in (0, 1):
+        are.are_prepare(ctx, res.layer, res.yet, p, stream)
+        are.are_simulate(ctx, res.layer, res.yet, 0, n, p, ref, stream)
+        ms = timed(lambda: are.are_simulate_occurrences(ctx, res.layer, res.yet, 0, n, p, marg, occ_max,
+                                                       ylt, stream))
+        torch.cuda.synchronize()
+        diff = float(((ylt - ref).abs() / ref.abs().clamp_min(1e-300)).max())
+        hbm_bytes = y.n_events * (4 + 8) + n * 16   # ids in, marginals, maxima and YLT out
+        out[f"per_occurrence_outputs_{PRECISION_NAMES[p]}"] = {
+            "ms": round(ms, 4), "value": round(y.n_events * J / (ms * 1e-3) / 1e9, 3),
+            "unit": UNIT, "hbm_bytes_per_launch": hbm_bytes,
+            "hbm_frac": round(hbm_bytes / (ms * 1e-3) / 1e9 / hbm, 4),
+            "ylt_rel_diff_max_vs_analysis": diff,
+            "what": "are_simulate_occurrences: every occurrence's marginal (8 B), each trial's "
+                    "largest occurrence loss and the YLT"}
+    del marg
+    torch.cuda.empty_cache()
+    are.are_prepare(ctx, res.layer, res.yet, 1, stream)
+    are.are_simulate(ctx, res.layer, res.yet, 0, n, 1, ref, stream)
+    are.are_set_table_layout(ctx, res.layer, are.ARE_LAYOUT_COMPACT)
+    try:
+        are.are_prepare(ctx, res.layer, res.yet, 1, stream)
+        ms = timed(lambda: are.are_simulate(ctx, res.layer, res.yet, 0, n, 1, ylt, stream))
+        torch.cuda.synchronize()
+        diff = float(((ylt - ref).abs() / ref.abs().clamp_min(1e-300)).max())
+        out["compact_table_fp32_kahan"] = {
+            "ms": round(ms, 4), "value": round(y.n_events * J / (ms * 1e-3) / 1e9, 3), "unit": UNIT,
+            "ylt_rel_diff_max_vs_direct": diff,
+            "what": "the compact layout (a row index over the catalog and rows of the events some "
+                    "ELT holds) on the staged kernel: the rows of absent events are not read"}
+    finally:
+        are.are_set_table_layout(ctx, res.layer, are.ARE_LAYOUT_DIRECT)
+    return out
+
+
+# ---------------------------------------------------------------------------
 # portfolio batching: 64 uneven layers over one ragged YET
 # ---------------------------------------------------------------------------
 
@@ -1082,6 +1151,9 @@ def main():
 
     if not args.no_e2e:
         line["e2e"] = run_e2e(are, torch, ctx, wl, prec, max(1, min(args.steps, 10)), 1, world)
+
+    if world == 1 and not args.no_subrecords and not args.no_variants:
+        line["next_rows"] = next_record(are, torch, res, max(3, min(args.steps, 10)), 3)
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, n, cores, dt = oracle_rate(wl, args.cpu_seconds)

@@ -572,7 +572,7 @@ int run_single(are_ctx *ctx, const Layer &L, const Yet &y, int64_t trial_begin, 
             a.jp64 = t.jp;
             return launch_screen64(a, L.t32u.jp, t64, ctx->num_sms, s);
         }
-        return launch_staged64(a, t.jp, t64, false, ctx->num_sms, s);   // (or an aux table not built)
+        return launch_staged64(a, t.jp, t64, ctx->num_sms, s);   // (or an aux table not built)
     }
     return launch_simulate(a, precision, t.jp, &t32, &t64, ctx->num_sms, s);
 }
@@ -1493,7 +1493,10 @@ are_status are_simulate_occurrences(are_ctx *ctx, int32_t layer, int32_t yet, in
         CallStream cs(ctx, stream);
         const bool fp32 = precision != ARE_FP64;
         Table &t = fp32 ? L.t32 : L.t64;
-        if (!t.d || t.catalog != y.catalog) build_table(ctx, L, y.catalog, fp32, cs.s);
+        // the rows of the register-rows form (the direct layout, whatever the
+        // layer's analysis layout): packed where the layer's row size calls for them
+        const bool packed = ensure_packed(ctx, L, y.catalog, fp32, cs.s, false);
+        if (!packed && (!t.d || t.catalog != y.catalog)) build_table(ctx, L, y.catalog, fp32, cs.s);
         SimArgs a{};
         a.ids = y.d_ids;
         a.off = y.d_off;
@@ -1516,8 +1519,15 @@ are_status are_simulate_occurrences(are_ctx *ctx, int32_t layer, int32_t yet, in
         TermsF32 t32;
         TermsF64 t64;
         fill_terms(L, t32, t64);
-        ctx->launches += fp32 ? launch_staged32_occ(a, t.jp, t32, ctx->num_sms, cs.s)
-                              : launch_staged64(a, t.jp, t64, true, ctx->num_sms, cs.s);
+        if (packed) {
+            const Packed &p = fp32 ? L.p32 : L.p64;
+            a.table = p.rows();
+            a.table2 = p.ovf();
+            ctx->launches += launch_rows_occ(a, fp32 ? 1 : 0, p.rw, t32, t64, fixed_scale(ctx, L), ctx->num_sms,
+                                             cs.s);
+        } else {         // dense FP32 rows
+            ctx->launches += launch_rows_occ(a, 2, t.jp, t32, t64, fixed_scale(ctx, L), ctx->num_sms, cs.s);
+        }
         cs.finish();
     });
 }

@@ -345,16 +345,18 @@ int launch_check_timestamps(const float *ts, const int64_t *off, int64_t n_trial
 int launch_items(const ItemWork &w, int jp, const ItemConfig &cfg, are_precision prec,
                  int num_sms, cudaStream_t s);
 
-// staged64.cu / staged_occ.cu: one event per lane, rows staged in shared
-// memory; `occ` also writes per-occurrence marginals and occurrence maxima.
-int launch_staged64(const SimArgs &a, int jp, const TermsF64 &t, bool occ, int num_sms,
-                    cudaStream_t s);
-int launch_staged32_occ(const SimArgs &a, int jp, const TermsF32 &t, int num_sms, cudaStream_t s);
+// staged64.cu: one event per lane, FP64 rows staged in shared memory.
+int launch_staged64(const SimArgs &a, int jp, const TermsF64 &t, int num_sms, cudaStream_t s);
 
 // rows64.cu: the FP64 register-rows kernel over the packed FP64 table
 // (a.table, row_words words per row; a.table2: its overflow terms); `scale`
 // is the fixed-point scale of its exact running sums (every occurrence loss
 // times 2^scale below 2^126).
+// rows_occ.cu: the per-occurrence outputs over the register-rows kernels'
+// rows (form 0 packed FP64, 1 packed FP32, 2 dense FP32; a.table and
+// a.table2 the rows and their overflow).
+int launch_rows_occ(const SimArgs &a, int form, int row_words, const TermsF32 &t32, const TermsF64 &t64, int scale,
+                    int num_sms, cudaStream_t s);
 int launch_rows64(const SimArgs &a, int row_words, const TermsF64 &t, int scale, int num_sms,
                   cudaStream_t s);
 

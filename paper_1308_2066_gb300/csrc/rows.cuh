@@ -235,9 +235,20 @@ struct BodyF32 {
     const float *table;      // [catalog][JP] terms
     float occ_r, occ_l;
 
+    static constexpr int R = JP / 8, RPW = 32 / R;
+    using Occ = float;
+
     __device__ __forceinline__ void batch(const int32_t (&id)[U], bool full, int lane, Sum &acc) const
     {
-        constexpr int R = JP / 8;
+        float o[U];
+        occ(id, full, lane, o);
+#pragma unroll
+        for (int u = 0; u < U; ++u) acc.add(o[u]);   // the running sum of step 4
+    }
+    // Steps 1-3 for a batch: lane (row, col) ends with the occurrence loss of
+    // event col * RPW + row of each group (0 past the trial).
+    __device__ __forceinline__ void occ(const int32_t (&id)[U], bool full, int lane, float (&o)[U]) const
+    {
         const int col = lane % R;
         F8 v[U][R];
         load_rows<JP, U>(table, id, full, lane, v);   // step 1: every ELT's entry, one row read
@@ -259,8 +270,7 @@ struct BodyF32 {
                     p[m] = __fadd_rn(keep, __shfl_xor_sync(kFull, send, h));
                 }
             }
-            // step 3 (occurrence terms), then the running sum of step 4
-            acc.add(fminf(fmaxf(__fsub_rn(p[0], occ_r), 0.f), occ_l));
+            o[u] = fminf(fmaxf(__fsub_rn(p[0], occ_r), 0.f), occ_l);   // step 3 (occurrence terms)
         }
     }
     __device__ __forceinline__ double total(const Sum &t) const
@@ -282,11 +292,21 @@ template <int PW, int U, int ACC>
 struct BodyPackedF32 {
     using Sum = typename std::conditional<ACC == ARE_FP32_KAHAN, SumKahan, SumF64>::type;
     static constexpr int R = PW / 8, RPW = 32 / R, SLOTS = PW - 1;
+    using Occ = float;
     const float *rows;       // [catalog][PW]
     const float *ovf;        // the terms past the inline ones of the longer rows
     float occ_r, occ_l;
 
     __device__ __forceinline__ void batch(const int32_t (&id)[U], bool full, int lane, Sum &acc) const
+    {
+        float o[U];
+        occ(id, full, lane, o);
+#pragma unroll
+        for (int u = 0; u < U; ++u) acc.add(o[u]);   // the running sum of step 4
+    }
+    // Steps 1-3 for a batch: lane (row, col) ends with the occurrence loss of
+    // event col * RPW + row of each group (0 past the trial).
+    __device__ __forceinline__ void occ(const int32_t (&id)[U], bool full, int lane, float (&o)[U]) const
     {
         const int row = lane / R, col = lane % R;
         F8 v[U][R];
@@ -336,8 +356,8 @@ struct BodyPackedF32 {
             }
         }
 #pragma unroll
-        for (int u = 0; u < U; ++u)   // step 3 (occurrence terms), then the running sum of step 4
-            acc.add(fminf(fmaxf(__fsub_rn(g[u], occ_r), 0.f), occ_l));
+        for (int u = 0; u < U; ++u)   // step 3 (occurrence terms)
+            o[u] = fminf(fmaxf(__fsub_rn(g[u], occ_r), 0.f), occ_l);
     }
     __device__ __forceinline__ double total(const Sum &t) const
     {
@@ -372,12 +392,28 @@ template <int RW, int U>
 struct BodyP64 {
     using Sum = SumFixed;
     static constexpr int R = RW / 4, RPW = 32 / R, CAP = RW - 1;
+    using Occ = double;
     const unsigned long long *rows;   // [catalog][RW]
     const double *ovf;                // overflow terms
     int32_t scale;                    // fixed-point scale s: every occurrence loss * 2^s < 2^126
     double occ_r, occ_l;
 
     __device__ __forceinline__ void batch(const int32_t (&id)[U], bool full, int lane, Sum &acc) const
+    {
+        double o[U];
+        occ(id, full, lane, o);
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            if (bits(o[u]) != 0) {   // step 4's running sum, exact
+                unsigned long long lo, hi;
+                fixed::to_fixed(o[u], scale, lo, hi);
+                acc.a.add(lo, hi, 0u);
+            }
+    }
+    // Steps 1-3 for a batch: lane (row, col) ends with the occurrence loss of
+    // event col * RPW + row of each group (0 past the trial), the oracle's
+    // bit for bit.
+    __device__ __forceinline__ void occ(const int32_t (&id)[U], bool full, int lane, double (&out)[U]) const
     {
         const int row = lane / R, col = lane % R;
         // step 1: each event's whole row -- lane (row, col) reads piece col
@@ -437,12 +473,7 @@ struct BodyP64 {
                 const double d = vsub(g, occ_r);
                 if (need) o = dbl(bits(d) < bits(occ_l) ? bits(d) : bits(occ_l));
             }
-            // step 4's running sum, exact
-            if (bits(o) != 0) {
-                unsigned long long lo, hi;
-                fixed::to_fixed(o, scale, lo, hi);
-                acc.a.add(lo, hi, 0u);
-            }
+            out[u] = o;
         }
     }
     __device__ __forceinline__ double total(const Sum &t) const { return fixed::to_double(t.a, scale); }

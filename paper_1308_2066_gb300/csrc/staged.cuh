@@ -1,7 +1,6 @@
 // staged.cuh -- the analysis stage with one event per lane and the event's
 // table row staged in shared memory (cp.async, coalesced: one L1 wavefront
-// per row).  Instantiated by staged64.cu (FP64 tables) and staged_occ.cu
-// (per-occurrence outputs).
+// per row).  Instantiated by staged64.cu (FP64 tables).
 //
 // A table entry is the event's financial term in one ELT (formed in FP64 as
 // the table is built).  FP64 tables: GB300 issues an FP64 add at about 1/66
@@ -12,14 +11,6 @@
 // Columns with a zero term add an exact 0, which changes nothing, so the
 // event loss is the sum over ELTs of step 2 in layer order, as the paper's
 // loop forms it.
-//
-// Per-occurrence outputs (step 4 of the Basic Algorithm, before its final sum): a
-// warp-shuffle inclusive scan of the batch's occurrence losses plus the
-// running total carried from the previous batch gives S_d, the aggregate
-// terms give A_d and the marginal m_d = A_d - A_{d-1} takes A_{d-1} from the
-// neighbouring lane (from the carry for the first lane).  The largest
-// occurrence loss of each trial (for occurrence-exceedance PML) comes from a
-// warp max at the end of the trial.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -158,10 +149,7 @@ __device__ __forceinline__ Batch next_batch(const SimArgs &a, Cursor &c, int64_t
             }
             return b;
         }
-        if (lane == 0) {
-            if (a.ylt) a.ylt[c.t] = empty_loss;
-            if (a.occ_max) a.occ_max[c.t] = 0.0;
-        }
+        if (lane == 0 && a.ylt) a.ylt[c.t] = empty_loss;
         c.t += step;
         if (c.t < a.n_trials) trial_bounds<FIXED>(a, c.t, c.pos, c.end);
     }
@@ -253,18 +241,7 @@ __device__ __forceinline__ double warp_sum(double v)
     for (int off = 16; off > 0; off >>= 1) v = __dadd_rn(v, __shfl_xor_sync(kFull, v, off));
     return v;
 }
-__device__ __forceinline__ double warp_max_nn(double v)
-{
-    uint64_t b = bits(v);
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-        const uint64_t o = __shfl_xor_sync(kFull, b, off);
-        b = o > b ? o : b;
-    }
-    return dbl(b);
-}
-
-template <typename T, int JP, bool FIXED, bool OCC>
+template <typename T, int JP, bool FIXED>
 __global__ void __launch_bounds__(kWarps * 32) k_staged(const SimArgs a, const TermsOf<T> tm)
 {
     constexpr int VPL = 16 / (int)sizeof(T);
@@ -308,78 +285,19 @@ __global__ void __launch_bounds__(kWarps * 32) k_staged(const SimArgs a, const T
         cp_commit();
     };
 
-    // per-trial state
-    SumF64 sum;                 // YLT-only: per-lane running sums
-    double carry_s = 0.0;       // occurrences: running total before this batch
-    double carry_a = 0.0;       // occurrences: aggregate-clamped running total
-    double omax = 0.0;          // occurrences: largest occurrence loss (per lane)
-    const uint64_t agg_l_bits = bits(a.agg_l);
+    SumF64 sum;   // per-lane running sums of the trial
 
     auto compute = [&](const Batch &b, float4 *buf) {
         T g;
         if constexpr (sizeof(T) == 8) g = event_loss64<JP>(buf, lane);
         else g = event_loss<JP>(buf, lane);
         const T o = occ_clamp(g, tm);
-        if constexpr (!OCC) {
-            if constexpr (sizeof(T) == 8) sum.add(o);
-            else sum.add(widen(o));
-            if (b.last) {
-                const double S = warp_sum(sum.s);
-                if (lane == 0) a.ylt[b.t] = clamp_d(S, a.agg_r, a.agg_l);
-                sum = SumF64{};
-            }
-        } else {
-            // inclusive scan of the batch's occurrence losses
-            double s;
-            if constexpr (sizeof(T) == 4) {
-                float f = o;
-#pragma unroll
-                for (int off = 1; off < 32; off <<= 1) {
-                    const float u = __shfl_up_sync(kFull, f, off);
-                    if (lane >= off) f = __fadd_rn(f, u);
-                }
-                s = widen(f);
-            } else {
-                s = o;
-#pragma unroll
-                for (int off = 1; off < 32; off <<= 1) {
-                    const double u = __shfl_up_sync(kFull, s, off);
-                    if (lane >= off) s = vadd(s, u);
-                }
-            }
-            const double S = vadd(carry_s, s);
-            // A_d is non-decreasing in d; a shuffle scan rounds its partial
-            // sums in different orders, so take the running maximum (on bit
-            // patterns: integer work) to keep every marginal >= 0 exactly
-            uint64_t ab = bits(clamp_bits(vsub(S, a.agg_r), agg_l_bits));
-            const uint64_t cb = bits(carry_a);
-            ab = ab > cb ? ab : cb;
-#pragma unroll
-            for (int off = 1; off < 32; off <<= 1) {
-                const uint64_t u = __shfl_up_sync(kFull, ab, off);
-                if (lane >= off && u > ab) ab = u;
-            }
-            const double A = dbl(ab);
-            double prev = __shfl_up_sync(kFull, A, 1);
-            if (lane == 0) prev = carry_a;
-            const double m = vsub(A, prev);
-            if (lane < b.cnt) a.marg[b.pos + lane - a.marg_base] = m;
-            double ow;
-            if constexpr (sizeof(T) == 4) ow = widen(o);
-            else ow = o;
-            omax = bits(ow) > bits(omax) ? ow : omax;
-            // carry from the batch's last event (the lanes after it hold zeros,
-            // but their scan partials are rounded in other orders)
-            carry_s = __shfl_sync(kFull, S, b.cnt - 1);
-            carry_a = __shfl_sync(kFull, A, b.cnt - 1);
-            if (b.last) {
-                const double mx = warp_max_nn(omax);
-                if (lane == 0) {
-                    if (a.ylt) a.ylt[b.t] = carry_a;
-                    if (a.occ_max) a.occ_max[b.t] = mx;
-                }
-                carry_s = carry_a = omax = 0.0;
-            }
+        if constexpr (sizeof(T) == 8) sum.add(o);
+        else sum.add(widen(o));
+        if (b.last) {
+            const double S = warp_sum(sum.s);
+            if (lane == 0) a.ylt[b.t] = clamp_d(S, a.agg_r, a.agg_l);
+            sum = SumF64{};
         }
     };
 
@@ -412,10 +330,10 @@ __global__ void __launch_bounds__(kWarps * 32) k_staged(const SimArgs a, const T
     cp_wait0();
 }
 
-template <typename T, int JP, bool FIXED, bool OCC>
+template <typename T, int JP, bool FIXED>
 void launch_staged_t(const SimArgs &a, const TermsOf<T> &tm, int num_sms, cudaStream_t s)
 {
-    auto kern = k_staged<T, JP, FIXED, OCC>;
+    auto kern = k_staged<T, JP, FIXED>;
     constexpr int smem = smem_bytes<T, JP>();
     const int per_sm = fit_blocks(reinterpret_cast<const void *>(kern), kWarps * 32, smem);
     int64_t blocks = (a.n_trials + kWarps - 1) / kWarps;
