@@ -207,33 +207,35 @@ def items_bytes(wl) -> int:
     return sum(algorithmic_bytes(y.n_events, y.n_trials, len(L.elts), 4) for L in wl.layers)
 
 
-def kernel_key(prec: int, J: int, tuned=None, rows=None) -> str:
+def kernel_key(prec: int, J: int, tuned=None, rows=None, ragged=False) -> str:
     """Name of the kernel that runs the analysis stage for this precision
-    under the tuned choice (untuned: the register-rows kernels with two
-    groups of 32 events per batch).  rows: (row_bytes, packed) from
-    are_layer_rows, which names the packed-row instances."""
+    under the tuned choice (untuned: the register-rows kernels with their
+    default batch: one group of 32 events over 32-byte FP32 rows, two
+    otherwise).  rows: (row_bytes, packed) from are_layer_rows, which names
+    the packed-row instances; ragged: the YET has trials of varying length."""
     if prec == "folded":
         return "k_folded<fixed,smem_bits>"
     t = tuned or {}
     rb, packed = rows if rows else (None, False)
-    u = t.get("rows_in_flight", 2)
+    u = t.get("rows_in_flight") or (1 if prec != 0 and (rb == 32 or (rb is None and J <= 8)) else 2)
+    cur = "ragged" if ragged else "fixed"
     if prec == 0:
         jp = math.ceil(J / 4) * 4
         kind = t.get("kernel", 2)
         if kind == 3:
-            return f"k_screen64<{8 if J <= 8 else 16 if J <= 16 else 32},fixed>"
+            return f"k_screen64<{8 if J <= 8 else 16 if J <= 16 else 32},{cur}>"
         if kind == 1:
-            return f"k_staged<double,{jp},fixed,ylt>"
-        return f"k_rows64<{(rb or 64) // 8},{u},fixed>"
+            return f"k_staged<double,{jp},{cur},ylt>"
+        return f"k_rows64<{(rb or 64) // 8},{u},{cur}>"
     jp = 8 if J <= 8 else 16 if J <= 16 else 32
     kind = t.get("kernel", 2)
     if kind == 0:
-        return f"k_sim_items<{jp},{u},{prec},fixed>"
+        return f"k_sim_items<{jp},{u},{prec},{cur}>"
     if kind == 2:
         if packed:
-            return f"k_rows_packed<{rb // 4},{u},{prec},fixed>"
-        return f"k_rows<{jp},{u},{prec},fixed>"
-    return f"k_simulate_staged<{jp},{prec},fixed,epl{2 if u == 2 else 1}>"
+            return f"k_rows_packed<{rb // 4},{u},{prec},{cur}>"
+        return f"k_rows<{jp},{u},{prec},{cur}>"
+    return f"k_simulate_staged<{jp},{prec},{cur},epl{2 if u == 2 else 1}>"
 
 
 def layer_rows(are, ctx, layer, yet, prec, tuned=None):
@@ -634,7 +636,7 @@ def next_record(are, torch, res, steps, warmup):
 def portfolio_kernel_name(tuned, prec) -> str:
     """What runs the batched analysis under the tuned choice."""
     kind = (tuned or {}).get("kernel", 2)
-    u = (tuned or {}).get("rows_in_flight", 2)
+    u = (tuned or {}).get("rows_in_flight") or "U"   # untuned: 1 over 32-byte rows, else 2
     if kind == 0:
         return (f"k_sim_items<jp,{u},{prec},ragged>: one persistent launch per table width, "
                 f"{(tuned or {}).get('trials_per_item')} trials per work item")
@@ -856,7 +858,8 @@ def precision_record(are, torch, steps, warmup, tune=True, compact=True, n_trial
             rp, rt = oracle.risk_measures(full, RPS, LEVELS)
             rows[PRECISION_NAMES[p]] = {
                 "sim_ms": round(ms, 4), "tuned": tuned,
-                "kernel": kernel_key(p, len(L.elts), tuned, layer_rows(are, ctx, layer, yet, p, tuned)),
+                "kernel": kernel_key(p, len(L.elts), tuned, layer_rows(are, ctx, layer, yet, p, tuned),
+                                     ragged=True),
                 "value": round(y.n_events * len(L.elts) / (ms * 1e-3) / 1e9, 3),
                 "ylt_rel_err_max": float(rel.max()), "ylt_rel_err_median": float(np.median(rel)),
                 "pml": [float(x) for x in pml], "pml_oracle": [float(x) for x in rp],

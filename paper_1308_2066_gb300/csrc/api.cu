@@ -543,7 +543,7 @@ int run_single(are_ctx *ctx, const Layer &L, const Yet &y, int64_t trial_begin, 
     a.agg_l = L.terms.agg_lim;
     a.ylt = d_out;
     a.kernel = te.kernel;
-    a.epl = te.cfg.rows_in_flight == 2 ? 2 : 1;
+    a.epl = te.cfg.rows_in_flight;   // 0 (untuned): the kernel's default
     TermsF32 t32;
     TermsF64 t64;
     fill_terms(L, t32, t64);
@@ -581,9 +581,9 @@ TuneEntry tuned(are_ctx *ctx, are_precision p, const Yet &y, int jp, bool multi)
 {
     auto it = ctx->tune.find(tune_key(p, y, jp, multi));
     if (it != ctx->tune.end()) return it->second;
-    TuneEntry d;   // untuned: the register-rows kernels, two groups of 32 events per batch
+    TuneEntry d;   // untuned: the register-rows kernels with their default batch
     d.kernel = 2;
-    d.cfg.rows_in_flight = 2;
+    d.cfg.rows_in_flight = 0;
     return d;
 }
 

@@ -184,7 +184,9 @@ struct SimArgs {
     double *ylt;             // n_trials (may be null when occurrences are written)
     int kernel;              // 1 staged, 2 register rows, 3 (FP64) staged screen
     int epl;                 // staged FP32 kernel: events per lane per batch (1 or 2);
-                             // register-rows kernel: groups of 32 events per batch (1 or 2)
+                             // register-rows kernel: groups of 32 events per batch (1 or 2);
+                             // 0: the kernel's default (one event per lane; one group over
+                             // 32-byte FP32 rows, two over wider rows and FP64 rows)
     double *marg;            // per-occurrence marginals, or null
     double *occ_max;         // largest occurrence loss per trial, or null
     int64_t marg_base;       // event index of marg[0]

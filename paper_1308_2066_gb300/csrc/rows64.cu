@@ -24,11 +24,17 @@
 namespace are {
 namespace {
 
-// Blocks per SM the register budget is set for (RW * U words per lane in flight).
-__host__ __device__ constexpr int rows64_min_blocks(int rw, int u) { return rw * u <= 8 ? 4 : rw * u <= 16 ? 3 : 2; }
+// Blocks per SM the register budget is set for: the most that leave at most
+// a word of spill for RW * U words per lane in flight (a ragged YET's cursor
+// needs a few registers more).
+__host__ __device__ constexpr int rows64_min_blocks(int rw, int u, bool fixed)
+{
+    return !fixed ? (rw * u <= 4 ? 5 : rw * u <= 8 ? 4 : rw * u <= 16 ? 3 : 2)
+                  : rw == 4 ? (u == 1 ? 6 : 5) : rw * u <= 8 ? 4 : rw * u <= 16 ? 3 : 2;
+}
 
 template <int RW, int U, bool FIXED>
-__global__ void __launch_bounds__(256, rows64_min_blocks(RW, U))
+__global__ void __launch_bounds__(256, rows64_min_blocks(RW, U, FIXED))
     k_rows64(const rows::Trials a, const rows::BodyP64<RW, U> body, const int64_t n_trials)
 {
     const int lane = threadIdx.x & 31;

@@ -522,7 +522,7 @@ void scheduler(Server *SP)
                 sa.agg_l = sl.rec.agg_l;
                 sa.ylt = sl.rec.ylt + sl.launched;
                 sa.kernel = 2;
-                sa.epl = 2;
+                sa.epl = 0;   // the kernel's default batch for the row width
                 if (sl.pw) {   // over the packed rows
                     sa.table = packed_rows(S, sl);
                     sa.table2 = packed_ovf(S, sl);

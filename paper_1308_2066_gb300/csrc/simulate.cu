@@ -356,10 +356,12 @@ void launch_staged_fx(const SimArgs &a, const TermsF32 &terms, int num_sms, cuda
 // ---------------------------------------------------------------------------
 
 // Blocks per SM the register budget is set for: the row pieces in flight
-// (JP * U floats per lane) decide it.
+// (JP * U floats per lane) decide it.  One 32-byte piece per lane runs best
+// at 6 blocks (40 registers, no spill): 7 or 8 blocks force 32 registers and
+// a slower loop, 5 leave fewer rows in flight.
 __host__ __device__ constexpr int rows_min_blocks(int jp, int u)
 {
-    return jp * u <= 16 ? 5 : jp * u <= 32 ? 4 : 2;
+    return jp * u <= 8 ? 6 : jp * u <= 16 ? 5 : jp * u <= 32 ? 4 : 2;
 }
 
 template <int JP, int U, int ACC, bool FIXED>
@@ -438,7 +440,7 @@ void launch_packed_t(const SimArgs &a, const TermsF32 &tm, int num_sms, cudaStre
 template <int PW, int ACC>
 void launch_packed(const SimArgs &a, const TermsF32 &tm, int num_sms, cudaStream_t s)
 {
-    const bool two = a.epl != 1;
+    const bool two = a.epl == 0 ? PW > 8 : a.epl != 1;
     if (a.off)
         two ? launch_packed_t<PW, 2, ACC, false>(a, tm, num_sms, s)
             : launch_packed_t<PW, 1, ACC, false>(a, tm, num_sms, s);
@@ -450,7 +452,7 @@ void launch_packed(const SimArgs &a, const TermsF32 &tm, int num_sms, cudaStream
 template <int JP, int ACC>
 void launch_rows(const SimArgs &a, const TermsF32 &tm, int num_sms, cudaStream_t s)
 {
-    const bool two = a.epl != 1;
+    const bool two = a.epl == 0 ? JP > 8 : a.epl != 1;
     if (a.off)
         two ? launch_rows_t<JP, 2, ACC, false>(a, tm, num_sms, s)
             : launch_rows_t<JP, 1, ACC, false>(a, tm, num_sms, s);
