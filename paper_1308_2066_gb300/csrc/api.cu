@@ -181,6 +181,15 @@ std::vector<T> to_host(const T *src, size_t n, cudaStream_t s)
 bool nonneg_finite(double x) { return std::isfinite(x) && x >= 0.0; }
 bool nonneg_limit(double x) { return !std::isnan(x) && x >= 0.0; }
 
+// A layer's terms with -0.0 read as +0.0: the kernels compare non-negative
+// doubles by their bit patterns.
+are_layer_terms positive_zeros(are_layer_terms t)
+{
+    for (double *x : {&t.occ_ret, &t.occ_lim, &t.agg_ret, &t.agg_lim})
+        if (*x == 0.0) *x = 0.0;
+    return t;
+}
+
 int check_flag(are_ctx *ctx, cudaStream_t s)
 {
     ARE_CUDA_TRY(cudaMemcpyAsync(ctx->h_flag, ctx->d_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -1020,7 +1029,7 @@ are_status are_define_layer(are_ctx *ctx, const int32_t *elt_handles, int32_t n_
                       "ELT " + std::to_string(h) + " appears twice in the layer");
             L.elts.push_back(h);
         }
-        L.terms = t;
+        L.terms = positive_zeros(t);
         for (int32_t h : L.elts) ctx->elts[h].users++;
         const int32_t h = ctx->next_handle++;
         ctx->layers[h] = L;

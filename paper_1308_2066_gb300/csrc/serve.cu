@@ -269,6 +269,15 @@ void fill_record(Server &S, Slot &sl)
     o.agg_l = sl.req.terms.agg_lim;
 }
 
+// A request's terms with -0.0 read as +0.0 (as are_define_layer does): the
+// kernels compare non-negative doubles by their bit patterns.
+are_layer_terms positive_zeros(are_layer_terms t)
+{
+    for (double *x : {&t.occ_ret, &t.occ_lim, &t.agg_ret, &t.agg_lim})
+        if (*x == 0.0) *x = 0.0;
+    return t;
+}
+
 // Waits for an event without blocking forever (the GPU is shared).
 bool bounded_wait(cudaEvent_t ev)
 {
@@ -736,7 +745,7 @@ are_status are_submit(are_ctx *ctx, const are_request *req, int64_t *ticket)
                 ARE_CHECK(r.ranks[req->n_rp + i] >= 1, ARE_EINVAL, "TVaR level must lie in (0, 1)");
             }
         }
-        r.terms = req->terms;
+        r.terms = positive_zeros(req->terms);
         r.n_trials = req->n_trials;
         r.n_rp = req->n_rp;
         r.n_tv = req->n_tv;

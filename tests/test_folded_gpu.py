@@ -13,6 +13,7 @@ the oracle's sequential sums, its results are pinned exactly:
   the largest or more), computed here with Python fractions;
 * it does not depend on the order of a trial's events or on how the trials
   are split into calls."""
+import json
 import math
 from fractions import Fraction
 
@@ -111,6 +112,36 @@ def test_folded_is_the_exact_sum_of_oracle_occurrence_losses(are, ctx, orc, J, r
             h = oracle_h(orc, wl, layer)
             pick = np.random.default_rng(J).choice(wl.yet.n_trials, 400, replace=False)
             np.testing.assert_array_equal(got[pick], exact_ylt(wl, layer, h, pick))
+    finally:
+        L.release()
+
+
+@pytest.mark.parametrize("J,ragged", [(4, True), (9, False), (16, True), (32, False)])
+def test_fp64_per_elt_analysis_equals_the_exact_sum(are, ctx, orc, tmp_path, J, ragged):
+    """The FP64 analysis over the per-ELT rows forms every occurrence loss as
+    the oracle does and sums a trial's exactly, in whatever order it takes
+    them, so on trials of many events it gives the folded pass's result bit
+    for bit (every occurrence loss here converts to both fixed-point scales
+    without rounding), with one or two groups of 32 events per batch and
+    32- or 64-byte rows (4 and 9 ELTs hold few entries per catalog event,
+    16 and 32 many)."""
+    wl = small_workload(300 + J, J, 20_000, 3000, 90, ragged)
+    L = Loaded(are, ctx, wl, timestamps=False)
+    try:
+        are.are_autotune(ctx, L.layers[:1], L.yet, 0)
+        path = tmp_path / "t.jsonl"
+        are.are_tune_save(ctx, str(path))
+        entries = [json.loads(l) for l in open(path) if l.strip()]
+        key = [e for e in entries if e["key"].startswith("p0_") and e["key"].endswith("_single")]
+        assert key
+        for layer in (0, 1):
+            want = L.folded(layer)
+            assert (want > 0).mean() > 0.2
+            for u in (1, 2):
+                path.write_text("".join(json.dumps(dict(e, kernel=2, rows_in_flight=u)) + "\n"
+                                        for e in key))
+                are.are_tune_load(ctx, str(path))
+                np.testing.assert_array_equal(L.simulate(layer, 0), want, err_msg=f"layer {layer}, U {u}")
     finally:
         L.release()
 

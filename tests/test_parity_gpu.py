@@ -325,6 +325,30 @@ def test_trial_ranges_and_host_buffers(are, ctx, tiny):
         np.testing.assert_array_equal(tiny.simulate(0, p, 17, 5000, device=False), whole[17:5017])
 
 
+def test_negative_zero_terms_read_as_zero(are, ctx, orc, tiny):
+    """Retentions and limits of -0.0 pass validation (they are >= 0) and act
+    as +0.0: with both retentions 0 and then the occurrence limit 0, every
+    precision gives the same trial losses as the layer defined with +0.0,
+    and the oracle's."""
+    for occ_r, occ_l, agg_r in ((0.0, 2e6, 0.0), (5e4, 0.0, 1e5)):
+        pos = tiny.define(W.Layer([0, 1, 2, 3], occ_r, occ_l, agg_r, INF))
+        neg = tiny.define(W.Layer([0, 1, 2, 3], -occ_r if occ_r == 0 else occ_r,
+                                  -occ_l if occ_l == 0 else occ_l, -agg_r if agg_r == 0 else agg_r, INF))
+        try:
+            wl = W.Workload("z", tiny.wl.yet, tiny.wl.elts, [W.Layer([0, 1, 2, 3], occ_r, occ_l, agg_r, INF)])
+            ref = orc.simulate_layer(wl, 0)
+            for p in PRECISIONS:
+                want = tiny.simulate(0, p, handle=pos)
+                np.testing.assert_array_equal(tiny.simulate(0, p, handle=neg), want)
+                ok, st = mixed_check(want, ref.ylt, trial_bound(wl, 0), RTOL[p])
+                assert ok, (occ_r, occ_l, p, st)
+            if occ_l == 0:
+                assert np.all(want == 0)
+        finally:
+            are.are_free_layer(ctx, neg)
+            are.are_free_layer(ctx, pos)
+
+
 def test_single_trial_single_event(are, ctx, orc, golden):
     """The hand-worked cases of tests/golden through the GPU, every precision."""
     spec = golden["layers"]["two_elts"]
