@@ -257,7 +257,8 @@ typedef struct {
                                 table */
     int32_t rows_in_flight;  /* register rows and persistent kernel: groups of 32 events
                                 per batch, 1 or 2; staged kernel: events per lane per
-                                batch, 1 or 2 */
+                                batch, 1 or 2; 0 (in a loaded tuning file): the
+                                kernel's default */
     int32_t trials_per_item; /* trials per work item (persistent kernel) */
     int32_t blocks_per_sm;   /* 0 = as many as fit */
     double ms;               /* measured time of one pass */
@@ -270,6 +271,8 @@ typedef struct {
  * and keep the fastest for this kind of work: precision, YET layout, widest
  * table row, mean events per trial and one layer vs several.  Later
  * are_simulate and are_simulate_portfolio calls of that kind use it.
+ * Untuned work runs the register-rows kernel with one group of 32 events per
+ * batch over 32-byte FP32 rows and two over wider rows and FP64 rows.
  * *best (may be NULL) receives the winner.  Runs on `stream` and waits. */
 ARE_API are_status are_autotune(are_ctx *ctx, const int32_t *layers, int32_t n_layers,
                                 int32_t yet, are_precision precision, void *stream,

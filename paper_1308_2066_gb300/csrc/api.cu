@@ -1924,7 +1924,8 @@ are_status are_tune_load(are_ctx *ctx, const char *path)
                             "\"trials_per_item\": %d, \"blocks_per_sm\": %d, \"ms\": %lf}",
                             key, &e.kernel, &e.cfg.rows_in_flight, &e.cfg.trials_per_item,
                             &e.cfg.blocks_per_sm, &ms) == 6 &&
-                e.kernel >= 0 && e.kernel <= 3 && e.cfg.trials_per_item > 0) {
+                e.kernel >= 0 && e.kernel <= 3 && e.cfg.rows_in_flight >= 0 && e.cfg.rows_in_flight <= 2 &&
+                e.cfg.trials_per_item > 0) {
                 e.ms = ms;
                 ctx->tune[key] = e;
                 ++loaded;
