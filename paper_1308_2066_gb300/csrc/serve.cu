@@ -124,6 +124,7 @@ struct Slot {
     int pw = 0;                     // large: words per packed row (0: the dense rows)
     size_t dense_bytes = 0;         // the dense table (0 for packed rows, which fill the block)
     uint64_t finish_iter = 0;       // iteration whose completion posts the result
+    cudaEvent_t done_ev = nullptr;  // recorded after the result's copy: posts it as soon as it fires
     SelectScratch sel;
     double *h_res = nullptr;        // pinned, 2 * kMaxTargets
     Clock::time_point t_admit;
@@ -278,17 +279,20 @@ are_layer_terms positive_zeros(are_layer_terms t)
     return t;
 }
 
-// Waits for an event without blocking forever (the GPU is shared).
-bool bounded_wait(cudaEvent_t ev)
+// Posts slot sl's result (or drops it when cancelled) and frees the slot.
+// Caller holds S.mu.
+void release_slot(Server &S, Slot &sl)
 {
-    const Clock::time_point t0 = Clock::now();
-    for (;;) {
-        const cudaError_t e = cudaEventQuery(ev);
-        if (e == cudaSuccess) return true;
-        if (e != cudaErrorNotReady) throw Error{ARE_ECUDA, std::string("server: ") + cudaGetErrorString(e)};
-        if (us_between(t0, Clock::now()) > kWaitLimitUs) return false;
-        std::this_thread::sleep_for(std::chrono::microseconds(20));
+    if (sl.cancelled) {
+        S.results.erase(sl.req.ticket);
+    } else {
+        post(S, sl.req, ARE_OK, sl.h_res, sl.t_admit, true);
     }
+    S.running.erase(sl.req.ticket);
+    S.arena.give(sl.tab_off, sl.tab_bytes);
+    S.arena.give(sl.ylt_off, sl.ylt_bytes);
+    sl.busy = sl.cancelled = sl.finishing = false;
+    sl.launched = 0;
 }
 
 // Posts the results of every slot whose last iteration has completed.
@@ -301,19 +305,45 @@ void retire(Server &S, uint64_t completed_iter)
         const bool done = sl.finishing && sl.finish_iter <= completed_iter;
         const bool dropped = sl.cancelled && (!sl.finishing || done) && sl.finish_iter <= completed_iter;
         if (!done && !dropped) continue;
-        if (sl.cancelled) {
-            S.results.erase(sl.req.ticket);
-        } else {
-            post(S, sl.req, ARE_OK, sl.h_res, sl.t_admit, true);
-        }
-        S.running.erase(sl.req.ticket);
-        S.arena.give(sl.tab_off, sl.tab_bytes);
-        S.arena.give(sl.ylt_off, sl.ylt_bytes);
-        sl.busy = sl.cancelled = sl.finishing = false;
-        sl.launched = 0;
+        release_slot(S, sl);
     }
     S.cv_done.notify_all();
     S.cv_work.notify_all();
+}
+
+// Posts the results whose own work has finished, before the rest of their
+// iteration has: a request's latency is its own work and what ran before it.
+void retire_finished(Server &S)
+{
+    std::lock_guard<std::mutex> lk(S.mu);
+    bool any = false;
+    for (Slot &sl : S.slots) {
+        if (!sl.busy || !sl.finishing || sl.cancelled) continue;
+        const cudaError_t e = cudaEventQuery(sl.done_ev);
+        if (e == cudaErrorNotReady) continue;
+        if (e != cudaSuccess) throw Error{ARE_ECUDA, std::string("server: ") + cudaGetErrorString(e)};
+        release_slot(S, sl);
+        any = true;
+    }
+    if (any) {
+        S.cv_done.notify_all();
+        S.cv_work.notify_all();
+    }
+}
+
+// Waits for an event without blocking forever (the GPU is shared), posting
+// the results that finish meanwhile.
+bool bounded_wait(Server &S, cudaEvent_t ev)
+{
+    const Clock::time_point t0 = Clock::now();
+    for (;;) {
+        const cudaError_t e = cudaEventQuery(ev);
+        if (e == cudaSuccess) return true;
+        if (e != cudaErrorNotReady) throw Error{ARE_ECUDA, std::string("server: ") + cudaGetErrorString(e)};
+        retire_finished(S);
+        if (us_between(t0, Clock::now()) > kWaitLimitUs) return false;
+        std::this_thread::sleep_for(std::chrono::microseconds(20));
+    }
 }
 
 void fail_all(Server &S, are_status st, const std::string &msg)
@@ -409,6 +439,7 @@ void scheduler(Server *SP)
             const int buf = (int)(S.iter & 1);
             std::vector<int> part[3], big, fold;
             std::vector<int64_t> slice;
+            bool big_first = false;   // the oldest request is a large one: its launch goes first
             {
                 std::lock_guard<std::mutex> lk(S.mu);
                 std::vector<std::pair<double, int>> order;
@@ -441,6 +472,7 @@ void scheduler(Server *SP)
                     }
                     slice[o.second] = take;
                     left_budget -= (double)take;
+                    if (head) big_first = sl.large && !S.cfg.folded;
                     if (S.cfg.folded)
                         fold.push_back(o.second);
                     else if (sl.large)
@@ -474,91 +506,111 @@ void scheduler(Server *SP)
             if (off)
                 ARE_CUDA_TRY(cudaMemcpyAsync(d, h, off, cudaMemcpyHostToDevice, S.stream));
             int launches = 0;
-            for (int g = 0; g < 3; ++g) {
-                if (part[g].empty()) continue;
-                ItemWork w;
-                std::memset(&w, 0, sizeof w);
-                w.ids = S.y->d_ids;
-                w.off = S.y->d_off;
-                w.k = S.y->k;
-                w.trial_begin = 0;
-                w.n_trials = S.y->n_trials;
-                w.trials_per_item = tpi;
-                w.layers = reinterpret_cast<const LayerF32 *>(d + offs[g]);
-                w.n_layers = (int32_t)part[g].size();
-                int64_t items = 0;
-                for (int i : part[g]) items += (slice[i] + tpi - 1) / tpi;
-                w.n_items = items;
-                w.counter = reinterpret_cast<unsigned long long *>(d + off) + g;
-                ARE_CUDA_TRY(cudaMemsetAsync(w.counter, 0, sizeof(unsigned long long), S.stream));
-                ItemConfig cfg;
-                cfg.trials_per_item = tpi;
-                cfg.rows_in_flight = 2;
-                launches += launch_items(w, kWidths3[g], cfg, S.cfg.precision, S.ctx->num_sms, S.stream);
-            }
-            // folded tables: one trial-pass launch per request slice
-            for (int i : fold) {
-                const Slot &sl = S.slots[i];
-                char *b = S.d_arena + sl.tab_off;
-                FoldArgs fa{};
-                fa.ids = S.y->d_ids;
-                fa.off = S.y->d_off;
-                fa.k = S.y->k;
-                fa.trial_begin = sl.launched;
-                fa.n_trials = slice[i];
-                fa.n_events = S.y->n_events;
-                fa.F = folded_F(b, S.y->catalog);
-                fa.bits = folded_bits(b);
-                fa.words = folded_words(S.y->catalog);
-                fa.hmax = folded_hmax(b);
-                fa.agg_r = sl.req.terms.agg_ret;
-                fa.agg_l = sl.req.terms.agg_lim;
-                fa.ylt = reinterpret_cast<double *>(S.d_arena + sl.ylt_off) + sl.launched;
-                launches += launch_folded(fa, S.ctx->num_sms, S.stream);
-            }
-            // large slices, one single-layer register-rows launch each
-            for (int i : big) {
-                const Slot &sl = S.slots[i];
-                SimArgs sa;
-                std::memset(&sa, 0, sizeof sa);
-                sa.ids = S.y->d_ids;
-                sa.off = S.y->d_off;
-                sa.k = S.y->k;
-                sa.trial_begin = sl.launched;
-                sa.n_trials = slice[i];
-                sa.table = sl.rec.table;
-                sa.agg_r = sl.rec.agg_r;
-                sa.agg_l = sl.rec.agg_l;
-                sa.ylt = sl.rec.ylt + sl.launched;
-                sa.kernel = 2;
-                sa.epl = 0;   // the kernel's default batch for the row width
-                if (sl.pw) {   // over the packed rows
-                    sa.table = packed_rows(S, sl);
-                    sa.table2 = packed_ovf(S, sl);
-                    sa.kernel = 5;
+            // A request whose last slice is in this launch has its risk
+            // measures selected and copied right after its own kernels, then
+            // its own completion event: its result is posted when that
+            // fires, not when the whole iteration has.
+            auto finish_if_last = [&](int i) {
+                std::lock_guard<std::mutex> lk(S.mu);
+                Slot &sl = S.slots[i];
+                sl.launched += slice[i];
+                if (sl.launched < sl.req.n_trials) return;
+                launches += launch_select(reinterpret_cast<const double *>(S.d_arena + sl.ylt_off),
+                                          sl.req.n_trials, sl.req.ranks, sl.req.n_rp + sl.req.n_tv, sl.sel,
+                                          S.ctx->num_sms, S.stream);
+                ARE_CUDA_TRY(cudaMemcpyAsync(sl.h_res, sl.sel.result, sizeof(double) * 2 * kMaxTargets,
+                                             cudaMemcpyDeviceToHost, S.stream));
+                ARE_CUDA_TRY(cudaEventRecord(sl.done_ev, S.stream));
+                sl.finishing = true;
+                sl.finish_iter = S.iter;
+            };
+            // small requests, many per persistent launch, then the folded tables
+            auto launch_small = [&] {
+                for (int g = 0; g < 3; ++g) {
+                    if (part[g].empty()) continue;
+                    ItemWork w;
+                    std::memset(&w, 0, sizeof w);
+                    w.ids = S.y->d_ids;
+                    w.off = S.y->d_off;
+                    w.k = S.y->k;
+                    w.trial_begin = 0;
+                    w.n_trials = S.y->n_trials;
+                    w.trials_per_item = tpi;
+                    w.layers = reinterpret_cast<const LayerF32 *>(d + offs[g]);
+                    w.n_layers = (int32_t)part[g].size();
+                    int64_t items = 0;
+                    for (int i : part[g]) items += (slice[i] + tpi - 1) / tpi;
+                    w.n_items = items;
+                    w.counter = reinterpret_cast<unsigned long long *>(d + off) + g;
+                    ARE_CUDA_TRY(cudaMemsetAsync(w.counter, 0, sizeof(unsigned long long), S.stream));
+                    ItemConfig cfg;
+                    cfg.trials_per_item = tpi;
+                    cfg.rows_in_flight = 2;
+                    launches += launch_items(w, kWidths3[g], cfg, S.cfg.precision, S.ctx->num_sms, S.stream);
+                    for (int i : part[g]) finish_if_last(i);
                 }
-                TermsF32 tm;
-                tm.occ_r = sl.rec.occ_r;
-                tm.occ_l = sl.rec.occ_l;
-                launches += launch_simulate(sa, S.cfg.precision, sl.pw ? sl.pw : sl.jp, &tm, nullptr,
-                                            S.ctx->num_sms, S.stream);
+                // folded tables: one trial-pass launch per request slice
+                for (int i : fold) {
+                    const Slot &sl = S.slots[i];
+                    char *b = S.d_arena + sl.tab_off;
+                    FoldArgs fa{};
+                    fa.ids = S.y->d_ids;
+                    fa.off = S.y->d_off;
+                    fa.k = S.y->k;
+                    fa.trial_begin = sl.launched;
+                    fa.n_trials = slice[i];
+                    fa.n_events = S.y->n_events;
+                    fa.F = folded_F(b, S.y->catalog);
+                    fa.bits = folded_bits(b);
+                    fa.words = folded_words(S.y->catalog);
+                    fa.hmax = folded_hmax(b);
+                    fa.agg_r = sl.req.terms.agg_ret;
+                    fa.agg_l = sl.req.terms.agg_lim;
+                    fa.ylt = reinterpret_cast<double *>(S.d_arena + sl.ylt_off) + sl.launched;
+                    launches += launch_folded(fa, S.ctx->num_sms, S.stream);
+                    finish_if_last(i);
+                }
+            };
+            auto launch_large = [&] {
+                // large slices, one single-layer register-rows launch each
+                for (int i : big) {
+                    const Slot &sl = S.slots[i];
+                    SimArgs sa;
+                    std::memset(&sa, 0, sizeof sa);
+                    sa.ids = S.y->d_ids;
+                    sa.off = S.y->d_off;
+                    sa.k = S.y->k;
+                    sa.trial_begin = sl.launched;
+                    sa.n_trials = slice[i];
+                    sa.table = sl.rec.table;
+                    sa.agg_r = sl.rec.agg_r;
+                    sa.agg_l = sl.rec.agg_l;
+                    sa.ylt = sl.rec.ylt + sl.launched;
+                    sa.kernel = 2;
+                    sa.epl = 0;   // the kernel's default batch for the row width
+                    if (sl.pw) {   // over the packed rows
+                        sa.table = packed_rows(S, sl);
+                        sa.table2 = packed_ovf(S, sl);
+                        sa.kernel = 5;
+                    }
+                    TermsF32 tm;
+                    tm.occ_r = sl.rec.occ_r;
+                    tm.occ_l = sl.rec.occ_l;
+                    launches += launch_simulate(sa, S.cfg.precision, sl.pw ? sl.pw : sl.jp, &tm, nullptr,
+                                                S.ctx->num_sms, S.stream);
+                    finish_if_last(i);
+                }
+            };
+            // the oldest request's kind of work first
+            if (big_first) {
+                launch_large();
+                launch_small();
+            } else {
+                launch_small();
+                launch_large();
             }
-            // requests whose last slice is in this launch: select their risk measures
             {
                 std::lock_guard<std::mutex> lk(S.mu);
-                for (int i = 0; i < (int)S.slots.size(); ++i) {
-                    Slot &sl = S.slots[i];
-                    if (!slice[i]) continue;
-                    sl.launched += slice[i];
-                    if (sl.launched < sl.req.n_trials) continue;
-                    launches += launch_select(reinterpret_cast<const double *>(S.d_arena + sl.ylt_off),
-                                              sl.req.n_trials, sl.req.ranks, sl.req.n_rp + sl.req.n_tv,
-                                              sl.sel, S.ctx->num_sms, S.stream);
-                    ARE_CUDA_TRY(cudaMemcpyAsync(sl.h_res, sl.sel.result, sizeof(double) * 2 * kMaxTargets,
-                                                 cudaMemcpyDeviceToHost, S.stream));
-                    sl.finishing = true;
-                    sl.finish_iter = S.iter;
-                }
                 // cancelled slots with nothing in flight retire with this iteration
                 for (Slot &sl : S.slots)
                     if (sl.busy && sl.cancelled && !sl.finishing) sl.finish_iter = S.iter;
@@ -567,7 +619,7 @@ void scheduler(Server *SP)
             ARE_CUDA_TRY(cudaEventRecord(S.iter_done[buf], S.stream));
             // wait for the previous iteration (this one stays queued behind it)
             if (S.iter > 0) {
-                if (!bounded_wait(S.iter_done[buf ^ 1]))
+                if (!bounded_wait(S, S.iter_done[buf ^ 1]))
                     throw Error{ARE_ETIMEOUT, "server: a launch did not finish within its time limit"};
                 retire(S, S.iter - 1);
             }
@@ -581,7 +633,7 @@ void scheduler(Server *SP)
                 more |= !S.pending.empty();
             }
             if (!more) {
-                if (!bounded_wait(S.iter_done[buf]))
+                if (!bounded_wait(S, S.iter_done[buf]))
                     throw Error{ARE_ETIMEOUT, "server: a launch did not finish within its time limit"};
                 retire(S, S.iter - 1);
             }
@@ -602,6 +654,7 @@ void server_free(Server *S)
     for (Slot &sl : S->slots) {
         select_free(sl.sel);
         if (sl.h_res) cudaFreeHost(sl.h_res);
+        if (sl.done_ev) cudaEventDestroy(sl.done_ev);
     }
     for (int b = 0; b < 2; ++b) {
         if (S->h_layers[b]) cudaFreeHost(S->h_layers[b]);
@@ -687,6 +740,7 @@ are_status are_server_start(are_ctx *ctx, int32_t yet, const are_server_cfg *cfg
             for (Slot &sl : S->slots) {
                 select_alloc(sl.sel, ctx->num_sms);
                 ARE_CUDA_TRY(cudaMallocHost(&sl.h_res, sizeof(double) * 2 * kMaxTargets));
+                ARE_CUDA_TRY(cudaEventCreateWithFlags(&sl.done_ev, cudaEventDisableTiming));
             }
             S->work_bytes = 3 * up(sizeof(LayerF32) * cfg->max_inflight) + 3 * sizeof(unsigned long long);
             for (int b = 0; b < 2; ++b) {
